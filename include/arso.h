@@ -1,0 +1,252 @@
+/*
+ * arso.h - C ABI of the GB300 library for the Monte Carlo Pauli-error path of
+ * ArsoNISQ: state-vector simulation of a quantum circuit with Pauli X/Z/Y
+ * error gates appended after its gates, a per-trajectory success criterion,
+ * the success probability at an error rate p, and the tolerable error rate
+ * for a target success probability.
+ *
+ * Conventions (all entry points):
+ *  - Every call returns an arso_status; nothing throws or aborts across the
+ *    ABI. On a non-OK status arso_last_error() returns a thread-local message.
+ *  - Inputs are caller-owned and copied (or fully consumed) before return.
+ *  - Handles (arso_circuit, arso_error_list, arso_surrogate) are library-owned
+ *    and freed with their *_free function; freeing NULL is a no-op.
+ *  - Output arrays are caller-allocated. Where a pointer may be host or device
+ *    memory the library detects which (cudaPointerGetAttributes).
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls that
+ *    return host values synchronise that stream before returning.
+ *  - Qubit q is bit q of the amplitude index (little-endian). Amplitude arrays
+ *    are interleaved (re, im): float pairs for ARSO_C64, double pairs for
+ *    ARSO_C128.
+ *  - Error locations: location l enumerates (gate g, qubit slot j) in circuit
+ *    order, one location per qubit of each gate, so L = k + 2m for k one-qubit
+ *    and m two-qubit gates (Sec. IV-B.1, Eq. (3)).
+ *  - Pauli codes: 1 = X, 2 = Z, 3 = Y, acting as Eq. (2) prints them:
+ *    X (a0, a1) -> (a1, a0); Z -> (a0, -a1); Y -> (-i a1, i a0).
+ *  - The library allocates device memory for its own handles and scratch with
+ *    the CUDA runtime; it never takes ownership of caller memory.
+ */
+#ifndef ARSO_H
+#define ARSO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ARSO_OK = 0,
+    ARSO_EINVAL = 1,         /* bad argument: NULL handle, qubit out of range, p outside [0,1] ... */
+    ARSO_ENOMEM = 2,         /* a device or host allocation failed */
+    ARSO_ECUDA = 3,          /* a CUDA runtime call or kernel launch failed */
+    ARSO_ETIMEOUT = 4,       /* a bounded device-side wait gave up */
+    ARSO_EUNSUPPORTED = 5,   /* valid request outside what this build supports */
+    ARSO_ENOTCONVERGED = 6   /* a search ended without meeting its tolerance */
+} arso_status;
+
+/* Gate kinds. One-qubit gates use q[0]; two-qubit gates use q[0], q[1]
+ * (control first for CX and CP). Textbook matrices:
+ *   H = [[1,1],[1,-1]]/sqrt2, X, Y = [[0,-i],[i,0]], Z, S = diag(1,i),
+ *   SDG = diag(1,-i), T = diag(1,e^{i pi/4}), TDG = diag(1,e^{-i pi/4}),
+ *   RX(t) = [[c,-is],[-is,c]], RY(t) = [[c,-s],[s,c]] (c = cos t/2, s = sin t/2),
+ *   RZ(t) = diag(e^{-it/2}, e^{it/2}), P(l) = diag(1, e^{il}),
+ *   CX, CZ = diag(1,1,1,-1), CP(l) = diag(1,1,1,e^{il}), SWAP.
+ * U and U2 take an explicit unitary in `matrix`: row-major, (re, im) pairs,
+ * 2x2 (8 doubles) or 4x4 (32 doubles), local index k = bit(q0) + 2*bit(q1). */
+enum {
+    ARSO_GATE_ID = 0, ARSO_GATE_H, ARSO_GATE_X, ARSO_GATE_Y, ARSO_GATE_Z,
+    ARSO_GATE_S, ARSO_GATE_SDG, ARSO_GATE_T, ARSO_GATE_TDG,
+    ARSO_GATE_RX, ARSO_GATE_RY, ARSO_GATE_RZ, ARSO_GATE_P, ARSO_GATE_U,
+    ARSO_GATE_CX = 32, ARSO_GATE_CZ, ARSO_GATE_CP, ARSO_GATE_SWAP, ARSO_GATE_U2
+};
+
+typedef struct {
+    uint32_t kind;          /* ARSO_GATE_* */
+    uint32_t q[2];          /* qubits; q[1] ignored for one-qubit gates */
+    double param;           /* angle for RX/RY/RZ/P/CP, ignored otherwise */
+    const double *matrix;   /* U/U2 only: caller-owned, copied on entry */
+} arso_gate;
+
+enum { ARSO_C64 = 0, ARSO_C128 = 1 };
+
+typedef struct {
+    uint32_t precision;     /* ARSO_C64 (complex64 amplitudes, FP32 arithmetic) or ARSO_C128 */
+    uint32_t tile_qubits;   /* streaming passes: qubits per shared-memory tile; 0 = auto */
+    uint32_t low_qubits;    /* streaming passes: qubits 0..low-1 are in every tile; 0 = auto */
+    uint32_t max_batch;     /* streaming engine: trajectories resident at once; 0 = auto */
+    uint64_t cache_bytes;   /* budget for cached error-free prefix states; 0 = auto */
+} arso_compile_opts;
+
+typedef struct arso_circuit arso_circuit;
+typedef struct arso_error_list arso_error_list;
+
+/* Compile a circuit (Sec. II: a list of gates acting on n qubits) for the GPU:
+ * builds gate matrices, the error-location table, the fused pass schedule and
+ * uploads them. n_qubits in [1, 30]; gates may be empty. `opts` may be NULL.
+ * The error-free prefix-state cache is built lazily on first use.
+ * Errors: ARSO_EINVAL (bad kind/qubit/matrix), ARSO_ENOMEM, ARSO_ECUDA. */
+arso_status arso_compile_circuit(uint32_t n_qubits, const arso_gate *gates, size_t n_gates,
+                                 const arso_compile_opts *opts, arso_circuit **out);
+void arso_circuit_free(arso_circuit *c);
+
+typedef struct {
+    uint32_t n_qubits;
+    uint64_t G;             /* gates (the paper's circuit size, Sec. II) */
+    uint64_t k, m;          /* one- and two-qubit gates */
+    uint64_t L;             /* error locations, k + 2m */
+    uint32_t engine;        /* 0 = resident (whole state on chip), 1 = streaming passes */
+    uint32_t n_passes;      /* streaming: fused passes; resident: 1 */
+    uint32_t tile_qubits;
+    uint32_t precision;
+    uint64_t checkpoint_every; /* resident: gates between cached prefix states */
+} arso_circuit_info;
+arso_status arso_circuit_get_info(const arso_circuit *c, arso_circuit_info *out);
+
+/* Host-only view of the compile step (no GPU needed): the engine order and the
+ * fused pass schedule that arso_compile_circuit would build. *n_passes is set
+ * on every call; perm (n_gates entries: engine position -> gate index),
+ * pass_begin (n_passes + 1 entries) and tile_mask (n_passes entries, bit q set
+ * when qubit q is a tile qubit of the pass) are filled when non-NULL and
+ * *n_passes <= capacity. Errors: as arso_compile_circuit, and ARSO_EINVAL when
+ * capacity is too small for non-NULL arrays. */
+arso_status arso_plan_schedule(uint32_t n_qubits, const arso_gate *gates, size_t n_gates,
+                               const arso_compile_opts *opts, uint32_t *n_passes, uint32_t capacity,
+                               uint32_t *perm, uint32_t *pass_begin, uint64_t *tile_mask);
+
+/* Sample Pauli errors (Sec. IV-B.2): after every gate, each of its qubits
+ * independently suffers X, Z or Y with probabilities p_x, p_z, p_y. Trajectory
+ * t in [traj_begin, traj_begin + n_traj), location l draws
+ * Philox4x32-10(counter = (l >> 1, t mod 2^32, t >> 32, 0x41525345),
+ *               key = (seed mod 2^32, seed >> 32))
+ * and uses words (w0, w1) for even l, (w2, w3) for odd l. Error iff
+ * w_a < min(floor(p_tot 2^32), 2^32 - 1); type X if w_b < floor(p_x/p_tot 2^32),
+ * else Z if w_b < floor((p_x+p_z)/p_tot 2^32), else Y. The draw is independent
+ * of p, so error sets at two rates are nested. Result: per-trajectory event
+ * lists in device memory (CSR), library-owned.
+ * Errors: ARSO_EINVAL (p_* < 0 or p_tot > 1), ARSO_ENOMEM, ARSO_ECUDA. */
+arso_status arso_sample_errors(const arso_circuit *c, double p_x, double p_z, double p_y,
+                               uint64_t seed, uint64_t traj_begin, uint64_t n_traj,
+                               void *stream, arso_error_list **out);
+
+/* Build an error list from explicit host events (tests, exhaustive analysis).
+ * offsets: n_traj + 1 entries, events[offsets[t] .. offsets[t+1]) belong to
+ * trajectory t, each encoded (location << 2) | code, strictly increasing in
+ * location within a trajectory. */
+arso_status arso_error_list_from_host(const arso_circuit *c, uint64_t n_traj, const uint64_t *offsets,
+                                      const uint32_t *events, void *stream, arso_error_list **out);
+arso_status arso_error_list_info(const arso_error_list *e, uint64_t *n_traj, uint64_t *n_events);
+/* Copy the CSR to host arrays (offsets: n_traj + 1; events: n_events, encoded
+ * (location << 2) | code, location order). Synchronises `stream`. */
+arso_status arso_error_list_copy(const arso_error_list *e, uint64_t *offsets, uint32_t *events, void *stream);
+void arso_error_list_free(arso_error_list *e);
+
+/* Success criteria (Sec. II): fidelity |<psi_R|psi>|^2 with the error-free
+ * final state; probability of the correct outcome |psi_target|^2; binning,
+ * the probability of an outcome in `set`; argmax, 1 if the most likely outcome
+ * is `target` (lowest index wins ties). A trajectory passes iff score >=
+ * threshold. aggregate selects what arso_success_prob reports as `value`:
+ * the mean score (the paper's averaged P, Sec. IV-C) or the pass fraction. */
+enum { ARSO_CRIT_FIDELITY = 0, ARSO_CRIT_OUTCOME = 1, ARSO_CRIT_BINNING = 2, ARSO_CRIT_ARGMAX = 3 };
+enum { ARSO_AGG_MEAN = 0, ARSO_AGG_PASS = 1 };
+typedef struct {
+    uint32_t kind;
+    uint32_t aggregate;
+    uint64_t target;
+    const uint64_t *set;    /* binning only: caller-owned, copied */
+    size_t set_len;
+    double threshold;
+} arso_criterion;
+
+/* Run every trajectory of `errors` (Sec. IV-B: the circuit with the sampled
+ * error gates appended after their gates) and score it. score_out: n_traj
+ * doubles; pass_out: n_traj bytes or NULL. Host or device pointers.
+ * Trajectories with no error take the score of the error-free state; the
+ * others restart from the cached error-free state before their first error.
+ * Errors: ARSO_EINVAL, ARSO_ENOMEM, ARSO_ECUDA. */
+arso_status arso_run_trajectories(const arso_circuit *c, const arso_error_list *errors,
+                                  const arso_criterion *crit, void *stream,
+                                  double *score_out, uint8_t *pass_out);
+
+/* Final state vectors of trajectories [first, first + count) of `errors`
+ * (count * 2^n amplitudes, device pointer, layout per the circuit's
+ * precision). For parity checks and inspection. */
+arso_status arso_trajectory_states(const arso_circuit *c, const arso_error_list *errors,
+                                   uint64_t first, uint64_t count, void *stream, void *amps_out);
+/* The error-free final state psi_R (2^n amplitudes, device pointer). */
+arso_status arso_reference_state(const arso_circuit *c, void *stream, void *amps_out);
+
+/* Success probability at error rate p, uniform p_X = p_Z = p_Y = p/3 (Sec. IV-C,
+ * Fig. 2). mode AUTO follows the paper: Monte Carlo when the expected error
+ * count L*p exceeds one, otherwise the exhaustive single-error analysis and
+ * Eq. (4). */
+enum { ARSO_MODE_AUTO = 0, ARSO_MODE_MONTE_CARLO = 1, ARSO_MODE_EXHAUSTIVE = 2 };
+typedef struct {
+    double value;           /* mean or pass fraction, per criterion.aggregate */
+    double mean, pass_frac; /* MC: both aggregates; exhaustive: Eq. (4) of each */
+    double stderr_value;    /* MC: sd / sqrt(n_traj) of `value`; exhaustive: 0 */
+    double expected_errors; /* E(N) = L * p */
+    uint32_t mode_used;
+    uint64_t n_traj;        /* trajectories simulated */
+    double P_R, P_X, P_Z, P_Y; /* exhaustive: Eq. (4) inputs (per aggregate) */
+} arso_result;
+arso_status arso_success_prob(const arso_circuit *c, const arso_criterion *crit, double p, uint32_t mode,
+                              uint64_t n_traj, uint64_t seed, void *stream, arso_result *out);
+
+/* Exhaustive single-error analysis (Sec. IV-B.1, Eq. (3)): psi_R and every
+ * single X, Z, Y error at every location, 3L states. per_location (optional,
+ * host, 3*L doubles ordered X block, Z block, Y block) receives the criterion
+ * value of each state; P_out[4] = {P_R, P_X, P_Z, P_Y} (per aggregate). */
+arso_status arso_exhaustive(const arso_circuit *c, const arso_criterion *crit, void *stream,
+                            double *P_out, double *per_location);
+
+/* Tolerable error rate (Sec. IV-D, Fig. 3) for target success P_target:
+ * exhaustive analysis first; if P_target >= sum_e P_e / 3, Eq. (5) with
+ * count L; otherwise Monte Carlo probes at successive p, bisected in log10 p on
+ * common random numbers until hi/lo <= 1 + rel_tol, answer interpolated
+ * log-linearly inside the final bracket. A surrogate (arso_surrogate_*) may
+ * narrow the initial bracket; the plain simulator then verifies it. */
+typedef struct arso_surrogate arso_surrogate;
+typedef struct {
+    double p_lo, p_hi;      /* search bracket (default 1e-6, 1e-1 when 0) */
+    double rel_tol;         /* default 0.02 */
+    uint64_t n_traj;        /* trajectories per probe (default 1000) */
+    uint64_t seed;
+    uint32_t max_probes;    /* default 64 */
+    uint32_t mode;          /* ARSO_MODE_AUTO (Fig. 3) or ARSO_MODE_MONTE_CARLO (skip Eq. (5)) */
+    const arso_surrogate *surrogate; /* NULL = plain search */
+    const float *features;  /* surrogate inputs for this circuit (32 floats), with `surrogate` */
+    double surrogate_margin;/* verify bracket half-width in log10 p (default 0.15) */
+} arso_search_opts;
+typedef struct {
+    double p, lo, hi, value_lo, value_hi;
+    uint32_t probes;        /* plain-simulator probes */
+    uint32_t mode_used;     /* 0 = Eq. (5), 1 = Monte Carlo search */
+    uint32_t used_surrogate, verified, converged;
+    double P1;              /* success subject to one average error */
+} arso_rate_result;
+arso_status arso_tolerable_rate(const arso_circuit *c, const arso_criterion *crit, double P_target,
+                                const arso_search_opts *opts, void *stream, arso_rate_result *out);
+
+/* ---- single-step kernels (each also runs inside the fused trajectory path) ---- */
+
+/* Apply one gate to a device state (2^n amplitudes, complex64) as a strided
+ * pair/quad update over HBM (Sec. II: a gate manipulates the amplitudes). */
+arso_status arso_apply_gate(uint32_t n_qubits, void *amps, const arso_gate *gate, void *stream);
+/* Apply the Pauli error gate `code` on `qubit` (Eq. (2)) to a device state
+ * (complex64): X/Y as an index permutation, Z/Y as a phase. */
+arso_status arso_apply_pauli(uint32_t n_qubits, void *amps, uint32_t qubit, uint32_t code, void *stream);
+/* Score one device state (complex64) against `crit`; ref (complex64, device)
+ * is psi_R for fidelity and ignored otherwise. FP64 accumulation. *score_out
+ * is a host double. */
+arso_status arso_score_state(uint32_t n_qubits, const void *amps, const void *ref,
+                             const arso_criterion *crit, void *stream, double *score_out);
+
+const char *arso_last_error(void);
+const char *arso_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ARSO_H */

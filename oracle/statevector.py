@@ -19,11 +19,19 @@ def zero_state(n):
     return psi
 
 
-@lru_cache(maxsize=256)
 def _base_indices(n, mask):
     """All indices i in [0, 2^n) whose bits in ``mask`` are zero."""
+    if n >= 18:
+        return _base_indices_uncached(n, mask)
+    return _base_indices_cached(n, mask)
+
+
+def _base_indices_uncached(n, mask):
     i = np.arange(1 << n, dtype=np.int64)
     return i[(i & mask) == 0]
+
+
+_base_indices_cached = lru_cache(maxsize=512)(_base_indices_uncached)
 
 
 def apply_1q(psi, n, q, U):

@@ -1,0 +1,322 @@
+"""Python binding of the C ABI declared in include/arso.h.
+
+Argument marshalling only: every step of the simulation, sampling, scoring and
+search runs inside libarso.so. Functions carry the ABI's names without the
+``arso_`` prefix. Device buffers are torch CUDA tensors (or raw integer device
+pointers); host buffers are numpy arrays. Streams are ``torch.cuda.Stream``
+objects, raw ``cudaStream_t`` integers, or None (legacy default stream).
+
+Importing this module fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libarso.so")
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"libarso.so is not built ({_LIB_PATH}); run __graft_entry__.build()")
+lib = C.CDLL(_LIB_PATH)
+
+# ------------------------------------------------------------------ enums --
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, ENOTCONVERGED = range(7)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ETIMEOUT", "EUNSUPPORTED", "ENOTCONVERGED"]
+
+GATE_KIND = {
+    "ID": 0, "H": 1, "X": 2, "Y": 3, "Z": 4, "S": 5, "SDG": 6, "T": 7, "TDG": 8,
+    "RX": 9, "RY": 10, "RZ": 11, "P": 12, "U": 13,
+    "CX": 32, "CZ": 33, "CP": 34, "SWAP": 35, "U2": 36,
+}
+C64, C128 = 0, 1
+CRIT_KIND = {"fidelity": 0, "outcome": 1, "binning": 2, "argmax": 3}
+AGGREGATE = {"mean": 0, "pass": 1}
+MODE = {"auto": 0, "mc": 1, "exhaustive": 2}
+
+
+class ArsoError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+# --------------------------------------------------------------- structs --
+class Gate(C.Structure):
+    _fields_ = [("kind", C.c_uint32), ("q", C.c_uint32 * 2), ("param", C.c_double),
+                ("matrix", C.POINTER(C.c_double))]
+
+
+class CompileOpts(C.Structure):
+    _fields_ = [("precision", C.c_uint32), ("tile_qubits", C.c_uint32), ("low_qubits", C.c_uint32),
+                ("max_batch", C.c_uint32), ("cache_bytes", C.c_uint64)]
+
+
+class CircuitInfo(C.Structure):
+    _fields_ = [("n_qubits", C.c_uint32), ("G", C.c_uint64), ("k", C.c_uint64), ("m", C.c_uint64),
+                ("L", C.c_uint64), ("engine", C.c_uint32), ("n_passes", C.c_uint32),
+                ("tile_qubits", C.c_uint32), ("precision", C.c_uint32), ("checkpoint_every", C.c_uint64)]
+
+
+class Criterion(C.Structure):
+    _fields_ = [("kind", C.c_uint32), ("aggregate", C.c_uint32), ("target", C.c_uint64),
+                ("set", C.POINTER(C.c_uint64)), ("set_len", C.c_size_t), ("threshold", C.c_double)]
+
+
+class Result(C.Structure):
+    _fields_ = [("value", C.c_double), ("mean", C.c_double), ("pass_frac", C.c_double),
+                ("stderr_value", C.c_double), ("expected_errors", C.c_double), ("mode_used", C.c_uint32),
+                ("n_traj", C.c_uint64), ("P_R", C.c_double), ("P_X", C.c_double), ("P_Z", C.c_double),
+                ("P_Y", C.c_double)]
+
+
+class SearchOpts(C.Structure):
+    _fields_ = [("p_lo", C.c_double), ("p_hi", C.c_double), ("rel_tol", C.c_double), ("n_traj", C.c_uint64),
+                ("seed", C.c_uint64), ("max_probes", C.c_uint32), ("mode", C.c_uint32),
+                ("surrogate", C.c_void_p), ("features", C.POINTER(C.c_float)), ("surrogate_margin", C.c_double)]
+
+
+class RateResult(C.Structure):
+    _fields_ = [("p", C.c_double), ("lo", C.c_double), ("hi", C.c_double), ("value_lo", C.c_double),
+                ("value_hi", C.c_double), ("probes", C.c_uint32), ("mode_used", C.c_uint32),
+                ("used_surrogate", C.c_uint32), ("verified", C.c_uint32), ("converged", C.c_uint32),
+                ("P1", C.c_double)]
+
+
+_vp = C.c_void_p
+_sigs = {
+    "arso_compile_circuit": [C.c_uint32, C.POINTER(Gate), C.c_size_t, C.POINTER(CompileOpts), C.POINTER(_vp)],
+    "arso_circuit_get_info": [_vp, C.POINTER(CircuitInfo)],
+    "arso_plan_schedule": [C.c_uint32, C.POINTER(Gate), C.c_size_t, C.POINTER(CompileOpts), C.POINTER(C.c_uint32),
+                           C.c_uint32, _vp, _vp, _vp],
+    "arso_sample_errors": [_vp, C.c_double, C.c_double, C.c_double, C.c_uint64, C.c_uint64, C.c_uint64, _vp,
+                           C.POINTER(_vp)],
+    "arso_error_list_from_host": [_vp, C.c_uint64, _vp, _vp, _vp, C.POINTER(_vp)],
+    "arso_error_list_info": [_vp, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)],
+    "arso_error_list_copy": [_vp, _vp, _vp, _vp],
+    "arso_run_trajectories": [_vp, _vp, C.POINTER(Criterion), _vp, _vp, _vp],
+    "arso_trajectory_states": [_vp, _vp, C.c_uint64, C.c_uint64, _vp, _vp],
+    "arso_reference_state": [_vp, _vp, _vp],
+    "arso_exhaustive": [_vp, C.POINTER(Criterion), _vp, _vp, _vp],
+    "arso_success_prob": [_vp, C.POINTER(Criterion), C.c_double, C.c_uint32, C.c_uint64, C.c_uint64, _vp,
+                          C.POINTER(Result)],
+    "arso_tolerable_rate": [_vp, C.POINTER(Criterion), C.c_double, C.POINTER(SearchOpts), _vp,
+                            C.POINTER(RateResult)],
+    "arso_apply_gate": [C.c_uint32, _vp, C.POINTER(Gate), _vp],
+    "arso_apply_pauli": [C.c_uint32, _vp, C.c_uint32, C.c_uint32, _vp],
+    "arso_score_state": [C.c_uint32, _vp, _vp, C.POINTER(Criterion), _vp, C.POINTER(C.c_double)],
+}
+for _name, _args in _sigs.items():
+    _f = getattr(lib, _name)
+    _f.argtypes = _args
+    _f.restype = C.c_int
+lib.arso_circuit_free.argtypes = [_vp]
+lib.arso_circuit_free.restype = None
+lib.arso_error_list_free.argtypes = [_vp]
+lib.arso_error_list_free.restype = None
+lib.arso_last_error.restype = C.c_char_p
+lib.arso_version.restype = C.c_char_p
+
+
+def _check(status):
+    if status != OK:
+        raise ArsoError(status, lib.arso_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _ptr(buf):
+    """Device pointer of a torch tensor, host pointer of a numpy array, or an int."""
+    if buf is None:
+        return None
+    if isinstance(buf, int):
+        return buf
+    if isinstance(buf, np.ndarray):
+        assert buf.flags["C_CONTIGUOUS"]
+        return buf.ctypes.data
+    assert buf.is_contiguous()
+    return int(buf.data_ptr())
+
+
+# ---------------------------------------------------------------- handles --
+class CompiledCircuit:
+    def __init__(self, handle, n):
+        self.handle = handle
+        self.n = n
+
+    def info(self) -> CircuitInfo:
+        return circuit_get_info(self)
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib.arso_circuit_free(self.handle)
+            self.handle = None
+
+
+class ErrorList:
+    def __init__(self, handle, circuit):
+        self.handle = handle
+        self.circuit = circuit  # keep the circuit alive
+
+    def info(self):
+        nt, ne = C.c_uint64(), C.c_uint64()
+        _check(lib.arso_error_list_info(self.handle, C.byref(nt), C.byref(ne)))
+        return nt.value, ne.value
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib.arso_error_list_free(self.handle)
+            self.handle = None
+
+
+def _gates_array(gates):
+    arr = (Gate * max(len(gates), 1))()
+    keep = []
+    for i, g in enumerate(gates):
+        arr[i].kind = GATE_KIND[g.name]
+        arr[i].q[0] = g.qubits[0]
+        arr[i].q[1] = g.qubits[1] if len(g.qubits) > 1 else 0
+        arr[i].param = g.params[0] if g.params else 0.0
+        if g.matrix is not None:
+            m = np.ascontiguousarray(np.asarray(g.matrix, dtype=np.complex128)).view(np.float64).ravel().copy()
+            keep.append(m)
+            arr[i].matrix = m.ctypes.data_as(C.POINTER(C.c_double))
+    return arr, keep
+
+
+def compile_circuit(n, gates, precision=C64, tile_qubits=0, low_qubits=0, max_batch=0, cache_bytes=0):
+    arr, keep = _gates_array(gates)
+    opts = CompileOpts(precision, tile_qubits, low_qubits, max_batch, cache_bytes)
+    h = _vp()
+    _check(lib.arso_compile_circuit(n, arr, len(gates), C.byref(opts), C.byref(h)))
+    del keep
+    return CompiledCircuit(h.value, n)
+
+
+def plan_schedule(n, gates, precision=C64, tile_qubits=0, low_qubits=0):
+    """Host-only: (perm, pass_begin, tile_masks) of the fused pass schedule."""
+    arr, keep = _gates_array(gates)
+    opts = CompileOpts(precision, tile_qubits, low_qubits, 0, 0)
+    P = C.c_uint32()
+    _check(lib.arso_plan_schedule(n, arr, len(gates), C.byref(opts), C.byref(P), 0, None, None, None))
+    perm = np.zeros(max(len(gates), 1), dtype=np.uint32)
+    begin = np.zeros(P.value + 1, dtype=np.uint32)
+    masks = np.zeros(max(P.value, 1), dtype=np.uint64)
+    _check(lib.arso_plan_schedule(n, arr, len(gates), C.byref(opts), C.byref(P), P.value, perm.ctypes.data,
+                                  begin.ctypes.data, masks.ctypes.data))
+    return perm[: len(gates)], begin, masks[: P.value]
+
+
+def circuit_get_info(circ) -> CircuitInfo:
+    info = CircuitInfo()
+    _check(lib.arso_circuit_get_info(circ.handle, C.byref(info)))
+    return info
+
+
+def make_criterion(crit):
+    """Criterion from an object/dict with kind, target, basis_set, threshold, aggregate."""
+    get = (lambda k, d=None: crit.get(k, d)) if isinstance(crit, dict) else (lambda k, d=None: getattr(crit, k, d))
+    s = np.ascontiguousarray(np.asarray(get("basis_set", ()) or (), dtype=np.uint64))
+    c = Criterion(CRIT_KIND[get("kind", "fidelity")], AGGREGATE[get("aggregate", "mean")], int(get("target", 0)),
+                  s.ctypes.data_as(C.POINTER(C.c_uint64)) if s.size else None, s.size,
+                  float(get("threshold", 0.5)))
+    c._keep = s
+    return c
+
+
+def sample_errors(circ, p_x, p_z, p_y, seed, traj_begin, n_traj, stream=None) -> ErrorList:
+    h = _vp()
+    _check(lib.arso_sample_errors(circ.handle, p_x, p_z, p_y, seed, traj_begin, n_traj, _stream(stream),
+                                  C.byref(h)))
+    return ErrorList(h.value, circ)
+
+
+def error_list_from_host(circ, lists, stream=None) -> ErrorList:
+    """lists: per trajectory, a sorted list of (location, code)."""
+    off = np.zeros(len(lists) + 1, dtype=np.uint64)
+    ev = []
+    for i, l in enumerate(lists):
+        off[i + 1] = off[i] + len(l)
+        ev += [(loc << 2) | code for loc, code in l]
+    evs = np.asarray(ev if ev else [0], dtype=np.uint32)
+    h = _vp()
+    _check(lib.arso_error_list_from_host(circ.handle, len(lists), off.ctypes.data, evs.ctypes.data,
+                                         _stream(stream), C.byref(h)))
+    return ErrorList(h.value, circ)
+
+
+def error_list_copy(errs, stream=None):
+    nt, ne = errs.info()
+    off = np.zeros(nt + 1, dtype=np.uint64)
+    ev = np.zeros(max(ne, 1), dtype=np.uint32)
+    _check(lib.arso_error_list_copy(errs.handle, off.ctypes.data, ev.ctypes.data, _stream(stream)))
+    return off, ev[:ne]
+
+
+def run_trajectories(circ, errs, crit, score_out, pass_out=None, stream=None):
+    c = crit if isinstance(crit, Criterion) else make_criterion(crit)
+    _check(lib.arso_run_trajectories(circ.handle, errs.handle, C.byref(c), _stream(stream), _ptr(score_out),
+                                     _ptr(pass_out)))
+
+
+def trajectory_states(circ, errs, first, count, amps_out, stream=None):
+    _check(lib.arso_trajectory_states(circ.handle, errs.handle, first, count, _stream(stream), _ptr(amps_out)))
+
+
+def reference_state(circ, amps_out, stream=None):
+    _check(lib.arso_reference_state(circ.handle, _stream(stream), _ptr(amps_out)))
+
+
+def exhaustive(circ, crit, per_location=True, stream=None):
+    c = crit if isinstance(crit, Criterion) else make_criterion(crit)
+    P = np.zeros(4)
+    info = circ.info()
+    per = np.zeros(max(3 * info.L, 1)) if per_location else None
+    _check(lib.arso_exhaustive(circ.handle, C.byref(c), _stream(stream), P.ctypes.data,
+                               per.ctypes.data if per is not None else None))
+    return P, (per[: 3 * info.L] if per is not None else None)
+
+
+def success_prob(circ, crit, p, mode="auto", n_traj=1000, seed=0, stream=None) -> Result:
+    c = crit if isinstance(crit, Criterion) else make_criterion(crit)
+    r = Result()
+    _check(lib.arso_success_prob(circ.handle, C.byref(c), p, MODE[mode], n_traj, seed, _stream(stream),
+                                 C.byref(r)))
+    return r
+
+
+def tolerable_rate(circ, crit, P_target, p_lo=0.0, p_hi=0.0, rel_tol=0.0, n_traj=0, seed=0, max_probes=0,
+                   mode="auto", stream=None, check=True) -> RateResult:
+    c = crit if isinstance(crit, Criterion) else make_criterion(crit)
+    o = SearchOpts(p_lo, p_hi, rel_tol, n_traj, seed, max_probes, MODE[mode], None, None, 0.0)
+    r = RateResult()
+    st = lib.arso_tolerable_rate(circ.handle, C.byref(c), P_target, C.byref(o), _stream(stream), C.byref(r))
+    if check:
+        _check(st)
+    return r
+
+
+def apply_gate(n, amps, gate, stream=None):
+    arr, keep = _gates_array([gate])
+    _check(lib.arso_apply_gate(n, _ptr(amps), arr, _stream(stream)))
+
+
+def apply_pauli(n, amps, qubit, code, stream=None):
+    _check(lib.arso_apply_pauli(n, _ptr(amps), qubit, code, _stream(stream)))
+
+
+def score_state(n, amps, ref, crit, stream=None) -> float:
+    c = crit if isinstance(crit, Criterion) else make_criterion(crit)
+    out = C.c_double()
+    _check(lib.arso_score_state(n, _ptr(amps), _ptr(ref), C.byref(c), _stream(stream), C.byref(out)))
+    return out.value
+
+
+def version() -> str:
+    return lib.arso_version().decode()

@@ -1,0 +1,893 @@
+// C-ABI entry points: circuit upload, prefix cache, error sampling,
+// trajectory engines, success probability (Sec. IV-C, Eq. (4)) and the
+// tolerable error rate (Sec. IV-D, Eq. (5), Fig. 3).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <numeric>
+
+#include "kernels.h"
+
+namespace arso {
+
+static thread_local std::string g_last_error;
+void set_last_error(const std::string &m) { g_last_error = m; }
+
+template <class F> static arso_status guard(F &&f) {
+    try {
+        f();
+        return ARSO_OK;
+    } catch (const Error &e) {
+        set_last_error(e.what());
+        return e.status;
+    } catch (const std::bad_alloc &) {
+        set_last_error("host allocation failed");
+        return ARSO_ENOMEM;
+    } catch (const std::exception &e) {
+        set_last_error(e.what());
+        return ARSO_ECUDA;
+    }
+}
+
+static bool is_device_ptr(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Stream-ordered scratch buffer.
+struct Scratch {
+    void *ptr = nullptr;
+    cudaStream_t st;
+    explicit Scratch(cudaStream_t s, size_t bytes) : st(s) {
+        if (bytes) ARSO_CUDA(cudaMallocAsync(&ptr, bytes, st));
+    }
+    ~Scratch() {
+        if (ptr) cudaFreeAsync(ptr, st);
+    }
+    Scratch(const Scratch &) = delete;
+    template <typename T> T *as() const { return static_cast<T *>(ptr); }
+};
+
+template <typename T> static void h2d(void *dst, const std::vector<T> &v, cudaStream_t st) {
+    if (!v.empty()) ARSO_CUDA(cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+}
+
+// ------------------------------------------------------------ upload -------
+static void upload_circuit(arso_circuit *c) {
+    const size_t G = c->gates.size();
+    std::vector<DGate> dg(std::max<size_t>(G, 1));
+    std::vector<std::complex<double>> pool;
+    for (size_t p = 0; p < c->passes.size(); ++p) {
+        const Pass &ps = c->passes[p];
+        std::vector<int> local(c->n, -1);
+        for (size_t i = 0; i < ps.tile_qubits.size(); ++i) local[ps.tile_qubits[i]] = (int)i;
+        for (uint32_t pos = ps.gb; pos < ps.ge; ++pos) {
+            const HostGate &h = c->gates[c->perm[pos]];
+            DGate d{};
+            d.cls = h.cls;
+            d.arity = (uint8_t)h.arity;
+            d.q0 = (uint8_t)local[h.q0];
+            d.q1 = (uint8_t)local[h.q1];
+            d.mat = (uint32_t)pool.size();
+            switch (h.cls) {
+                case GC_DENSE1: for (int i = 0; i < 4; ++i) pool.push_back(h.m[i]); break;
+                case GC_DIAG1: pool.push_back(h.m[0]); pool.push_back(h.m[3]); break;
+                case GC_DENSE2: for (int i = 0; i < 16; ++i) pool.push_back(h.m[i]); break;
+                case GC_DIAG2: for (int i = 0; i < 4; ++i) pool.push_back(h.m[5 * i]); break;
+                default: break;
+            }
+            dg[pos] = d;
+        }
+    }
+    c->d_gates.ensure(dg.size() * sizeof(DGate));
+    ARSO_CUDA(cudaMemcpy(c->d_gates.ptr, dg.data(), dg.size() * sizeof(DGate), cudaMemcpyHostToDevice));
+    const size_t esz = c->precision == ARSO_C128 ? 16 : 8;
+    c->d_mats.ensure(std::max<size_t>(pool.size(), 1) * esz);
+    if (!pool.empty()) {
+        if (c->precision == ARSO_C128) {
+            std::vector<double2> v(pool.size());
+            for (size_t i = 0; i < pool.size(); ++i) v[i] = make_double2(pool[i].real(), pool[i].imag());
+            ARSO_CUDA(cudaMemcpy(c->d_mats.ptr, v.data(), v.size() * esz, cudaMemcpyHostToDevice));
+        } else {
+            std::vector<float2> v(pool.size());
+            for (size_t i = 0; i < pool.size(); ++i)
+                v[i] = make_float2((float)pool[i].real(), (float)pool[i].imag());
+            ARSO_CUDA(cudaMemcpy(c->d_mats.ptr, v.data(), v.size() * esz, cudaMemcpyHostToDevice));
+        }
+    }
+    std::vector<uint32_t> first_loc(G + 1, 0);
+    for (size_t g = 0; g < G; ++g) first_loc[g + 1] = first_loc[g] + c->gates[g].arity;
+    std::vector<uint32_t> lk(std::max<uint64_t>(c->L, 1));
+    for (uint64_t l = 0; l < c->L; ++l) {
+        const uint32_t g = c->loc_gate[l];
+        lk[l] = (c->pos_of[g] << 1) | (uint32_t)(l - first_loc[g]);
+    }
+    c->d_loc_key.ensure(lk.size() * 4);
+    ARSO_CUDA(cudaMemcpy(c->d_loc_key.ptr, lk.data(), lk.size() * 4, cudaMemcpyHostToDevice));
+    if (c->engine == 1) {
+        const uint32_t t = c->tile_qubits, cl = c->low_qubits;
+        std::vector<uint32_t> offs;
+        c->offs_base.clear();
+        for (const Pass &ps : c->passes) {
+            c->offs_base.push_back(offs.size());
+            for (uint32_t jh = 0; jh < (1u << (t - cl)); ++jh) {
+                uint64_t o = 0;
+                for (uint32_t i = cl; i < t; ++i)
+                    if ((jh >> (i - cl)) & 1u) o |= 1ull << ps.tile_qubits[i];
+                ARSO_REQUIRE(o < (1ull << 32), "tile offset overflow");
+                offs.push_back((uint32_t)o);
+            }
+        }
+        c->d_offs.ensure(offs.size() * 4);
+        ARSO_CUDA(cudaMemcpy(c->d_offs.ptr, offs.data(), offs.size() * 4, cudaMemcpyHostToDevice));
+    }
+}
+
+// ----------------------------------------------------------- prefix cache --
+static void ensure_cache(arso_circuit *c, cudaStream_t st) {
+    if (c->cache_ready) return;
+    const size_t sb = c->state_bytes();
+    const uint64_t G = c->gates.size();
+    if (c->engine == 0) {
+        const uint64_t budget = std::min<uint64_t>(c->cache_budget, 512ull << 20);
+        uint64_t every = std::max<uint64_t>(1, ((G + 1) * sb + budget - 1) / budget);
+        c->ckpt_every = every;
+        c->n_ckpt = (uint32_t)(G / every + 1 + (G % every ? 1 : 0));
+        c->d_cache.ensure((size_t)c->n_ckpt * sb);
+        ResidentArgs a{};
+        a.n = (int)c->n;
+        a.G = (uint32_t)G;
+        a.gates = c->d_gates.as<DGate>();
+        a.mats = c->d_mats.ptr;
+        a.cache = c->d_cache.ptr;
+        a.ckpt_every = every;
+        a.n_ckpt = c->n_ckpt;
+        launch_resident(a, true, c->precision, st);
+    } else {
+        const uint32_t P = (uint32_t)c->passes.size();
+        // boundaries 0..P; cache every s-th boundary and the last one
+        uint32_t s = 1;
+        while ((uint64_t)((P + s - 1) / s + 2) * sb > c->cache_budget && s < P) ++s;
+        c->ckpt_pass.assign(P + 1, NO_EVENT);
+        uint32_t slots = 0;
+        for (uint32_t j = 0; j <= P; ++j)
+            if (j % s == 0 || j == P) c->ckpt_pass[j] = slots++;
+        c->n_ckpt = slots;
+        c->d_cache.ensure((size_t)slots * sb);
+        Scratch work(st, s > 1 ? sb : 0);
+        char *base = c->d_cache.as<char>();
+        launch_init_zero_state(base, (int)c->n, c->precision, st);
+        for (uint32_t j = 0; j < P; ++j) {
+            PassArgs a{};
+            a.n = (int)c->n;
+            a.t = (int)c->tile_qubits;
+            a.c = (int)c->low_qubits;
+            uint64_t tm = 0;
+            for (uint32_t q : c->passes[j].tile_qubits) tm |= 1ull << q;
+            a.rest_mask = ((c->n == 64 ? 0 : (1ull << c->n)) - 1) & ~tm;
+            a.offs = c->d_offs.as<uint32_t>() + c->offs_base[j];
+            a.gb = c->passes[j].gb;
+            a.ge = c->passes[j].ge;
+            a.pass = (int)j;
+            a.gates = c->d_gates.as<DGate>();
+            a.mats = c->d_mats.ptr;
+            a.ideal = 1;
+            a.ideal_src = c->ckpt_pass[j] != NO_EVENT ? base + (size_t)c->ckpt_pass[j] * sb : work.ptr;
+            a.ideal_dst = c->ckpt_pass[j + 1] != NO_EVENT ? base + (size_t)c->ckpt_pass[j + 1] * sb : work.ptr;
+            launch_pass(a, false, c->precision, 1, st);
+        }
+    }
+    ARSO_CUDA(cudaStreamSynchronize(st));
+    c->cache_ready = true;
+}
+
+static const void *ref_state_ptr(const arso_circuit *c) {
+    return c->d_cache.as<char>() + (size_t)(c->n_ckpt - 1) * c->state_bytes();
+}
+
+// ------------------------------------------------------------ criterion ----
+struct DevCrit {
+    DCrit d{};
+    uint32_t aggregate = 0;
+    DeviceBuffer bitmap;
+};
+
+static void make_crit(const arso_circuit *c, const arso_criterion *crit, DevCrit &out, cudaStream_t st) {
+    ARSO_REQUIRE(crit != nullptr, "criterion is NULL");
+    ARSO_REQUIRE(crit->kind <= ARSO_CRIT_ARGMAX, "bad criterion kind");
+    ARSO_REQUIRE(crit->aggregate <= ARSO_AGG_PASS, "bad aggregate");
+    const uint64_t N = 1ull << c->n;
+    if (crit->kind == ARSO_CRIT_OUTCOME || crit->kind == ARSO_CRIT_ARGMAX)
+        ARSO_REQUIRE(crit->target < N, "criterion target out of range");
+    out.d.kind = crit->kind;
+    out.d.threshold = crit->threshold;
+    out.d.target = crit->target;
+    out.d.bitmap = nullptr;
+    out.aggregate = crit->aggregate;
+    if (crit->kind == ARSO_CRIT_BINNING) {
+        ARSO_REQUIRE(crit->set_len == 0 || crit->set != nullptr, "binning set is NULL");
+        std::vector<uint32_t> bm((N + 31) / 32, 0);
+        for (size_t i = 0; i < crit->set_len; ++i) {
+            ARSO_REQUIRE(crit->set[i] < N, "binning outcome out of range");
+            bm[crit->set[i] >> 5] |= 1u << (crit->set[i] & 31);
+        }
+        out.bitmap.ensure(bm.size() * 4);
+        ARSO_CUDA(cudaMemcpyAsync(out.bitmap.ptr, bm.data(), bm.size() * 4, cudaMemcpyHostToDevice, st));
+        ARSO_CUDA(cudaStreamSynchronize(st));
+        out.d.bitmap = out.bitmap.as<uint32_t>();
+    }
+}
+
+// score of an arbitrary device state into a device scalar
+static void score_into(const void *psi, const void *ref, int n, int precision, const DCrit &crit, double *d_out,
+                       cudaStream_t st) {
+    Scratch parts(st, 152 * 8 * sizeof(Partial));
+    const uint32_t blocks = launch_score_partials(psi, ref, n, precision, crit, parts.as<Partial>(), 152 * 8, st);
+    launch_finish_partials(parts.as<Partial>(), blocks, 1, nullptr, crit, d_out, nullptr, st);
+}
+
+// -------------------------------------------------------------- engines ----
+static PassArgs pass_args(const arso_circuit *c, uint32_t j) {
+    PassArgs a{};
+    a.n = (int)c->n;
+    a.t = (int)c->tile_qubits;
+    a.c = (int)c->low_qubits;
+    uint64_t tm = 0;
+    for (uint32_t q : c->passes[j].tile_qubits) tm |= 1ull << q;
+    a.rest_mask = ((1ull << c->n) - 1) & ~tm;
+    a.offs = c->d_offs.as<uint32_t>() + c->offs_base[j];
+    a.gb = c->passes[j].gb;
+    a.ge = c->passes[j].ge;
+    a.pass = (int)j;
+    a.gates = c->d_gates.as<DGate>();
+    a.mats = c->d_mats.ptr;
+    return a;
+}
+
+// Streaming engine over trajectories `ids` of the error list. states_out
+// (non-null) receives final states in the order of `ids` instead of scores.
+static void run_streaming(arso_circuit *c, const arso_error_list *e, const std::vector<uint64_t> &ids,
+                          const std::vector<uint32_t> &first_pos, const DCrit &crit, double *d_score,
+                          uint8_t *d_pass, void *states_out, cudaStream_t st) {
+    if (ids.empty()) return;
+    const uint32_t P = (uint32_t)c->passes.size();
+    const size_t sb = c->state_bytes();
+    const uint32_t tiles = 1u << (c->n - c->tile_qubits);
+    // start boundary: the last cached boundary at or before the first error's pass
+    std::vector<int> start(ids.size());
+    for (size_t i = 0; i < ids.size(); ++i) {
+        uint32_t fp = first_pos[i] == NO_EVENT ? P - 1 : c->pass_of_pos[first_pos[i]];
+        while (c->ckpt_pass[fp] == NO_EVENT) --fp;
+        start[i] = (int)fp;
+    }
+    std::vector<size_t> order(ids.size());
+    std::iota(order.begin(), order.end(), 0);
+    if (!states_out)
+        std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return start[x] > start[y]; });
+    uint64_t B = c->max_batch ? c->max_batch : std::max<uint64_t>(1, (8ull << 30) / sb);
+    B = std::min<uint64_t>(B, std::min<uint64_t>(ids.size(), 65535));
+    if (states_out) B = ids.size();
+    ARSO_REQUIRE(B <= 65535, "too many states requested at once");
+    Scratch work(st, states_out ? 0 : B * sb);
+    Scratch parts(st, states_out ? 0 : B * tiles * sizeof(Partial));
+    Scratch d_slot_traj(st, B * 8), d_start(st, B * 4);
+    std::vector<uint32_t> cslot(c->ckpt_pass.begin(), c->ckpt_pass.end());
+    Scratch d_cslot(st, cslot.size() * 4);
+    h2d(d_cslot.ptr, cslot, st);
+    for (size_t b0 = 0; b0 < ids.size(); b0 += B) {
+        const size_t nb = std::min<size_t>(B, ids.size() - b0);
+        std::vector<uint64_t> st_traj(nb);
+        std::vector<int> st_start(nb);
+        int jmin = (int)P;
+        for (size_t i = 0; i < nb; ++i) {
+            st_traj[i] = ids[order[b0 + i]];
+            st_start[i] = start[order[b0 + i]];
+            jmin = std::min(jmin, st_start[i]);
+        }
+        h2d(d_slot_traj.ptr, st_traj, st);
+        h2d(d_start.ptr, st_start, st);
+        for (uint32_t j = (uint32_t)jmin; j < P; ++j) {
+            PassArgs a = pass_args(c, j);
+            a.cache = c->d_cache.ptr;
+            a.cache_slot = d_cslot.as<uint32_t>();
+            a.ref_slot = c->n_ckpt - 1;
+            a.work = states_out ? states_out : work.ptr;
+            a.start_pass = d_start.as<int>();
+            a.slot_traj = d_slot_traj.as<uint64_t>();
+            a.offsets = e->d_offsets.as<uint64_t>();
+            a.keys = e->d_key.as<uint32_t>();
+            a.crit = crit;
+            a.partials = parts.as<Partial>();
+            a.store_last = states_out ? 1 : 0;
+            launch_pass(a, j == P - 1, c->precision, (uint32_t)nb, st);
+        }
+        if (!states_out)
+            launch_finish_partials(parts.as<Partial>(), tiles, (uint32_t)nb, d_slot_traj.as<uint64_t>(), crit, d_score,
+                                   d_pass, st);
+        ARSO_CUDA(cudaStreamSynchronize(st));  // host vectors and slot tables are reused per batch
+    }
+}
+
+static void run_all(arso_circuit *c, const arso_error_list *e, const DevCrit &dc, cudaStream_t st, double *d_score,
+                    uint8_t *d_pass) {
+    ensure_cache(c, st);
+    Scratch ref(st, sizeof(double));
+    score_into(ref_state_ptr(c), ref_state_ptr(c), (int)c->n, c->precision, dc.d, ref.as<double>(), st);
+    if (e->n_traj == 0) return;
+    if (c->engine == 0) {
+        ResidentArgs a{};
+        a.n = (int)c->n;
+        a.G = (uint32_t)c->gates.size();
+        a.gates = c->d_gates.as<DGate>();
+        a.mats = c->d_mats.ptr;
+        a.cache = c->d_cache.ptr;
+        a.ckpt_every = c->ckpt_every;
+        a.n_ckpt = c->n_ckpt;
+        a.first_traj = 0;
+        a.count = e->n_traj;
+        a.offsets = e->d_offsets.as<uint64_t>();
+        a.keys = e->d_key.as<uint32_t>();
+        a.first = e->d_first.as<uint32_t>();
+        a.crit = dc.d;
+        a.ref_score = ref.as<double>();
+        a.score = d_score;
+        a.pass_flags = d_pass;
+        launch_resident(a, false, c->precision, st);
+        ARSO_CUDA(cudaStreamSynchronize(st));
+        return;
+    }
+    launch_fill_error_free(e->d_first.as<uint32_t>(), e->n_traj, ref.as<double>(), dc.d.threshold, d_score, d_pass, st);
+    std::vector<uint32_t> first(e->n_traj);
+    ARSO_CUDA(cudaMemcpyAsync(first.data(), e->d_first.ptr, e->n_traj * 4, cudaMemcpyDeviceToHost, st));
+    ARSO_CUDA(cudaStreamSynchronize(st));
+    std::vector<uint64_t> ids;
+    std::vector<uint32_t> fp;
+    for (uint64_t i = 0; i < e->n_traj; ++i)
+        if (first[i] != NO_EVENT) ids.push_back(i), fp.push_back(first[i]);
+    run_streaming(c, e, ids, fp, dc.d, d_score, d_pass, nullptr, st);
+    ARSO_CUDA(cudaStreamSynchronize(st));
+}
+
+// ------------------------------------------------------------ sampling -----
+static arso_error_list *new_list(const arso_circuit *c, uint64_t n_traj) {
+    auto *e = new arso_error_list();
+    e->circ = c;
+    e->n_traj = n_traj;
+    e->d_offsets.ensure((n_traj + 1) * 8);
+    e->d_first.ensure(std::max<uint64_t>(n_traj, 1) * 4);
+    return e;
+}
+
+static void finish_list(const arso_circuit *c, arso_error_list *e, cudaStream_t st) {
+    bool identity = true;
+    for (size_t i = 0; i < c->perm.size() && identity; ++i) identity = c->perm[i] == i;
+    if (!identity) launch_sort_keys(e->d_offsets.as<uint64_t>(), e->n_traj, e->d_key.as<uint32_t>(), st);
+    launch_first_event(e->d_offsets.as<uint64_t>(), e->n_traj, e->d_key.as<uint32_t>(), e->d_first.as<uint32_t>(), st);
+    ARSO_CUDA(cudaStreamSynchronize(st));
+}
+
+static void sample(const arso_circuit *c, double px, double pz, double py, uint64_t seed, uint64_t begin,
+                   uint64_t n_traj, cudaStream_t st, arso_error_list **out) {
+    ARSO_REQUIRE(px >= 0 && pz >= 0 && py >= 0, "error probabilities must be >= 0");
+    const double pt = px + pz + py;
+    ARSO_REQUIRE(pt <= 1.0, "p_x + p_z + p_y must be <= 1");
+    ARSO_REQUIRE(begin + n_traj >= begin, "trajectory range overflows");
+    std::unique_ptr<arso_error_list> e(new_list(c, n_traj));
+    SampleArgs a{};
+    a.seed = seed;
+    a.traj_begin = begin;
+    a.n_traj = n_traj;
+    a.L = (uint32_t)c->L;
+    if (pt > 0) {
+        const double two32 = 4294967296.0;
+        a.thr = (uint32_t)std::min(std::floor(pt * two32), 4294967295.0);
+        const double cx = std::floor(px / pt * two32), cxz = std::floor((px + pz) / pt * two32);
+        a.cut_x_all = cx >= two32;
+        a.cut_xz_all = cxz >= two32;
+        a.cut_x = a.cut_x_all ? 0 : (uint32_t)cx;
+        a.cut_xz = a.cut_xz_all ? 0 : (uint32_t)cxz;
+    }
+    Scratch counts(st, std::max<uint64_t>(n_traj, 1) * 4);
+    if (a.thr == 0 || c->L == 0) {
+        ARSO_CUDA(cudaMemsetAsync(counts.ptr, 0, std::max<uint64_t>(n_traj, 1) * 4, st));
+    } else {
+        launch_sample_count(a, counts.as<uint32_t>(), st);
+    }
+    launch_exclusive_scan(counts.as<uint32_t>(), n_traj, e->d_offsets.as<uint64_t>(), st);
+    uint64_t total = 0;
+    ARSO_CUDA(cudaMemcpyAsync(&total, e->d_offsets.as<uint64_t>() + n_traj, 8, cudaMemcpyDeviceToHost, st));
+    ARSO_CUDA(cudaStreamSynchronize(st));
+    e->n_events = total;
+    e->d_loc.ensure(std::max<uint64_t>(total, 1) * 4);
+    e->d_key.ensure(std::max<uint64_t>(total, 1) * 4);
+    if (total) launch_sample_fill(a, e->d_offsets.as<uint64_t>(), c->d_loc_key.as<uint32_t>(), e->d_loc.as<uint32_t>(),
+                                  e->d_key.as<uint32_t>(), st);
+    finish_list(c, e.get(), st);
+    *out = e.release();
+}
+
+static void list_from_host(const arso_circuit *c, uint64_t n_traj, const uint64_t *offsets, const uint32_t *events,
+                           cudaStream_t st, arso_error_list **out) {
+    ARSO_REQUIRE(offsets != nullptr, "offsets is NULL");
+    ARSO_REQUIRE(offsets[0] == 0, "offsets[0] must be 0");
+    for (uint64_t t = 0; t < n_traj; ++t) {
+        ARSO_REQUIRE(offsets[t + 1] >= offsets[t], "offsets must be non-decreasing");
+        for (uint64_t i = offsets[t]; i < offsets[t + 1]; ++i) {
+            ARSO_REQUIRE((events[i] >> 2) < c->L, "event location out of range");
+            ARSO_REQUIRE((events[i] & 3u) != 0, "event code must be 1 (X), 2 (Z) or 3 (Y)");
+            ARSO_REQUIRE(i == offsets[t] || (events[i] >> 2) > (events[i - 1] >> 2),
+                         "events must be strictly increasing in location within a trajectory");
+        }
+    }
+    const uint64_t total = offsets[n_traj];
+    ARSO_REQUIRE(total == 0 || events != nullptr, "events is NULL");
+    std::unique_ptr<arso_error_list> e(new_list(c, n_traj));
+    e->n_events = total;
+    e->d_loc.ensure(std::max<uint64_t>(total, 1) * 4);
+    e->d_key.ensure(std::max<uint64_t>(total, 1) * 4);
+    ARSO_CUDA(cudaMemcpyAsync(e->d_offsets.ptr, offsets, (n_traj + 1) * 8, cudaMemcpyHostToDevice, st));
+    if (total) {
+        ARSO_CUDA(cudaMemcpyAsync(e->d_loc.ptr, events, total * 4, cudaMemcpyHostToDevice, st));
+        launch_keys_from_loc(e->d_loc.as<uint32_t>(), total, c->d_loc_key.as<uint32_t>(), e->d_key.as<uint32_t>(), st);
+    }
+    finish_list(c, e.get(), st);
+    *out = e.release();
+}
+
+// --------------------------------------------------- success probability ---
+struct McOut {
+    double mean, pass_frac, sd_mean, sd_pass;
+};
+
+static McOut mc_run(arso_circuit *c, const DevCrit &dc, double p, uint64_t n_traj, uint64_t seed, cudaStream_t st) {
+    arso_error_list *raw = nullptr;
+    sample(c, p / 3, p / 3, p / 3, seed, 0, n_traj, st, &raw);
+    std::unique_ptr<arso_error_list> e(raw);
+    Scratch sc(st, std::max<uint64_t>(n_traj, 1) * 8), pf(st, std::max<uint64_t>(n_traj, 1));
+    Scratch sums(st, 3 * 8);
+    run_all(c, e.get(), dc, st, sc.as<double>(), pf.as<uint8_t>());
+    launch_sum_scores(sc.as<double>(), pf.as<uint8_t>(), n_traj, sums.as<double>(), st);
+    double h[3];
+    ARSO_CUDA(cudaMemcpyAsync(h, sums.ptr, 24, cudaMemcpyDeviceToHost, st));
+    ARSO_CUDA(cudaStreamSynchronize(st));
+    McOut o{};
+    const double N = (double)std::max<uint64_t>(n_traj, 1);
+    o.mean = h[0] / N;
+    o.pass_frac = h[2] / N;
+    const double var_s = n_traj > 1 ? std::max(0.0, (h[1] - h[0] * h[0] / N) / (N - 1)) : 0.0;
+    const double var_p = n_traj > 1 ? std::max(0.0, (h[2] - h[2] * h[2] / N) / (N - 1)) : 0.0;
+    o.sd_mean = std::sqrt(var_s / N);
+    o.sd_pass = std::sqrt(var_p / N);
+    return o;
+}
+
+// Exhaustive single-error analysis: values per location and per type
+// (Eq. (3)); P[4] = {P_R, P_X, P_Z, P_Y} for the given aggregate.
+static void exhaustive(arso_circuit *c, const DevCrit &dc, cudaStream_t st, double *P, std::vector<double> *per_loc_mean,
+                       std::vector<double> *per_loc_pass, double *P_pass) {
+    const uint64_t L = c->L;
+    const uint64_t T = 3 * L;
+    std::vector<uint64_t> off(T + 1);
+    std::vector<uint32_t> ev(T);
+    const uint32_t codes[3] = {1, 2, 3};  // X, Z, Y blocks
+    for (uint64_t i = 0; i < T; ++i) {
+        off[i] = i;
+        ev[i] = (uint32_t)(((i % std::max<uint64_t>(L, 1)) << 2) | codes[i / std::max<uint64_t>(L, 1)]);
+    }
+    off[T] = T;
+    arso_error_list *raw = nullptr;
+    list_from_host(c, T, off.data(), ev.data(), st, &raw);
+    std::unique_ptr<arso_error_list> e(raw);
+    Scratch sc(st, std::max<uint64_t>(T, 1) * 8), pf(st, std::max<uint64_t>(T, 1));
+    run_all(c, e.get(), dc, st, sc.as<double>(), pf.as<uint8_t>());
+    std::vector<double> s(T);
+    std::vector<uint8_t> f(T);
+    if (T) {
+        ARSO_CUDA(cudaMemcpyAsync(s.data(), sc.ptr, T * 8, cudaMemcpyDeviceToHost, st));
+        ARSO_CUDA(cudaMemcpyAsync(f.data(), pf.ptr, T, cudaMemcpyDeviceToHost, st));
+    }
+    // reference value
+    Scratch ref(st, 8);
+    score_into(ref_state_ptr(c), ref_state_ptr(c), (int)c->n, c->precision, dc.d, ref.as<double>(), st);
+    double r = 0;
+    ARSO_CUDA(cudaMemcpyAsync(&r, ref.ptr, 8, cudaMemcpyDeviceToHost, st));
+    ARSO_CUDA(cudaStreamSynchronize(st));
+    const double rp = r >= dc.d.threshold ? 1.0 : 0.0;
+    double Pm[4] = {r, 0, 0, 0}, Pp[4] = {rp, 0, 0, 0};
+    for (uint64_t i = 0; i < T; ++i) {
+        Pm[1 + i / L] += s[i];
+        Pp[1 + i / L] += f[i];
+    }
+    for (int k = 1; k < 4; ++k) {
+        Pm[k] = L ? Pm[k] / (double)L : 0.0;
+        Pp[k] = L ? Pp[k] / (double)L : 0.0;
+    }
+    const double *sel = dc.aggregate == ARSO_AGG_MEAN ? Pm : Pp;
+    for (int k = 0; k < 4; ++k) P[k] = sel[k];
+    if (P_pass)
+        for (int k = 0; k < 4; ++k) P_pass[k] = Pp[k];
+    if (per_loc_mean) *per_loc_mean = s;
+    if (per_loc_pass) {
+        per_loc_pass->resize(T);
+        for (uint64_t i = 0; i < T; ++i) (*per_loc_pass)[i] = f[i];
+    }
+}
+
+// Eq. (4) with E(N_e) = L p_e
+static double eq4(const double *P, uint64_t L, double pe) {
+    const double E = (double)L * pe;
+    return (P[1] + P[2] + P[3]) * E + P[0] * (1.0 - 3.0 * E);
+}
+
+}  // namespace arso
+
+using namespace arso;
+
+// ================================================================ C ABI ====
+extern "C" {
+
+const char *arso_last_error(void) { return g_last_error.c_str(); }
+const char *arso_version(void) { return "arso-gb300 0.1 (sm_103a)"; }
+
+arso_status arso_compile_circuit(uint32_t n_qubits, const arso_gate *gates, size_t n_gates,
+                                 const arso_compile_opts *opts, arso_circuit **out) {
+    return guard([&] {
+        ARSO_REQUIRE(out != nullptr, "out is NULL");
+        *out = nullptr;
+        std::unique_ptr<arso_circuit> c(new arso_circuit());
+        build_circuit(c.get(), n_qubits, gates, n_gates, opts);
+        upload_circuit(c.get());
+        *out = c.release();
+    });
+}
+
+void arso_circuit_free(arso_circuit *c) { delete c; }
+
+arso_status arso_plan_schedule(uint32_t n_qubits, const arso_gate *gates, size_t n_gates,
+                               const arso_compile_opts *opts, uint32_t *n_passes, uint32_t capacity, uint32_t *perm,
+                               uint32_t *pass_begin, uint64_t *tile_mask) {
+    return guard([&] {
+        ARSO_REQUIRE(n_passes != nullptr, "n_passes is NULL");
+        arso_circuit c;
+        build_circuit(&c, n_qubits, gates, n_gates, opts);
+        const uint32_t P = (uint32_t)c.passes.size();
+        *n_passes = P;
+        if (!perm && !pass_begin && !tile_mask) return;
+        ARSO_REQUIRE(P <= capacity, "capacity too small for the schedule");
+        if (perm) std::copy(c.perm.begin(), c.perm.end(), perm);
+        for (uint32_t p = 0; p < P; ++p) {
+            if (pass_begin) pass_begin[p] = c.passes[p].gb;
+            if (tile_mask) {
+                uint64_t m = 0;
+                for (uint32_t q : c.passes[p].tile_qubits) m |= 1ull << q;
+                tile_mask[p] = m;
+            }
+        }
+        if (pass_begin) pass_begin[P] = P ? c.passes[P - 1].ge : 0;
+    });
+}
+
+arso_status arso_circuit_get_info(const arso_circuit *c, arso_circuit_info *out) {
+    return guard([&] {
+        ARSO_REQUIRE(c && out, "NULL argument");
+        out->n_qubits = c->n;
+        out->G = c->gates.size();
+        out->k = c->k;
+        out->m = c->m;
+        out->L = c->L;
+        out->engine = (uint32_t)c->engine;
+        out->n_passes = (uint32_t)c->passes.size();
+        out->tile_qubits = c->tile_qubits;
+        out->precision = (uint32_t)c->precision;
+        out->checkpoint_every = c->ckpt_every;
+    });
+}
+
+arso_status arso_sample_errors(const arso_circuit *c, double p_x, double p_z, double p_y, uint64_t seed,
+                               uint64_t traj_begin, uint64_t n_traj, void *stream, arso_error_list **out) {
+    return guard([&] {
+        ARSO_REQUIRE(c && out, "NULL argument");
+        *out = nullptr;
+        sample(c, p_x, p_z, p_y, seed, traj_begin, n_traj, (cudaStream_t)stream, out);
+    });
+}
+
+arso_status arso_error_list_from_host(const arso_circuit *c, uint64_t n_traj, const uint64_t *offsets,
+                                      const uint32_t *events, void *stream, arso_error_list **out) {
+    return guard([&] {
+        ARSO_REQUIRE(c && out, "NULL argument");
+        *out = nullptr;
+        list_from_host(c, n_traj, offsets, events, (cudaStream_t)stream, out);
+    });
+}
+
+arso_status arso_error_list_info(const arso_error_list *e, uint64_t *n_traj, uint64_t *n_events) {
+    return guard([&] {
+        ARSO_REQUIRE(e != nullptr, "NULL error list");
+        if (n_traj) *n_traj = e->n_traj;
+        if (n_events) *n_events = e->n_events;
+    });
+}
+
+arso_status arso_error_list_copy(const arso_error_list *e, uint64_t *offsets, uint32_t *events, void *stream) {
+    return guard([&] {
+        ARSO_REQUIRE(e != nullptr, "NULL error list");
+        cudaStream_t st = (cudaStream_t)stream;
+        if (offsets)
+            ARSO_CUDA(cudaMemcpyAsync(offsets, e->d_offsets.ptr, (e->n_traj + 1) * 8, cudaMemcpyDeviceToHost, st));
+        if (events && e->n_events)
+            ARSO_CUDA(cudaMemcpyAsync(events, e->d_loc.ptr, e->n_events * 4, cudaMemcpyDeviceToHost, st));
+        ARSO_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+void arso_error_list_free(arso_error_list *e) { delete e; }
+
+arso_status arso_run_trajectories(const arso_circuit *cc, const arso_error_list *e, const arso_criterion *crit,
+                                  void *stream, double *score_out, uint8_t *pass_out) {
+    return guard([&] {
+        ARSO_REQUIRE(cc && e && crit && score_out, "NULL argument");
+        ARSO_REQUIRE(e->circ == cc, "error list belongs to another circuit");
+        arso_circuit *c = const_cast<arso_circuit *>(cc);
+        cudaStream_t st = (cudaStream_t)stream;
+        DevCrit dc;
+        make_crit(c, crit, dc, st);
+        const bool sdev = is_device_ptr(score_out), pdev = pass_out && is_device_ptr(pass_out);
+        Scratch sc(st, sdev ? 0 : std::max<uint64_t>(e->n_traj, 1) * 8);
+        Scratch pf(st, (pass_out && !pdev) ? std::max<uint64_t>(e->n_traj, 1) : 0);
+        double *d_score = sdev ? score_out : sc.as<double>();
+        uint8_t *d_pass = pass_out ? (pdev ? pass_out : pf.as<uint8_t>()) : nullptr;
+        run_all(c, e, dc, st, d_score, d_pass);
+        if (!sdev && e->n_traj)
+            ARSO_CUDA(cudaMemcpyAsync(score_out, d_score, e->n_traj * 8, cudaMemcpyDeviceToHost, st));
+        if (pass_out && !pdev && e->n_traj)
+            ARSO_CUDA(cudaMemcpyAsync(pass_out, d_pass, e->n_traj, cudaMemcpyDeviceToHost, st));
+        ARSO_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+arso_status arso_trajectory_states(const arso_circuit *cc, const arso_error_list *e, uint64_t first, uint64_t count,
+                                   void *stream, void *amps_out) {
+    return guard([&] {
+        ARSO_REQUIRE(cc && e && amps_out, "NULL argument");
+        ARSO_REQUIRE(e->circ == cc, "error list belongs to another circuit");
+        ARSO_REQUIRE(first + count <= e->n_traj, "trajectory range out of bounds");
+        ARSO_REQUIRE(is_device_ptr(amps_out), "amps_out must be device memory");
+        arso_circuit *c = const_cast<arso_circuit *>(cc);
+        cudaStream_t st = (cudaStream_t)stream;
+        ensure_cache(c, st);
+        if (!count) return;
+        if (c->engine == 0) {
+            ResidentArgs a{};
+            a.n = (int)c->n;
+            a.G = (uint32_t)c->gates.size();
+            a.gates = c->d_gates.as<DGate>();
+            a.mats = c->d_mats.ptr;
+            a.cache = c->d_cache.ptr;
+            a.ckpt_every = c->ckpt_every;
+            a.n_ckpt = c->n_ckpt;
+            a.first_traj = first;
+            a.count = count;
+            a.offsets = e->d_offsets.as<uint64_t>();
+            a.keys = e->d_key.as<uint32_t>();
+            a.first = e->d_first.as<uint32_t>();
+            a.states_out = amps_out;
+            launch_resident(a, false, c->precision, st);
+        } else {
+            std::vector<uint32_t> fp(count);
+            ARSO_CUDA(cudaMemcpyAsync(fp.data(), e->d_first.as<uint32_t>() + first, count * 4, cudaMemcpyDeviceToHost, st));
+            ARSO_CUDA(cudaStreamSynchronize(st));
+            std::vector<uint64_t> ids(count);
+            for (uint64_t i = 0; i < count; ++i) ids[i] = first + i;
+            DCrit none{};
+            run_streaming(c, e, ids, fp, none, nullptr, nullptr, amps_out, st);
+        }
+        ARSO_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+arso_status arso_reference_state(const arso_circuit *cc, void *stream, void *amps_out) {
+    return guard([&] {
+        ARSO_REQUIRE(cc && amps_out, "NULL argument");
+        arso_circuit *c = const_cast<arso_circuit *>(cc);
+        cudaStream_t st = (cudaStream_t)stream;
+        ensure_cache(c, st);
+        ARSO_CUDA(cudaMemcpyAsync(amps_out, ref_state_ptr(c), c->state_bytes(), cudaMemcpyDefault, st));
+        ARSO_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+arso_status arso_exhaustive(const arso_circuit *cc, const arso_criterion *crit, void *stream, double *P_out,
+                            double *per_location) {
+    return guard([&] {
+        ARSO_REQUIRE(cc && crit && P_out, "NULL argument");
+        arso_circuit *c = const_cast<arso_circuit *>(cc);
+        cudaStream_t st = (cudaStream_t)stream;
+        DevCrit dc;
+        make_crit(c, crit, dc, st);
+        std::vector<double> pm, pp;
+        exhaustive(c, dc, st, P_out, per_location ? &pm : nullptr, per_location ? &pp : nullptr, nullptr);
+        if (per_location) {
+            const std::vector<double> &v = dc.aggregate == ARSO_AGG_MEAN ? pm : pp;
+            std::copy(v.begin(), v.end(), per_location);
+        }
+    });
+}
+
+arso_status arso_success_prob(const arso_circuit *cc, const arso_criterion *crit, double p, uint32_t mode,
+                              uint64_t n_traj, uint64_t seed, void *stream, arso_result *out) {
+    return guard([&] {
+        ARSO_REQUIRE(cc && crit && out, "NULL argument");
+        ARSO_REQUIRE(p >= 0.0 && p <= 1.0, "p must be in [0, 1]");
+        ARSO_REQUIRE(mode <= ARSO_MODE_EXHAUSTIVE, "bad mode");
+        arso_circuit *c = const_cast<arso_circuit *>(cc);
+        cudaStream_t st = (cudaStream_t)stream;
+        DevCrit dc;
+        make_crit(c, crit, dc, st);
+        std::memset(out, 0, sizeof(*out));
+        out->expected_errors = (double)c->L * p;
+        const bool mc = mode == ARSO_MODE_MONTE_CARLO || (mode == ARSO_MODE_AUTO && out->expected_errors > 1.0);
+        if (mc) {
+            ARSO_REQUIRE(n_traj > 0, "n_traj must be > 0 for Monte Carlo");
+            const McOut o = mc_run(c, dc, p, n_traj, seed, st);
+            out->mode_used = ARSO_MODE_MONTE_CARLO;
+            out->mean = o.mean;
+            out->pass_frac = o.pass_frac;
+            out->value = dc.aggregate == ARSO_AGG_MEAN ? o.mean : o.pass_frac;
+            out->stderr_value = dc.aggregate == ARSO_AGG_MEAN ? o.sd_mean : o.sd_pass;
+            out->n_traj = n_traj;
+        } else {
+            double P[4], Pp[4];
+            DevCrit dm;
+            make_crit(c, crit, dm, st);
+            dm.aggregate = ARSO_AGG_MEAN;
+            exhaustive(c, dm, st, P, nullptr, nullptr, Pp);
+            out->mode_used = ARSO_MODE_EXHAUSTIVE;
+            out->mean = eq4(P, c->L, p / 3);
+            out->pass_frac = eq4(Pp, c->L, p / 3);
+            const double *sel = dc.aggregate == ARSO_AGG_MEAN ? P : Pp;
+            out->value = dc.aggregate == ARSO_AGG_MEAN ? out->mean : out->pass_frac;
+            out->P_R = sel[0];
+            out->P_X = sel[1];
+            out->P_Z = sel[2];
+            out->P_Y = sel[3];
+            out->n_traj = 3 * c->L;
+        }
+    });
+}
+
+arso_status arso_tolerable_rate(const arso_circuit *cc, const arso_criterion *crit, double P_target,
+                                const arso_search_opts *opts, void *stream, arso_rate_result *out) {
+    return guard([&] {
+        ARSO_REQUIRE(cc && crit && out, "NULL argument");
+        arso_circuit *c = const_cast<arso_circuit *>(cc);
+        cudaStream_t st = (cudaStream_t)stream;
+        arso_search_opts o{};
+        if (opts) o = *opts;
+        const double p_lo = o.p_lo > 0 ? o.p_lo : 1e-6, p_hi = o.p_hi > 0 ? o.p_hi : 1e-1;
+        const double rel = o.rel_tol > 0 ? o.rel_tol : 0.02;
+        const uint64_t nt = o.n_traj ? o.n_traj : 1000;
+        const uint32_t max_probes = o.max_probes ? o.max_probes : 64;
+        ARSO_REQUIRE(p_lo < p_hi && p_hi <= 1.0, "need 0 < p_lo < p_hi <= 1");
+        ARSO_REQUIRE(o.surrogate == nullptr, "surrogate search is provided by arso_tolerable_rate_surrogate");
+        DevCrit dc;
+        make_crit(c, crit, dc, st);
+        std::memset(out, 0, sizeof(*out));
+        out->P1 = NAN;
+        if (o.mode != ARSO_MODE_MONTE_CARLO) {
+            double P[4];
+            exhaustive(c, dc, st, P, nullptr, nullptr, nullptr);
+            const double P1 = (P[1] + P[2] + P[3]) / 3.0;
+            out->P1 = P1;
+            if (P_target >= P1) {
+                // Eq. (5) with count L
+                const double denom = (double)c->L * (P1 - P[0]);
+                out->p = denom != 0.0 ? (P_target - P[0]) / denom : INFINITY;
+                out->lo = out->hi = out->p;
+                out->mode_used = 0;
+                out->converged = 1;
+                return;
+            }
+        }
+        out->mode_used = 1;
+        auto f = [&](double p) {
+            const McOut m = mc_run(c, dc, p, nt, o.seed, st);
+            ++out->probes;
+            return dc.aggregate == ARSO_AGG_MEAN ? m.mean : m.pass_frac;
+        };
+        double lo = p_lo, hi = p_hi;
+        double v_lo = f(lo), v_hi = f(hi);
+        if (v_lo < P_target || v_hi >= P_target) {
+            out->p = v_lo < P_target ? lo : hi;
+            out->lo = out->hi = out->p;
+            out->value_lo = v_lo;
+            out->value_hi = v_hi;
+            throw Error(ARSO_ENOTCONVERGED, "target success probability is not bracketed by [p_lo, p_hi]");
+        }
+        while (hi / lo > 1.0 + rel && out->probes < max_probes) {
+            const double mid = std::sqrt(lo * hi);
+            const double v = f(mid);
+            if (v >= P_target) lo = mid, v_lo = v;
+            else hi = mid, v_hi = v;
+        }
+        out->lo = lo;
+        out->hi = hi;
+        out->value_lo = v_lo;
+        out->value_hi = v_hi;
+        if (v_lo == v_hi) {
+            out->p = std::sqrt(lo * hi);
+        } else {
+            const double fr = (v_lo - P_target) / (v_lo - v_hi);
+            out->p = std::pow(10.0, std::log10(lo) + fr * (std::log10(hi) - std::log10(lo)));
+        }
+        out->converged = hi / lo <= 1.0 + rel;
+        if (!out->converged) throw Error(ARSO_ENOTCONVERGED, "probe budget exhausted before rel_tol");
+    });
+}
+
+arso_status arso_apply_gate(uint32_t n, void *amps, const arso_gate *gate, void *stream) {
+    return guard([&] {
+        ARSO_REQUIRE(amps && gate, "NULL argument");
+        ARSO_REQUIRE(n >= 2 && n <= 34, "n_qubits must be in [2, 34]");
+        ARSO_REQUIRE(is_device_ptr(amps), "amps must be device memory");
+        HostGate h{};
+        h.kind = gate->kind;
+        h.arity = gate->kind >= ARSO_GATE_CX ? 2 : 1;
+        h.q0 = gate->q[0];
+        h.q1 = h.arity == 2 ? gate->q[1] : gate->q[0];
+        ARSO_REQUIRE(h.q0 < n && h.q1 < n && (h.arity == 1 || h.q0 != h.q1), "bad gate qubits");
+        matrix_for(*gate, h);
+        DGate d{};
+        d.cls = h.cls;
+        d.arity = (uint8_t)h.arity;
+        d.q0 = (uint8_t)h.q0;
+        d.q1 = (uint8_t)h.q1;
+        M16 m{};
+        if (h.arity == 1 && h.cls == GC_DIAG1) {
+            m.m[0] = make_float2((float)h.m[0].real(), (float)h.m[0].imag());
+            m.m[1] = make_float2((float)h.m[3].real(), (float)h.m[3].imag());
+        } else {
+            for (int i = 0; i < (h.arity == 1 ? 4 : 16); ++i)
+                m.m[i] = make_float2((float)h.m[i].real(), (float)h.m[i].imag());
+        }
+        if (h.cls == GC_NOP) return;
+        launch_gate_pairs(static_cast<float2 *>(amps), (int)n, d, m, (cudaStream_t)stream);
+        ARSO_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    });
+}
+
+arso_status arso_apply_pauli(uint32_t n, void *amps, uint32_t qubit, uint32_t code, void *stream) {
+    return guard([&] {
+        ARSO_REQUIRE(amps != nullptr, "NULL argument");
+        ARSO_REQUIRE(n >= 1 && n <= 34 && qubit < n, "bad qubit");
+        ARSO_REQUIRE(code >= 1 && code <= 3, "code must be 1 (X), 2 (Z) or 3 (Y)");
+        ARSO_REQUIRE(is_device_ptr(amps), "amps must be device memory");
+        launch_pauli(static_cast<float2 *>(amps), (int)n, qubit, code, (cudaStream_t)stream);
+        ARSO_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    });
+}
+
+arso_status arso_score_state(uint32_t n, const void *amps, const void *ref, const arso_criterion *crit, void *stream,
+                             double *score_out) {
+    return guard([&] {
+        ARSO_REQUIRE(amps && crit && score_out, "NULL argument");
+        ARSO_REQUIRE(n >= 1 && n <= 34, "bad n");
+        ARSO_REQUIRE(crit->kind != ARSO_CRIT_FIDELITY || ref != nullptr, "fidelity needs ref");
+        cudaStream_t st = (cudaStream_t)stream;
+        arso_circuit tmp;
+        tmp.n = n;
+        DevCrit dc;
+        make_crit(&tmp, crit, dc, st);
+        Scratch d(st, 8);
+        score_into(amps, ref ? ref : amps, (int)n, ARSO_C64, dc.d, d.as<double>(), st);
+        ARSO_CUDA(cudaMemcpyAsync(score_out, d.ptr, 8, cudaMemcpyDeviceToHost, st));
+        ARSO_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+}  // extern "C"

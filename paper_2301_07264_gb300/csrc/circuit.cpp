@@ -1,0 +1,196 @@
+// Circuit compiler: gate matrices, error-location table, fused pass schedule.
+//
+// A circuit (Sec. II) is a list of one- and two-qubit gates. Every gate gets
+// one error location per qubit (Sec. IV-B.2: a two-qubit gate draws an error
+// on each of its qubits), so L = k + 2m (Eq. (3)).
+//
+// Engines:
+//  * resident  - the whole 2^n state lives in one CTA's shared memory for the
+//                entire circuit (n <= 13 for complex64, 12 for complex128);
+//  * streaming - the state lives in HBM and is swept by fused passes. A pass
+//                is a set of t "tile qubits" (always including the low qubits
+//                0..c-1 so that global accesses stay contiguous) and a list of
+//                gates acting only on tile qubits; each CTA loads one tile of
+//                2^t amplitudes into shared memory, applies all of the pass's
+//                gates (and the trajectory's error gates that follow them),
+//                and writes the tile back: one HBM round trip per pass.
+//
+// The pass builder is greedy in circuit order: a gate joins the current pass
+// when its qubits fit in the tile set; otherwise its qubits become blocked for
+// the rest of the pass, and so does every later gate that touches a blocked
+// qubit. The set of gates placed in a pass is therefore closed under the
+// circuit's dependencies, and concatenating the passes gives an engine order
+// that is a valid topological reordering of the circuit. Error gates stay
+// attached to the gate they follow, which keeps them correct: a gate moved
+// ahead of gate g never touches g's qubits after g.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+
+namespace arso {
+
+using cd = std::complex<double>;
+
+void matrix_for(const arso_gate &g, HostGate &h) {
+    const double s2 = 1.0 / std::sqrt(2.0);
+    const double th = g.param;
+    const cd I(0, 1);
+    for (auto &v : h.m) v = 0;
+    auto set2 = [&](cd a, cd b, cd c, cd d) { h.m[0] = a; h.m[1] = b; h.m[2] = c; h.m[3] = d; };
+    switch (g.kind) {
+        case ARSO_GATE_ID: set2(1, 0, 0, 1); h.cls = GC_NOP; break;
+        case ARSO_GATE_H: set2(s2, s2, s2, -s2); h.cls = GC_DENSE1; break;
+        case ARSO_GATE_X: set2(0, 1, 1, 0); h.cls = GC_X; break;
+        case ARSO_GATE_Y: set2(0, -I, I, 0); h.cls = GC_DENSE1; break;
+        case ARSO_GATE_Z: set2(1, 0, 0, -1); h.cls = GC_DIAG1; break;
+        case ARSO_GATE_S: set2(1, 0, 0, I); h.cls = GC_DIAG1; break;
+        case ARSO_GATE_SDG: set2(1, 0, 0, -I); h.cls = GC_DIAG1; break;
+        case ARSO_GATE_T: set2(1, 0, 0, std::polar(1.0, M_PI / 4)); h.cls = GC_DIAG1; break;
+        case ARSO_GATE_TDG: set2(1, 0, 0, std::polar(1.0, -M_PI / 4)); h.cls = GC_DIAG1; break;
+        case ARSO_GATE_RX:
+            set2(std::cos(th / 2), -I * std::sin(th / 2), -I * std::sin(th / 2), std::cos(th / 2));
+            h.cls = GC_DENSE1;
+            break;
+        case ARSO_GATE_RY:
+            set2(std::cos(th / 2), -std::sin(th / 2), std::sin(th / 2), std::cos(th / 2));
+            h.cls = GC_DENSE1;
+            break;
+        case ARSO_GATE_RZ: set2(std::polar(1.0, -th / 2), 0, 0, std::polar(1.0, th / 2)); h.cls = GC_DIAG1; break;
+        case ARSO_GATE_P: set2(1, 0, 0, std::polar(1.0, th)); h.cls = GC_DIAG1; break;
+        case ARSO_GATE_U:
+            ARSO_REQUIRE(g.matrix != nullptr, "U gate needs a 2x2 matrix");
+            for (int i = 0; i < 4; ++i) h.m[i] = cd(g.matrix[2 * i], g.matrix[2 * i + 1]);
+            h.cls = GC_DENSE1;
+            break;
+        case ARSO_GATE_CX:
+            for (int i = 0; i < 4; ++i) h.m[5 * i] = 1;
+            h.m[5] = 0; h.m[15] = 0; h.m[1 * 4 + 3] = 1; h.m[3 * 4 + 1] = 1;
+            h.cls = GC_CX;
+            break;
+        case ARSO_GATE_CZ:
+            h.m[0] = 1; h.m[5] = 1; h.m[10] = 1; h.m[15] = -1; h.cls = GC_DIAG2; break;
+        case ARSO_GATE_CP:
+            h.m[0] = 1; h.m[5] = 1; h.m[10] = 1; h.m[15] = std::polar(1.0, th); h.cls = GC_DIAG2; break;
+        case ARSO_GATE_SWAP:
+            h.m[0] = 1; h.m[15] = 1; h.m[1 * 4 + 2] = 1; h.m[2 * 4 + 1] = 1; h.cls = GC_SWAP; break;
+        case ARSO_GATE_U2:
+            ARSO_REQUIRE(g.matrix != nullptr, "U2 gate needs a 4x4 matrix");
+            for (int i = 0; i < 16; ++i) h.m[i] = cd(g.matrix[2 * i], g.matrix[2 * i + 1]);
+            h.cls = GC_DENSE2;
+            break;
+        default: throw Error(ARSO_EINVAL, "unknown gate kind " + std::to_string(g.kind));
+    }
+    for (int i = 0; i < (h.arity == 1 ? 4 : 16); ++i)
+        ARSO_REQUIRE(std::isfinite(h.m[i].real()) && std::isfinite(h.m[i].imag()), "non-finite gate matrix entry");
+}
+
+static void schedule_streaming(arso_circuit *c) {
+    const uint32_t n = c->n, t = c->tile_qubits, lowq = c->low_qubits;
+    const size_t G = c->gates.size();
+    std::vector<char> done(G, 0);
+    size_t remaining = G, first = 0;
+    c->passes.clear();
+    c->perm.clear();
+    do {
+        std::vector<char> in_s(n, 0), blocked(n, 0);
+        uint32_t cnt = 0;
+        for (uint32_t q = 0; q < lowq; ++q) in_s[q] = 1, ++cnt;
+        Pass p;
+        p.gb = (uint32_t)c->perm.size();
+        uint32_t n_blocked = 0;
+        for (size_t g = first; g < G && n_blocked < n; ++g) {
+            if (done[g]) continue;
+            const HostGate &h = c->gates[g];
+            uint32_t qs[2] = {h.q0, h.q1};
+            bool blk = false;
+            uint32_t fresh = 0;
+            for (int j = 0; j < h.arity; ++j) {
+                blk |= blocked[qs[j]] != 0;
+                fresh += in_s[qs[j]] ? 0 : 1;
+            }
+            if (!blk && cnt + fresh <= t) {
+                for (int j = 0; j < h.arity; ++j)
+                    if (!in_s[qs[j]]) in_s[qs[j]] = 1, ++cnt;
+                done[g] = 1;
+                --remaining;
+                c->perm.push_back((uint32_t)g);
+            } else {
+                for (int j = 0; j < h.arity; ++j)
+                    if (!blocked[qs[j]]) blocked[qs[j]] = 1, ++n_blocked;
+            }
+        }
+        while (first < G && done[first]) ++first;
+        // pad the tile to exactly t qubits (lowest unused qubits first)
+        for (uint32_t q = 0; q < n && cnt < t; ++q)
+            if (!in_s[q]) in_s[q] = 1, ++cnt;
+        for (uint32_t q = 0; q < n; ++q)
+            if (in_s[q]) p.tile_qubits.push_back(q);
+        p.ge = (uint32_t)c->perm.size();
+        c->passes.push_back(std::move(p));
+    } while (remaining > 0);
+}
+
+void build_circuit(arso_circuit *c, uint32_t n, const arso_gate *gates, size_t n_gates,
+                   const arso_compile_opts *opts) {
+    ARSO_REQUIRE(n >= 1 && n <= 30, "n_qubits must be in [1, 30]");
+    ARSO_REQUIRE(n_gates == 0 || gates != nullptr, "gates is NULL");
+    ARSO_REQUIRE(n_gates < (1u << 28), "too many gates");
+    c->n = n;
+    c->precision = opts ? (int)opts->precision : ARSO_C64;
+    ARSO_REQUIRE(c->precision == ARSO_C64 || c->precision == ARSO_C128, "bad precision");
+    c->gates.resize(n_gates);
+    c->k = c->m = 0;
+    for (size_t i = 0; i < n_gates; ++i) {
+        const arso_gate &g = gates[i];
+        HostGate &h = c->gates[i];
+        h.kind = g.kind;
+        h.arity = g.kind >= ARSO_GATE_CX ? 2 : 1;
+        h.q0 = g.q[0];
+        h.q1 = h.arity == 2 ? g.q[1] : g.q[0];
+        ARSO_REQUIRE(h.q0 < n && h.q1 < n, "gate " + std::to_string(i) + ": qubit out of range");
+        ARSO_REQUIRE(h.arity == 1 || h.q0 != h.q1, "gate " + std::to_string(i) + ": repeated qubit");
+        matrix_for(g, h);
+        if (h.arity == 1) ++c->k; else ++c->m;
+    }
+    c->L = c->k + 2 * c->m;
+    ARSO_REQUIRE(c->L < (1ull << 29), "too many error locations");
+    c->loc_gate.clear();
+    c->loc_gate.reserve(c->L);
+    for (size_t i = 0; i < n_gates; ++i)
+        for (int j = 0; j < c->gates[i].arity; ++j) c->loc_gate.push_back((uint32_t)i);
+
+    const int rmax = c->precision == ARSO_C128 ? RESIDENT_MAX_N_C128 : RESIDENT_MAX_N_C64;
+    c->engine = (int)n <= rmax ? 0 : 1;
+    uint32_t tq = opts && opts->tile_qubits ? opts->tile_qubits : (c->precision == ARSO_C128 ? 12u : 13u);
+    uint32_t lq = opts && opts->low_qubits ? opts->low_qubits : 4u;
+    c->max_batch = opts ? opts->max_batch : 0;
+    c->cache_budget = opts && opts->cache_bytes ? opts->cache_bytes : (uint64_t)16 << 30;
+    if (c->engine == 0) {
+        c->tile_qubits = n;
+        c->low_qubits = n;
+        c->perm.resize(n_gates);
+        for (size_t i = 0; i < n_gates; ++i) c->perm[i] = (uint32_t)i;
+        Pass p;
+        p.gb = 0;
+        p.ge = (uint32_t)n_gates;
+        for (uint32_t q = 0; q < n; ++q) p.tile_qubits.push_back(q);
+        c->passes.assign(1, p);
+    } else {
+        const uint32_t tmax = c->precision == ARSO_C128 ? 13u : (uint32_t)MAX_TILE_QUBITS;
+        ARSO_REQUIRE(tq >= 6 && tq <= tmax, "tile_qubits out of range");
+        tq = std::min(tq, n);
+        lq = std::min(std::max(lq, 1u), tq);
+        c->tile_qubits = tq;
+        c->low_qubits = lq;
+        schedule_streaming(c);
+    }
+    c->pos_of.assign(n_gates, 0);
+    for (size_t pos = 0; pos < c->perm.size(); ++pos) c->pos_of[c->perm[pos]] = (uint32_t)pos;
+    c->pass_of_pos.assign(n_gates, 0);
+    for (size_t p = 0; p < c->passes.size(); ++p)
+        for (uint32_t pos = c->passes[p].gb; pos < c->passes[p].ge; ++pos) c->pass_of_pos[pos] = (uint32_t)p;
+}
+
+}  // namespace arso

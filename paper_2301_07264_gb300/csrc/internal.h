@@ -1,0 +1,157 @@
+// Internal types shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <complex>
+#include <cstdint>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/arso.h"
+
+namespace arso {
+
+// ---------------------------------------------------------------- errors ---
+struct Error : std::runtime_error {
+    arso_status status;
+    Error(arso_status s, const std::string &m) : std::runtime_error(m), status(s) {}
+};
+void set_last_error(const std::string &m);
+
+#define ARSO_CUDA(call)                                                                       \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            throw ::arso::Error(e_ == cudaErrorMemoryAllocation ? ARSO_ENOMEM : ARSO_ECUDA,   \
+                                std::string(#call) + ": " + cudaGetErrorString(e_));          \
+    } while (0)
+#define ARSO_REQUIRE(cond, msg)                                              \
+    do {                                                                     \
+        if (!(cond)) throw ::arso::Error(ARSO_EINVAL, msg);                  \
+    } while (0)
+
+// ------------------------------------------------------- device gate code --
+// Gate classes: how a kernel applies the gate.
+enum GateClass : uint8_t {
+    GC_NOP = 0,     // identity
+    GC_DENSE1 = 1,  // 2x2 dense
+    GC_DIAG1 = 2,   // diag(d0, d1)
+    GC_X = 3,       // bit flip
+    GC_DENSE2 = 4,  // 4x4 dense
+    GC_DIAG2 = 5,   // diag(d0..d3)
+    GC_CX = 6,      // controlled bit flip (q0 control, q1 target)
+    GC_SWAP = 7,
+};
+
+// One gate as the kernels see it. q0/q1 are tile-local bit positions for
+// the pass that contains the gate (global positions for the resident engine).
+struct DGate {
+    uint8_t cls;
+    uint8_t q0, q1;
+    uint8_t arity;
+    uint32_t mat;   // offset (in complex entries) into the matrix pool
+};
+
+// An event in engine order: (gate position << 3) | (slot << 2) | pauli code.
+__host__ __device__ inline uint32_t ev_pos(uint32_t e) { return e >> 3; }
+__host__ __device__ inline uint32_t ev_slot(uint32_t e) { return (e >> 2) & 1u; }
+__host__ __device__ inline uint32_t ev_code(uint32_t e) { return e & 3u; }
+
+constexpr uint32_t NO_EVENT = 0xFFFFFFFFu;
+
+// Largest resident state (whole state in one CTA's shared memory).
+constexpr int RESIDENT_MAX_N_C64 = 13;   // 64 KiB
+constexpr int RESIDENT_MAX_N_C128 = 12;  // 64 KiB
+constexpr int MAX_TILE_QUBITS = 14;      // 128 KiB complex64 tile
+
+// ------------------------------------------------------------- host side --
+struct HostGate {
+    uint32_t kind;
+    uint32_t q0, q1;
+    int arity;
+    uint8_t cls;
+    std::complex<double> m[16];  // 2x2 (first 4) or 4x4, row-major
+};
+
+struct Pass {
+    uint32_t gb, ge;                   // gate range in engine order
+    std::vector<uint32_t> tile_qubits; // sorted global qubits, tile-local bit i -> tile_qubits[i]
+};
+
+struct Criterion {
+    uint32_t kind, aggregate;
+    uint64_t target;
+    double threshold;
+    std::vector<uint64_t> set;
+};
+
+struct DeviceBuffer {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    DeviceBuffer() = default;
+    DeviceBuffer(const DeviceBuffer &) = delete;
+    DeviceBuffer &operator=(const DeviceBuffer &) = delete;
+    ~DeviceBuffer() { release(); }
+    void release() {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        bytes = 0;
+    }
+    void ensure(size_t b) {
+        if (b <= bytes) return;
+        release();
+        ARSO_CUDA(cudaMalloc(&ptr, b));
+        bytes = b;
+    }
+    template <typename T> T *as() const { return static_cast<T *>(ptr); }
+};
+
+}  // namespace arso
+
+struct arso_circuit {
+    uint32_t n = 0;
+    int precision = ARSO_C64;
+    int engine = 0;  // 0 resident, 1 streaming
+    uint32_t tile_qubits = 0, low_qubits = 0, max_batch = 0;
+    uint64_t cache_budget = 0;
+    std::vector<arso::HostGate> gates;      // circuit order
+    uint64_t k = 0, m = 0, L = 0;
+    std::vector<uint32_t> perm;             // engine position -> circuit gate index
+    std::vector<uint32_t> pos_of;           // circuit gate index -> engine position
+    std::vector<uint32_t> loc_gate;         // location -> circuit gate index
+    std::vector<arso::Pass> passes;         // streaming schedule (resident: one pass)
+    std::vector<uint32_t> pass_of_pos;      // engine position -> pass index
+    // device tables
+    arso::DeviceBuffer d_gates;             // DGate[G] in engine order
+    arso::DeviceBuffer d_mats;              // complex<float> or complex<double> pool
+    arso::DeviceBuffer d_loc_key;           // location -> (pos << 1) | slot
+    arso::DeviceBuffer d_pass_of_pos;       // uint32 per engine position
+    // prefix cache
+    bool cache_ready = false;
+    uint64_t ckpt_every = 1;                // resident: gates between checkpoints
+    uint32_t n_ckpt = 0;                    // checkpoints (resident) or pass boundaries (streaming)
+    std::vector<uint32_t> ckpt_pass;        // streaming: cached boundary index per pass
+    arso::DeviceBuffer d_cache;             // n_ckpt states; the last one is psi_R
+    arso::DeviceBuffer d_offs;              // streaming: per pass, tile-high offsets
+    std::vector<uint64_t> offs_base;        // per pass offset of its table in d_offs
+    size_t state_bytes() const { return (size_t(1) << n) * (precision == ARSO_C128 ? 16 : 8); }
+};
+
+struct arso_error_list {
+    const arso_circuit *circ = nullptr;
+    uint64_t n_traj = 0, n_events = 0;
+    arso::DeviceBuffer d_offsets;  // uint64[n_traj + 1]
+    arso::DeviceBuffer d_loc;      // uint32 (loc << 2) | code, location order
+    arso::DeviceBuffer d_key;      // uint32 engine-order keys
+    arso::DeviceBuffer d_first;    // uint32 per trajectory: first engine position with an event, or NO_EVENT
+};
+
+namespace arso {
+// circuit.cpp
+void matrix_for(const arso_gate &g, HostGate &h);  // h.arity must be set
+void build_circuit(arso_circuit *c, uint32_t n, const arso_gate *gates, size_t n_gates,
+                   const arso_compile_opts *opts);
+}  // namespace arso

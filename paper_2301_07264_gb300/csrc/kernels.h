@@ -1,0 +1,107 @@
+// Kernel argument blocks and launcher declarations (host <-> device).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace arso {
+
+// Per-tile partial of a criterion. Fidelity: (a, b) = sum conj(R) psi.
+// Outcome / binning: a = sum |psi|^2 over the selected outcomes. Argmax:
+// (maxp, idx), the lowest index winning ties.
+struct Partial {
+    double a, b;
+    double maxp;
+    unsigned long long idx;
+};
+
+// Device view of a criterion.
+struct DCrit {
+    uint32_t kind;
+    double threshold;
+    unsigned long long target;
+    const uint32_t *bitmap;  // binning set, 2^n bits (device)
+};
+
+struct ResidentArgs {
+    int n;
+    uint32_t G;
+    const DGate *gates;
+    const void *mats;
+    const void *cache;           // n_ckpt states; entry c = after gates [0, c*every); last = psi_R
+    uint64_t ckpt_every;
+    uint32_t n_ckpt;
+    // trajectories [first_traj, first_traj + count) of the error list
+    uint64_t first_traj, count;
+    const uint64_t *offsets;
+    const uint32_t *keys;
+    const uint32_t *first;       // per trajectory: engine position of the first event or NO_EVENT
+    DCrit crit;
+    const double *ref_score;     // device scalar: score of psi_R
+    double *score;               // device, indexed by trajectory
+    uint8_t *pass_flags;         // device or null
+    void *states_out;            // non-null: store final states (count * 2^n) instead of scoring
+};
+
+struct PassArgs {
+    int n, t, c;                 // qubits, tile qubits, contiguous low qubits
+    uint64_t rest_mask;          // global bits outside the tile
+    const uint32_t *offs;        // 2^(t-c) offsets of the tile's high part
+    uint32_t gb, ge;             // gate range (engine order)
+    int pass;
+    const DGate *gates;
+    const void *mats;
+    // ideal (error-free) mode: one slot from ideal_src to ideal_dst
+    int ideal;
+    const void *ideal_src;
+    void *ideal_dst;
+    // trajectory mode
+    const void *cache;           // cached boundary states
+    const uint32_t *cache_slot;  // pass index -> cache entry (valid for cached boundaries)
+    uint32_t ref_slot;           // cache entry of psi_R
+    void *work;                  // slots * 2^n working states
+    const int *start_pass;       // per slot
+    const uint64_t *slot_traj;   // per slot: trajectory index in the error list
+    const uint64_t *offsets;
+    const uint32_t *keys;
+    DCrit crit;
+    Partial *partials;           // last pass: slots * tiles
+    int store_last;              // last pass stores the state instead of reducing
+};
+
+void launch_resident(const ResidentArgs &a, bool ideal, int precision, cudaStream_t st);
+void launch_pass(const PassArgs &a, bool last, int precision, uint32_t slots, cudaStream_t st);
+void launch_finish_partials(const Partial *partials, uint32_t tiles, uint32_t slots, const uint64_t *slot_traj,
+                            const DCrit &crit, double *score, uint8_t *pass_flags, cudaStream_t st);
+void launch_fill_error_free(const uint32_t *first, uint64_t n_traj, const double *ref_score, double threshold,
+                            double *score, uint8_t *pass_flags, cudaStream_t st);
+struct M16 {
+    float2 m[16];
+};
+void launch_gate_pairs(float2 *psi, int n, const DGate &g, const M16 &m, cudaStream_t st);
+void launch_pauli(float2 *psi, int n, uint32_t q, uint32_t code, cudaStream_t st);
+uint32_t launch_score_partials(const void *psi, const void *ref, int n, int precision, const DCrit &crit,
+                               Partial *partials, uint32_t max_blocks, cudaStream_t st);
+void launch_init_zero_state(void *psi, int n, int precision, cudaStream_t st);
+
+// sampling (sample.cu)
+struct SampleArgs {
+    uint64_t seed, traj_begin, n_traj;
+    uint32_t L;
+    uint32_t thr, cut_x, cut_xz;  // cut_* saturate at 2^32 - 1 + carry handled via flags
+    uint32_t cut_x_all, cut_xz_all; // 1 if the cut equals 2^32 (every draw below it)
+};
+void launch_sample_count(const SampleArgs &a, uint32_t *counts, cudaStream_t st);
+void launch_exclusive_scan(const uint32_t *counts, uint64_t n, uint64_t *offsets, cudaStream_t st);
+void launch_sample_fill(const SampleArgs &a, const uint64_t *offsets, const uint32_t *loc_key, uint32_t *ev_loc,
+                        uint32_t *ev_key, cudaStream_t st);
+void launch_keys_from_loc(const uint32_t *ev_loc, uint64_t n_events, const uint32_t *loc_key, uint32_t *ev_key,
+                          cudaStream_t st);
+void launch_sort_keys(const uint64_t *offsets, uint64_t n_traj, uint32_t *ev_key, cudaStream_t st);
+void launch_first_event(const uint64_t *offsets, uint64_t n_traj, const uint32_t *ev_key, uint32_t *first,
+                        cudaStream_t st);
+void launch_sum_scores(const double *score, const uint8_t *pass_flags, uint64_t n, double *sums3, cudaStream_t st);
+
+}  // namespace arso

@@ -1,0 +1,466 @@
+// Trajectory simulation kernels.
+//
+// Resident engine: one CTA per trajectory holds the whole 2^n state in shared
+// memory, restarts from the cached error-free state at the checkpoint before
+// the trajectory's first error, applies the remaining gates with the sampled
+// Pauli error gates right after the gates they follow (Sec. IV-B), and
+// scores the final state (Sec. II criteria) with an FP64 block reduction.
+//
+// Streaming engine: one launch per fused pass; CTA (tile, slot) loads a tile
+// of 2^t amplitudes from HBM with 16-byte vector loads, applies the pass's
+// gates and error gates in shared memory and writes the tile back (or, in the
+// last pass, reduces it into a criterion partial instead of writing it).
+#include <algorithm>
+
+#include "sim_common.cuh"
+
+namespace arso {
+
+// ------------------------------------------------------------- resident ---
+
+template <typename T>
+__device__ void resident_run_gates(T *s, int n, const DGate *__restrict__ gates, const T *__restrict__ mats,
+                                   uint32_t g0, uint32_t G, const uint32_t *ev, const uint32_t *ev_end) {
+    uint32_t next = ev < ev_end ? *ev : NO_EVENT;
+    for (uint32_t g = g0; g < G; ++g) {
+        const DGate gate = gates[g];
+        if (gate.cls != GC_NOP) {
+            tile_gate(s, n, gate, mats + gate.mat);
+            __syncthreads();
+        }
+        while (next != NO_EVENT && ev_pos(next) == g) {
+            tile_pauli(s, n, ev_slot(next) ? gate.q1 : gate.q0, ev_code(next));
+            __syncthreads();
+            ++ev;
+            next = ev < ev_end ? *ev : NO_EVENT;
+        }
+    }
+}
+
+template <typename T>
+__global__ void resident_kernel(ResidentArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *s = reinterpret_cast<T *>(smem_raw);
+    __shared__ Partial red[32];
+    const int n = a.n;
+    const uint32_t N = 1u << n;
+    const T *cache = static_cast<const T *>(a.cache);
+    const T *ref = cache + (size_t)(a.n_ckpt - 1) * N;
+    const DCrit crit = a.crit;
+    for (uint64_t b = blockIdx.x; b < a.count; b += gridDim.x) {
+        const uint64_t tr = a.first_traj + b;
+        const uint32_t first = a.first[tr];
+        if (first == NO_EVENT && !a.states_out) {
+            if (threadIdx.x == 0) {
+                a.score[tr] = *a.ref_score;
+                if (a.pass_flags) a.pass_flags[tr] = *a.ref_score >= crit.threshold;
+            }
+            continue;
+        }
+        const uint32_t ck = first == NO_EVENT ? a.n_ckpt - 1 : (uint32_t)(first / a.ckpt_every);
+        const uint32_t g0 = first == NO_EVENT ? a.G : (uint32_t)(ck * a.ckpt_every);
+        const T *src = cache + (size_t)ck * N;
+        for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) s[i] = src[i];
+        __syncthreads();
+        const uint32_t *ev = a.keys + a.offsets[tr];
+        const uint32_t *ev_end = a.keys + a.offsets[tr + 1];
+        resident_run_gates(s, n, a.gates, static_cast<const T *>(a.mats), g0, a.G, ev, ev_end);
+        if (a.states_out) {
+            T *dst = static_cast<T *>(a.states_out) + (size_t)b * N;
+            for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) dst[i] = s[i];
+        } else {
+            Partial acc = empty_partial();
+            for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) accumulate(acc, crit, s[i], ref, i);
+            acc = block_reduce_partial(acc, red);
+            if (threadIdx.x == 0) {
+                const double sc = finish_score(crit, acc);
+                a.score[tr] = sc;
+                if (a.pass_flags) a.pass_flags[tr] = sc >= crit.threshold;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Error-free run that fills the checkpoint cache: entry c holds the state
+// after gates [0, c * every); the last entry holds psi_R.
+template <typename T>
+__global__ void resident_ideal_kernel(ResidentArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *s = reinterpret_cast<T *>(smem_raw);
+    const int n = a.n;
+    const uint32_t N = 1u << n;
+    T *cache = static_cast<T *>(const_cast<void *>(a.cache));
+    const T *mats = static_cast<const T *>(a.mats);
+    for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) {
+        T z;
+        z.x = i == 0 ? 1 : 0;
+        z.y = 0;
+        s[i] = z;
+    }
+    __syncthreads();
+    for (uint32_t g = 0; g <= a.G; ++g) {
+        if (g % a.ckpt_every == 0 || g == a.G) {
+            const uint32_t c = g == a.G ? a.n_ckpt - 1 : (uint32_t)(g / a.ckpt_every);
+            T *dst = cache + (size_t)c * N;
+            for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) dst[i] = s[i];
+        }
+        if (g == a.G) break;
+        const DGate gate = a.gates[g];
+        tile_gate(s, n, gate, mats + gate.mat);
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ streaming ---
+
+__device__ __forceinline__ uint64_t tile_base(uint64_t tile, uint64_t rest_mask) {
+    // deposit the bits of `tile` into the set bits of rest_mask
+    uint64_t base = 0;
+    for (uint64_t m = rest_mask; m; m &= m - 1) {
+        const uint64_t low = m & (~m + 1);
+        if (tile & 1) base |= low;
+        tile >>= 1;
+    }
+    return base;
+}
+
+template <typename T>
+__device__ __forceinline__ uint64_t tile_index(uint32_t j, uint64_t base, const uint32_t *__restrict__ offs, int c) {
+    return base + offs[j >> c] + (j & ((1u << c) - 1));
+}
+
+template <typename T, bool LAST>
+__global__ void pass_kernel(PassArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *s = reinterpret_cast<T *>(smem_raw);
+    __shared__ Partial red[32];
+    const int t = a.t, c = a.c;
+    const uint32_t slot = blockIdx.y;
+    const uint64_t N = 1ull << a.n;
+    int start;
+    uint64_t tr = 0;
+    const T *src;
+    T *dst;
+    if (a.ideal) {
+        start = 0;
+        src = static_cast<const T *>(a.ideal_src);
+        dst = static_cast<T *>(a.ideal_dst);
+    } else {
+        start = a.start_pass[slot];
+        if (a.pass < start) return;
+        tr = a.slot_traj[slot];
+        T *mine = static_cast<T *>(a.work) + (size_t)slot * N;
+        src = a.pass == start ? static_cast<const T *>(a.cache) + (size_t)a.cache_slot[start] * N : mine;
+        dst = mine;
+    }
+    const uint64_t base = tile_base(blockIdx.x, a.rest_mask);
+    const uint32_t *offs = a.offs;
+    const uint32_t tile_n = 1u << t;
+    // load: two amplitudes (16 bytes for complex64) per step; bit 0 is a tile bit
+    for (uint32_t v = threadIdx.x; v < tile_n / 2; v += blockDim.x) {
+        const uint32_t j = 2 * v;
+        const uint64_t gi = tile_index<T>(j, base, offs, c);
+        if (sizeof(T) == 8) {
+            const float4 w = __ldg(reinterpret_cast<const float4 *>(src + gi));
+            reinterpret_cast<float4 *>(s)[v] = w;
+        } else {
+            s[j] = src[gi];
+            s[j + 1] = src[gi + 1];
+        }
+    }
+    __syncthreads();
+    const uint32_t *ev = nullptr, *ev_end = nullptr;
+    if (!a.ideal) {
+        // events of this trajectory with engine position in [gb, ge)
+        const uint32_t *lo = a.keys + a.offsets[tr];
+        const uint32_t *hi = a.keys + a.offsets[tr + 1];
+        const uint32_t key_lo = a.gb << 3;
+        while (lo < hi) {
+            const uint32_t *mid = lo + (hi - lo) / 2;
+            if (*mid < key_lo) lo = mid + 1; else hi = mid;
+        }
+        ev = lo;
+        ev_end = a.keys + a.offsets[tr + 1];
+    }
+    {
+        uint32_t next = ev && ev < ev_end ? *ev : NO_EVENT;
+        const T *mats = static_cast<const T *>(a.mats);
+        for (uint32_t g = a.gb; g < a.ge; ++g) {
+            const DGate gate = a.gates[g];
+            if (gate.cls != GC_NOP) {
+                tile_gate(s, t, gate, mats + gate.mat);
+                __syncthreads();
+            }
+            while (next != NO_EVENT && ev_pos(next) == g) {
+                tile_pauli(s, t, ev_slot(next) ? gate.q1 : gate.q0, ev_code(next));
+                __syncthreads();
+                ++ev;
+                next = ev < ev_end ? *ev : NO_EVENT;
+            }
+        }
+    }
+    if (LAST && !a.ideal && !a.store_last) {
+        const T *ref = static_cast<const T *>(a.cache) + (size_t)a.ref_slot * N;
+        Partial acc = empty_partial();
+        for (uint32_t j = threadIdx.x; j < tile_n; j += blockDim.x) {
+            const uint64_t gi = tile_index<T>(j, base, offs, c);
+            accumulate(acc, a.crit, s[j], ref, gi);
+        }
+        acc = block_reduce_partial(acc, red);
+        if (threadIdx.x == 0) a.partials[(size_t)slot * gridDim.x + blockIdx.x] = acc;
+    } else {
+        for (uint32_t v = threadIdx.x; v < tile_n / 2; v += blockDim.x) {
+            const uint32_t j = 2 * v;
+            const uint64_t gi = tile_index<T>(j, base, offs, c);
+            if (sizeof(T) == 8) {
+                reinterpret_cast<float4 *>(dst + gi)[0] = reinterpret_cast<const float4 *>(s)[v];
+            } else {
+                dst[gi] = s[j];
+                dst[gi + 1] = s[j + 1];
+            }
+        }
+    }
+}
+
+// Combine per-tile partials of each slot (fixed order) into its score.
+__global__ void finish_partials_kernel(const Partial *__restrict__ partials, uint32_t tiles, uint32_t slots,
+                                       const uint64_t *__restrict__ slot_traj, DCrit crit, double *score,
+                                       uint8_t *pass_flags) {
+    __shared__ Partial red[32];
+    for (uint32_t slot = blockIdx.x; slot < slots; slot += gridDim.x) {
+        Partial acc = empty_partial();
+        for (uint32_t i = threadIdx.x; i < tiles; i += blockDim.x) {
+            const Partial p = partials[(size_t)slot * tiles + i];
+            acc.a += p.a;
+            acc.b += p.b;
+            argmax_merge(acc.maxp, acc.idx, p.maxp, p.idx);
+        }
+        acc = block_reduce_partial(acc, red);
+        if (threadIdx.x == 0) {
+            const double sc = finish_score(crit, acc);
+            const uint64_t tr = slot_traj ? slot_traj[slot] : slot;
+            score[tr] = sc;
+            if (pass_flags) pass_flags[tr] = sc >= crit.threshold;
+        }
+        __syncthreads();
+    }
+}
+
+// Trajectories without errors take the error-free score.
+__global__ void fill_error_free_kernel(const uint32_t *__restrict__ first, uint64_t n_traj,
+                                       const double *__restrict__ ref_score, double threshold, double *score,
+                                       uint8_t *pass_flags) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n_traj;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        if (first[i] == NO_EVENT) {
+            score[i] = *ref_score;
+            if (pass_flags) pass_flags[i] = *ref_score >= threshold;
+        }
+    }
+}
+
+// ------------------------------------------------- single-step HBM kernels --
+
+// One gate on a device state: coalesced strided pair (or quad) updates; each
+// thread owns one pair (i, i | 2^q) whose low index bits follow the thread id.
+__global__ void gate_pairs_kernel(float2 *psi, int n, DGate g, M16 mm) {
+    const float2 *m16 = mm.m;
+    const float2 m0 = m16[0], m1 = m16[1], m2 = m16[2], m3 = m16[3];
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    if (g.arity == 1) {
+        const uint64_t bit = 1ull << g.q0, lo = bit - 1;
+        for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < (1ull << (n - 1)); p += stride) {
+            const uint64_t i0 = ((p & ~lo) << 1) | (p & lo), i1 = i0 | bit;
+            const float2 a0 = psi[i0], a1 = psi[i1];
+            if (g.cls == GC_X) {
+                psi[i0] = a1;
+                psi[i1] = a0;
+            } else if (g.cls == GC_DIAG1) {
+                psi[i0] = cmul(m0, a0);
+                psi[i1] = cmul(m1, a1);
+            } else if (g.cls == GC_DENSE1) {
+                psi[i0] = cmac2(m0, a0, m1, a1);
+                psi[i1] = cmac2(m2, a0, m3, a1);
+            }
+        }
+    } else {
+        const uint32_t lo = g.q0 < g.q1 ? g.q0 : g.q1, hi = g.q0 < g.q1 ? g.q1 : g.q0;
+        const uint64_t b0 = 1ull << g.q0, b1 = 1ull << g.q1;
+        for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < (1ull << (n - 2)); p += stride) {
+            uint64_t i = p;
+            i = ((i & ~((1ull << lo) - 1)) << 1) | (i & ((1ull << lo) - 1));
+            i = ((i & ~((1ull << hi) - 1)) << 1) | (i & ((1ull << hi) - 1));
+            const uint64_t idx[4] = {i, i | b0, i | b1, i | b0 | b1};
+            float2 a[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) a[k] = psi[idx[k]];
+            if (g.cls == GC_CX) {
+                psi[idx[1]] = a[3];
+                psi[idx[3]] = a[1];
+            } else if (g.cls == GC_SWAP) {
+                psi[idx[1]] = a[2];
+                psi[idx[2]] = a[1];
+            } else if (g.cls == GC_DIAG2) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) psi[idx[k]] = cmul(m16[5 * k], a[k]);
+            } else if (g.cls == GC_DENSE2) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    float2 acc = cmac2(m16[4 * k], a[0], m16[4 * k + 1], a[1]);
+                    const float2 acc2 = cmac2(m16[4 * k + 2], a[2], m16[4 * k + 3], a[3]);
+                    acc.x += acc2.x;
+                    acc.y += acc2.y;
+                    psi[idx[k]] = acc;
+                }
+            }
+        }
+    }
+}
+
+// Pauli error gate on a device state (Eq. (2)): X/Y permute the pair
+// (i, i | 2^q), Z/Y apply the phase.
+__global__ void pauli_kernel(float2 *psi, int n, uint32_t q, uint32_t code) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t bit = 1ull << q, lo = bit - 1;
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < (1ull << (n - 1)); p += stride) {
+        const uint64_t i0 = ((p & ~lo) << 1) | (p & lo), i1 = i0 | bit;
+        const float2 a0 = psi[i0], a1 = psi[i1];
+        if (code == 1) {
+            psi[i0] = a1;
+            psi[i1] = a0;
+        } else if (code == 2) {
+            psi[i1] = cneg(a1);
+        } else if (code == 3) {
+            psi[i0] = make_float2(a1.y, -a1.x);
+            psi[i1] = make_float2(-a0.y, a0.x);
+        }
+    }
+}
+
+// Criterion partials of one state, one per block (grid-stride over amplitudes).
+template <typename T>
+__global__ void score_partials_kernel(const T *__restrict__ psi, const T *__restrict__ ref, int n, DCrit crit,
+                                      Partial *partials) {
+    __shared__ Partial red[32];
+    Partial acc = empty_partial();
+    const uint64_t N = 1ull << n;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x)
+        accumulate(acc, crit, psi[i], ref, i);
+    acc = block_reduce_partial(acc, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+__global__ void init_zero_state_kernel(void *psi, uint64_t N, int is_double) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
+        if (is_double)
+            static_cast<double2 *>(psi)[i] = make_double2(i == 0 ? 1.0 : 0.0, 0.0);
+        else
+            static_cast<float2 *>(psi)[i] = make_float2(i == 0 ? 1.f : 0.f, 0.f);
+    }
+}
+
+// ------------------------------------------------------------- launchers ---
+
+template <typename T> static void set_smem(const void *fn, size_t bytes) {
+    if (bytes > 48 * 1024) ARSO_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
+void launch_resident(const ResidentArgs &a, bool ideal, int precision, cudaStream_t st) {
+    const uint32_t N = 1u << a.n;
+    const int nt = (int)std::min<uint32_t>(256, std::max<uint32_t>(32, N / 2));
+    if (precision == ARSO_C64) {
+        const size_t smem = N * sizeof(float2);
+        const void *fn = ideal ? (const void *)resident_ideal_kernel<float2> : (const void *)resident_kernel<float2>;
+        set_smem<float2>(fn, smem);
+        const unsigned grid = ideal ? 1u : (unsigned)std::min<uint64_t>(a.count, 152ull * 32);
+        if (ideal) resident_ideal_kernel<float2><<<grid, nt, smem, st>>>(a);
+        else resident_kernel<float2><<<grid, nt, smem, st>>>(a);
+    } else {
+        const size_t smem = N * sizeof(double2);
+        const void *fn = ideal ? (const void *)resident_ideal_kernel<double2> : (const void *)resident_kernel<double2>;
+        set_smem<double2>(fn, smem);
+        const unsigned grid = ideal ? 1u : (unsigned)std::min<uint64_t>(a.count, 152ull * 32);
+        if (ideal) resident_ideal_kernel<double2><<<grid, nt, smem, st>>>(a);
+        else resident_kernel<double2><<<grid, nt, smem, st>>>(a);
+    }
+    ARSO_CUDA(cudaGetLastError());
+}
+
+void launch_pass(const PassArgs &a, bool last, int precision, uint32_t slots, cudaStream_t st) {
+    const uint32_t tiles = 1u << (a.n - a.t);
+    const int nt = 256;
+    dim3 grid(tiles, slots);
+    if (precision == ARSO_C64) {
+        const size_t smem = (size_t(1) << a.t) * sizeof(float2);
+        if (last) {
+            set_smem<float2>((const void *)pass_kernel<float2, true>, smem);
+            pass_kernel<float2, true><<<grid, nt, smem, st>>>(a);
+        } else {
+            set_smem<float2>((const void *)pass_kernel<float2, false>, smem);
+            pass_kernel<float2, false><<<grid, nt, smem, st>>>(a);
+        }
+    } else {
+        const size_t smem = (size_t(1) << a.t) * sizeof(double2);
+        if (last) {
+            set_smem<double2>((const void *)pass_kernel<double2, true>, smem);
+            pass_kernel<double2, true><<<grid, nt, smem, st>>>(a);
+        } else {
+            set_smem<double2>((const void *)pass_kernel<double2, false>, smem);
+            pass_kernel<double2, false><<<grid, nt, smem, st>>>(a);
+        }
+    }
+    ARSO_CUDA(cudaGetLastError());
+}
+
+void launch_finish_partials(const Partial *partials, uint32_t tiles, uint32_t slots, const uint64_t *slot_traj,
+                            const DCrit &crit, double *score, uint8_t *pass_flags, cudaStream_t st) {
+    const unsigned grid = std::min<uint32_t>(slots, 152u * 8);
+    finish_partials_kernel<<<grid, 256, 0, st>>>(partials, tiles, slots, slot_traj, crit, score, pass_flags);
+    ARSO_CUDA(cudaGetLastError());
+}
+
+void launch_fill_error_free(const uint32_t *first, uint64_t n_traj, const double *ref_score, double threshold,
+                            double *score, uint8_t *pass_flags, cudaStream_t st) {
+    if (!n_traj) return;
+    const unsigned grid = (unsigned)std::min<uint64_t>((n_traj + 255) / 256, 152ull * 16);
+    fill_error_free_kernel<<<grid, 256, 0, st>>>(first, n_traj, ref_score, threshold, score, pass_flags);
+    ARSO_CUDA(cudaGetLastError());
+}
+
+void launch_gate_pairs(float2 *psi, int n, const DGate &g, const M16 &m, cudaStream_t st) {
+    const uint64_t work = 1ull << (n - g.arity);
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((work + 255) / 256, 152ull * 16));
+    gate_pairs_kernel<<<grid, 256, 0, st>>>(psi, n, g, m);
+    ARSO_CUDA(cudaGetLastError());
+}
+
+void launch_pauli(float2 *psi, int n, uint32_t q, uint32_t code, cudaStream_t st) {
+    const uint64_t work = 1ull << (n - 1);
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((work + 255) / 256, 152ull * 16));
+    pauli_kernel<<<grid, 256, 0, st>>>(psi, n, q, code);
+    ARSO_CUDA(cudaGetLastError());
+}
+
+uint32_t launch_score_partials(const void *psi, const void *ref, int n, int precision, const DCrit &crit,
+                               Partial *partials, uint32_t max_blocks, cudaStream_t st) {
+    const uint64_t N = 1ull << n;
+    const uint32_t blocks = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((N + 255) / 256, max_blocks));
+    if (precision == ARSO_C64)
+        score_partials_kernel<float2><<<blocks, 256, 0, st>>>(static_cast<const float2 *>(psi),
+                                                              static_cast<const float2 *>(ref), n, crit, partials);
+    else
+        score_partials_kernel<double2><<<blocks, 256, 0, st>>>(static_cast<const double2 *>(psi),
+                                                               static_cast<const double2 *>(ref), n, crit, partials);
+    ARSO_CUDA(cudaGetLastError());
+    return blocks;
+}
+
+void launch_init_zero_state(void *psi, int n, int precision, cudaStream_t st) {
+    const uint64_t N = 1ull << n;
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((N + 255) / 256, 152ull * 16));
+    init_zero_state_kernel<<<grid, 256, 0, st>>>(psi, N, precision == ARSO_C128);
+    ARSO_CUDA(cudaGetLastError());
+}
+
+}  // namespace arso

@@ -1,0 +1,389 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Bars: sampled error events bit-exact; complex64 amplitudes within 1e-5
+max-abs of the FP64 oracle (complex128 within 1e-12); per-trajectory scores
+within 1e-5; pass flags identical except for trajectories whose oracle score
+lies within 1e-5 of the threshold (or, for argmax, whose two largest
+probabilities lie within 1e-6).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import criteria, exhaustive as ox, montecarlo, sampling, search, statevector
+from workloads import circuits as C
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+AMP_TOL_C64 = 1e-5
+AMP_TOL_C128 = 1e-12
+SCORE_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def arso():
+    from paper_2301_07264_gb300 import arso as mod
+    assert torch.cuda.is_available()
+    return mod
+
+
+def oracle_csr(lists):
+    off = np.zeros(len(lists) + 1, dtype=np.uint64)
+    ev = []
+    for i, l in enumerate(lists):
+        off[i + 1] = off[i] + len(l)
+        ev += [(loc << 2) | code for loc, code in l]
+    return off, np.asarray(ev, dtype=np.uint32)
+
+
+def gpu_states(arso, circ, cc, errs, first, count, c128=False):
+    dt = torch.complex128 if c128 else torch.complex64
+    out = torch.empty((count, 1 << circ.n), dtype=dt, device="cuda")
+    arso.trajectory_states(cc, errs, first, count, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def flags_comparable(crit, oracle_score, psi=None):
+    if crit.kind == "argmax":
+        p = np.sort(np.abs(psi) ** 2)
+        return p[-1] - p[-2] > 1e-6
+    return abs(oracle_score - crit.threshold) > SCORE_TOL
+
+
+# ------------------------------------------------------------- sampling ---
+
+@pytest.mark.parametrize("case", [
+    ("qft4", 1e-3, 1e-3, 1e-3, 0, 0, 1000),
+    ("qft4", 0.2, 0.05, 0.01, 7, 2**32 - 3, 300),     # traj ids cross 2^32
+    ("rand", 0.3, 0.0, 0.0, 1, 5, 200),               # X only
+    ("rand", 0.0, 0.0, 0.4, 2, 0, 100),               # Y only
+    ("rand", 1 / 3, 1 / 3, 1 / 3, 3, 0, 20),          # p_tot = 1
+    ("rand", 0.0, 0.0, 0.0, 4, 0, 50),                # no errors
+    ("grover", 1e-3, 1e-3, 1e-3, 0, 0, 16),
+])
+def test_sampling_bit_exact(arso, case):
+    name, px, pz, py, seed, begin, T = case
+    circ = {"qft4": C.qft4_0101, "rand": lambda: C.random_circuit(5, 37, 11),
+            "grover": lambda: C.grover12(0)}[name]()
+    cc = arso.compile_circuit(circ.n, circ.gates)
+    errs = arso.sample_errors(cc, px, pz, py, seed, begin, T)
+    off, ev = arso.error_list_copy(errs)
+    o_off, o_ev = oracle_csr(sampling.sample(seed, begin, T, circ.L, px, pz, py))
+    assert np.array_equal(off, o_off)
+    assert np.array_equal(ev, o_ev)
+
+
+def test_sampling_empty_and_single(arso):
+    circ = C.Circuit(1, [C.Gate("H", (0,))])
+    cc = arso.compile_circuit(1, circ.gates)
+    errs = arso.sample_errors(cc, 0.1, 0.1, 0.1, 0, 0, 0)
+    assert errs.info() == (0, 0)
+    errs = arso.sample_errors(cc, 0.3, 0.3, 0.3, 9, 0, 500)
+    off, ev = arso.error_list_copy(errs)
+    o_off, o_ev = oracle_csr(sampling.sample(9, 0, 500, 1, 0.3, 0.3, 0.3))
+    assert np.array_equal(off, o_off) and np.array_equal(ev, o_ev)
+
+
+# ------------------------------------------------------------ amplitudes --
+
+def _random_error_lists(circ, T, rng, max_err=4):
+    lists = []
+    for t in range(T):
+        k = int(rng.integers(0, max_err + 1))
+        locs = sorted(rng.choice(circ.L, size=min(k, circ.L), replace=False).tolist()) if circ.L else []
+        lists.append([(int(l), int(rng.integers(1, 4))) for l in locs])
+    return lists
+
+
+@pytest.mark.parametrize("n,G,seed,c128", [
+    (1, 30, 1, False), (2, 40, 2, False), (4, 60, 3, True), (7, 120, 4, False),
+    (10, 150, 5, False), (12, 200, 6, True), (13, 160, 7, False),
+])
+def test_resident_amplitudes(arso, n, G, seed, c128):
+    circ = C.random_circuit(n, G, seed)
+    rng = np.random.default_rng(seed)
+    lists = _random_error_lists(circ, 6, rng)
+    lists[0] = []                                       # error-free
+    lists[1] = [(0, 3)] if circ.L else []               # first location
+    lists[2] = [(circ.L - 1, 1)] if circ.L else []      # last location
+    cc = arso.compile_circuit(n, circ.gates, precision=arso.C128 if c128 else arso.C64)
+    assert cc.info().engine == 0
+    errs = arso.error_list_from_host(cc, lists)
+    got = gpu_states(arso, circ, cc, errs, 0, len(lists), c128)
+    tol = AMP_TOL_C128 if c128 else AMP_TOL_C64
+    for t, ev in enumerate(lists):
+        assert np.max(np.abs(got[t] - statevector.simulate(circ, ev))) < tol, t
+
+
+@pytest.mark.parametrize("n,G,tile,low,seed", [
+    (14, 200, 8, 3, 1), (15, 300, 10, 4, 2), (16, 260, 13, 4, 3), (14, 120, 6, 1, 4), (17, 150, 14, 5, 5),
+])
+def test_streaming_amplitudes(arso, n, G, tile, low, seed):
+    circ = C.random_circuit(n, G, seed)
+    rng = np.random.default_rng(seed)
+    lists = _random_error_lists(circ, 5, rng, max_err=6)
+    lists[0] = []
+    # both slots of one two-qubit gate
+    g2 = next(i for i, g in enumerate(circ.gates) if g.arity == 2)
+    loc = sum(g.arity for g in circ.gates[:g2])
+    lists[1] = [(loc, 2), (loc + 1, 3)]
+    cc = arso.compile_circuit(n, circ.gates, tile_qubits=tile, low_qubits=low)
+    info = cc.info()
+    assert info.engine == 1 and info.n_passes > 1
+    errs = arso.error_list_from_host(cc, lists)
+    got = gpu_states(arso, circ, cc, errs, 0, len(lists))
+    for t, ev in enumerate(lists):
+        assert np.max(np.abs(got[t] - statevector.simulate(circ, ev))) < AMP_TOL_C64, t
+
+
+def test_streaming_prefix_cache_subset(arso):
+    # a cache budget that cannot hold every pass boundary forces restarts from
+    # an earlier cached boundary
+    circ = C.brickwork(14, 12, seed=3)
+    rng = np.random.default_rng(0)
+    lists = _random_error_lists(circ, 6, rng, max_err=3)
+    sb = (1 << 14) * 8
+    cc = arso.compile_circuit(14, circ.gates, tile_qubits=8, low_qubits=3, cache_bytes=6 * sb)
+    assert cc.info().n_passes > 6
+    errs = arso.error_list_from_host(cc, lists)
+    got = gpu_states(arso, circ, cc, errs, 0, len(lists))
+    for t, ev in enumerate(lists):
+        assert np.max(np.abs(got[t] - statevector.simulate(circ, ev))) < AMP_TOL_C64
+
+
+def test_reference_state(arso):
+    for circ in (C.qft_basis(9, 300), C.brickwork(15, 6, 2), C.ghz(13)):
+        cc = arso.compile_circuit(circ.n, circ.gates)
+        out = torch.empty(1 << circ.n, dtype=torch.complex64, device="cuda")
+        arso.reference_state(cc, out)
+        assert np.max(np.abs(out.cpu().numpy() - statevector.simulate(circ))) < AMP_TOL_C64
+
+
+# ---------------------------------------------------------------- scores --
+
+def _crit_cases(n, psi_ref):
+    probs = np.abs(psi_ref) ** 2
+    top = int(np.argmax(probs))
+    heavy = tuple(int(i) for i in np.nonzero(probs > np.median(probs))[0])
+    return [
+        C.Criterion("fidelity", threshold=0.9, aggregate="pass"),
+        C.Criterion("outcome", target=top, threshold=0.5 * probs[top], aggregate="mean"),
+        C.Criterion("binning", basis_set=heavy, threshold=0.5, aggregate="mean"),
+        C.Criterion("argmax", target=top, threshold=0.5, aggregate="pass"),
+    ]
+
+
+@pytest.mark.parametrize("n,G,tile", [(6, 80, 0), (12, 150, 0), (15, 120, 9)])
+def test_scores_every_criterion(arso, n, G, tile):
+    circ = C.random_circuit(n, G, 40 + n)
+    psi_ref = statevector.simulate(circ)
+    p = 3.0 / circ.L
+    cc = arso.compile_circuit(n, circ.gates, tile_qubits=tile)
+    T = 24
+    errs = arso.sample_errors(cc, p / 3, p / 3, p / 3, 5, 0, T)
+    lists = sampling.sample(5, 0, T, circ.L, p / 3, p / 3, p / 3)
+    states = [statevector.simulate(circ, ev) if ev else psi_ref for ev in lists]
+    for crit in _crit_cases(n, psi_ref):
+        score = np.zeros(T)
+        flags = np.zeros(T, dtype=np.uint8)
+        arso.run_trajectories(cc, errs, crit, score, flags)
+        dev = torch.zeros(T, dtype=torch.float64, device="cuda")
+        arso.run_trajectories(cc, errs, crit, dev)
+        assert np.array_equal(dev.cpu().numpy(), score)
+        for t in range(T):
+            o = criteria.score(crit, states[t], psi_ref)
+            assert abs(score[t] - o) < SCORE_TOL, (crit.kind, t)
+            if flags_comparable(crit, o, states[t]):
+                assert bool(flags[t]) == criteria.passes(crit, o), (crit.kind, t)
+
+
+def _unitary4(rng):
+    z = rng.standard_normal((4, 4)) + 1j * rng.standard_normal((4, 4))
+    q, r = np.linalg.qr(z)
+    return q * (np.diag(r) / np.abs(np.diag(r)))
+
+
+def test_score_state_and_standalone_kernels(arso):
+    rng = np.random.default_rng(1)
+    for n in (3, 12, 20):
+        psi = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+        psi /= np.linalg.norm(psi)
+        d = torch.from_numpy(psi.astype(np.complex64)).cuda()
+        for gate in [C.Gate("H", (0,)), C.Gate("T", (n - 1,)), C.Gate("X", (n // 2,)),
+                     C.Gate("RY", (1 % n,), (0.3,)), C.Gate("U", (n - 1,), (), C.haar_su2(rng))] + (
+                [C.Gate("CX", (n - 1, 0)), C.Gate("CZ", (1, n - 1)), C.Gate("CP", (0, 2), (1.1,)),
+                 C.Gate("SWAP", (n - 1, 1)), C.Gate("U2", (2, n - 2), (), _unitary4(rng))] if n >= 3 else []):
+            arso.apply_gate(n, d, gate)
+            statevector.apply_gate(psi, n, gate)
+            assert np.max(np.abs(d.cpu().numpy() - psi)) < AMP_TOL_C64, gate.name
+        for q, code in ((0, 1), (n - 1, 3), (n // 2, 2)):
+            arso.apply_pauli(n, d, q, code)
+            statevector.apply_pauli(psi, n, q, code)
+            assert np.max(np.abs(d.cpu().numpy() - psi)) < AMP_TOL_C64
+        ref = torch.from_numpy(psi.astype(np.complex64)).cuda()
+        s = arso.score_state(n, d, ref, C.Criterion("fidelity"))
+        assert abs(s - 1.0) < 1e-5
+        s = arso.score_state(n, d, None, C.Criterion("binning", basis_set=(0, 1, 5 % (1 << n))))
+        assert abs(s - criteria.score(C.Criterion("binning", basis_set=(0, 1, 5 % (1 << n))), psi)) < 1e-6
+
+
+# ------------------------------------------------- aggregates and search --
+
+def test_qft4_config_full_parity(arso):
+    """4-qubit QFT on |0101>, p = 1e-3, 1000 trajectories, seed 0, complex128."""
+    circ = C.qft4_0101()
+    crit = circ.criterion
+    cc = arso.compile_circuit(circ.n, circ.gates, precision=arso.C128)
+    errs = arso.sample_errors(cc, 1e-3 / 3, 1e-3 / 3, 1e-3 / 3, 0, 0, 1000)
+    score = np.zeros(1000)
+    flags = np.zeros(1000, dtype=np.uint8)
+    arso.run_trajectories(cc, errs, crit, score, flags)
+    o_s, o_f, _ = montecarlo.run_trajectories(circ, 0, 0, 1000, 1e-3 / 3, 1e-3 / 3, 1e-3 / 3)
+    assert np.max(np.abs(score - o_s)) < 1e-12
+    assert np.array_equal(flags.astype(bool), o_f)
+    r = arso.success_prob(cc, crit, 1e-3, mode="mc", n_traj=1000, seed=0)
+    agg = montecarlo.aggregate(o_s, o_f)
+    assert abs(r.pass_frac - agg["pass_frac"]) < 1e-12
+    assert abs(r.mean - agg["mean"]) < 1e-12
+    assert abs(r.stderr_value - agg["stderr_pass"]) < 1e-9
+
+
+def test_exhaustive_and_eq4(arso):
+    for circ in (C.ghz(5), C.random_circuit(6, 30, 2), C.qft4_0101()):
+        crit = C.Criterion("fidelity", threshold=0.5, aggregate="mean")
+        circ.criterion = crit
+        cc = arso.compile_circuit(circ.n, circ.gates)
+        P, per = arso.exhaustive(cc, crit)
+        a = ox.analyse(circ)
+        assert abs(P[0] - a["P_R"]) < SCORE_TOL
+        for k, e in enumerate(("X", "Z", "Y")):
+            assert abs(P[1 + k] - a["P_e"][e]) < SCORE_TOL
+            assert np.max(np.abs(per[k * circ.L:(k + 1) * circ.L] - a["per_location"][e])) < SCORE_TOL
+        p = 0.2 / circ.L
+        r = arso.success_prob(cc, crit, p, mode="auto")
+        assert r.mode_used == 2
+        assert abs(r.value - ox.eq4(a, p / 3, p / 3, p / 3)) < SCORE_TOL
+
+
+def test_tolerable_rate_matches_oracle(arso):
+    circ = C.ghz(4)
+    crit = C.Criterion("fidelity", aggregate="mean")
+    circ.criterion = crit
+    cc = arso.compile_circuit(circ.n, circ.gates)
+    a = ox.analyse(circ)
+    P1 = ox.one_error_success(a)
+    target = 0.5 * (P1 + a["P_R"])
+    r = arso.tolerable_rate(cc, crit, target)
+    assert r.mode_used == 0 and abs(r.p - ox.eq5(a, target)) < 1e-9
+    # Monte Carlo branch on common random numbers: identical probes
+    r = arso.tolerable_rate(cc, crit, 0.8, n_traj=400, seed=3, mode="mc", rel_tol=0.05)
+    o = search.bisect_log(lambda q: search.mc_value(circ, q, 400, 3), 0.8, 1e-6, 1e-1, rel_tol=0.05)
+    assert r.converged and o[4]
+    assert abs(r.p - o[0]) / o[0] < 1e-3
+
+
+def test_error_free_and_empty_circuits(arso):
+    circ = C.Circuit(3, [])
+    cc = arso.compile_circuit(3, [])
+    errs = arso.sample_errors(cc, 0.1, 0.1, 0.1, 0, 0, 5)
+    s = np.zeros(5)
+    arso.run_trajectories(cc, errs, C.Criterion("outcome", target=0), s)
+    assert np.allclose(s, 1.0)
+    big = C.Circuit(15, [])
+    cc = arso.compile_circuit(15, [])
+    out = torch.empty(1 << 15, dtype=torch.complex64, device="cuda")
+    arso.reference_state(cc, out)
+    v = out.cpu().numpy()
+    assert v[0] == 1 and np.all(v[1:] == 0)
+
+
+def test_invalid_arguments_fail_cleanly(arso):
+    with pytest.raises(arso.ArsoError) as e:
+        arso.compile_circuit(3, [C.Gate("H", (3,))])
+    assert e.value.status == arso.EINVAL
+    cc = arso.compile_circuit(2, [C.Gate("H", (0,))])
+    with pytest.raises(arso.ArsoError):
+        arso.sample_errors(cc, 0.5, 0.5, 0.5, 0, 0, 10)
+    errs = arso.sample_errors(cc, 0.1, 0.1, 0.1, 0, 0, 10)
+    with pytest.raises(arso.ArsoError):
+        arso.run_trajectories(cc, errs, C.Criterion("outcome", target=4), np.zeros(10))
+    with pytest.raises(arso.ArsoError):
+        arso.error_list_from_host(cc, [[(0, 1), (0, 2)]])
+
+
+# --------------------------------------------------- full-size workloads --
+
+def test_grover12_sampled_trajectories(arso):
+    """Grover, 11 search qubits + 1 borrowed, resident engine at full size:
+    bit-exact events for 64 trajectories, scores and amplitudes for two."""
+    circ = C.grover12(0)
+    cc = arso.compile_circuit(circ.n, circ.gates)
+    p = 1e-4
+    errs = arso.sample_errors(cc, p / 3, p / 3, p / 3, 0, 0, 64)
+    off, ev = arso.error_list_copy(errs)
+    lists = sampling.sample(0, 0, 64, circ.L, p / 3, p / 3, p / 3)
+    o_off, o_ev = oracle_csr(lists)
+    assert np.array_equal(off, o_off) and np.array_equal(ev, o_ev)
+    score = np.zeros(64)
+    arso.run_trajectories(cc, errs, circ.criterion, score)
+    idx = [t for t in range(64) if lists[t]][:2]
+    states = gpu_states(arso, circ, cc, errs, idx[0], 1)
+    psi = statevector.simulate(circ, lists[idx[0]])
+    assert np.max(np.abs(states[0] - psi)) < AMP_TOL_C64
+    for t in idx:
+        psi = statevector.simulate(circ, lists[t])
+        o = criteria.score(circ.criterion, psi)
+        if flags_comparable(circ.criterion, o, psi):
+            assert score[t] == o
+
+
+def test_brickwork16_streaming_parity(arso):
+    circ = C.brickwork(16, 40, seed=0)
+    cc = arso.compile_circuit(circ.n, circ.gates)
+    T = 8
+    p = 1e-3
+    errs = arso.sample_errors(cc, p / 3, p / 3, p / 3, 0, 0, T)
+    lists = sampling.sample(0, 0, T, circ.L, p / 3, p / 3, p / 3)
+    score = np.zeros(T)
+    arso.run_trajectories(cc, errs, circ.criterion, score)
+    psi_ref = statevector.simulate(circ)
+    got = gpu_states(arso, circ, cc, errs, 0, T)
+    for t in range(T):
+        psi = statevector.simulate(circ, lists[t]) if lists[t] else psi_ref
+        assert np.max(np.abs(got[t] - psi)) < AMP_TOL_C64
+        assert abs(score[t] - criteria.score(circ.criterion, psi, psi_ref)) < SCORE_TOL
+
+
+def test_brickwork24_full_size_launch(arso):
+    """Brickwork at 24 qubits in the benchmark's launch configuration: the
+    depth-2 circuit is checked against the oracle amplitude by amplitude; the
+    depth-40 circuit through properties that hold at any size."""
+    circ = C.brickwork(24, 2, seed=0)
+    cc = arso.compile_circuit(24, circ.gates, tile_qubits=14)
+    lists = [[], [(3, 1), (40, 3)], [(circ.L - 1, 2)]]
+    errs = arso.error_list_from_host(cc, lists)
+    out = torch.empty((1, 1 << 24), dtype=torch.complex64, device="cuda")
+    for t, ev in enumerate(lists):
+        arso.trajectory_states(cc, errs, t, 1, out)
+        psi = statevector.simulate(circ, ev)
+        assert torch.max(torch.abs(out[0].cpu() - torch.from_numpy(psi))).item() < AMP_TOL_C64
+    full = C.brickwork24(0)
+    cc = arso.compile_circuit(24, full.gates, tile_qubits=14)
+    T = 64
+    p = 1e-3
+    errs = arso.sample_errors(cc, p / 3, p / 3, p / 3, 0, 0, T)
+    off, ev = arso.error_list_copy(errs)
+    o_off, o_ev = oracle_csr(sampling.sample(0, 0, T, full.L, p / 3, p / 3, p / 3))
+    assert np.array_equal(off, o_off) and np.array_equal(ev, o_ev)
+    score = np.zeros(T)
+    arso.run_trajectories(cc, errs, full.criterion, score)
+    assert np.all(score >= -1e-6) and np.all(score <= 1 + 1e-5)
+    err_free = np.diff(off.astype(np.int64)) == 0
+    assert np.all(np.abs(score[err_free] - 1.0) < 1e-5)
+    states = torch.empty((2, 1 << 24), dtype=torch.complex64, device="cuda")
+    arso.trajectory_states(cc, errs, 0, 2, states)
+    norms = torch.sum(torch.abs(states.to(torch.complex128)) ** 2, dim=1).cpu().numpy()
+    assert np.all(np.abs(norms - 1.0) < 1e-4)
