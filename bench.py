@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Benchmark: error-injected Monte Carlo trajectories per second.
+
+Workload (default): random brickwork circuit, 24 qubits, depth 40 (per layer
+Haar SU(2) on every qubit, then CZ on alternating neighbour pairs, open chain;
+G = 1420 gates, L = 1880 error locations), uniform Pauli errors at
+p in {1e-4, 1e-3}, fidelity with the error-free state >= 0.9, complex64
+amplitudes (FP32 arithmetic, FP64 reductions), prefix-state reuse. The full
+workload is 10,000 trajectories per p; one step is one batch of
+--traj-per-step trajectories split evenly over the two rates and runs every
+row of the path: Philox error sampling, prefix reuse, fused passes with
+folded Pauli errors, fused fidelity reduction and aggregation.
+
+Prints ONE JSON line (rank 0). Under torchrun every rank runs its own
+trajectory range (weak scaling, no collective on the data path); the time is
+the max over ranks after a barrier.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+P_RATES = (1e-4, 1e-3)
+TRAJ_PER_P = 10_000
+METRIC = "error-injected trajectories/sec"
+UNIT = "traj/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_sha():
+    h = hashlib.sha256()
+    for f in ("sim.cu", "sim_common.cuh", "kernels.h", "internal.h"):
+        with open(os.path.join(ROOT, "paper_2301_07264_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_per_slot():
+    """DRAM bytes per active trajectory slot per pass launch from the committed
+    ncu summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "pass_kernel_brickwork24.md")
+    try:
+        vals = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line and line.strip().startswith("- "):
+                    k, v = line.strip()[2:].split(":", 1)
+                    vals[k.strip()] = v.strip().strip("`")
+        if vals.get("source_sha") != _kernel_sha():
+            return None
+        return float(vals["dram_bytes_per_slot_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm", "clocks.max.sm", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.samples = []
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == len(self.FIELDS):
+                self.samples.append(parts)
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[2 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------- CPU oracle ---
+
+def oracle_sample(circ, seconds=12.0):
+    """Time the FP64 oracle, as it stands, on a bounded sample of the
+    workload: the first gates of one trajectory's simulation (every errored
+    trajectory simulates all G gates; error-free ones reuse psi_R). Returns
+    (seconds per gate, gates run)."""
+    import numpy as np
+    from oracle import statevector
+    psi = statevector.zero_state(circ.n)
+    g = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds and g < circ.G:
+        statevector.apply_gate(psi, circ.n, circ.gates[g])
+        g += 1
+    dt = time.perf_counter() - t0
+    del psi, np
+    return dt / max(g, 1), g
+
+
+def errored_fraction(L):
+    return sum(1.0 - (1.0 - p) ** L for p in P_RATES) / len(P_RATES)
+
+
+def run_reference(args):
+    """--impl reference: the FP64 CPU oracle timed on this host's cores."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from workloads import circuits as C
+    circ = C.brickwork24(0)
+    frac = errored_fraction(circ.L)
+    per_step = max(1.0, 60.0 / max(args.steps + args.warmup, 1))
+    for _ in range(args.warmup):
+        oracle_sample(circ, seconds=min(per_step, 2.0))
+    times = []
+    gates = 0
+    for _ in range(args.steps):
+        sg, g = oracle_sample(circ, seconds=per_step)
+        times.append(sg)
+        gates += g
+    sec_per_gate = statistics.median(times)
+    traj_per_s = 1.0 / (frac * circ.G * sec_per_gate)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": traj_per_s, "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * args.traj_per_step / traj_per_s, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config(circ, args),
+        "cpu_baseline": {"value": traj_per_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"oracle state-vector simulate() of the first gates of a 24-qubit brickwork "
+                                   f"trajectory, {gates} gates over {args.steps} steps; traj/s = 1 / "
+                                   f"(errored fraction {frac:.3f} x G {circ.G} x sec/gate)"},
+        "e2e": {"value": traj_per_s, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config(circ, args, tile=None, passes=None):
+    return {"workload": "brickwork24_depth40_p1e-4_1e-3", "n_qubits": circ.n, "depth": 40, "G": circ.G,
+            "L": circ.L, "p": list(P_RATES), "trajectories_per_p": TRAJ_PER_P,
+            "traj_per_step": args.traj_per_step, "criterion": "fidelity >= 0.9 (pass fraction)",
+            "prefix_reuse": True, "tile_qubits": tile, "passes": passes,
+            "l2": "inputs larger than L2: every trajectory state is 128 MiB (> 126 MiB L2)"}
+
+
+# ------------------------------------------------------------------ ours ---
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    from paper_2301_07264_gb300 import arso
+    from workloads import circuits as C
+
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream()
+    circ = C.brickwork24(0)
+    crit = arso.make_criterion(circ.criterion)
+    cc = arso.compile_circuit(circ.n, circ.gates, tile_qubits=args.tile,
+                              cache_bytes=int(args.cache_gb * (1 << 30)) if args.cache_gb else 0)
+    info = cc.info()
+    half = args.traj_per_step // len(P_RATES)
+    score = {p: torch.empty(half, dtype=torch.float64, device="cuda") for p in P_RATES}
+    flags = {p: torch.empty(half, dtype=torch.uint8, device="cuda") for p in P_RATES}
+
+    def begin_of(step_idx):
+        return (rank * 1_000_000_000) + (step_idx * half) % TRAJ_PER_P
+
+    def step(step_idx, host_out=None):
+        res = []
+        for p in P_RATES:
+            errs = arso.sample_errors(cc, p / 3, p / 3, p / 3, 0, begin_of(step_idx), half, stream)
+            if host_out is None:
+                arso.run_trajectories(cc, errs, crit, score[p], flags[p], stream)
+                res.append(arso.aggregate(score[p], flags[p], stream))
+            else:
+                s_h, f_h = host_out[p]
+                arso.run_trajectories(cc, errs, crit, s_h, f_h, stream)
+                res.append((float(np.mean(s_h)), float(np.mean(f_h))))
+        return res
+
+    # warm-up (also builds the prefix cache); warm-up batches lie outside the timed ranges
+    for w in range(args.warmup):
+        step(TRAJ_PER_P // half + w)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    arso.profile_reset()
+    arso.profile_enable(True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    aggs = []
+    for k in range(args.steps):
+        aggs.append(step(k))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    arso.profile_enable(False)
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    launches, _, _ = arso.profile_counters()
+    kstats = {name: arso.profile_read(k) for name, k in
+              (("pass", arso.K_PASS), ("pass_last", arso.K_PASS_LAST), ("resident", arso.K_RESIDENT),
+               ("sample", arso.K_SAMPLE), ("reduce", arso.K_REDUCE), ("other", arso.K_OTHER))}
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+
+    # end to end through the public API with host (pinned) result buffers
+    host_out = {p: (torch.empty(half, dtype=torch.float64, pin_memory=True).numpy(),
+                    torch.empty(half, dtype=torch.uint8, pin_memory=True).numpy()) for p in P_RATES}
+    e2e_steps = max(1, min(args.steps, 5))
+    arso.profile_reset()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        step(k, host_out)
+    torch.cuda.synchronize()
+    e2e_time = time.perf_counter() - t0
+    _, h2d, d2h = arso.profile_counters()
+    if dist:
+        t = torch.tensor([e2e_time], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_time = float(t.item())
+
+    if rank != 0:
+        dist.destroy_process_group() if dist else None
+        return 0
+
+    total = args.traj_per_step * args.steps * ws
+    value = total / elapsed
+    peak, peak_kind = _peaks()
+    ps = kstats["pass"]
+    achieved = (ps.bytes / (ps.ms / 1e3)) / 1e9 if ps.ms > 0 else 0.0
+    tr = _traffic_per_slot()
+    avg_slots = ps.bytes / max(ps.launches, 1) / (2.0 * 8 * (1 << circ.n))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": _config(circ, args, info.tile_qubits, info.n_passes),
+        "roofline": {"bound": "hbm", "kernel": "pass_kernel (fused tile pass, state written back)",
+                     "achieved": achieved, "peak": peak, "peak_kind": f"{peak_kind} copy bandwidth (burst)",
+                     "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": (tr * avg_slots) if tr is not None else None,
+                     "algorithmic_bytes_per_launch": ps.bytes / max(ps.launches, 1),
+                     "avg_launch_ms": ps.ms / max(ps.launches, 1), "launches": ps.launches},
+        "kernels": {k: {"launches": v.launches, "ms": v.ms, "GB": v.bytes / 1e9} for k, v in kstats.items()},
+        "e2e": {"value": args.traj_per_step * e2e_steps * ws / e2e_time, "unit": UNIT,
+                "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "results": {"pass_frac_p1e-4": float(np.mean([a[0][1] for a in aggs])),
+                    "pass_frac_p1e-3": float(np.mean([a[1][1] for a in aggs]))},
+    }
+    if not args.no_cpu_baseline:
+        sg, g = oracle_sample(circ, seconds=args.cpu_seconds)
+        frac = errored_fraction(circ.L)
+        v = 1.0 / (frac * circ.G * sg)
+        line["cpu_baseline"] = {
+            "value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 numpy oracle simulate() of the first {g} gates of one 24-qubit brickwork trajectory "
+                      f"({sg * 1e3:.1f} ms/gate, single-threaded); traj/s = 1 / (errored fraction {frac:.3f} x "
+                      f"G {circ.G} x sec/gate)"}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--traj-per-step", type=int, default=1000)
+    ap.add_argument("--tile", type=int, default=0, help="tile qubits (0 = library default)")
+    ap.add_argument("--cache-gb", type=float, default=0.0, help="prefix-cache budget (0 = library default)")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

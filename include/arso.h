@@ -169,6 +169,13 @@ arso_status arso_run_trajectories(const arso_circuit *c, const arso_error_list *
                                   const arso_criterion *crit, void *stream,
                                   double *score_out, uint8_t *pass_out);
 
+/* Aggregate per-trajectory results (Sec. IV-C, last paragraph: the success
+ * probability is the average of the criterion over the simulated states).
+ * score (n doubles) and pass_flags (n bytes, may be NULL) are device
+ * pointers; out[5] (host) = {mean score, pass fraction, stderr of the mean
+ * score, stderr of the pass fraction, n}. FP64 sums in a fixed order. */
+arso_status arso_aggregate(const double *score, const uint8_t *pass_flags, uint64_t n, void *stream, double *out);
+
 /* Final state vectors of trajectories [first, first + count) of `errors`
  * (count * 2^n amplitudes, device pointer, layout per the circuit's
  * precision). For parity checks and inspection. */
@@ -242,6 +249,34 @@ arso_status arso_apply_pauli(uint32_t n_qubits, void *amps, uint32_t qubit, uint
  * is a host double. */
 arso_status arso_score_state(uint32_t n_qubits, const void *amps, const void *ref,
                              const arso_criterion *crit, void *stream, double *score_out);
+
+/* ---- tracing: per-kernel device time and traffic (not part of the paper) ----
+ * When enabled, the library records a CUDA event pair on the launching stream
+ * around every kernel launch and accumulates, per kernel family, the number
+ * of launches, their summed device time and the algorithmic bytes they move
+ * (the reads and writes the algorithm requires, not cache-level traffic).
+ * Launch and host<->device transfer counters run whether or not timing is
+ * enabled. Process-wide, thread-safe; reading resolves pending events. */
+enum {
+    ARSO_K_PASS = 0,        /* streaming pass, state written back to HBM */
+    ARSO_K_PASS_LAST = 1,   /* last streaming pass, fused criterion reduction */
+    ARSO_K_RESIDENT = 2,    /* resident whole-state trajectory kernel */
+    ARSO_K_SAMPLE = 3,      /* Philox error sampling (count + fill) */
+    ARSO_K_REDUCE = 4,      /* criterion partials, finish, sums */
+    ARSO_K_OTHER = 5,       /* bookkeeping kernels (scan, sort, fill, init) */
+    ARSO_K_COUNT = 6
+};
+typedef struct {
+    uint64_t launches;
+    double ms;              /* summed device time (timing enabled only) */
+    double bytes;           /* summed algorithmic bytes (timing enabled only) */
+} arso_kernel_stats;
+arso_status arso_profile_enable(int on);
+arso_status arso_profile_reset(void);
+arso_status arso_profile_read(uint32_t kernel, arso_kernel_stats *out);
+/* Total kernel launches and bytes copied host->device / device->host by the
+ * library since the last reset. */
+arso_status arso_profile_counters(uint64_t *launches, uint64_t *h2d_bytes, uint64_t *d2h_bytes);
 
 const char *arso_last_error(void);
 const char *arso_version(void);

@@ -105,6 +105,11 @@ _sigs = {
     "arso_apply_gate": [C.c_uint32, _vp, C.POINTER(Gate), _vp],
     "arso_apply_pauli": [C.c_uint32, _vp, C.c_uint32, C.c_uint32, _vp],
     "arso_score_state": [C.c_uint32, _vp, _vp, C.POINTER(Criterion), _vp, C.POINTER(C.c_double)],
+    "arso_aggregate": [_vp, _vp, C.c_uint64, _vp, _vp],
+    "arso_profile_enable": [C.c_int],
+    "arso_profile_reset": [],
+    "arso_profile_read": [C.c_uint32, _vp],
+    "arso_profile_counters": [_vp, _vp, _vp],
 }
 for _name, _args in _sigs.items():
     _f = getattr(lib, _name)
@@ -263,6 +268,41 @@ def run_trajectories(circ, errs, crit, score_out, pass_out=None, stream=None):
     c = crit if isinstance(crit, Criterion) else make_criterion(crit)
     _check(lib.arso_run_trajectories(circ.handle, errs.handle, C.byref(c), _stream(stream), _ptr(score_out),
                                      _ptr(pass_out)))
+
+
+def aggregate(score, pass_flags=None, stream=None):
+    """(mean, pass_frac, stderr_mean, stderr_pass, n) of device score / flag arrays."""
+    out = np.zeros(5)
+    n = score.numel() if hasattr(score, "numel") else len(score)
+    _check(lib.arso_aggregate(_ptr(score), _ptr(pass_flags), n, _stream(stream), out.ctypes.data))
+    return tuple(out)
+
+
+class KernelStats(C.Structure):
+    _fields_ = [("launches", C.c_uint64), ("ms", C.c_double), ("bytes", C.c_double)]
+
+
+K_PASS, K_PASS_LAST, K_RESIDENT, K_SAMPLE, K_REDUCE, K_OTHER = range(6)
+
+
+def profile_enable(on=True):
+    _check(lib.arso_profile_enable(1 if on else 0))
+
+
+def profile_reset():
+    _check(lib.arso_profile_reset())
+
+
+def profile_read(kernel) -> KernelStats:
+    s = KernelStats()
+    _check(lib.arso_profile_read(kernel, C.byref(s)))
+    return s
+
+
+def profile_counters():
+    a, b, c = C.c_uint64(), C.c_uint64(), C.c_uint64()
+    _check(lib.arso_profile_counters(C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
 
 
 def trajectory_states(circ, errs, first, count, amps_out, stream=None):

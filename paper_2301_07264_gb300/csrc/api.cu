@@ -8,6 +8,7 @@
 #include <numeric>
 
 #include "kernels.h"
+#include "prof.h"
 
 namespace arso {
 
@@ -53,8 +54,16 @@ struct Scratch {
     template <typename T> T *as() const { return static_cast<T *>(ptr); }
 };
 
+static void copy_h2d(void *dst, const void *src, size_t bytes, cudaStream_t st) {
+    ARSO_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st));
+    prof_count_h2d(bytes);
+}
+static void copy_d2h(void *dst, const void *src, size_t bytes, cudaStream_t st) {
+    ARSO_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st));
+    prof_count_d2h(bytes);
+}
 template <typename T> static void h2d(void *dst, const std::vector<T> &v, cudaStream_t st) {
-    if (!v.empty()) ARSO_CUDA(cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    if (!v.empty()) copy_h2d(dst, v.data(), v.size() * sizeof(T), st);
 }
 
 // ------------------------------------------------------------ upload -------
@@ -73,7 +82,7 @@ static void upload_circuit(arso_circuit *c) {
             d.arity = (uint8_t)h.arity;
             d.q0 = (uint8_t)local[h.q0];
             d.q1 = (uint8_t)local[h.q1];
-            d.mat = (uint32_t)pool.size();
+            d.mat = h.cls == GC_OMEGA ? h.omega_k : (uint32_t)pool.size();
             switch (h.cls) {
                 case GC_DENSE1: for (int i = 0; i < 4; ++i) pool.push_back(h.m[i]); break;
                 case GC_DIAG1: pool.push_back(h.m[0]); pool.push_back(h.m[3]); break;
@@ -147,7 +156,7 @@ static void ensure_cache(arso_circuit *c, cudaStream_t st) {
         a.cache = c->d_cache.ptr;
         a.ckpt_every = every;
         a.n_ckpt = c->n_ckpt;
-        launch_resident(a, true, c->precision, st);
+        launch_resident(a, true, c->precision, (double)c->n_ckpt * sb, st);
     } else {
         const uint32_t P = (uint32_t)c->passes.size();
         // boundaries 0..P; cache every s-th boundary and the last one
@@ -179,7 +188,7 @@ static void ensure_cache(arso_circuit *c, cudaStream_t st) {
             a.ideal = 1;
             a.ideal_src = c->ckpt_pass[j] != NO_EVENT ? base + (size_t)c->ckpt_pass[j] * sb : work.ptr;
             a.ideal_dst = c->ckpt_pass[j + 1] != NO_EVENT ? base + (size_t)c->ckpt_pass[j + 1] * sb : work.ptr;
-            launch_pass(a, false, c->precision, 1, st);
+            launch_pass(a, false, c->precision, 1, 2.0 * sb, st);
         }
     }
     ARSO_CUDA(cudaStreamSynchronize(st));
@@ -217,7 +226,7 @@ static void make_crit(const arso_circuit *c, const arso_criterion *crit, DevCrit
             bm[crit->set[i] >> 5] |= 1u << (crit->set[i] & 31);
         }
         out.bitmap.ensure(bm.size() * 4);
-        ARSO_CUDA(cudaMemcpyAsync(out.bitmap.ptr, bm.data(), bm.size() * 4, cudaMemcpyHostToDevice, st));
+        copy_h2d(out.bitmap.ptr, bm.data(), bm.size() * 4, st);
         ARSO_CUDA(cudaStreamSynchronize(st));
         out.d.bitmap = out.bitmap.as<uint32_t>();
     }
@@ -304,7 +313,9 @@ static void run_streaming(arso_circuit *c, const arso_error_list *e, const std::
             a.crit = crit;
             a.partials = parts.as<Partial>();
             a.store_last = states_out ? 1 : 0;
-            launch_pass(a, j == P - 1, c->precision, (uint32_t)nb, st);
+            uint32_t active = 0;
+            for (size_t i = 0; i < nb; ++i) active += st_start[i] <= (int)j;
+            launch_pass(a, j == P - 1, c->precision, (uint32_t)nb, 2.0 * (double)sb * active, st);
         }
         if (!states_out)
             launch_finish_partials(parts.as<Partial>(), tiles, (uint32_t)nb, d_slot_traj.as<uint64_t>(), crit, d_score,
@@ -337,13 +348,13 @@ static void run_all(arso_circuit *c, const arso_error_list *e, const DevCrit &dc
         a.ref_score = ref.as<double>();
         a.score = d_score;
         a.pass_flags = d_pass;
-        launch_resident(a, false, c->precision, st);
+        launch_resident(a, false, c->precision, (double)e->n_traj * c->state_bytes(), st);
         ARSO_CUDA(cudaStreamSynchronize(st));
         return;
     }
     launch_fill_error_free(e->d_first.as<uint32_t>(), e->n_traj, ref.as<double>(), dc.d.threshold, d_score, d_pass, st);
     std::vector<uint32_t> first(e->n_traj);
-    ARSO_CUDA(cudaMemcpyAsync(first.data(), e->d_first.ptr, e->n_traj * 4, cudaMemcpyDeviceToHost, st));
+    copy_d2h(first.data(), e->d_first.ptr, e->n_traj * 4, st);
     ARSO_CUDA(cudaStreamSynchronize(st));
     std::vector<uint64_t> ids;
     std::vector<uint32_t> fp;
@@ -400,7 +411,7 @@ static void sample(const arso_circuit *c, double px, double pz, double py, uint6
     }
     launch_exclusive_scan(counts.as<uint32_t>(), n_traj, e->d_offsets.as<uint64_t>(), st);
     uint64_t total = 0;
-    ARSO_CUDA(cudaMemcpyAsync(&total, e->d_offsets.as<uint64_t>() + n_traj, 8, cudaMemcpyDeviceToHost, st));
+    copy_d2h(&total, e->d_offsets.as<uint64_t>() + n_traj, 8, st);
     ARSO_CUDA(cudaStreamSynchronize(st));
     e->n_events = total;
     e->d_loc.ensure(std::max<uint64_t>(total, 1) * 4);
@@ -430,9 +441,9 @@ static void list_from_host(const arso_circuit *c, uint64_t n_traj, const uint64_
     e->n_events = total;
     e->d_loc.ensure(std::max<uint64_t>(total, 1) * 4);
     e->d_key.ensure(std::max<uint64_t>(total, 1) * 4);
-    ARSO_CUDA(cudaMemcpyAsync(e->d_offsets.ptr, offsets, (n_traj + 1) * 8, cudaMemcpyHostToDevice, st));
+    copy_h2d(e->d_offsets.ptr, offsets, (n_traj + 1) * 8, st);
     if (total) {
-        ARSO_CUDA(cudaMemcpyAsync(e->d_loc.ptr, events, total * 4, cudaMemcpyHostToDevice, st));
+        copy_h2d(e->d_loc.ptr, events, total * 4, st);
         launch_keys_from_loc(e->d_loc.as<uint32_t>(), total, c->d_loc_key.as<uint32_t>(), e->d_key.as<uint32_t>(), st);
     }
     finish_list(c, e.get(), st);
@@ -453,7 +464,7 @@ static McOut mc_run(arso_circuit *c, const DevCrit &dc, double p, uint64_t n_tra
     run_all(c, e.get(), dc, st, sc.as<double>(), pf.as<uint8_t>());
     launch_sum_scores(sc.as<double>(), pf.as<uint8_t>(), n_traj, sums.as<double>(), st);
     double h[3];
-    ARSO_CUDA(cudaMemcpyAsync(h, sums.ptr, 24, cudaMemcpyDeviceToHost, st));
+    copy_d2h(h, sums.ptr, 24, st);
     ARSO_CUDA(cudaStreamSynchronize(st));
     McOut o{};
     const double N = (double)std::max<uint64_t>(n_traj, 1);
@@ -488,14 +499,14 @@ static void exhaustive(arso_circuit *c, const DevCrit &dc, cudaStream_t st, doub
     std::vector<double> s(T);
     std::vector<uint8_t> f(T);
     if (T) {
-        ARSO_CUDA(cudaMemcpyAsync(s.data(), sc.ptr, T * 8, cudaMemcpyDeviceToHost, st));
-        ARSO_CUDA(cudaMemcpyAsync(f.data(), pf.ptr, T, cudaMemcpyDeviceToHost, st));
+        copy_d2h(s.data(), sc.ptr, T * 8, st);
+        copy_d2h(f.data(), pf.ptr, T, st);
     }
     // reference value
     Scratch ref(st, 8);
     score_into(ref_state_ptr(c), ref_state_ptr(c), (int)c->n, c->precision, dc.d, ref.as<double>(), st);
     double r = 0;
-    ARSO_CUDA(cudaMemcpyAsync(&r, ref.ptr, 8, cudaMemcpyDeviceToHost, st));
+    copy_d2h(&r, ref.ptr, 8, st);
     ARSO_CUDA(cudaStreamSynchronize(st));
     const double rp = r >= dc.d.threshold ? 1.0 : 0.0;
     double Pm[4] = {r, 0, 0, 0}, Pp[4] = {rp, 0, 0, 0};
@@ -619,9 +630,9 @@ arso_status arso_error_list_copy(const arso_error_list *e, uint64_t *offsets, ui
         ARSO_REQUIRE(e != nullptr, "NULL error list");
         cudaStream_t st = (cudaStream_t)stream;
         if (offsets)
-            ARSO_CUDA(cudaMemcpyAsync(offsets, e->d_offsets.ptr, (e->n_traj + 1) * 8, cudaMemcpyDeviceToHost, st));
+            copy_d2h(offsets, e->d_offsets.ptr, (e->n_traj + 1) * 8, st);
         if (events && e->n_events)
-            ARSO_CUDA(cudaMemcpyAsync(events, e->d_loc.ptr, e->n_events * 4, cudaMemcpyDeviceToHost, st));
+            copy_d2h(events, e->d_loc.ptr, e->n_events * 4, st);
         ARSO_CUDA(cudaStreamSynchronize(st));
     });
 }
@@ -644,10 +655,31 @@ arso_status arso_run_trajectories(const arso_circuit *cc, const arso_error_list 
         uint8_t *d_pass = pass_out ? (pdev ? pass_out : pf.as<uint8_t>()) : nullptr;
         run_all(c, e, dc, st, d_score, d_pass);
         if (!sdev && e->n_traj)
-            ARSO_CUDA(cudaMemcpyAsync(score_out, d_score, e->n_traj * 8, cudaMemcpyDeviceToHost, st));
+            copy_d2h(score_out, d_score, e->n_traj * 8, st);
         if (pass_out && !pdev && e->n_traj)
-            ARSO_CUDA(cudaMemcpyAsync(pass_out, d_pass, e->n_traj, cudaMemcpyDeviceToHost, st));
+            copy_d2h(pass_out, d_pass, e->n_traj, st);
         ARSO_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+arso_status arso_aggregate(const double *score, const uint8_t *pass_flags, uint64_t n, void *stream, double *out) {
+    return guard([&] {
+        ARSO_REQUIRE(score && out, "NULL argument");
+        ARSO_REQUIRE(is_device_ptr(score) && (!pass_flags || is_device_ptr(pass_flags)), "inputs must be device memory");
+        cudaStream_t st = (cudaStream_t)stream;
+        Scratch sums(st, 24);
+        launch_sum_scores(score, pass_flags, n, sums.as<double>(), st);
+        double h[3];
+        copy_d2h(h, sums.ptr, 24, st);
+        ARSO_CUDA(cudaStreamSynchronize(st));
+        const double N = (double)std::max<uint64_t>(n, 1);
+        const double vs = n > 1 ? std::max(0.0, (h[1] - h[0] * h[0] / N) / (N - 1)) : 0.0;
+        const double vp = n > 1 ? std::max(0.0, (h[2] - h[2] * h[2] / N) / (N - 1)) : 0.0;
+        out[0] = h[0] / N;
+        out[1] = h[2] / N;
+        out[2] = std::sqrt(vs / N);
+        out[3] = std::sqrt(vp / N);
+        out[4] = (double)n;
     });
 }
 
@@ -677,10 +709,10 @@ arso_status arso_trajectory_states(const arso_circuit *cc, const arso_error_list
             a.keys = e->d_key.as<uint32_t>();
             a.first = e->d_first.as<uint32_t>();
             a.states_out = amps_out;
-            launch_resident(a, false, c->precision, st);
+            launch_resident(a, false, c->precision, 2.0 * (double)count * c->state_bytes(), st);
         } else {
             std::vector<uint32_t> fp(count);
-            ARSO_CUDA(cudaMemcpyAsync(fp.data(), e->d_first.as<uint32_t>() + first, count * 4, cudaMemcpyDeviceToHost, st));
+            copy_d2h(fp.data(), e->d_first.as<uint32_t>() + first, count * 4, st);
             ARSO_CUDA(cudaStreamSynchronize(st));
             std::vector<uint64_t> ids(count);
             for (uint64_t i = 0; i < count; ++i) ids[i] = first + i;
@@ -843,12 +875,13 @@ arso_status arso_apply_gate(uint32_t n, void *amps, const arso_gate *gate, void 
         ARSO_REQUIRE(h.q0 < n && h.q1 < n && (h.arity == 1 || h.q0 != h.q1), "bad gate qubits");
         matrix_for(*gate, h);
         DGate d{};
-        d.cls = h.cls;
+        // the single-gate HBM kernel takes H and the omega phases as plain dense/diagonal gates
+        d.cls = h.cls == GC_H ? (uint8_t)GC_DENSE1 : h.cls == GC_OMEGA ? (uint8_t)GC_DIAG1 : h.cls;
         d.arity = (uint8_t)h.arity;
         d.q0 = (uint8_t)h.q0;
         d.q1 = (uint8_t)h.q1;
         M16 m{};
-        if (h.arity == 1 && h.cls == GC_DIAG1) {
+        if (h.arity == 1 && d.cls == GC_DIAG1) {
             m.m[0] = make_float2((float)h.m[0].real(), (float)h.m[0].imag());
             m.m[1] = make_float2((float)h.m[3].real(), (float)h.m[3].imag());
         } else {
@@ -885,7 +918,7 @@ arso_status arso_score_state(uint32_t n, const void *amps, const void *ref, cons
         make_crit(&tmp, crit, dc, st);
         Scratch d(st, 8);
         score_into(amps, ref ? ref : amps, (int)n, ARSO_C64, dc.d, d.as<double>(), st);
-        ARSO_CUDA(cudaMemcpyAsync(score_out, d.ptr, 8, cudaMemcpyDeviceToHost, st));
+        copy_d2h(score_out, d.ptr, 8, st);
         ARSO_CUDA(cudaStreamSynchronize(st));
     });
 }

@@ -41,14 +41,15 @@ void matrix_for(const arso_gate &g, HostGate &h) {
     auto set2 = [&](cd a, cd b, cd c, cd d) { h.m[0] = a; h.m[1] = b; h.m[2] = c; h.m[3] = d; };
     switch (g.kind) {
         case ARSO_GATE_ID: set2(1, 0, 0, 1); h.cls = GC_NOP; break;
-        case ARSO_GATE_H: set2(s2, s2, s2, -s2); h.cls = GC_DENSE1; break;
+        case ARSO_GATE_H: set2(s2, s2, s2, -s2); h.cls = GC_H; break;
         case ARSO_GATE_X: set2(0, 1, 1, 0); h.cls = GC_X; break;
         case ARSO_GATE_Y: set2(0, -I, I, 0); h.cls = GC_DENSE1; break;
-        case ARSO_GATE_Z: set2(1, 0, 0, -1); h.cls = GC_DIAG1; break;
-        case ARSO_GATE_S: set2(1, 0, 0, I); h.cls = GC_DIAG1; break;
-        case ARSO_GATE_SDG: set2(1, 0, 0, -I); h.cls = GC_DIAG1; break;
-        case ARSO_GATE_T: set2(1, 0, 0, std::polar(1.0, M_PI / 4)); h.cls = GC_DIAG1; break;
-        case ARSO_GATE_TDG: set2(1, 0, 0, std::polar(1.0, -M_PI / 4)); h.cls = GC_DIAG1; break;
+        // diag(1, e^{i k pi/4}): Z (k=4), S (2), SDG (6), T (1), TDG (7)
+        case ARSO_GATE_Z: set2(1, 0, 0, -1); h.cls = GC_OMEGA; h.omega_k = 4; break;
+        case ARSO_GATE_S: set2(1, 0, 0, I); h.cls = GC_OMEGA; h.omega_k = 2; break;
+        case ARSO_GATE_SDG: set2(1, 0, 0, -I); h.cls = GC_OMEGA; h.omega_k = 6; break;
+        case ARSO_GATE_T: set2(1, 0, 0, std::polar(1.0, M_PI / 4)); h.cls = GC_OMEGA; h.omega_k = 1; break;
+        case ARSO_GATE_TDG: set2(1, 0, 0, std::polar(1.0, -M_PI / 4)); h.cls = GC_OMEGA; h.omega_k = 7; break;
         case ARSO_GATE_RX:
             set2(std::cos(th / 2), -I * std::sin(th / 2), -I * std::sin(th / 2), std::cos(th / 2));
             h.cls = GC_DENSE1;

@@ -44,7 +44,16 @@ enum GateClass : uint8_t {
     GC_DIAG2 = 5,   // diag(d0..d3)
     GC_CX = 6,      // controlled bit flip (q0 control, q1 target)
     GC_SWAP = 7,
+    GC_H = 8,       // Hadamard, 1/sqrt2 applied as a two-float constant (unbiased rounding)
+    GC_OMEGA = 9,   // diag(1, e^{i k pi/4}), k in DGate::mat; exact for even k, two-float 1/sqrt2 for odd k
 };
+
+// 1/sqrt(2) split into a float and its float remainder, so that c*x can be
+// formed as fma(hi, x, lo*x) without the bias of a rounded constant; the bias
+// would otherwise shrink the norm by ~2.4e-8 per H or T gate.
+constexpr double RSQRT2_D = 0.70710678118654752440084436210485;
+constexpr float RSQRT2_HI = (float)RSQRT2_D;
+constexpr float RSQRT2_LO = (float)(RSQRT2_D - (double)RSQRT2_HI);
 
 // One gate as the kernels see it. q0/q1 are tile-local bit positions for
 // the pass that contains the gate (global positions for the resident engine).
@@ -73,6 +82,7 @@ struct HostGate {
     uint32_t q0, q1;
     int arity;
     uint8_t cls;
+    uint32_t omega_k = 0;        // GC_OMEGA exponent
     std::complex<double> m[16];  // 2x2 (first 4) or 4x4, row-major
 };
 

@@ -71,8 +71,8 @@ struct PassArgs {
     int store_last;              // last pass stores the state instead of reducing
 };
 
-void launch_resident(const ResidentArgs &a, bool ideal, int precision, cudaStream_t st);
-void launch_pass(const PassArgs &a, bool last, int precision, uint32_t slots, cudaStream_t st);
+void launch_resident(const ResidentArgs &a, bool ideal, int precision, double bytes, cudaStream_t st);
+void launch_pass(const PassArgs &a, bool last, int precision, uint32_t slots, double bytes, cudaStream_t st);
 void launch_finish_partials(const Partial *partials, uint32_t tiles, uint32_t slots, const uint64_t *slot_traj,
                             const DCrit &crit, double *score, uint8_t *pass_flags, cudaStream_t st);
 void launch_fill_error_free(const uint32_t *first, uint64_t n_traj, const double *ref_score, double threshold,

@@ -1,0 +1,27 @@
+// Launch tracing: CUDA-event timing, algorithmic bytes, launch and transfer
+// counters. A ProfScope placed around a kernel launch records an event pair
+// on the launching stream when timing is enabled.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/arso.h"
+
+namespace arso {
+
+void prof_begin(int kind, double bytes, cudaStream_t st, cudaEvent_t *ev_out);
+void prof_end(int kind, double bytes, cudaStream_t st, cudaEvent_t start);
+void prof_count_h2d(uint64_t bytes);
+void prof_count_d2h(uint64_t bytes);
+
+struct ProfScope {
+    int kind;
+    double bytes;
+    cudaStream_t st;
+    cudaEvent_t start = nullptr;
+    ProfScope(int k, double b, cudaStream_t s) : kind(k), bytes(b), st(s) { prof_begin(kind, bytes, st, &start); }
+    ~ProfScope() { prof_end(kind, bytes, st, start); }
+};
+
+}  // namespace arso

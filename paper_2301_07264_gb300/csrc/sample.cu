@@ -13,6 +13,7 @@
 #include <algorithm>
 
 #include "kernels.h"
+#include "prof.h"
 
 namespace arso {
 
@@ -233,10 +234,12 @@ void launch_sample_count(const SampleArgs &a, uint32_t *counts, cudaStream_t st)
     if (!a.n_traj) return;
     const unsigned grid = (unsigned)std::min<uint64_t>(a.n_traj, 152ull * 64);
     const int nt = a.L <= 64 ? 32 : (a.L <= 512 ? 128 : 256);
+    ProfScope ps_(ARSO_K_SAMPLE, 4.0 * a.n_traj, st);
     sample_count_kernel<<<grid, nt, 0, st>>>(a, counts);
     ARSO_CUDA(cudaGetLastError());
 }
 void launch_exclusive_scan(const uint32_t *counts, uint64_t n, uint64_t *offsets, cudaStream_t st) {
+    ProfScope ps_(ARSO_K_OTHER, 0.0, st);
     exclusive_scan_kernel<<<1, 1024, 0, st>>>(counts, n, offsets);
     ARSO_CUDA(cudaGetLastError());
 }
@@ -245,27 +248,32 @@ void launch_sample_fill(const SampleArgs &a, const uint64_t *offsets, const uint
     if (!a.n_traj) return;
     const unsigned grid = (unsigned)std::min<uint64_t>(a.n_traj, 152ull * 64);
     const int nt = a.L <= 64 ? 32 : (a.L <= 512 ? 128 : 256);
+    ProfScope ps_(ARSO_K_SAMPLE, 0.0, st);
     sample_fill_kernel<<<grid, nt, 0, st>>>(a, offsets, loc_key, ev_loc, ev_key);
     ARSO_CUDA(cudaGetLastError());
 }
 void launch_keys_from_loc(const uint32_t *ev_loc, uint64_t n_events, const uint32_t *loc_key, uint32_t *ev_key,
                           cudaStream_t st) {
     if (!n_events) return;
+    ProfScope ps_(ARSO_K_OTHER, 0.0, st);
     keys_from_loc_kernel<<<grid_for(n_events, 256, 152 * 16), 256, 0, st>>>(ev_loc, n_events, loc_key, ev_key);
     ARSO_CUDA(cudaGetLastError());
 }
 void launch_sort_keys(const uint64_t *offsets, uint64_t n_traj, uint32_t *ev_key, cudaStream_t st) {
     if (!n_traj) return;
+    ProfScope ps_(ARSO_K_OTHER, 0.0, st);
     sort_keys_kernel<<<grid_for(n_traj, 128, 152 * 16), 128, 0, st>>>(offsets, n_traj, ev_key);
     ARSO_CUDA(cudaGetLastError());
 }
 void launch_first_event(const uint64_t *offsets, uint64_t n_traj, const uint32_t *ev_key, uint32_t *first,
                         cudaStream_t st) {
     if (!n_traj) return;
+    ProfScope ps_(ARSO_K_OTHER, 0.0, st);
     first_event_kernel<<<grid_for(n_traj, 256, 152 * 16), 256, 0, st>>>(offsets, n_traj, ev_key, first);
     ARSO_CUDA(cudaGetLastError());
 }
 void launch_sum_scores(const double *score, const uint8_t *pass_flags, uint64_t n, double *sums3, cudaStream_t st) {
+    ProfScope ps_(ARSO_K_REDUCE, 0.0, st);
     sum_scores_kernel<<<1, 1024, 0, st>>>(score, pass_flags, n, sums3);
     ARSO_CUDA(cudaGetLastError());
 }

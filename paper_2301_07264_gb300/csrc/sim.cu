@@ -13,6 +13,7 @@
 #include <algorithm>
 
 #include "sim_common.cuh"
+#include "prof.h"
 
 namespace arso {
 
@@ -366,7 +367,8 @@ template <typename T> static void set_smem(const void *fn, size_t bytes) {
     if (bytes > 48 * 1024) ARSO_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
 }
 
-void launch_resident(const ResidentArgs &a, bool ideal, int precision, cudaStream_t st) {
+void launch_resident(const ResidentArgs &a, bool ideal, int precision, double bytes, cudaStream_t st) {
+    ProfScope ps_(ARSO_K_RESIDENT, bytes, st);
     const uint32_t N = 1u << a.n;
     const int nt = (int)std::min<uint32_t>(256, std::max<uint32_t>(32, N / 2));
     if (precision == ARSO_C64) {
@@ -387,7 +389,8 @@ void launch_resident(const ResidentArgs &a, bool ideal, int precision, cudaStrea
     ARSO_CUDA(cudaGetLastError());
 }
 
-void launch_pass(const PassArgs &a, bool last, int precision, uint32_t slots, cudaStream_t st) {
+void launch_pass(const PassArgs &a, bool last, int precision, uint32_t slots, double bytes, cudaStream_t st) {
+    ProfScope ps_(last && !a.store_last ? ARSO_K_PASS_LAST : ARSO_K_PASS, bytes, st);
     const uint32_t tiles = 1u << (a.n - a.t);
     const int nt = 256;
     dim3 grid(tiles, slots);
@@ -416,6 +419,7 @@ void launch_pass(const PassArgs &a, bool last, int precision, uint32_t slots, cu
 void launch_finish_partials(const Partial *partials, uint32_t tiles, uint32_t slots, const uint64_t *slot_traj,
                             const DCrit &crit, double *score, uint8_t *pass_flags, cudaStream_t st) {
     const unsigned grid = std::min<uint32_t>(slots, 152u * 8);
+    ProfScope ps_(ARSO_K_REDUCE, 0.0, st);
     finish_partials_kernel<<<grid, 256, 0, st>>>(partials, tiles, slots, slot_traj, crit, score, pass_flags);
     ARSO_CUDA(cudaGetLastError());
 }
@@ -424,6 +428,7 @@ void launch_fill_error_free(const uint32_t *first, uint64_t n_traj, const double
                             double *score, uint8_t *pass_flags, cudaStream_t st) {
     if (!n_traj) return;
     const unsigned grid = (unsigned)std::min<uint64_t>((n_traj + 255) / 256, 152ull * 16);
+    ProfScope ps_(ARSO_K_OTHER, 0.0, st);
     fill_error_free_kernel<<<grid, 256, 0, st>>>(first, n_traj, ref_score, threshold, score, pass_flags);
     ARSO_CUDA(cudaGetLastError());
 }
@@ -431,6 +436,7 @@ void launch_fill_error_free(const uint32_t *first, uint64_t n_traj, const double
 void launch_gate_pairs(float2 *psi, int n, const DGate &g, const M16 &m, cudaStream_t st) {
     const uint64_t work = 1ull << (n - g.arity);
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((work + 255) / 256, 152ull * 16));
+    ProfScope ps_(ARSO_K_OTHER, 16.0 * (double)(1ull << n), st);
     gate_pairs_kernel<<<grid, 256, 0, st>>>(psi, n, g, m);
     ARSO_CUDA(cudaGetLastError());
 }
@@ -438,6 +444,7 @@ void launch_gate_pairs(float2 *psi, int n, const DGate &g, const M16 &m, cudaStr
 void launch_pauli(float2 *psi, int n, uint32_t q, uint32_t code, cudaStream_t st) {
     const uint64_t work = 1ull << (n - 1);
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((work + 255) / 256, 152ull * 16));
+    ProfScope ps_(ARSO_K_OTHER, 16.0 * (double)(1ull << n), st);
     pauli_kernel<<<grid, 256, 0, st>>>(psi, n, q, code);
     ARSO_CUDA(cudaGetLastError());
 }
@@ -446,6 +453,7 @@ uint32_t launch_score_partials(const void *psi, const void *ref, int n, int prec
                                Partial *partials, uint32_t max_blocks, cudaStream_t st) {
     const uint64_t N = 1ull << n;
     const uint32_t blocks = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((N + 255) / 256, max_blocks));
+    ProfScope ps_(ARSO_K_REDUCE, (double)N * (precision == ARSO_C64 ? 8 : 16), st);
     if (precision == ARSO_C64)
         score_partials_kernel<float2><<<blocks, 256, 0, st>>>(static_cast<const float2 *>(psi),
                                                               static_cast<const float2 *>(ref), n, crit, partials);
@@ -459,6 +467,7 @@ uint32_t launch_score_partials(const void *psi, const void *ref, int n, int prec
 void launch_init_zero_state(void *psi, int n, int precision, cudaStream_t st) {
     const uint64_t N = 1ull << n;
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((N + 255) / 256, 152ull * 16));
+    ProfScope ps_(ARSO_K_OTHER, 0.0, st);
     init_zero_state_kernel<<<grid, 256, 0, st>>>(psi, N, precision == ARSO_C128);
     ARSO_CUDA(cudaGetLastError());
 }

@@ -37,6 +37,26 @@ template <typename T> __device__ __forceinline__ T cneg(T a) {
     return a;
 }
 
+// x / sqrt(2): FP32 uses the two-float constant (fma(hi, x, lo * x)), so the
+// product carries only the unbiased rounding of the operations.
+__device__ __forceinline__ float mul_rsqrt2(float x) { return fmaf(RSQRT2_HI, x, RSQRT2_LO * x); }
+__device__ __forceinline__ double mul_rsqrt2(double x) { return x * RSQRT2_D; }
+
+// v * e^{i k pi / 4}
+template <typename T> __device__ __forceinline__ T omega_mul(T v, uint32_t k) {
+    T r = v;
+    if (k & 1u) {  // e^{i pi/4} (x + iy) = (x - y)/sqrt2 + i (x + y)/sqrt2
+        r.x = mul_rsqrt2(v.x - v.y);
+        r.y = mul_rsqrt2(v.x + v.y);
+    }
+    const uint32_t q = (k >> 1) & 3u;  // remaining factor i^q
+    T o = r;
+    if (q == 1) { o.x = -r.y; o.y = r.x; }
+    else if (q == 2) { o.x = -r.x; o.y = -r.y; }
+    else if (q == 3) { o.x = r.y; o.y = -r.x; }
+    return o;
+}
+
 __device__ __forceinline__ uint32_t insert_zero(uint32_t p, uint32_t b) {
     const uint32_t lo = (1u << b) - 1u;
     return ((p & ~lo) << 1) | (p & lo);
@@ -70,6 +90,29 @@ __device__ __forceinline__ void tile_gate(T *s, int t, const DGate &g, const T *
                 const uint32_t i0 = insert_zero(p, b), i1 = i0 | bit;
                 s[i0] = cmul(d0, s[i0]);
                 s[i1] = cmul(d1, s[i1]);
+            }
+            break;
+        }
+        case GC_H: {
+            const uint32_t b = g.q0, bit = 1u << b;
+            for (uint32_t p = tid; p < (1u << (t - 1)); p += nt) {
+                const uint32_t i0 = insert_zero(p, b), i1 = i0 | bit;
+                const T a0 = s[i0], a1 = s[i1];
+                T r0, r1;
+                r0.x = mul_rsqrt2(a0.x + a1.x);
+                r0.y = mul_rsqrt2(a0.y + a1.y);
+                r1.x = mul_rsqrt2(a0.x - a1.x);
+                r1.y = mul_rsqrt2(a0.y - a1.y);
+                s[i0] = r0;
+                s[i1] = r1;
+            }
+            break;
+        }
+        case GC_OMEGA: {
+            const uint32_t b = g.q0, bit = 1u << b, k = g.mat;
+            for (uint32_t p = tid; p < (1u << (t - 1)); p += nt) {
+                const uint32_t i1 = insert_zero(p, b) | bit;
+                s[i1] = omega_mul(s[i1], k);
             }
             break;
         }

@@ -277,7 +277,8 @@ def test_tolerable_rate_matches_oracle(arso):
     P1 = ox.one_error_success(a)
     target = 0.5 * (P1 + a["P_R"])
     r = arso.tolerable_rate(cc, crit, target)
-    assert r.mode_used == 0 and abs(r.p - ox.eq5(a, target)) < 1e-9
+    # complex64 scores agree within 1e-5, so Eq. (5) agrees to ~1e-5 relative
+    assert r.mode_used == 0 and abs(r.p - ox.eq5(a, target)) < 1e-4 * ox.eq5(a, target)
     # Monte Carlo branch on common random numbers: identical probes
     r = arso.tolerable_rate(cc, crit, 0.8, n_traj=400, seed=3, mode="mc", rel_tol=0.05)
     o = search.bisect_log(lambda q: search.mc_value(circ, q, 400, 3), 0.8, 1e-6, 1e-1, rel_tol=0.05)
@@ -387,3 +388,16 @@ def test_brickwork24_full_size_launch(arso):
     arso.trajectory_states(cc, errs, 0, 2, states)
     norms = torch.sum(torch.abs(states.to(torch.complex128)) ** 2, dim=1).cpu().numpy()
     assert np.all(np.abs(norms - 1.0) < 1e-4)
+
+
+def test_grover12_reference_state_unbiased(arso):
+    """60,771 gates, ~37k of them H or T: with a rounded 1/sqrt(2) the norm would
+    drift by ~5e-4; the two-float constant keeps complex64 within 1e-5."""
+    circ = C.grover12(0)
+    cc = arso.compile_circuit(circ.n, circ.gates)
+    out = torch.empty(1 << circ.n, dtype=torch.complex64, device="cuda")
+    arso.reference_state(cc, out)
+    got = out.cpu().numpy()
+    psi = statevector.simulate(circ)
+    assert np.max(np.abs(got - psi)) < AMP_TOL_C64
+    assert abs(np.vdot(got, got).real - 1.0) < 1e-5
