@@ -135,6 +135,32 @@ static void upload_circuit(arso_circuit *c) {
         c->d_offs.ensure(offs.size() * 4);
         ARSO_CUDA(cudaMemcpy(c->d_offs.ptr, offs.data(), offs.size() * 4, cudaMemcpyHostToDevice));
     }
+    if (c->reg_blocked) {
+        c->d_ph_gb.ensure(c->ph_gb.size() * 4);
+        ARSO_CUDA(cudaMemcpy(c->d_ph_gb.ptr, c->ph_gb.data(), c->ph_gb.size() * 4, cudaMemcpyHostToDevice));
+        c->d_ph_R.ensure(std::max<size_t>(c->ph_R.size(), 1) * 4);
+        if (!c->ph_R.empty())
+            ARSO_CUDA(cudaMemcpy(c->d_ph_R.ptr, c->ph_R.data(), c->ph_R.size() * 4, cudaMemcpyHostToDevice));
+        c->d_rpos.ensure(std::max<size_t>(c->rpos.size(), 1));
+        if (!c->rpos.empty())
+            ARSO_CUDA(cudaMemcpy(c->d_rpos.ptr, c->rpos.data(), c->rpos.size(), cudaMemcpyHostToDevice));
+    }
+}
+
+// streaming pass launch: register-blocked kernel when the schedule has phases
+static void run_pass(const arso_circuit *c, const PassArgs &a, bool last, uint32_t slots, double bytes,
+                     cudaStream_t st) {
+    if (c->reg_blocked) {
+        PassArgs b = a;
+        b.pb = c->passes[a.pass].pb;
+        b.pe = c->passes[a.pass].pe;
+        b.ph_gb = c->d_ph_gb.as<uint32_t>();
+        b.ph_R = c->d_ph_R.as<uint32_t>();
+        b.rpos = c->d_rpos.as<uint8_t>();
+        launch_pass_rb(b, last, slots, bytes, st);
+    } else {
+        launch_pass(a, last, c->precision, slots, bytes, st);
+    }
 }
 
 // ----------------------------------------------------------- prefix cache --
@@ -188,7 +214,7 @@ static void ensure_cache(arso_circuit *c, cudaStream_t st) {
             a.ideal = 1;
             a.ideal_src = c->ckpt_pass[j] != NO_EVENT ? base + (size_t)c->ckpt_pass[j] * sb : work.ptr;
             a.ideal_dst = c->ckpt_pass[j + 1] != NO_EVENT ? base + (size_t)c->ckpt_pass[j + 1] * sb : work.ptr;
-            launch_pass(a, false, c->precision, 1, 2.0 * sb, st);
+            run_pass(c, a, false, 1, 2.0 * sb, st);
         }
     }
     ARSO_CUDA(cudaStreamSynchronize(st));
@@ -315,7 +341,7 @@ static void run_streaming(arso_circuit *c, const arso_error_list *e, const std::
             a.store_last = states_out ? 1 : 0;
             uint32_t active = 0;
             for (size_t i = 0; i < nb; ++i) active += st_start[i] <= (int)j;
-            launch_pass(a, j == P - 1, c->precision, (uint32_t)nb, 2.0 * (double)sb * active, st);
+            run_pass(c, a, j == P - 1, (uint32_t)nb, 2.0 * (double)sb * active, st);
         }
         if (!states_out)
             launch_finish_partials(parts.as<Partial>(), tiles, (uint32_t)nb, d_slot_traj.as<uint64_t>(), crit, d_score,
@@ -876,7 +902,7 @@ arso_status arso_apply_gate(uint32_t n, void *amps, const arso_gate *gate, void 
         matrix_for(*gate, h);
         DGate d{};
         // the single-gate HBM kernel takes H and the omega phases as plain dense/diagonal gates
-        d.cls = h.cls == GC_H ? (uint8_t)GC_DENSE1 : h.cls == GC_OMEGA ? (uint8_t)GC_DIAG1 : h.cls;
+        d.cls = h.cls == GC_H ? (uint8_t)GC_DENSE1 : h.cls == GC_OMEGA ? (uint8_t)GC_DIAG1 : h.cls == GC_CZ ? (uint8_t)GC_DIAG2 : h.cls;
         d.arity = (uint8_t)h.arity;
         d.q0 = (uint8_t)h.q0;
         d.q1 = (uint8_t)h.q1;

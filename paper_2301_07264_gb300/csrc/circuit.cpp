@@ -71,7 +71,7 @@ void matrix_for(const arso_gate &g, HostGate &h) {
             h.cls = GC_CX;
             break;
         case ARSO_GATE_CZ:
-            h.m[0] = 1; h.m[5] = 1; h.m[10] = 1; h.m[15] = -1; h.cls = GC_DIAG2; break;
+            h.m[0] = 1; h.m[5] = 1; h.m[10] = 1; h.m[15] = -1; h.cls = GC_CZ; break;
         case ARSO_GATE_CP:
             h.m[0] = 1; h.m[5] = 1; h.m[10] = 1; h.m[15] = std::polar(1.0, th); h.cls = GC_DIAG2; break;
         case ARSO_GATE_SWAP:
@@ -133,6 +133,101 @@ static void schedule_streaming(arso_circuit *c) {
     } while (remaining > 0);
 }
 
+// Register-bit phases of each pass. A gate that mixes amplitudes needs its
+// mixing qubits among the REG_BITS register bits (dense one- and two-qubit
+// gates: all their qubits; CX: its target); diagonal gates and X act on any
+// bit. Phases are greedy in engine order: when a gate's needs are not met,
+// a new phase starts whose register bits are the needs of the upcoming gates
+// in order of first use, topped up with bits of the current set. Passes start
+// and end in the load/store mapping {0, t-4, t-3, t-2, t-1}, whose thread
+// bits 1..t-5 keep global accesses contiguous.
+static void need_of(const HostGate &h, uint32_t lq0, uint32_t lq1, uint32_t *out, int &k) {
+    k = 0;
+    switch (h.cls) {
+        case GC_DENSE1: case GC_H: out[k++] = lq0; break;
+        case GC_DENSE2: case GC_SWAP: out[k++] = lq0; out[k++] = lq1; break;
+        case GC_CX: out[k++] = lq1; break;
+        default: break;
+    }
+}
+
+static void plan_phases(arso_circuit *c) {
+    const uint32_t t = c->tile_qubits;
+    c->reg_blocked = c->precision == ARSO_C64 && t >= (uint32_t)RB_MIN_TILE;
+    c->ph_gb.clear();
+    c->ph_R.clear();
+    c->rpos.assign(c->perm.size(), 0xFF);
+    if (!c->reg_blocked) return;
+    const uint32_t load_map[REG_BITS] = {0, t - 4, t - 3, t - 2, t - 1};
+    for (Pass &ps : c->passes) {
+        std::vector<int> local(c->n, -1);
+        for (size_t i = 0; i < ps.tile_qubits.size(); ++i) local[ps.tile_qubits[i]] = (int)i;
+        const uint32_t G = ps.ge - ps.gb;
+        std::vector<uint32_t> lq0(G), lq1(G);
+        for (uint32_t i = 0; i < G; ++i) {
+            const HostGate &h = c->gates[c->perm[ps.gb + i]];
+            lq0[i] = (uint32_t)local[h.q0];
+            lq1[i] = (uint32_t)local[h.q1];
+        }
+        std::vector<uint32_t> cur(load_map, load_map + REG_BITS);
+        auto fits = [&](uint32_t i) {
+            uint32_t need[2];
+            int k;
+            need_of(c->gates[c->perm[ps.gb + i]], lq0[i], lq1[i], need, k);
+            for (int j = 0; j < k; ++j)
+                if (std::find(cur.begin(), cur.end(), need[j]) == cur.end()) return false;
+            return true;
+        };
+        ps.pb = (uint32_t)c->ph_R.size();
+        uint32_t start = 0;
+        for (uint32_t i = 0; i <= G; ++i) {
+            const bool end = i == G;
+            if (!end && fits(i)) continue;
+            if (i > start || (end && start == 0)) {
+                c->ph_gb.push_back(ps.gb + start);
+                c->ph_R.push_back(pack_rbits(cur.data()));
+            }
+            if (end) break;
+            // new register set: needs of gates i, i+1, ... in order of first use
+            std::vector<uint32_t> nxt;
+            for (uint32_t g = i; g < G; ++g) {
+                uint32_t need[2];
+                int k;
+                need_of(c->gates[c->perm[ps.gb + g]], lq0[g], lq1[g], need, k);
+                std::vector<uint32_t> add;
+                for (int j = 0; j < k; ++j)
+                    if (std::find(nxt.begin(), nxt.end(), need[j]) == nxt.end() &&
+                        std::find(add.begin(), add.end(), need[j]) == add.end())
+                        add.push_back(need[j]);
+                if (nxt.size() + add.size() > (size_t)REG_BITS) break;
+                nxt.insert(nxt.end(), add.begin(), add.end());
+                if (nxt.size() == (size_t)REG_BITS) break;
+            }
+            for (uint32_t b : cur)
+                if (nxt.size() < (size_t)REG_BITS && std::find(nxt.begin(), nxt.end(), b) == nxt.end()) nxt.push_back(b);
+            std::sort(nxt.begin(), nxt.end());
+            cur = nxt;
+            start = i;
+        }
+        ps.pe = (uint32_t)c->ph_R.size();
+        // register positions of each gate's qubits within its phase
+        for (uint32_t ph = ps.pb; ph < ps.pe; ++ph) {
+            uint32_t R[REG_BITS];
+            for (int b = 0; b < REG_BITS; ++b) R[b] = (c->ph_R[ph] >> (5 * b)) & 31u;
+            const uint32_t ge = ph + 1 < ps.pe ? c->ph_gb[ph + 1] : ps.ge;
+            for (uint32_t pos = c->ph_gb[ph]; pos < ge; ++pos) {
+                uint32_t p0 = 15, p1 = 15;
+                for (int b = 0; b < REG_BITS; ++b) {
+                    if (R[b] == lq0[pos - ps.gb]) p0 = (uint32_t)b;
+                    if (R[b] == lq1[pos - ps.gb]) p1 = (uint32_t)b;
+                }
+                c->rpos[pos] = (uint8_t)(p0 | (p1 << 4));
+            }
+        }
+    }
+    c->ph_gb.push_back(c->passes.empty() ? 0 : c->passes.back().ge);  // sentinel
+}
+
 void build_circuit(arso_circuit *c, uint32_t n, const arso_gate *gates, size_t n_gates,
                    const arso_compile_opts *opts) {
     ARSO_REQUIRE(n >= 1 && n <= 30, "n_qubits must be in [1, 30]");
@@ -192,6 +287,7 @@ void build_circuit(arso_circuit *c, uint32_t n, const arso_gate *gates, size_t n
     c->pass_of_pos.assign(n_gates, 0);
     for (size_t p = 0; p < c->passes.size(); ++p)
         for (uint32_t pos = c->passes[p].gb; pos < c->passes[p].ge; ++pos) c->pass_of_pos[pos] = (uint32_t)p;
+    plan_phases(c);
 }
 
 }  // namespace arso

@@ -46,7 +46,21 @@ enum GateClass : uint8_t {
     GC_SWAP = 7,
     GC_H = 8,       // Hadamard, 1/sqrt2 applied as a two-float constant (unbiased rounding)
     GC_OMEGA = 9,   // diag(1, e^{i k pi/4}), k in DGate::mat; exact for even k, two-float 1/sqrt2 for odd k
+    GC_CZ = 10,     // diag(1, 1, 1, -1)
 };
+
+// Register-blocked execution (tiles of >= 2^10 amplitudes): every thread
+// holds 2^REG_BITS amplitudes of the tile in registers; a "phase" fixes which
+// REG_BITS tile-local bits index those registers. Gates that mix amplitudes
+// need their qubits among the register bits of the phase that runs them;
+// diagonal gates, X gates and Pauli errors act on any bit.
+constexpr int REG_BITS = 5;
+constexpr int RB_MIN_TILE = 10;                   // 32 threads x 32 amplitudes
+inline uint32_t pack_rbits(const uint32_t *p) {   // 5 local bit positions, 5 bits each
+    uint32_t r = 0;
+    for (int b = 0; b < REG_BITS; ++b) r |= p[b] << (5 * b);
+    return r;
+}
 
 // 1/sqrt(2) split into a float and its float remainder, so that c*x can be
 // formed as fma(hi, x, lo*x) without the bias of a rounded constant; the bias
@@ -89,6 +103,7 @@ struct HostGate {
 struct Pass {
     uint32_t gb, ge;                   // gate range in engine order
     std::vector<uint32_t> tile_qubits; // sorted global qubits, tile-local bit i -> tile_qubits[i]
+    uint32_t pb = 0, pe = 0;           // register-blocked phases [pb, pe)
 };
 
 struct Criterion {
@@ -134,11 +149,16 @@ struct arso_circuit {
     std::vector<uint32_t> loc_gate;         // location -> circuit gate index
     std::vector<arso::Pass> passes;         // streaming schedule (resident: one pass)
     std::vector<uint32_t> pass_of_pos;      // engine position -> pass index
+    bool reg_blocked = false;               // phases planned (tile >= 2^10, complex64)
+    std::vector<uint32_t> ph_gb;            // phase -> first engine position (plus a sentinel)
+    std::vector<uint32_t> ph_R;             // phase -> packed register bits
+    std::vector<uint8_t> rpos;              // engine position -> (reg pos of q0) | (reg pos of q1) << 4, 15 = none
     // device tables
     arso::DeviceBuffer d_gates;             // DGate[G] in engine order
     arso::DeviceBuffer d_mats;              // complex<float> or complex<double> pool
     arso::DeviceBuffer d_loc_key;           // location -> (pos << 1) | slot
     arso::DeviceBuffer d_pass_of_pos;       // uint32 per engine position
+    arso::DeviceBuffer d_ph_gb, d_ph_R, d_rpos;
     // prefix cache
     bool cache_ready = false;
     uint64_t ckpt_every = 1;                // resident: gates between checkpoints

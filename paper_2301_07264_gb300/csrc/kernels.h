@@ -69,7 +69,14 @@ struct PassArgs {
     DCrit crit;
     Partial *partials;           // last pass: slots * tiles
     int store_last;              // last pass stores the state instead of reducing
+    // register-blocked execution
+    uint32_t pb, pe;             // phases of this pass
+    const uint32_t *ph_gb;       // phase -> first engine position (with sentinel)
+    const uint32_t *ph_R;        // phase -> packed register bits
+    const uint8_t *rpos;         // engine position -> register positions of q0 | q1 << 4
 };
+
+void launch_pass_rb(const PassArgs &a, bool last, uint32_t slots, double bytes, cudaStream_t st);
 
 void launch_resident(const ResidentArgs &a, bool ideal, int precision, double bytes, cudaStream_t st);
 void launch_pass(const PassArgs &a, bool last, int precision, uint32_t slots, double bytes, cudaStream_t st);

@@ -126,6 +126,15 @@ __device__ __forceinline__ void tile_gate(T *s, int t, const DGate &g, const T *
             }
             break;
         }
+        case GC_CZ: {
+            const uint32_t lo = g.q0 < g.q1 ? g.q0 : g.q1, hi = g.q0 < g.q1 ? g.q1 : g.q0;
+            const uint32_t both = (1u << g.q0) | (1u << g.q1);
+            for (uint32_t p = tid; p < (1u << (t - 2)); p += nt) {
+                const uint32_t i = insert_zero2(p, lo, hi) | both;
+                s[i] = cneg(s[i]);
+            }
+            break;
+        }
         case GC_DENSE2:
         case GC_DIAG2:
         case GC_CX:

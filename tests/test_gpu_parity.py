@@ -139,6 +139,20 @@ def test_streaming_amplitudes(arso, n, G, tile, low, seed):
         assert np.max(np.abs(got[t] - statevector.simulate(circ, ev))) < AMP_TOL_C64, t
 
 
+@pytest.mark.parametrize("tile,seed", [(10, 11), (11, 12), (13, 13)])
+def test_register_blocked_many_errors(arso, tile, seed):
+    """Dense error lists: X/Y errors become index masks that later gates
+    (dense, CX, CZ, diagonal, SWAP, U2) must see through."""
+    circ = C.random_circuit(15, 250, seed, two_qubit_frac=0.5)
+    rng = np.random.default_rng(seed)
+    lists = _random_error_lists(circ, 6, rng, max_err=40)
+    cc = arso.compile_circuit(15, circ.gates, tile_qubits=tile)
+    errs = arso.error_list_from_host(cc, lists)
+    got = gpu_states(arso, circ, cc, errs, 0, len(lists))
+    for t, ev in enumerate(lists):
+        assert np.max(np.abs(got[t] - statevector.simulate(circ, ev))) < AMP_TOL_C64, t
+
+
 def test_streaming_prefix_cache_subset(arso):
     # a cache budget that cannot hold every pass boundary forces restarts from
     # an earlier cached boundary
@@ -243,10 +257,14 @@ def test_qft4_config_full_parity(arso):
     arso.run_trajectories(cc, errs, crit, score, flags)
     o_s, o_f, _ = montecarlo.run_trajectories(circ, 0, 0, 1000, 1e-3 / 3, 1e-3 / 3, 1e-3 / 3)
     assert np.max(np.abs(score - o_s)) < 1e-12
-    assert np.array_equal(flags.astype(bool), o_f)
+    # some single errors leave the fidelity at exactly 1/2 = threshold; there the
+    # flag depends on the last rounding, so only scores away from it are compared
+    away = np.abs(o_s - crit.threshold) > 1e-9
+    assert away.sum() > 900
+    assert np.array_equal(flags.astype(bool)[away], o_f[away])
     r = arso.success_prob(cc, crit, 1e-3, mode="mc", n_traj=1000, seed=0)
     agg = montecarlo.aggregate(o_s, o_f)
-    assert abs(r.pass_frac - agg["pass_frac"]) < 1e-12
+    assert abs(r.pass_frac - agg["pass_frac"]) <= (~away).sum() / 1000 + 1e-12
     assert abs(r.mean - agg["mean"]) < 1e-12
     assert abs(r.stderr_value - agg["stderr_pass"]) < 1e-9
 
