@@ -186,7 +186,8 @@ def _config(circ, args, tile=None, passes=None):
     return {"workload": "brickwork24_depth40_p1e-4_1e-3", "n_qubits": circ.n, "depth": 40, "G": circ.G,
             "L": circ.L, "p": list(P_RATES), "trajectories_per_p": TRAJ_PER_P,
             "traj_per_step": args.traj_per_step, "criterion": "fidelity >= 0.9 (pass fraction)",
-            "prefix_reuse": True, "tile_qubits": tile, "passes": passes,
+            "prefix_reuse": True, "suffix_reuse": not getattr(args, "no_suffix", False),
+            "tile_qubits": tile, "passes": passes,
             "l2": "inputs larger than L2: every trajectory state is 128 MiB (> 126 MiB L2)"}
 
 
@@ -211,7 +212,8 @@ def run_ours(args):
     circ = C.brickwork24(0)
     crit = arso.make_criterion(circ.criterion)
     cc = arso.compile_circuit(circ.n, circ.gates, tile_qubits=args.tile,
-                              cache_bytes=int(args.cache_gb * (1 << 30)) if args.cache_gb else 0)
+                              cache_bytes=int(args.cache_gb * (1 << 30)) if args.cache_gb else 0,
+                              flags=arso.OPT_NO_SUFFIX_REUSE if args.no_suffix else 0)
     info = cc.info()
     half = args.traj_per_step // len(P_RATES)
     score = {p: torch.empty(half, dtype=torch.float64, device="cuda") for p in P_RATES}
@@ -339,6 +341,8 @@ def main():
     ap.add_argument("--cache-gb", type=float, default=0.0, help="prefix-cache budget (0 = library default)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-suffix", action="store_true",
+                    help="run every trajectory to the end instead of scoring after its last error")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

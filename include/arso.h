@@ -77,7 +77,13 @@ typedef struct {
     uint32_t low_qubits;    /* streaming passes: qubits 0..low-1 are in every tile; 0 = auto */
     uint32_t max_batch;     /* streaming engine: trajectories resident at once; 0 = auto */
     uint64_t cache_bytes;   /* budget for cached error-free prefix states; 0 = auto */
+    uint32_t flags;         /* ARSO_OPT_* */
 } arso_compile_opts;
+/* Fidelity scores are taken right after a trajectory's last error, against the
+ * cached error-free state at that pass boundary: the error-free suffix W is
+ * unitary and common to both states, so <W a|W b> = <a|b> (exact). This flag
+ * turns that off (every trajectory then runs to the end; for comparisons). */
+enum { ARSO_OPT_NO_SUFFIX_REUSE = 1 };
 
 typedef struct arso_circuit arso_circuit;
 typedef struct arso_error_list arso_error_list;

@@ -49,7 +49,7 @@ class Gate(C.Structure):
 
 class CompileOpts(C.Structure):
     _fields_ = [("precision", C.c_uint32), ("tile_qubits", C.c_uint32), ("low_qubits", C.c_uint32),
-                ("max_batch", C.c_uint32), ("cache_bytes", C.c_uint64)]
+                ("max_batch", C.c_uint32), ("cache_bytes", C.c_uint64), ("flags", C.c_uint32)]
 
 
 class CircuitInfo(C.Structure):
@@ -195,9 +195,12 @@ def _gates_array(gates):
     return arr, keep
 
 
-def compile_circuit(n, gates, precision=C64, tile_qubits=0, low_qubits=0, max_batch=0, cache_bytes=0):
+OPT_NO_SUFFIX_REUSE = 1
+
+
+def compile_circuit(n, gates, precision=C64, tile_qubits=0, low_qubits=0, max_batch=0, cache_bytes=0, flags=0):
     arr, keep = _gates_array(gates)
-    opts = CompileOpts(precision, tile_qubits, low_qubits, max_batch, cache_bytes)
+    opts = CompileOpts(precision, tile_qubits, low_qubits, max_batch, cache_bytes, flags)
     h = _vp()
     _check(lib.arso_compile_circuit(n, arr, len(gates), C.byref(opts), C.byref(h)))
     del keep
@@ -207,7 +210,7 @@ def compile_circuit(n, gates, precision=C64, tile_qubits=0, low_qubits=0, max_ba
 def plan_schedule(n, gates, precision=C64, tile_qubits=0, low_qubits=0):
     """Host-only: (perm, pass_begin, tile_masks) of the fused pass schedule."""
     arr, keep = _gates_array(gates)
-    opts = CompileOpts(precision, tile_qubits, low_qubits, 0, 0)
+    opts = CompileOpts(precision, tile_qubits, low_qubits, 0, 0, 0)
     P = C.c_uint32()
     _check(lib.arso_plan_schedule(n, arr, len(gates), C.byref(opts), C.byref(P), 0, None, None, None))
     perm = np.zeros(max(len(gates), 1), dtype=np.uint32)

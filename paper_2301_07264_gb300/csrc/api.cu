@@ -144,7 +144,36 @@ static void upload_circuit(arso_circuit *c) {
         c->d_rpos.ensure(std::max<size_t>(c->rpos.size(), 1));
         if (!c->rpos.empty())
             ARSO_CUDA(cudaMemcpy(c->d_rpos.ptr, c->rpos.data(), c->rpos.size(), cudaMemcpyHostToDevice));
+        c->d_phase_of_pos.ensure(std::max<size_t>(c->phase_of_pos.size(), 1) * 4);
+        if (!c->phase_of_pos.empty())
+            ARSO_CUDA(cudaMemcpy(c->d_phase_of_pos.ptr, c->phase_of_pos.data(), c->phase_of_pos.size() * 4,
+                                 cudaMemcpyHostToDevice));
     }
+}
+
+// resident arguments common to every launch
+static ResidentArgs resident_args(const arso_circuit *c) {
+    ResidentArgs a{};
+    a.n = (int)c->n;
+    a.G = (uint32_t)c->gates.size();
+    a.gates = c->d_gates.as<DGate>();
+    a.mats = c->d_mats.ptr;
+    a.cache = c->d_cache.ptr;
+    a.ckpt_every = c->ckpt_every;
+    a.n_ckpt = c->n_ckpt;
+    if (c->reg_blocked) {
+        a.n_phases = (uint32_t)c->ph_R.size();
+        a.ph_gb = c->d_ph_gb.as<uint32_t>();
+        a.ph_R = c->d_ph_R.as<uint32_t>();
+        a.rpos = c->d_rpos.as<uint8_t>();
+        a.phase_of_pos = c->d_phase_of_pos.as<uint32_t>();
+    }
+    return a;
+}
+
+static void launch_resident_any(const arso_circuit *c, const ResidentArgs &a, int mode, double bytes, cudaStream_t st) {
+    if (c->reg_blocked) launch_resident_rb(a, mode, bytes, st);
+    else launch_resident(a, mode == 2, c->precision, bytes, st);
 }
 
 // streaming pass launch: register-blocked kernel when the schedule has phases
@@ -169,20 +198,14 @@ static void ensure_cache(arso_circuit *c, cudaStream_t st) {
     const size_t sb = c->state_bytes();
     const uint64_t G = c->gates.size();
     if (c->engine == 0) {
+        // checkpoints every `every` gates (or phases when register-blocked)
+        const uint64_t units = c->reg_blocked ? c->ph_R.size() : G;
         const uint64_t budget = std::min<uint64_t>(c->cache_budget, 512ull << 20);
-        uint64_t every = std::max<uint64_t>(1, ((G + 1) * sb + budget - 1) / budget);
+        uint64_t every = std::max<uint64_t>(1, ((units + 1) * sb + budget - 1) / budget);
         c->ckpt_every = every;
-        c->n_ckpt = (uint32_t)(G / every + 1 + (G % every ? 1 : 0));
+        c->n_ckpt = (uint32_t)(units / every + 1 + (units % every ? 1 : 0));
         c->d_cache.ensure((size_t)c->n_ckpt * sb);
-        ResidentArgs a{};
-        a.n = (int)c->n;
-        a.G = (uint32_t)G;
-        a.gates = c->d_gates.as<DGate>();
-        a.mats = c->d_mats.ptr;
-        a.cache = c->d_cache.ptr;
-        a.ckpt_every = every;
-        a.n_ckpt = c->n_ckpt;
-        launch_resident(a, true, c->precision, (double)c->n_ckpt * sb, st);
+        launch_resident_any(c, resident_args(c), 2, (double)c->n_ckpt * sb, st);
     } else {
         const uint32_t P = (uint32_t)c->passes.size();
         // boundaries 0..P; cache every s-th boundary and the last one
@@ -287,52 +310,70 @@ static PassArgs pass_args(const arso_circuit *c, uint32_t j) {
 // Streaming engine over trajectories `ids` of the error list. states_out
 // (non-null) receives final states in the order of `ids` instead of scores.
 static void run_streaming(arso_circuit *c, const arso_error_list *e, const std::vector<uint64_t> &ids,
-                          const std::vector<uint32_t> &first_pos, const DCrit &crit, double *d_score,
-                          uint8_t *d_pass, void *states_out, cudaStream_t st) {
+                          const std::vector<uint32_t> &first_pos, const std::vector<uint32_t> &last_pos,
+                          const DCrit &crit, double *d_score, uint8_t *d_pass, void *states_out, cudaStream_t st) {
     if (ids.empty()) return;
     const uint32_t P = (uint32_t)c->passes.size();
     const size_t sb = c->state_bytes();
     const uint32_t tiles = 1u << (c->n - c->tile_qubits);
-    // start boundary: the last cached boundary at or before the first error's pass
-    std::vector<int> start(ids.size());
+    // start: the last cached boundary at or before the first error's pass.
+    // end: the pass whose output is scored. Fidelity is invariant under the
+    // error-free suffix W that follows the last error (<W a|W b> = <a|b>), so
+    // the trajectory is scored right after its last error's pass against the
+    // cached error-free state at that boundary (the first cached one after
+    // it); other criteria need the final state (end = P - 1).
+    const bool suffix = !states_out && crit.kind == ARSO_CRIT_FIDELITY && !(c->flags & ARSO_OPT_NO_SUFFIX_REUSE);
+    std::vector<int> start(ids.size()), end(ids.size());
     for (size_t i = 0; i < ids.size(); ++i) {
         uint32_t fp = first_pos[i] == NO_EVENT ? P - 1 : c->pass_of_pos[first_pos[i]];
         while (c->ckpt_pass[fp] == NO_EVENT) --fp;
         start[i] = (int)fp;
+        uint32_t lp = P - 1;
+        if (suffix && last_pos[i] != NO_EVENT) {
+            lp = c->pass_of_pos[last_pos[i]];
+            while (c->ckpt_pass[lp + 1] == NO_EVENT) ++lp;
+        }
+        end[i] = (int)lp;
     }
     std::vector<size_t> order(ids.size());
     std::iota(order.begin(), order.end(), 0);
     if (!states_out)
-        std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return start[x] > start[y]; });
+        std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+            return start[x] != start[y] ? start[x] < start[y] : end[x] < end[y];
+        });
     uint64_t B = c->max_batch ? c->max_batch : std::max<uint64_t>(1, (8ull << 30) / sb);
     B = std::min<uint64_t>(B, std::min<uint64_t>(ids.size(), 65535));
     if (states_out) B = ids.size();
     ARSO_REQUIRE(B <= 65535, "too many states requested at once");
     Scratch work(st, states_out ? 0 : B * sb);
     Scratch parts(st, states_out ? 0 : B * tiles * sizeof(Partial));
-    Scratch d_slot_traj(st, B * 8), d_start(st, B * 4);
+    Scratch d_slot_traj(st, B * 8), d_start(st, B * 4), d_end(st, B * 4);
     std::vector<uint32_t> cslot(c->ckpt_pass.begin(), c->ckpt_pass.end());
     Scratch d_cslot(st, cslot.size() * 4);
     h2d(d_cslot.ptr, cslot, st);
     for (size_t b0 = 0; b0 < ids.size(); b0 += B) {
         const size_t nb = std::min<size_t>(B, ids.size() - b0);
         std::vector<uint64_t> st_traj(nb);
-        std::vector<int> st_start(nb);
-        int jmin = (int)P;
+        std::vector<int> st_start(nb), st_end(nb);
+        int jmin = (int)P, jmax = 0;
         for (size_t i = 0; i < nb; ++i) {
             st_traj[i] = ids[order[b0 + i]];
             st_start[i] = start[order[b0 + i]];
+            st_end[i] = end[order[b0 + i]];
             jmin = std::min(jmin, st_start[i]);
+            jmax = std::max(jmax, st_end[i]);
         }
         h2d(d_slot_traj.ptr, st_traj, st);
         h2d(d_start.ptr, st_start, st);
-        for (uint32_t j = (uint32_t)jmin; j < P; ++j) {
+        h2d(d_end.ptr, st_end, st);
+        for (uint32_t j = (uint32_t)jmin; j <= (uint32_t)jmax; ++j) {
             PassArgs a = pass_args(c, j);
             a.cache = c->d_cache.ptr;
             a.cache_slot = d_cslot.as<uint32_t>();
             a.ref_slot = c->n_ckpt - 1;
             a.work = states_out ? states_out : work.ptr;
             a.start_pass = d_start.as<int>();
+            a.end_pass = d_end.as<int>();
             a.slot_traj = d_slot_traj.as<uint64_t>();
             a.offsets = e->d_offsets.as<uint64_t>();
             a.keys = e->d_key.as<uint32_t>();
@@ -340,7 +381,7 @@ static void run_streaming(arso_circuit *c, const arso_error_list *e, const std::
             a.partials = parts.as<Partial>();
             a.store_last = states_out ? 1 : 0;
             uint32_t active = 0;
-            for (size_t i = 0; i < nb; ++i) active += st_start[i] <= (int)j;
+            for (size_t i = 0; i < nb; ++i) active += st_start[i] <= (int)j && (int)j <= st_end[i];
             run_pass(c, a, j == P - 1, (uint32_t)nb, 2.0 * (double)sb * active, st);
         }
         if (!states_out)
@@ -357,14 +398,7 @@ static void run_all(arso_circuit *c, const arso_error_list *e, const DevCrit &dc
     score_into(ref_state_ptr(c), ref_state_ptr(c), (int)c->n, c->precision, dc.d, ref.as<double>(), st);
     if (e->n_traj == 0) return;
     if (c->engine == 0) {
-        ResidentArgs a{};
-        a.n = (int)c->n;
-        a.G = (uint32_t)c->gates.size();
-        a.gates = c->d_gates.as<DGate>();
-        a.mats = c->d_mats.ptr;
-        a.cache = c->d_cache.ptr;
-        a.ckpt_every = c->ckpt_every;
-        a.n_ckpt = c->n_ckpt;
+        ResidentArgs a = resident_args(c);
         a.first_traj = 0;
         a.count = e->n_traj;
         a.offsets = e->d_offsets.as<uint64_t>();
@@ -374,19 +408,20 @@ static void run_all(arso_circuit *c, const arso_error_list *e, const DevCrit &dc
         a.ref_score = ref.as<double>();
         a.score = d_score;
         a.pass_flags = d_pass;
-        launch_resident(a, false, c->precision, (double)e->n_traj * c->state_bytes(), st);
+        launch_resident_any(c, a, 0, (double)e->n_traj * c->state_bytes(), st);
         ARSO_CUDA(cudaStreamSynchronize(st));
         return;
     }
     launch_fill_error_free(e->d_first.as<uint32_t>(), e->n_traj, ref.as<double>(), dc.d.threshold, d_score, d_pass, st);
-    std::vector<uint32_t> first(e->n_traj);
+    std::vector<uint32_t> first(e->n_traj), last(e->n_traj);
     copy_d2h(first.data(), e->d_first.ptr, e->n_traj * 4, st);
+    copy_d2h(last.data(), e->d_last.ptr, e->n_traj * 4, st);
     ARSO_CUDA(cudaStreamSynchronize(st));
     std::vector<uint64_t> ids;
-    std::vector<uint32_t> fp;
+    std::vector<uint32_t> fp, lp;
     for (uint64_t i = 0; i < e->n_traj; ++i)
-        if (first[i] != NO_EVENT) ids.push_back(i), fp.push_back(first[i]);
-    run_streaming(c, e, ids, fp, dc.d, d_score, d_pass, nullptr, st);
+        if (first[i] != NO_EVENT) ids.push_back(i), fp.push_back(first[i]), lp.push_back(last[i]);
+    run_streaming(c, e, ids, fp, lp, dc.d, d_score, d_pass, nullptr, st);
     ARSO_CUDA(cudaStreamSynchronize(st));
 }
 
@@ -397,6 +432,7 @@ static arso_error_list *new_list(const arso_circuit *c, uint64_t n_traj) {
     e->n_traj = n_traj;
     e->d_offsets.ensure((n_traj + 1) * 8);
     e->d_first.ensure(std::max<uint64_t>(n_traj, 1) * 4);
+    e->d_last.ensure(std::max<uint64_t>(n_traj, 1) * 4);
     return e;
 }
 
@@ -404,7 +440,8 @@ static void finish_list(const arso_circuit *c, arso_error_list *e, cudaStream_t 
     bool identity = true;
     for (size_t i = 0; i < c->perm.size() && identity; ++i) identity = c->perm[i] == i;
     if (!identity) launch_sort_keys(e->d_offsets.as<uint64_t>(), e->n_traj, e->d_key.as<uint32_t>(), st);
-    launch_first_event(e->d_offsets.as<uint64_t>(), e->n_traj, e->d_key.as<uint32_t>(), e->d_first.as<uint32_t>(), st);
+    launch_first_event(e->d_offsets.as<uint64_t>(), e->n_traj, e->d_key.as<uint32_t>(), e->d_first.as<uint32_t>(),
+                       e->d_last.as<uint32_t>(), st);
     ARSO_CUDA(cudaStreamSynchronize(st));
 }
 
@@ -721,21 +758,14 @@ arso_status arso_trajectory_states(const arso_circuit *cc, const arso_error_list
         ensure_cache(c, st);
         if (!count) return;
         if (c->engine == 0) {
-            ResidentArgs a{};
-            a.n = (int)c->n;
-            a.G = (uint32_t)c->gates.size();
-            a.gates = c->d_gates.as<DGate>();
-            a.mats = c->d_mats.ptr;
-            a.cache = c->d_cache.ptr;
-            a.ckpt_every = c->ckpt_every;
-            a.n_ckpt = c->n_ckpt;
+            ResidentArgs a = resident_args(c);
             a.first_traj = first;
             a.count = count;
             a.offsets = e->d_offsets.as<uint64_t>();
             a.keys = e->d_key.as<uint32_t>();
             a.first = e->d_first.as<uint32_t>();
             a.states_out = amps_out;
-            launch_resident(a, false, c->precision, 2.0 * (double)count * c->state_bytes(), st);
+            launch_resident_any(c, a, 1, 2.0 * (double)count * c->state_bytes(), st);
         } else {
             std::vector<uint32_t> fp(count);
             copy_d2h(fp.data(), e->d_first.as<uint32_t>() + first, count * 4, st);
@@ -743,7 +773,7 @@ arso_status arso_trajectory_states(const arso_circuit *cc, const arso_error_list
             std::vector<uint64_t> ids(count);
             for (uint64_t i = 0; i < count; ++i) ids[i] = first + i;
             DCrit none{};
-            run_streaming(c, e, ids, fp, none, nullptr, nullptr, amps_out, st);
+            run_streaming(c, e, ids, fp, fp, none, nullptr, nullptr, amps_out, st);
         }
         ARSO_CUDA(cudaStreamSynchronize(st));
     });

@@ -145,7 +145,7 @@ static void need_of(const HostGate &h, uint32_t lq0, uint32_t lq1, uint32_t *out
     k = 0;
     switch (h.cls) {
         case GC_DENSE1: case GC_H: out[k++] = lq0; break;
-        case GC_DENSE2: case GC_SWAP: out[k++] = lq0; out[k++] = lq1; break;
+        // dense two-qubit gates and SWAP run through shared memory: no register needs
         case GC_CX: out[k++] = lq1; break;
         default: break;
     }
@@ -226,6 +226,9 @@ static void plan_phases(arso_circuit *c) {
         }
     }
     c->ph_gb.push_back(c->passes.empty() ? 0 : c->passes.back().ge);  // sentinel
+    c->phase_of_pos.assign(c->perm.size(), 0);
+    for (size_t ph = 0; ph + 1 < c->ph_gb.size(); ++ph)
+        for (uint32_t pos = c->ph_gb[ph]; pos < c->ph_gb[ph + 1]; ++pos) c->phase_of_pos[pos] = (uint32_t)ph;
 }
 
 void build_circuit(arso_circuit *c, uint32_t n, const arso_gate *gates, size_t n_gates,
@@ -262,6 +265,7 @@ void build_circuit(arso_circuit *c, uint32_t n, const arso_gate *gates, size_t n
     uint32_t tq = opts && opts->tile_qubits ? opts->tile_qubits : (c->precision == ARSO_C128 ? 12u : 13u);
     uint32_t lq = opts && opts->low_qubits ? opts->low_qubits : 4u;
     c->max_batch = opts ? opts->max_batch : 0;
+    c->flags = opts ? opts->flags : 0;
     c->cache_budget = opts && opts->cache_bytes ? opts->cache_bytes : (uint64_t)16 << 30;
     if (c->engine == 0) {
         c->tile_qubits = n;

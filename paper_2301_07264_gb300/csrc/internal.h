@@ -140,7 +140,7 @@ struct arso_circuit {
     uint32_t n = 0;
     int precision = ARSO_C64;
     int engine = 0;  // 0 resident, 1 streaming
-    uint32_t tile_qubits = 0, low_qubits = 0, max_batch = 0;
+    uint32_t tile_qubits = 0, low_qubits = 0, max_batch = 0, flags = 0;
     uint64_t cache_budget = 0;
     std::vector<arso::HostGate> gates;      // circuit order
     uint64_t k = 0, m = 0, L = 0;
@@ -153,12 +153,13 @@ struct arso_circuit {
     std::vector<uint32_t> ph_gb;            // phase -> first engine position (plus a sentinel)
     std::vector<uint32_t> ph_R;             // phase -> packed register bits
     std::vector<uint8_t> rpos;              // engine position -> (reg pos of q0) | (reg pos of q1) << 4, 15 = none
+    std::vector<uint32_t> phase_of_pos;     // engine position -> phase
     // device tables
     arso::DeviceBuffer d_gates;             // DGate[G] in engine order
     arso::DeviceBuffer d_mats;              // complex<float> or complex<double> pool
     arso::DeviceBuffer d_loc_key;           // location -> (pos << 1) | slot
     arso::DeviceBuffer d_pass_of_pos;       // uint32 per engine position
-    arso::DeviceBuffer d_ph_gb, d_ph_R, d_rpos;
+    arso::DeviceBuffer d_ph_gb, d_ph_R, d_rpos, d_phase_of_pos;
     // prefix cache
     bool cache_ready = false;
     uint64_t ckpt_every = 1;                // resident: gates between checkpoints
@@ -177,6 +178,7 @@ struct arso_error_list {
     arso::DeviceBuffer d_loc;      // uint32 (loc << 2) | code, location order
     arso::DeviceBuffer d_key;      // uint32 engine-order keys
     arso::DeviceBuffer d_first;    // uint32 per trajectory: first engine position with an event, or NO_EVENT
+    arso::DeviceBuffer d_last;     // uint32 per trajectory: last engine position with an event, or NO_EVENT
 };
 
 namespace arso {

@@ -43,7 +43,15 @@ struct ResidentArgs {
     double *score;               // device, indexed by trajectory
     uint8_t *pass_flags;         // device or null
     void *states_out;            // non-null: store final states (count * 2^n) instead of scoring
+    // register-blocked execution: checkpoints sit at phase boundaries
+    uint32_t n_phases;
+    const uint32_t *ph_gb, *ph_R;
+    const uint8_t *rpos;
+    const uint32_t *phase_of_pos;  // gate position -> phase
 };
+
+// mode: 0 = score trajectories, 1 = store final states, 2 = error-free run filling the cache
+void launch_resident_rb(const ResidentArgs &a, int mode, double bytes, cudaStream_t st);
 
 struct PassArgs {
     int n, t, c;                 // qubits, tile qubits, contiguous low qubits
@@ -63,6 +71,8 @@ struct PassArgs {
     uint32_t ref_slot;           // cache entry of psi_R
     void *work;                  // slots * 2^n working states
     const int *start_pass;       // per slot
+    const int *end_pass;         // per slot: the pass whose output is scored, against the cached
+                                 // error-free state at the boundary after it (psi_R for the last pass)
     const uint64_t *slot_traj;   // per slot: trajectory index in the error list
     const uint64_t *offsets;
     const uint32_t *keys;
@@ -108,7 +118,7 @@ void launch_keys_from_loc(const uint32_t *ev_loc, uint64_t n_events, const uint3
                           cudaStream_t st);
 void launch_sort_keys(const uint64_t *offsets, uint64_t n_traj, uint32_t *ev_key, cudaStream_t st);
 void launch_first_event(const uint64_t *offsets, uint64_t n_traj, const uint32_t *ev_key, uint32_t *first,
-                        cudaStream_t st);
+                        uint32_t *last, cudaStream_t st);
 void launch_sum_scores(const double *score, const uint8_t *pass_flags, uint64_t n, double *sums3, cudaStream_t st);
 
 }  // namespace arso

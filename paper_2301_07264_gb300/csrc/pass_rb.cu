@@ -53,6 +53,10 @@ __device__ __forceinline__ uint32_t reg_part(int ri, const uint32_t (&r)[REG_BIT
 }
 
 // ------------------------------------------------------- register gates ---
+// Code size matters: the whole phase loop must stay resident in the
+// instruction cache, so only dense one-qubit gates, H and CX are specialised
+// per register position (5 copies each); everything else is position-free.
+
 template <int P>
 __device__ __forceinline__ void rg_dense1(float2 (&v)[32], float2 u00, float2 u01, float2 u10, float2 u11) {
 #pragma unroll
@@ -64,24 +68,17 @@ __device__ __forceinline__ void rg_dense1(float2 (&v)[32], float2 u00, float2 u0
     }
 }
 
-// X H X on the pair: (a0, a1) -> ((a1 - a0)/sqrt2, (a0 + a1)/sqrt2)
-template <int P> __device__ __forceinline__ void rg_hflip(float2 (&v)[32]) {
+// H on register bit P: (a0, a1) -> ((a0 + a1), (a0 - a1)) / sqrt2; with the
+// qubit's mask bit set the stored data sees X H X: ((a1 - a0), (a0 + a1)) / sqrt2.
+template <int P> __device__ __forceinline__ void rg_h(float2 (&v)[32], uint32_t flip) {
 #pragma unroll
     for (int ri = 0; ri < 32; ++ri) {
         if (ri & (1 << P)) continue;
         const float2 a0 = v[ri], a1 = v[ri | (1 << P)];
-        v[ri] = make_float2(mul_rsqrt2(a1.x - a0.x), mul_rsqrt2(a1.y - a0.y));
-        v[ri | (1 << P)] = make_float2(mul_rsqrt2(a0.x + a1.x), mul_rsqrt2(a0.y + a1.y));
-    }
-}
-
-template <int P> __device__ __forceinline__ void rg_h(float2 (&v)[32]) {
-#pragma unroll
-    for (int ri = 0; ri < 32; ++ri) {
-        if (ri & (1 << P)) continue;
-        const float2 a0 = v[ri], a1 = v[ri | (1 << P)];
-        v[ri] = make_float2(mul_rsqrt2(a0.x + a1.x), mul_rsqrt2(a0.y + a1.y));
-        v[ri | (1 << P)] = make_float2(mul_rsqrt2(a0.x - a1.x), mul_rsqrt2(a0.y - a1.y));
+        const float2 s = make_float2(mul_rsqrt2(a0.x + a1.x), mul_rsqrt2(a0.y + a1.y));
+        const float2 d = make_float2(mul_rsqrt2(a0.x - a1.x), mul_rsqrt2(a0.y - a1.y));
+        v[ri] = flip ? cneg(d) : s;
+        v[ri | (1 << P)] = flip ? s : d;
     }
 }
 
@@ -95,25 +92,6 @@ template <int P> __device__ __forceinline__ void rg_cx(float2 (&v)[32], uint32_t
         const float2 a0 = v[ri], a1 = v[ri | (1 << P)];
         v[ri] = ctl ? a1 : a0;
         v[ri | (1 << P)] = ctl ? a0 : a1;
-    }
-}
-
-template <int P0, int P1> __device__ __forceinline__ void rg_dense2(float2 (&v)[32], const float2 (&M)[16]) {
-#pragma unroll
-    for (int ri = 0; ri < 32; ++ri) {
-        if (ri & ((1 << P0) | (1 << P1))) continue;
-        const int ix[4] = {ri, ri | (1 << P0), ri | (1 << P1), ri | (1 << P0) | (1 << P1)};
-        float2 a[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) a[k] = v[ix[k]];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            float2 acc = cmac2(M[4 * k], a[0], M[4 * k + 1], a[1]);
-            const float2 acc2 = cmac2(M[4 * k + 2], a[2], M[4 * k + 3], a[3]);
-            acc.x += acc2.x;
-            acc.y += acc2.y;
-            v[ix[k]] = acc;
-        }
     }
 }
 
@@ -146,31 +124,46 @@ __device__ __forceinline__ void rg_diag1(float2 (&v)[32], const TileCtx &c, uint
     for (int ri = 0; ri < 32; ++ri) v[ri] = cmul(bit_of(ri, pos, mq, th) ? d1 : d0, v[ri]);
 }
 
+// diag(1, e^{i k pi/4}) on tile bit q: branch-free per register
 __device__ __forceinline__ void rg_omega(float2 (&v)[32], const TileCtx &c, uint32_t q, uint32_t k) {
     const uint32_t pos = reg_pos(c, q), mq = (c.m >> q) & 1u, th = ((c.tpart ^ c.m) >> q) & 1u;
-    if (pos >= REG_BITS) {
-        if (th) {
-#pragma unroll
-            for (int ri = 0; ri < 32; ++ri) v[ri] = omega_mul(v[ri], k);
-        }
-        return;
-    }
+    if (pos >= REG_BITS && !th) return;
+    const bool odd = k & 1u;
+    const uint32_t qq = (k >> 1) & 3u;  // remaining factor i^qq
+    const bool sw = qq & 1u, nx = qq == 1u || qq == 2u, ny = qq >= 2u;
 #pragma unroll
     for (int ri = 0; ri < 32; ++ri) {
-        const float2 w = omega_mul(v[ri], k);
-        v[ri] = bit_of(ri, pos, mq, th) ? w : v[ri];
+        const float2 a = v[ri];
+        const float2 r = odd ? make_float2(mul_rsqrt2(a.x - a.y), mul_rsqrt2(a.x + a.y)) : a;
+        float2 o = sw ? make_float2(r.y, r.x) : r;
+        o.x = nx ? -o.x : o.x;
+        o.y = ny ? -o.y : o.y;
+        v[ri] = bit_of(ri, pos, mq, th) ? o : a;
+    }
+}
+
+// Registers whose tile bit q (of the true index) is 1, as a 32-bit mask.
+__device__ __forceinline__ uint32_t reg_pattern(uint32_t pos) {
+    return pos == 0 ? 0xAAAAAAAAu : pos == 1 ? 0xCCCCCCCCu : pos == 2 ? 0xF0F0F0F0u : pos == 3 ? 0xFF00FF00u : 0xFFFF0000u;
+}
+__device__ __forceinline__ uint32_t bit_mask(const TileCtx &c, uint32_t q) {
+    const uint32_t pos = reg_pos(c, q);
+    if (pos < REG_BITS) return ((c.m >> q) & 1u) ? ~reg_pattern(pos) : reg_pattern(pos);
+    return (((c.tpart ^ c.m) >> q) & 1u) ? 0xFFFFFFFFu : 0u;
+}
+// negate the registers selected by mask: flip the sign bits
+__device__ __forceinline__ void negate_masked(float2 (&v)[32], uint32_t mask) {
+#pragma unroll
+    for (int ri = 0; ri < 32; ++ri) {
+        const uint32_t sgn = (mask << (31 - ri)) & 0x80000000u;
+        v[ri].x = __uint_as_float(__float_as_uint(v[ri].x) ^ sgn);
+        v[ri].y = __uint_as_float(__float_as_uint(v[ri].y) ^ sgn);
     }
 }
 
 __device__ __forceinline__ void rg_cz(float2 (&v)[32], const TileCtx &c, uint32_t qa, uint32_t qb) {
-    const uint32_t pa = reg_pos(c, qa), ma = (c.m >> qa) & 1u, ta = ((c.tpart ^ c.m) >> qa) & 1u;
-    const uint32_t pb = reg_pos(c, qb), mb = (c.m >> qb) & 1u, tb = ((c.tpart ^ c.m) >> qb) & 1u;
-    if (pa >= REG_BITS && pb >= REG_BITS && !(ta & tb)) return;
-#pragma unroll
-    for (int ri = 0; ri < 32; ++ri) {
-        const uint32_t s = bit_of(ri, pa, ma, ta) & bit_of(ri, pb, mb, tb);
-        v[ri] = s ? cneg(v[ri]) : v[ri];
-    }
+    const uint32_t mask = bit_mask(c, qa) & bit_mask(c, qb);
+    if (mask) negate_masked(v, mask);
 }
 
 __device__ __forceinline__ void rg_diag2(float2 (&v)[32], const TileCtx &c, uint32_t qa, uint32_t qb,
@@ -190,57 +183,111 @@ __device__ __forceinline__ void rg_diag2(float2 (&v)[32], const TileCtx &c, uint
 // bit q; X -> index mask; Y = i X Z.
 __device__ __forceinline__ void rg_pauli(float2 (&v)[32], TileCtx &c, uint32_t q, uint32_t code) {
     if (code & 2u) {  // Z part (Z or Y): negate where bit q of the true index is 1
-        const uint32_t pos = reg_pos(c, q), mq = (c.m >> q) & 1u, th = ((c.tpart ^ c.m) >> q) & 1u;
-#pragma unroll
-        for (int ri = 0; ri < 32; ++ri) v[ri] = bit_of(ri, pos, mq, th) ? cneg(v[ri]) : v[ri];
+        const uint32_t mask = bit_mask(c, q);
+        if (mask) negate_masked(v, mask);
     }
     if (code & 1u) c.m ^= 1u << q;          // X part (X or Y)
     if (code == 3u) c.gp = (c.gp + 1u) & 3u;  // Y = i X Z
 }
 
-template <int P>
-__device__ __forceinline__ void dispatch_dense1(float2 (&v)[32], const DGate &g, const float2 *__restrict__ M,
-                                                uint32_t flip) {
-    if (g.cls == GC_H) {
-        if (flip) rg_hflip<P>(v);
-        else rg_h<P>(v);
-        return;
-    }
-    if (!flip) rg_dense1<P>(v, M[0], M[1], M[2], M[3]);
-    else rg_dense1<P>(v, M[3], M[2], M[1], M[0]);
+// stored index -> tile-local index bits for the load/store mapping
+__device__ __forceinline__ void set_phase(TileCtx &c, uint32_t packed, int t) {
+    unpack_r(packed, c.r);
+    c.rmask = 0;
+#pragma unroll
+    for (int b = 0; b < REG_BITS; ++b) c.rmask |= 1u << c.r[b];
+    c.tpart = thread_part(threadIdx.x, c.rmask, t);
 }
 
-template <int P0, int P1>
-__device__ __forceinline__ void dispatch_dense2_pp(float2 (&v)[32], const float2 (&M)[16]) {
-    rg_dense2<P0, P1>(v, M);
+// The swizzle is linear over XOR, so the shared-memory slot of register ri is
+// swz(tpart) ^ (XOR of swz(1 << r[b]) over the set bits b of ri); walking the
+// registers in Gray-code order costs one XOR per register.
+__host__ __device__ constexpr int ctz5(int x) { return x & 1 ? 0 : x & 2 ? 1 : x & 4 ? 2 : x & 8 ? 3 : 4; }
+
+__device__ __forceinline__ void smem_basis(const TileCtx &c, uint32_t &base, uint32_t (&sw)[REG_BITS]) {
+    base = swz(c.tpart);
+#pragma unroll
+    for (int b = 0; b < REG_BITS; ++b) sw[b] = swz(1u << c.r[b]);
+}
+__device__ __forceinline__ void to_smem(const float2 (&v)[32], float2 *sm, const TileCtx &c) {
+    uint32_t idx, sw[REG_BITS];
+    smem_basis(c, idx, sw);
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        sm[idx] = v[k ^ (k >> 1)];
+        if (k < 31) idx ^= sw[ctz5(k + 1)];
+    }
+}
+__device__ __forceinline__ void from_smem(float2 (&v)[32], const float2 *sm, const TileCtx &c) {
+    uint32_t idx, sw[REG_BITS];
+    smem_basis(c, idx, sw);
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        v[k ^ (k >> 1)] = sm[idx];
+        if (k < 31) idx ^= sw[ctz5(k + 1)];
+    }
 }
 
-__device__ __forceinline__ void apply_dense2(float2 (&v)[32], uint32_t p0, uint32_t p1, const float2 (&M)[16]) {
-#define ARSO_D2(a, b) \
-    case a * 5 + b: dispatch_dense2_pp<a, b>(v, M); break;
-    switch (p0 * 5 + p1) {
-        ARSO_D2(0, 1) ARSO_D2(0, 2) ARSO_D2(0, 3) ARSO_D2(0, 4) ARSO_D2(1, 0) ARSO_D2(1, 2) ARSO_D2(1, 3)
-        ARSO_D2(1, 4) ARSO_D2(2, 0) ARSO_D2(2, 1) ARSO_D2(2, 3) ARSO_D2(2, 4) ARSO_D2(3, 0) ARSO_D2(3, 1)
-        ARSO_D2(3, 2) ARSO_D2(3, 4) ARSO_D2(4, 0) ARSO_D2(4, 1) ARSO_D2(4, 2) ARSO_D2(4, 3)
-        default: break;
+__device__ __forceinline__ void remap(float2 (&v)[32], float2 *sm, TileCtx &c, uint32_t packed, int t) {
+    __syncthreads();
+    to_smem(v, sm, c);
+    set_phase(c, packed, t);
+    __syncthreads();
+    from_smem(v, sm, c);
+}
+
+// Dense two-qubit gates and SWAP are rare: they run through shared memory on
+// the stored data (U already conjugated by the mask) with runtime indices.
+__device__ __forceinline__ void smem_dense2(float2 *sm, int t, uint32_t q0, uint32_t q1, const float2 *__restrict__ U) {
+    const uint32_t lo = q0 < q1 ? q0 : q1, hi = q0 < q1 ? q1 : q0;
+    const uint32_t m0 = 1u << q0, m1 = 1u << q1;
+    float2 M[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) M[k] = U[k];
+    for (uint32_t p = threadIdx.x; p < (1u << (t - 2)); p += blockDim.x) {
+        const uint32_t i = insert_zero2(p, lo, hi);
+        const uint32_t ix[4] = {swz(i), swz(i | m0), swz(i | m1), swz(i | m0 | m1)};
+        float2 a[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a[k] = sm[ix[k]];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float2 acc = cmac2(M[4 * k], a[0], M[4 * k + 1], a[1]);
+            const float2 acc2 = cmac2(M[4 * k + 2], a[2], M[4 * k + 3], a[3]);
+            acc.x += acc2.x;
+            acc.y += acc2.y;
+            sm[ix[k]] = acc;
+        }
     }
-#undef ARSO_D2
 }
 
 __device__ __forceinline__ void apply_gate_rb(float2 (&v)[32], TileCtx &c, const DGate &g, uint8_t rp,
-                                              const float2 *__restrict__ mats) {
+                                              const float2 *__restrict__ mats, float2 *sm, float2 *ubuf, int t) {
     const uint32_t p0 = rp & 15u, p1 = rp >> 4;
     const float2 *M = mats + g.mat;
     switch (g.cls) {
-        case GC_DENSE1:
         case GC_H: {
             const uint32_t flip = (c.m >> g.q0) & 1u;
             switch (p0) {
-                case 0: dispatch_dense1<0>(v, g, M, flip); break;
-                case 1: dispatch_dense1<1>(v, g, M, flip); break;
-                case 2: dispatch_dense1<2>(v, g, M, flip); break;
-                case 3: dispatch_dense1<3>(v, g, M, flip); break;
-                default: dispatch_dense1<4>(v, g, M, flip); break;
+                case 0: rg_h<0>(v, flip); break;
+                case 1: rg_h<1>(v, flip); break;
+                case 2: rg_h<2>(v, flip); break;
+                case 3: rg_h<3>(v, flip); break;
+                default: rg_h<4>(v, flip); break;
+            }
+            break;
+        }
+        case GC_DENSE1: {
+            // with the qubit's mask bit set the stored data sees X U X = [[u11, u10], [u01, u00]]
+            const uint32_t flip = (c.m >> g.q0) & 1u;
+            const float2 u00 = flip ? M[3] : M[0], u01 = flip ? M[2] : M[1];
+            const float2 u10 = flip ? M[1] : M[2], u11 = flip ? M[0] : M[3];
+            switch (p0) {
+                case 0: rg_dense1<0>(v, u00, u01, u10, u11); break;
+                case 1: rg_dense1<1>(v, u00, u01, u10, u11); break;
+                case 2: rg_dense1<2>(v, u00, u01, u10, u11); break;
+                case 3: rg_dense1<3>(v, u00, u01, u10, u11); break;
+                default: rg_dense1<4>(v, u00, u01, u10, u11); break;
             }
             break;
         }
@@ -264,19 +311,25 @@ __device__ __forceinline__ void apply_gate_rb(float2 (&v)[32], TileCtx &c, const
         }
         case GC_DENSE2:
         case GC_SWAP: {
-            float2 U[16];
             const uint32_t mab = ((c.m >> g.q0) & 1u) | (((c.m >> g.q1) & 1u) << 1);
-            if (g.cls == GC_SWAP) {
-#pragma unroll
-                for (int k = 0; k < 16; ++k) U[k] = make_float2(0.f, 0.f);
-                U[0] = U[15] = U[1 * 4 + 2] = U[2 * 4 + 1] = make_float2(1.f, 0.f);
-            } else {
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-#pragma unroll
-                    for (int l = 0; l < 4; ++l) U[4 * k + l] = M[4 * (k ^ mab) + (l ^ mab)];
+            if (threadIdx.x < 16) {
+                const uint32_t k = threadIdx.x >> 2, l = threadIdx.x & 3u;
+                float2 u;
+                if (g.cls == GC_SWAP) {
+                    const uint32_t perm[4] = {0, 2, 1, 3};
+                    u = make_float2(perm[k] == l ? 1.f : 0.f, 0.f);
+                } else {
+                    u = M[4 * (k ^ mab) + (l ^ mab)];
+                }
+                ubuf[threadIdx.x] = u;
             }
-            apply_dense2(v, p0, p1, U);
+            __syncthreads();
+            to_smem(v, sm, c);
+            __syncthreads();
+            smem_dense2(sm, t, g.q0, g.q1, ubuf);
+            __syncthreads();
+            from_smem(v, sm, c);
+            __syncthreads();
             // SWAP X^m = X^{m with bits q0, q1 exchanged} SWAP
             if (g.cls == GC_SWAP && (((c.m >> g.q0) ^ (c.m >> g.q1)) & 1u)) c.m ^= (1u << g.q0) | (1u << g.q1);
             break;
@@ -285,34 +338,16 @@ __device__ __forceinline__ void apply_gate_rb(float2 (&v)[32], TileCtx &c, const
     }
 }
 
-// stored index -> tile-local index bits for the load/store mapping
-__device__ __forceinline__ void set_phase(TileCtx &c, uint32_t packed, int t) {
-    unpack_r(packed, c.r);
-    c.rmask = 0;
-#pragma unroll
-    for (int b = 0; b < REG_BITS; ++b) c.rmask |= 1u << c.r[b];
-    c.tpart = thread_part(threadIdx.x, c.rmask, t);
-}
-
-__device__ __forceinline__ void remap(float2 (&v)[32], float2 *sm, TileCtx &c, uint32_t packed, int t) {
-    __syncthreads();
-#pragma unroll
-    for (int ri = 0; ri < 32; ++ri) sm[swz(c.tpart | reg_part(ri, c.r))] = v[ri];
-    set_phase(c, packed, t);
-    __syncthreads();
-#pragma unroll
-    for (int ri = 0; ri < 32; ++ri) v[ri] = sm[swz(c.tpart | reg_part(ri, c.r))];
-}
-
 template <bool LAST>
 __global__ void __launch_bounds__(512, 1) pass_rb_kernel(PassArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *sm = reinterpret_cast<float2 *>(smem_raw);
     __shared__ Partial red[32];
+    __shared__ float2 ubuf[16];
     const int t = a.t, cl = a.c;
     const uint32_t slot = blockIdx.y;
     const uint64_t N = 1ull << a.n;
-    int start;
+    int start, end = 0;
     uint64_t tr = 0;
     const float2 *src;
     float2 *dst;
@@ -322,7 +357,8 @@ __global__ void __launch_bounds__(512, 1) pass_rb_kernel(PassArgs a) {
         dst = static_cast<float2 *>(a.ideal_dst);
     } else {
         start = a.start_pass[slot];
-        if (a.pass < start) return;
+        end = a.end_pass[slot];
+        if (a.pass < start || a.pass > end) return;
         tr = a.slot_traj[slot];
         float2 *mine = static_cast<float2 *>(a.work) + (size_t)slot * N;
         src = a.pass == start ? static_cast<const float2 *>(a.cache) + (size_t)a.cache_slot[start] * N : mine;
@@ -382,7 +418,7 @@ __global__ void __launch_bounds__(512, 1) pass_rb_kernel(PassArgs a) {
         const uint32_t ge = a.ph_gb[ph + 1];
         for (uint32_t g = a.ph_gb[ph]; g < ge; ++g) {
             const DGate gate = a.gates[g];
-            apply_gate_rb(v, c, gate, a.rpos[g], mats);
+            apply_gate_rb(v, c, gate, a.rpos[g], mats, sm, ubuf, t);
             while (next != NO_EVENT && ev_pos(next) == g) {
                 rg_pauli(v, c, ev_slot(next) ? gate.q1 : gate.q0, ev_code(next));
                 ++ev;
@@ -395,8 +431,8 @@ __global__ void __launch_bounds__(512, 1) pass_rb_kernel(PassArgs a) {
 #pragma unroll
         for (int ri = 0; ri < 32; ++ri) v[ri] = omega_mul(v[ri], 2u * c.gp);
     }
-    if (LAST && !a.ideal && !a.store_last) {
-        const float2 *ref = static_cast<const float2 *>(a.cache) + (size_t)a.ref_slot * N;
+    if (!a.ideal && !a.store_last && a.pass == end) {
+        const float2 *ref = static_cast<const float2 *>(a.cache) + (size_t)a.cache_slot[end + 1] * N;
         Partial acc = empty_partial();
 #pragma unroll
         for (int ri = 0; ri < 32; ++ri) {
@@ -416,6 +452,162 @@ __global__ void __launch_bounds__(512, 1) pass_rb_kernel(PassArgs a) {
         const float2 o = flip0 ? v[2 * hi] : v[2 * hi + 1];
         reinterpret_cast<float4 *>(dst + gidx(j))[0] = make_float4(e.x, e.y, o.x, o.y);
     }
+}
+
+// ------------------------------------------------------------- resident ---
+// Whole state (2^n, 10 <= n <= 13) in one CTA: each trajectory restarts from
+// the cached error-free state at the checkpoint (phase boundary) at or before
+// its first error and runs the remaining phases; ckpt_every counts phases.
+
+__device__ __forceinline__ void rb_load_linear(float2 (&v)[32], const float2 *src, int t) {
+#pragma unroll
+    for (int hi = 0; hi < 16; ++hi) {
+        const uint32_t j = ((uint32_t)hi << (t - 4)) | (threadIdx.x << 1);
+        const float4 w = __ldg(reinterpret_cast<const float4 *>(src + j));
+        v[2 * hi] = make_float2(w.x, w.y);
+        v[2 * hi + 1] = make_float2(w.z, w.w);
+    }
+}
+
+// store the true state (mask and global phase applied); leaves v in the load mapping
+__device__ __forceinline__ void rb_store_linear(float2 (&v)[32], float2 *sm, TileCtx &c, uint32_t &cur_packed,
+                                                uint32_t load_packed, float2 *dst, int t) {
+    if (cur_packed != load_packed) {
+        remap(v, sm, c, load_packed, t);
+        cur_packed = load_packed;
+    }
+    const uint32_t flip0 = c.m & 1u;
+    const uint32_t k2 = 2u * c.gp;
+#pragma unroll
+    for (int hi = 0; hi < 16; ++hi) {
+        const uint32_t j = (((uint32_t)hi << (t - 4)) | (threadIdx.x << 1)) ^ (c.m & ~1u);
+        float2 e = flip0 ? v[2 * hi + 1] : v[2 * hi];
+        float2 o = flip0 ? v[2 * hi] : v[2 * hi + 1];
+        if (k2) {
+            e = omega_mul(e, k2);
+            o = omega_mul(o, k2);
+        }
+        reinterpret_cast<float4 *>(dst + j)[0] = make_float4(e.x, e.y, o.x, o.y);
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(512, 1) resident_rb_kernel(ResidentArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *sm = reinterpret_cast<float2 *>(smem_raw);
+    __shared__ Partial red[32];
+    __shared__ float2 ubuf[16];
+    const int t = a.n;
+    const uint32_t N = 1u << t;
+    const float2 *cache = static_cast<const float2 *>(a.cache);
+    const float2 *mats = static_cast<const float2 *>(a.mats);
+    const uint32_t load_packed = 0u | ((uint32_t)(t - 4) << 5) | ((uint32_t)(t - 3) << 10) |
+                                 ((uint32_t)(t - 2) << 15) | ((uint32_t)(t - 1) << 20);
+    const uint64_t count = MODE == 2 ? 1 : a.count;
+    for (uint64_t b = blockIdx.x; b < count; b += gridDim.x) {
+        float2 v[32];
+        TileCtx c;
+        c.m = 0;
+        c.gp = 0;
+        set_phase(c, load_packed, t);
+        uint32_t cur_packed = load_packed;
+        uint32_t ph0 = 0;
+        const uint32_t *ev = nullptr, *ev_end = nullptr;
+        uint64_t tr = 0;
+        if (MODE == 2) {
+#pragma unroll
+            for (int ri = 0; ri < 32; ++ri) v[ri] = make_float2(0.f, 0.f);
+            if (threadIdx.x == 0) v[0] = make_float2(1.f, 0.f);
+        } else {
+            tr = a.first_traj + b;
+            const uint32_t first = a.first[tr];
+            if (MODE == 0 && first == NO_EVENT) {
+                if (threadIdx.x == 0) {
+                    a.score[tr] = *a.ref_score;
+                    if (a.pass_flags) a.pass_flags[tr] = *a.ref_score >= a.crit.threshold;
+                }
+                continue;
+            }
+            uint32_t ck;
+            if (first == NO_EVENT) {
+                ck = a.n_ckpt - 1;
+                ph0 = a.n_phases;
+            } else {
+                ck = a.phase_of_pos[first] / (uint32_t)a.ckpt_every;
+                ph0 = ck * (uint32_t)a.ckpt_every;
+            }
+            rb_load_linear(v, cache + (size_t)ck * N, t);
+            ev = a.keys + a.offsets[tr];
+            ev_end = a.keys + a.offsets[tr + 1];
+        }
+        uint32_t next = ev && ev < ev_end ? *ev : NO_EVENT;
+        for (uint32_t ph = ph0; ph < a.n_phases; ++ph) {
+            if (MODE == 2 && ph % (uint32_t)a.ckpt_every == 0) {
+                float2 *dst = const_cast<float2 *>(cache) + (size_t)(ph / (uint32_t)a.ckpt_every) * N;
+                rb_store_linear(v, sm, c, cur_packed, load_packed, dst, t);
+            }
+            const uint32_t R = a.ph_R[ph];
+            if (R != cur_packed) {
+                remap(v, sm, c, R, t);
+                cur_packed = R;
+            }
+            const uint32_t ge = a.ph_gb[ph + 1];
+            for (uint32_t g = a.ph_gb[ph]; g < ge; ++g) {
+                const DGate gate = a.gates[g];
+                apply_gate_rb(v, c, gate, a.rpos[g], mats, sm, ubuf, t);
+                while (next != NO_EVENT && ev_pos(next) == g) {
+                    rg_pauli(v, c, ev_slot(next) ? gate.q1 : gate.q0, ev_code(next));
+                    ++ev;
+                    next = ev < ev_end ? *ev : NO_EVENT;
+                }
+            }
+        }
+        if (MODE == 2) {
+            rb_store_linear(v, sm, c, cur_packed, load_packed, const_cast<float2 *>(cache) + (size_t)(a.n_ckpt - 1) * N,
+                            t);
+        } else if (MODE == 1) {
+            rb_store_linear(v, sm, c, cur_packed, load_packed, static_cast<float2 *>(a.states_out) + (size_t)b * N, t);
+        } else {
+            if (c.gp) {
+#pragma unroll
+                for (int ri = 0; ri < 32; ++ri) v[ri] = omega_mul(v[ri], 2u * c.gp);
+            }
+            const float2 *ref = cache + (size_t)(a.n_ckpt - 1) * N;
+            Partial acc = empty_partial();
+#pragma unroll
+            for (int ri = 0; ri < 32; ++ri) {
+                const uint32_t jj = (c.tpart | reg_part(ri, c.r)) ^ c.m;
+                accumulate(acc, a.crit, v[ri], ref, jj);
+            }
+            acc = block_reduce_partial(acc, red);
+            if (threadIdx.x == 0) {
+                const double sc = finish_score(a.crit, acc);
+                a.score[tr] = sc;
+                if (a.pass_flags) a.pass_flags[tr] = sc >= a.crit.threshold;
+            }
+        }
+        __syncthreads();  // shared memory and red[] are reused by the next trajectory
+    }
+}
+
+void launch_resident_rb(const ResidentArgs &a, int mode, double bytes, cudaStream_t st) {
+    ProfScope ps_(ARSO_K_RESIDENT, bytes, st);
+    const int nt = 1 << (a.n - REG_BITS);
+    const size_t smem = (size_t(1) << a.n) * sizeof(float2);
+    const void *fn = mode == 0 ? (const void *)resident_rb_kernel<0>
+                   : mode == 1 ? (const void *)resident_rb_kernel<1> : (const void *)resident_rb_kernel<2>;
+    if (smem > 48 * 1024) ARSO_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 1;
+    ARSO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem));
+    int dev = 0, sms = 152;
+    ARSO_CUDA(cudaGetDevice(&dev));
+    ARSO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const uint64_t want = mode == 2 ? 1 : a.count;
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)std::max(per_sm, 1) * sms));
+    if (mode == 0) resident_rb_kernel<0><<<grid, nt, smem, st>>>(a);
+    else if (mode == 1) resident_rb_kernel<1><<<grid, nt, smem, st>>>(a);
+    else resident_rb_kernel<2><<<grid, nt, smem, st>>>(a);
+    ARSO_CUDA(cudaGetLastError());
 }
 
 void launch_pass_rb(const PassArgs &a, bool last, uint32_t slots, double bytes, cudaStream_t st) {

@@ -183,10 +183,13 @@ __global__ void sort_keys_kernel(const uint64_t *__restrict__ offsets, uint64_t 
 }
 
 __global__ void first_event_kernel(const uint64_t *__restrict__ offsets, uint64_t n_traj,
-                                   const uint32_t *__restrict__ ev_key, uint32_t *first) {
+                                   const uint32_t *__restrict__ ev_key, uint32_t *first, uint32_t *last) {
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < n_traj;
-         t += (uint64_t)gridDim.x * blockDim.x)
-        first[t] = offsets[t + 1] > offsets[t] ? (ev_key[offsets[t]] >> 3) : NO_EVENT;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const bool any = offsets[t + 1] > offsets[t];
+        first[t] = any ? (ev_key[offsets[t]] >> 3) : NO_EVENT;
+        last[t] = any ? (ev_key[offsets[t + 1] - 1] >> 3) : NO_EVENT;
+    }
 }
 
 // sums3 = {sum score, sum score^2, sum pass} in FP64 (fixed order per block,
@@ -266,10 +269,10 @@ void launch_sort_keys(const uint64_t *offsets, uint64_t n_traj, uint32_t *ev_key
     ARSO_CUDA(cudaGetLastError());
 }
 void launch_first_event(const uint64_t *offsets, uint64_t n_traj, const uint32_t *ev_key, uint32_t *first,
-                        cudaStream_t st) {
+                        uint32_t *last, cudaStream_t st) {
     if (!n_traj) return;
     ProfScope ps_(ARSO_K_OTHER, 0.0, st);
-    first_event_kernel<<<grid_for(n_traj, 256, 152 * 16), 256, 0, st>>>(offsets, n_traj, ev_key, first);
+    first_event_kernel<<<grid_for(n_traj, 256, 152 * 16), 256, 0, st>>>(offsets, n_traj, ev_key, first, last);
     ARSO_CUDA(cudaGetLastError());
 }
 void launch_sum_scores(const double *score, const uint8_t *pass_flags, uint64_t n, double *sums3, cudaStream_t st) {

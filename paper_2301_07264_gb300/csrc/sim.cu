@@ -139,7 +139,7 @@ __global__ void pass_kernel(PassArgs a) {
     const int t = a.t, c = a.c;
     const uint32_t slot = blockIdx.y;
     const uint64_t N = 1ull << a.n;
-    int start;
+    int start, end = 0;
     uint64_t tr = 0;
     const T *src;
     T *dst;
@@ -149,7 +149,8 @@ __global__ void pass_kernel(PassArgs a) {
         dst = static_cast<T *>(a.ideal_dst);
     } else {
         start = a.start_pass[slot];
-        if (a.pass < start) return;
+        end = a.end_pass[slot];
+        if (a.pass < start || a.pass > end) return;
         tr = a.slot_traj[slot];
         T *mine = static_cast<T *>(a.work) + (size_t)slot * N;
         src = a.pass == start ? static_cast<const T *>(a.cache) + (size_t)a.cache_slot[start] * N : mine;
@@ -201,8 +202,8 @@ __global__ void pass_kernel(PassArgs a) {
             }
         }
     }
-    if (LAST && !a.ideal && !a.store_last) {
-        const T *ref = static_cast<const T *>(a.cache) + (size_t)a.ref_slot * N;
+    if (!a.ideal && !a.store_last && a.pass == end) {
+        const T *ref = static_cast<const T *>(a.cache) + (size_t)a.cache_slot[end + 1] * N;
         Partial acc = empty_partial();
         for (uint32_t j = threadIdx.x; j < tile_n; j += blockDim.x) {
             const uint64_t gi = tile_index<T>(j, base, offs, c);

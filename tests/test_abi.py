@@ -1,0 +1,82 @@
+"""Host-side checks that need no GPU: the C-ABI library loads, exports every
+function declared in include/*.h, reports errors without a device, and the
+pass scheduler keeps the circuit's dependencies."""
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+from workloads import circuits as C
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(arso_[a-z0-9_]+)\s*\(", text))
+    return names
+
+
+@pytest.fixture(scope="module")
+def arso():
+    from paper_2301_07264_gb300 import build
+    build.build()
+    from paper_2301_07264_gb300 import arso as mod
+    return mod
+
+
+def test_library_exports_every_declared_symbol(arso):
+    declared = _declared()
+    assert len(declared) >= 20
+    missing = [n for n in declared if not hasattr(arso.lib, n)]
+    assert not missing, missing
+
+
+def test_version_and_errors_without_device(arso):
+    assert "sm_103a" in arso.version()
+    st = arso.lib.arso_circuit_get_info(None, None)
+    assert st == arso.EINVAL
+    assert arso.lib.arso_last_error()
+
+
+def _check_schedule(circ, tile, low):
+    from paper_2301_07264_gb300 import arso
+    perm, begin, masks = arso.plan_schedule(circ.n, circ.gates, tile_qubits=tile, low_qubits=low)
+    G = circ.G
+    assert sorted(perm.tolist()) == list(range(G))
+    # every gate's qubits are tile qubits of its pass; low qubits in every tile
+    for p in range(len(masks)):
+        m = int(masks[p])
+        assert bin(m).count("1") == min(tile, circ.n)
+        assert all((m >> q) & 1 for q in range(min(low, tile)))
+        for pos in range(begin[p], begin[p + 1]):
+            for q in circ.gates[perm[pos]].qubits:
+                assert (m >> q) & 1
+    # the engine order keeps the order of gates on every qubit
+    last = {}
+    for pos in range(G):
+        g = int(perm[pos])
+        for q in circ.gates[g].qubits:
+            assert last.get(q, -1) < g
+            last[q] = g
+    return len(masks)
+
+
+@pytest.mark.parametrize("n,G,tile,low,seed", [(14, 300, 8, 3, 1), (20, 400, 13, 4, 2), (24, 200, 14, 5, 3)])
+def test_schedule_respects_dependencies(arso, n, G, tile, low, seed):
+    _check_schedule(C.random_circuit(n, G, seed), tile, low)
+
+
+def test_brickwork24_schedule_is_fused(arso):
+    P = _check_schedule(C.brickwork24(0), 13, 4)
+    assert P <= 50  # 1420 gates in at most 50 HBM sweeps
+
+
+def test_resident_circuits_plan_one_pass(arso):
+    perm, begin, masks = arso.plan_schedule(12, C.grover12(0).gates)
+    assert len(masks) == 1 and np.array_equal(perm, np.arange(len(perm)))

@@ -153,6 +153,27 @@ def test_register_blocked_many_errors(arso, tile, seed):
         assert np.max(np.abs(got[t] - statevector.simulate(circ, ev))) < AMP_TOL_C64, t
 
 
+@pytest.mark.parametrize("cache_boundaries", [0, 5])
+def test_suffix_reuse_scores_equal_full_runs(arso, cache_boundaries):
+    """Fidelity taken right after the last error against the cached error-free
+    state equals fidelity of the full run (the error-free suffix is unitary)."""
+    circ = C.brickwork(18, 24, seed=4)
+    sb = (1 << 18) * 8
+    kw = dict(tile_qubits=12, cache_bytes=cache_boundaries * sb)
+    on = arso.compile_circuit(circ.n, circ.gates, **kw)
+    off = arso.compile_circuit(circ.n, circ.gates, flags=arso.OPT_NO_SUFFIX_REUSE, **kw)
+    T, p = 48, 2e-3
+    s_on, s_off = np.zeros(T), np.zeros(T)
+    arso.run_trajectories(on, arso.sample_errors(on, p / 3, p / 3, p / 3, 9, 0, T), circ.criterion, s_on)
+    arso.run_trajectories(off, arso.sample_errors(off, p / 3, p / 3, p / 3, 9, 0, T), circ.criterion, s_off)
+    assert np.max(np.abs(s_on - s_off)) < SCORE_TOL
+    lists = sampling.sample(9, 0, T, circ.L, p / 3, p / 3, p / 3)
+    psi_ref = statevector.simulate(circ)
+    for t in [i for i in range(T) if lists[i]][:3]:
+        o = criteria.score(circ.criterion, statevector.simulate(circ, lists[t]), psi_ref)
+        assert abs(s_on[t] - o) < SCORE_TOL
+
+
 def test_streaming_prefix_cache_subset(arso):
     # a cache budget that cannot hold every pass boundary forces restarts from
     # an earlier cached boundary
@@ -266,7 +287,9 @@ def test_qft4_config_full_parity(arso):
     agg = montecarlo.aggregate(o_s, o_f)
     assert abs(r.pass_frac - agg["pass_frac"]) <= (~away).sum() / 1000 + 1e-12
     assert abs(r.mean - agg["mean"]) < 1e-12
-    assert abs(r.stderr_value - agg["stderr_pass"]) < 1e-9
+    own = montecarlo.aggregate(score, flags.astype(bool))  # the GPU's own flags
+    assert abs(r.pass_frac - own["pass_frac"]) < 1e-12
+    assert abs(r.stderr_value - own["stderr_pass"]) < 1e-9
 
 
 def test_exhaustive_and_eq4(arso):
