@@ -256,6 +256,21 @@ arso_status arso_apply_pauli(uint32_t n_qubits, void *amps, uint32_t qubit, uint
 arso_status arso_score_state(uint32_t n_qubits, const void *amps, const void *ref,
                              const arso_criterion *crit, void *stream, double *score_out);
 
+/* Allocation-free variant of arso_score_state (the paper has no counterpart:
+ * this serves callers that cannot call cudaMalloc, such as code running inside
+ * another framework's memory arena or on a path where an allocation would
+ * synchronise the device or fail under memory pressure). Same arguments and
+ * result as arso_score_state; its scratch lives in fixed-size device arrays
+ * compiled into the library, which every GPU that loads the library holds
+ * until the process exits. Limits: binning criteria up to 20 qubits (an
+ * outcome bitmap of 2^20 bits), other criteria up to 34 qubits; larger
+ * requests return ARSO_EINVAL. The first call on a device looks up the
+ * arrays' device addresses, so make it before any stream capture. All calls on
+ * a device share the arrays (each call overwrites what it reads), so calls
+ * that overlap on the GPU race. It calls no cudaMalloc or cudaFree. */
+arso_status arso_score_state_noalloc(uint32_t n_qubits, const void *amps, const void *ref,
+                                     const arso_criterion *crit, void *stream, double *score_out);
+
 /* ---- tracing: per-kernel device time and traffic (not part of the paper) ----
  * When enabled, the library records a CUDA event pair on the launching stream
  * around every kernel launch and accumulates, per kernel family, the number
