@@ -242,6 +242,55 @@ typedef struct {
 arso_status arso_tolerable_rate(const arso_circuit *c, const arso_criterion *crit, double P_target,
                                 const arso_search_opts *opts, void *stream, arso_rate_result *out);
 
+/* ---- learned surrogate of the success probability (not part of the paper) ----
+ * A 33 -> 256 -> 256 -> 1 MLP (ReLU hidden layers, sigmoid output) that maps
+ * a circuit's features and log10 p to the probability that one trajectory
+ * passes its criterion. Weights are bfloat16 with FP32 master copies; all
+ * products accumulate in FP32. Training minimises the mean binary
+ * cross-entropy against pass flags produced by arso_run_trajectories, with
+ * Adam, entirely on the GPU. Inputs are standardised with the per-column mean
+ * and standard deviation of the training set (stored in the handle).
+ * It narrows the bracket of arso_tolerable_rate_surrogate; the plain
+ * simulator verifies the bracket and remains the fallback. */
+#define ARSO_N_FEATURES 32
+#define ARSO_SURROGATE_INPUTS 33
+/* 32 features of a compiled circuit and criterion (host floats): n, G, L, k,
+ * m, depth, two-qubit layers, log10 L, log10 G, two-qubit fraction, counts of
+ * H X Y Z S SDG T TDG RX RY RZ P U CX CZ CP SWAP U2, criterion one-hot (4). */
+arso_status arso_circuit_features(const arso_circuit *c, const arso_criterion *crit, float *out);
+arso_status arso_surrogate_create(uint64_t seed, arso_surrogate **out);
+void arso_surrogate_free(arso_surrogate *s);
+/* Train on n device rows x (n x 33 floats, row-major) with device labels y
+ * (n floats in {0, 1}): `epochs` passes in shuffled mini-batches of `batch`
+ * rows, Adam with learning rate lr. *loss_out (host, may be NULL) receives the
+ * mean loss of the last epoch. The first call fixes the standardisation. */
+arso_status arso_surrogate_train(arso_surrogate *s, const float *x, const float *y, uint64_t n, uint32_t epochs,
+                                 uint32_t batch, double lr, uint64_t seed, void *stream, double *loss_out);
+/* Predicted pass probabilities of n device rows into out (n device floats). */
+arso_status arso_surrogate_predict(const arso_surrogate *s, const float *x, uint64_t n, float *out, void *stream);
+/* Parameters as FP32 (host arrays, layout W1[33x256] b1[256] W2[256x256]
+ * b2[256] W3[256] b3[1], row-major; ARSO_SURROGATE_PARAMS floats). set also
+ * refreshes the bfloat16 copies; get returns the FP32 masters. */
+#define ARSO_SURROGATE_PARAMS (33 * 256 + 256 + 256 * 256 + 256 + 256 + 1)
+arso_status arso_surrogate_get_params(const arso_surrogate *s, float *out);
+arso_status arso_surrogate_set_params(arso_surrogate *s, const float *in);
+/* Standardisation (host, 33 means and 33 standard deviations). */
+arso_status arso_surrogate_set_norm(arso_surrogate *s, const float *mean, const float *stdev);
+/* Loss and gradients (host, ARSO_SURROGATE_PARAMS floats, same layout) of the
+ * mean binary cross-entropy on n device rows, with the current bfloat16
+ * weights; no update. For checking the backward kernels. */
+arso_status arso_surrogate_grads(const arso_surrogate *s, const float *x, const float *y, uint64_t n, void *stream,
+                                 float *grads_out, double *loss_out);
+/* Tolerable rate with the surrogate (Sec. IV-D, Monte Carlo branch): bisect
+ * log10 p on the surrogate's prediction for the circuit's features, take the
+ * bracket [p_s 10^-m, p_s 10^m] (m = opts->surrogate_margin), verify it with
+ * opts->n_traj plain trajectories at each end (values straddle P_target),
+ * widen it by 10^(2m) per side while it fails (at most 3 times), and answer by
+ * log-linear interpolation inside the verified bracket. If it cannot be
+ * verified, fall back to arso_tolerable_rate's Monte Carlo search. */
+arso_status arso_tolerable_rate_surrogate(const arso_circuit *c, const arso_criterion *crit, double P_target,
+                                          const arso_search_opts *opts, void *stream, arso_rate_result *out);
+
 /* ---- single-step kernels (each also runs inside the fused trajectory path) ---- */
 
 /* Apply one gate to a device state (2^n amplitudes, complex64) as a strided

@@ -363,3 +363,98 @@ def score_state(n, amps, ref, crit, stream=None) -> float:
 
 def version() -> str:
     return lib.arso_version().decode()
+
+
+# ------------------------------------------------------------- surrogate --
+N_FEATURES = 32
+SURROGATE_INPUTS = 33
+SURROGATE_PARAMS = 33 * 256 + 256 + 256 * 256 + 256 + 256 + 1
+
+for _name, _args in {
+    "arso_circuit_features": [_vp, C.POINTER(Criterion), _vp],
+    "arso_surrogate_create": [C.c_uint64, C.POINTER(_vp)],
+    "arso_surrogate_train": [_vp, _vp, _vp, C.c_uint64, C.c_uint32, C.c_uint32, C.c_double, C.c_uint64, _vp, _vp],
+    "arso_surrogate_predict": [_vp, _vp, C.c_uint64, _vp, _vp],
+    "arso_surrogate_get_params": [_vp, _vp],
+    "arso_surrogate_set_params": [_vp, _vp],
+    "arso_surrogate_set_norm": [_vp, _vp, _vp],
+    "arso_surrogate_grads": [_vp, _vp, _vp, C.c_uint64, _vp, _vp, _vp],
+    "arso_tolerable_rate_surrogate": [_vp, C.POINTER(Criterion), C.c_double, C.POINTER(SearchOpts), _vp,
+                                      C.POINTER(RateResult)],
+}.items():
+    _f = getattr(lib, _name)
+    _f.argtypes = _args
+    _f.restype = C.c_int
+lib.arso_surrogate_free.argtypes = [_vp]
+lib.arso_surrogate_free.restype = None
+
+
+class Surrogate:
+    def __init__(self, handle):
+        self.handle = handle
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib.arso_surrogate_free(self.handle)
+            self.handle = None
+
+
+def circuit_features(circ, crit):
+    c = crit if isinstance(crit, Criterion) else make_criterion(crit)
+    out = np.zeros(N_FEATURES, dtype=np.float32)
+    _check(lib.arso_circuit_features(circ.handle, C.byref(c), out.ctypes.data))
+    return out
+
+
+def surrogate_create(seed=0) -> Surrogate:
+    h = _vp()
+    _check(lib.arso_surrogate_create(seed, C.byref(h)))
+    return Surrogate(h.value)
+
+
+def surrogate_train(s, x, y, epochs=1, batch=4096, lr=1e-3, seed=0, stream=None):
+    """x: device (n, 33) float32; y: device (n,) float32 pass flags. Returns the last epoch's mean loss."""
+    loss = C.c_double()
+    n = x.shape[0]
+    _check(lib.arso_surrogate_train(s.handle, _ptr(x), _ptr(y), n, epochs, batch, lr, seed, _stream(stream),
+                                    C.byref(loss)))
+    return loss.value
+
+
+def surrogate_predict(s, x, out, stream=None):
+    _check(lib.arso_surrogate_predict(s.handle, _ptr(x), x.shape[0], _ptr(out), _stream(stream)))
+
+
+def surrogate_get_params(s):
+    out = np.zeros(SURROGATE_PARAMS, dtype=np.float32)
+    _check(lib.arso_surrogate_get_params(s.handle, out.ctypes.data))
+    return out
+
+
+def surrogate_set_params(s, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(lib.arso_surrogate_set_params(s.handle, p.ctypes.data))
+
+
+def surrogate_set_norm(s, mean, sd):
+    m = np.ascontiguousarray(mean, dtype=np.float32)
+    d = np.ascontiguousarray(sd, dtype=np.float32)
+    _check(lib.arso_surrogate_set_norm(s.handle, m.ctypes.data, d.ctypes.data))
+
+
+def surrogate_grads(s, x, y, stream=None):
+    g = np.zeros(SURROGATE_PARAMS, dtype=np.float32)
+    loss = C.c_double()
+    _check(lib.arso_surrogate_grads(s.handle, _ptr(x), _ptr(y), x.shape[0], _stream(stream), g.ctypes.data,
+                                    C.byref(loss)))
+    return g, loss.value
+
+
+def tolerable_rate_surrogate(circ, crit, P_target, surrogate, p_lo=0.0, p_hi=0.0, n_traj=0, seed=0, margin=0.0,
+                             rel_tol=0.0, max_probes=0, stream=None) -> RateResult:
+    c = crit if isinstance(crit, Criterion) else make_criterion(crit)
+    o = SearchOpts(p_lo, p_hi, rel_tol, n_traj, seed, max_probes, MODE["mc"], surrogate.handle, None, margin)
+    r = RateResult()
+    _check(lib.arso_tolerable_rate_surrogate(circ.handle, C.byref(c), P_target, C.byref(o), _stream(stream),
+                                             C.byref(r)))
+    return r

@@ -918,6 +918,85 @@ arso_status arso_tolerable_rate(const arso_circuit *cc, const arso_criterion *cr
     });
 }
 
+arso_status arso_tolerable_rate_surrogate(const arso_circuit *cc, const arso_criterion *crit, double P_target,
+                                          const arso_search_opts *opts, void *stream, arso_rate_result *out) {
+    return guard([&] {
+        ARSO_REQUIRE(cc && crit && out && opts && opts->surrogate, "NULL argument or no surrogate");
+        ARSO_REQUIRE(crit->aggregate == ARSO_AGG_PASS, "the surrogate predicts pass probabilities: aggregate must be PASS");
+        arso_circuit *c = const_cast<arso_circuit *>(cc);
+        cudaStream_t st = (cudaStream_t)stream;
+        const double p_lo = opts->p_lo > 0 ? opts->p_lo : 1e-6, p_hi = opts->p_hi > 0 ? opts->p_hi : 1e-1;
+        const double margin = opts->surrogate_margin > 0 ? opts->surrogate_margin : 0.15;
+        const uint64_t nt = opts->n_traj ? opts->n_traj : 1000;
+        ARSO_REQUIRE(p_lo < p_hi && p_hi <= 1.0, "need 0 < p_lo < p_hi <= 1");
+        DevCrit dc;
+        make_crit(c, crit, dc, st);
+        std::memset(out, 0, sizeof(*out));
+        out->P1 = NAN;
+        out->mode_used = 1;
+        out->used_surrogate = 1;
+        // 1. the surrogate's crossing on a fine grid of log10 p (one batched forward)
+        const std::vector<float> f = circuit_features(c, crit);
+        const int K = 1024;
+        const double a = std::log10(p_lo), b = std::log10(p_hi);
+        std::vector<float> rows((size_t)K * ARSO_SURROGATE_INPUTS);
+        for (int i = 0; i < K; ++i) {
+            std::copy(f.begin(), f.end(), rows.begin() + (size_t)i * ARSO_SURROGATE_INPUTS);
+            rows[(size_t)i * ARSO_SURROGATE_INPUTS + ARSO_N_FEATURES] = (float)(a + (b - a) * i / (K - 1));
+        }
+        Scratch d_rows(st, rows.size() * 4), d_pred(st, K * 4);
+        copy_h2d(d_rows.ptr, rows.data(), rows.size() * 4, st);
+        const arso_status ps = arso_surrogate_predict(opts->surrogate, d_rows.as<float>(), K, d_pred.as<float>(), st);
+        if (ps != ARSO_OK) throw Error(ps, arso_last_error());
+        std::vector<float> pred(K);
+        copy_d2h(pred.data(), d_pred.ptr, K * 4, st);
+        ARSO_CUDA(cudaStreamSynchronize(st));
+        int i0 = K - 1;
+        for (int i = 0; i < K; ++i)
+            if (pred[i] < P_target) { i0 = i; break; }
+        double lp_s = a + (b - a) * std::max(0, i0) / (K - 1);
+        if (i0 > 0 && pred[i0 - 1] != pred[i0]) {  // interpolate between the grid points around the crossing
+            const double fr = (pred[i0 - 1] - P_target) / (pred[i0 - 1] - pred[i0]);
+            lp_s = a + (b - a) * ((i0 - 1) + fr) / (K - 1);
+        }
+        // 2. verify the bracket with plain trajectories (common random numbers)
+        auto probe = [&](double p) {
+            const McOut m = mc_run(c, dc, p, nt, opts->seed, st);
+            ++out->probes;
+            return m.pass_frac;
+        };
+        double lo = std::max(p_lo, std::pow(10.0, lp_s - margin)), hi = std::min(p_hi, std::pow(10.0, lp_s + margin));
+        double v_lo = probe(lo), v_hi = probe(hi);
+        for (int widen = 0; widen < 3 && !(v_lo >= P_target && v_hi < P_target); ++widen) {
+            if (v_lo < P_target && lo > p_lo) lo = std::max(p_lo, lo * std::pow(10.0, -2 * margin)), v_lo = probe(lo);
+            if (v_hi >= P_target && hi < p_hi) hi = std::min(p_hi, hi * std::pow(10.0, 2 * margin)), v_hi = probe(hi);
+        }
+        if (v_lo >= P_target && v_hi < P_target) {
+            out->verified = 1;
+            out->converged = 1;
+            out->lo = lo;
+            out->hi = hi;
+            out->value_lo = v_lo;
+            out->value_hi = v_hi;
+            const double fr = (v_lo - P_target) / (v_lo - v_hi);
+            out->p = std::pow(10.0, std::log10(lo) + fr * (std::log10(hi) - std::log10(lo)));
+            return;
+        }
+        // 3. fall back to the plain Monte Carlo search
+        arso_search_opts plain = *opts;
+        plain.surrogate = nullptr;
+        plain.mode = ARSO_MODE_MONTE_CARLO;
+        arso_rate_result r{};
+        const uint32_t used = out->probes;
+        const arso_status st2 = arso_tolerable_rate(cc, crit, P_target, &plain, stream, &r);
+        *out = r;
+        out->probes += used;
+        out->used_surrogate = 1;
+        out->verified = 0;
+        if (st2 != ARSO_OK) throw Error(st2, arso_last_error());
+    });
+}
+
 arso_status arso_apply_gate(uint32_t n, void *amps, const arso_gate *gate, void *stream) {
     return guard([&] {
         ARSO_REQUIRE(amps && gate, "NULL argument");

@@ -295,3 +295,49 @@ void build_circuit(arso_circuit *c, uint32_t n, const arso_gate *gates, size_t n
 }
 
 }  // namespace arso
+
+namespace arso {
+
+// 32 surrogate features: n, G, L, k, m, depth, two-qubit layers, log10 L,
+// log10 G, two-qubit fraction, counts per gate kind (18), criterion one-hot (4).
+std::vector<float> circuit_features(const arso_circuit *c, const arso_criterion *crit) {
+    std::vector<float> f(ARSO_N_FEATURES, 0.f);
+    const size_t G = c->gates.size();
+    std::vector<uint32_t> level(c->n, 0);
+    uint32_t depth = 0;
+    std::vector<char> layer_has_2q;
+    static const uint32_t kinds[18] = {ARSO_GATE_H, ARSO_GATE_X, ARSO_GATE_Y, ARSO_GATE_Z, ARSO_GATE_S,
+                                       ARSO_GATE_SDG, ARSO_GATE_T, ARSO_GATE_TDG, ARSO_GATE_RX, ARSO_GATE_RY,
+                                       ARSO_GATE_RZ, ARSO_GATE_P, ARSO_GATE_U, ARSO_GATE_CX, ARSO_GATE_CZ,
+                                       ARSO_GATE_CP, ARSO_GATE_SWAP, ARSO_GATE_U2};
+    float counts[18] = {0};
+    for (const HostGate &h : c->gates) {
+        uint32_t lv = level[h.q0];
+        if (h.arity == 2) lv = std::max(lv, level[h.q1]);
+        lv += 1;
+        level[h.q0] = lv;
+        if (h.arity == 2) level[h.q1] = lv;
+        depth = std::max(depth, lv);
+        if (layer_has_2q.size() < lv + 1) layer_has_2q.resize(lv + 1, 0);
+        if (h.arity == 2) layer_has_2q[lv] = 1;
+        for (int i = 0; i < 18; ++i)
+            if (kinds[i] == h.kind) counts[i] += 1.f;
+    }
+    uint32_t layers2 = 0;
+    for (char b : layer_has_2q) layers2 += b ? 1 : 0;
+    f[0] = (float)c->n;
+    f[1] = (float)G;
+    f[2] = (float)c->L;
+    f[3] = (float)c->k;
+    f[4] = (float)c->m;
+    f[5] = (float)depth;
+    f[6] = (float)layers2;
+    f[7] = (float)std::log10(std::max<double>(1.0, (double)c->L));
+    f[8] = (float)std::log10(std::max<double>(1.0, (double)G));
+    f[9] = G ? (float)c->m / (float)G : 0.f;
+    for (int i = 0; i < 18; ++i) f[10 + i] = counts[i];
+    if (crit && crit->kind <= ARSO_CRIT_ARGMAX) f[28 + crit->kind] = 1.f;
+    return f;
+}
+
+}  // namespace arso

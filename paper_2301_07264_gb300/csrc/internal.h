@@ -184,6 +184,7 @@ struct arso_error_list {
 namespace arso {
 // circuit.cpp
 void matrix_for(const arso_gate &g, HostGate &h);  // h.arity must be set
+std::vector<float> circuit_features(const arso_circuit *c, const arso_criterion *crit);
 void build_circuit(arso_circuit *c, uint32_t n, const arso_gate *gates, size_t n_gates,
                    const arso_compile_opts *opts);
 }  // namespace arso

@@ -1,0 +1,136 @@
+"""GPU surrogate MLP against the FP64 reference (oracle/mlp.py), through the C ABI.
+
+The GPU holds bfloat16 weights and accumulates in FP32; the reference runs in
+float64 on the same bfloat16-rounded weights and the same inputs, so the
+bars are FP32 accumulation bars: forward probabilities within 1e-5, each
+gradient tensor within 1e-3 relative (max-abs over max-abs), the loss within
+1e-6. Then: one Adam step against the reference step, and the trained
+network recovering a known pass-probability law.
+"""
+import numpy as np
+import pytest
+
+from oracle import mlp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+IN, H = 33, 256
+SLICES = {"W1": (0, IN * H, (IN, H)), "b1": (IN * H, H, (H,)), "W2": (IN * H + H, H * H, (H, H)),
+          "b2": (IN * H + H + H * H, H, (H,)), "W3": (IN * H + 2 * H + H * H, H, (H, 1)),
+          "b3": (IN * H + 3 * H + H * H, 1, (1,))}
+
+
+def unpack(flat):
+    return {k: np.asarray(flat[o:o + n], dtype=np.float64).reshape(s) for k, (o, n, s) in SLICES.items()}
+
+
+def pack(p):
+    out = np.zeros(sum(n for _, n, _ in SLICES.values()), dtype=np.float32)
+    for k, (o, n, s) in SLICES.items():
+        out[o:o + n] = p[k].reshape(-1)
+    return out
+
+
+@pytest.fixture(scope="module")
+def arso():
+    from paper_2301_07264_gb300 import arso as mod
+    return mod
+
+
+def _setup(arso, seed=0, n=96):
+    rng = np.random.default_rng(seed)
+    p = mlp.init_params(rng)
+    for k in p:
+        if k.startswith("b"):
+            p[k] = rng.standard_normal(p[k].shape) * 0.05
+    s = arso.surrogate_create(seed)
+    arso.surrogate_set_params(s, pack(p))
+    arso.surrogate_set_norm(s, np.zeros(IN), np.ones(IN))
+    pb = {k: mlp.bf16_round(v) for k, v in p.items()}      # what the GPU computes with
+    x = rng.standard_normal((n, IN)).astype(np.float32)
+    y = (rng.random(n) < 0.4).astype(np.float32)
+    return s, p, pb, x, y
+
+
+def test_forward_matches_reference(arso):
+    s, p, pb, x, y = _setup(arso)
+    dx = torch.from_numpy(x).cuda()
+    out = torch.empty(x.shape[0], dtype=torch.float32, device="cuda")
+    arso.surrogate_predict(s, dx, out)
+    z, _ = mlp.forward(pb, x.astype(np.float64))
+    assert np.max(np.abs(out.cpu().numpy() - mlp.sigmoid(z))) < 1e-5
+
+
+def test_gradients_match_reference(arso):
+    s, p, pb, x, y = _setup(arso, seed=1)
+    g, loss = arso.surrogate_grads(s, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
+    z, cache = mlp.forward(pb, x.astype(np.float64))
+    ref = mlp.backward(pb, cache, z, y.astype(np.float64))
+    assert abs(loss - mlp.bce(z, y.astype(np.float64))) < 1e-6
+    got = unpack(g)
+    for k in ref:
+        scale = np.max(np.abs(ref[k]))
+        assert np.max(np.abs(got[k] - ref[k])) <= 1e-3 * scale + 1e-9, k
+
+
+def test_one_adam_step_matches_reference(arso):
+    s, p, pb, x, y = _setup(arso, seed=2, n=64)
+    dx, dy = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    arso.surrogate_train(s, dx, dy, epochs=1, batch=64, lr=1e-3, seed=0)
+    z, cache = mlp.forward(pb, x.astype(np.float64))
+    g = mlp.backward(pb, cache, z, y.astype(np.float64))
+    master = {k: np.asarray(v, dtype=np.float64).copy() for k, v in unpack(pack(p)).items()}
+    mlp.adam(master, g, {}, lr=1e-3)
+    got = unpack(arso.surrogate_get_params(s))
+    for k in master:
+        # first Adam step moves each weight by lr * sign(g) (or less where g ~ 0)
+        assert np.max(np.abs(got[k] - master[k])) < 2e-5, k
+
+
+def test_training_learns_a_known_law(arso):
+    """Labels drawn from P(pass) = sigmoid(3 - 2 x0 + x1); the trained network's
+    prediction approaches that law (binary cross-entropy near its entropy floor)."""
+    rng = np.random.default_rng(5)
+    n = 200_000
+    x = rng.standard_normal((n, IN)).astype(np.float32)
+    pr = 1 / (1 + np.exp(-(3 - 2 * x[:, 0] + x[:, 1])))
+    y = (rng.random(n) < pr).astype(np.float32)
+    s = arso.surrogate_create(3)
+    dx, dy = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    loss = arso.surrogate_train(s, dx, dy, epochs=4, batch=2048, lr=2e-3, seed=1)
+    floor = float(np.mean(-(pr * np.log(pr) + (1 - pr) * np.log(1 - pr))))
+    assert loss < floor + 0.01
+    xt = rng.standard_normal((4096, IN)).astype(np.float32)
+    out = torch.empty(4096, dtype=torch.float32, device="cuda")
+    arso.surrogate_predict(s, torch.from_numpy(xt).cuda(), out)
+    truth = 1 / (1 + np.exp(-(3 - 2 * xt[:, 0] + xt[:, 1])))
+    assert np.mean(np.abs(out.cpu().numpy() - truth)) < 0.03
+
+
+def test_surrogate_search_agrees_with_plain_search(arso):
+    """Train on simulator rows from QAOA / brickwork circuits, then bracket the
+    tolerable rate (pass fraction >= 2/3) of unseen circuits: the verified
+    answer lies within 5% of the plain Monte Carlo search on the same random
+    numbers, with fewer plain probes."""
+    from paper_2301_07264_gb300 import surrogate_data
+    from workloads import circuits as W
+    train = [W.qaoa_maxcut(n, 100 + n + 20 * d) for n in (8, 10, 12) for d in range(3)]
+    train += [W.brickwork(n, depth, 200 + n + depth) for n in (8, 10, 12) for depth in (4, 8, 12, 16)]
+    for c in train:
+        c.criterion = W.Criterion("fidelity", threshold=0.9, aggregate="pass")
+    x, y = surrogate_data.generate(train, 300_000, seed=1, lp_lo=-4.5, lp_hi=-1.0, p_points=40)
+    s = arso.surrogate_create(7)
+    arso.surrogate_train(s, x, y, epochs=6, batch=4096, lr=2e-3, seed=2)
+    test = [W.brickwork(10, 10, 901), W.qaoa_maxcut(12, 902)]
+    for circ in test:
+        crit = W.Criterion("fidelity", threshold=0.9, aggregate="pass")
+        cc = arso.compile_circuit(circ.n, circ.gates)
+        plain = arso.tolerable_rate(cc, crit, 2 / 3, n_traj=4000, seed=3, mode="mc", rel_tol=0.01,
+                                    p_lo=1e-5, p_hi=1e-1)
+        sur = arso.tolerable_rate_surrogate(cc, crit, 2 / 3, s, n_traj=4000, seed=3, margin=0.1,
+                                            p_lo=1e-5, p_hi=1e-1)
+        assert sur.used_surrogate == 1
+        assert abs(sur.p - plain.p) / plain.p < 0.05, (circ.family, sur.p, plain.p)
+        if sur.verified:
+            assert sur.probes < plain.probes
