@@ -83,7 +83,10 @@ typedef struct {
  * cached error-free state at that pass boundary: the error-free suffix W is
  * unitary and common to both states, so <W a|W b> = <a|b> (exact). This flag
  * turns that off (every trajectory then runs to the end; for comparisons). */
-enum { ARSO_OPT_NO_SUFFIX_REUSE = 1 };
+/* The streaming engine records each batch's pass launches into a CUDA graph
+ * (keyed by the batch's pass range and slot count) and replays it for later
+ * batches of the same shape; this flag launches every pass directly. */
+enum { ARSO_OPT_NO_SUFFIX_REUSE = 1, ARSO_OPT_NO_GRAPHS = 2 };
 
 typedef struct arso_circuit arso_circuit;
 typedef struct arso_error_list arso_error_list;
@@ -181,6 +184,31 @@ arso_status arso_run_trajectories(const arso_circuit *c, const arso_error_list *
  * pointers; out[5] (host) = {mean score, pass fraction, stderr of the mean
  * score, stderr of the pass fraction, n}. FP64 sums in a fixed order. */
 arso_status arso_aggregate(const double *score, const uint8_t *pass_flags, uint64_t n, void *stream, double *out);
+
+/* Run the trajectories of many circuits of uneven sizes and depths in one
+ * call (Sec. IV-B, Monte Carlo runs, for a batch of circuits). Circuits with
+ * 10..13 qubits (complex64) run together in ONE persistent launch: CTAs pull
+ * (circuit, block of trajectories) items from a device queue, longest first,
+ * and a 2^n-amplitude circuit runs 2^(13-n) trajectories side by side in one
+ * CTA. Other circuits run their own resident launch or fused pass sequence
+ * (replayed from captured CUDA graphs). score_out[i] (n_traj of errors[i]
+ * doubles) and pass_out[i] (bytes, or NULL; pass_out itself may be NULL) are
+ * device or host pointers as in arso_run_trajectories. */
+arso_status arso_run_batch(size_t count, arso_circuit *const *circuits, const arso_error_list *const *errors,
+                           const arso_criterion *crits, void *stream, double *const *score_out,
+                           uint8_t *const *pass_out);
+
+/* Autotune the fused-pass schedule of a circuit by measurement: for each
+ * candidate (tile_qubits in 10..14, low_qubits in 3..5) compile the circuit,
+ * time n_traj trajectories at uniform rate p (CUDA events on `stream`,
+ * after one warm-up run that also builds the prefix cache) and return the
+ * fastest options in *best (precision and the other fields copied from
+ * `base`, which may be NULL). ms_out (optional, capacity 16) receives each
+ * candidate's time in candidate order, tile-major; *n_candidates their number.
+ * Circuits that fit the resident engine have a single candidate. */
+arso_status arso_autotune(uint32_t n_qubits, const arso_gate *gates, size_t n_gates, const arso_criterion *crit,
+                          double p, uint64_t n_traj, uint64_t seed, const arso_compile_opts *base, void *stream,
+                          arso_compile_opts *best, double *ms_out, uint32_t *n_candidates);
 
 /* Final state vectors of trajectories [first, first + count) of `errors`
  * (count * 2^n amplitudes, device pointer, layout per the circuit's

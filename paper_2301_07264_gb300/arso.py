@@ -196,6 +196,7 @@ def _gates_array(gates):
 
 
 OPT_NO_SUFFIX_REUSE = 1
+OPT_NO_GRAPHS = 2
 
 
 def compile_circuit(n, gates, precision=C64, tile_qubits=0, low_qubits=0, max_batch=0, cache_bytes=0, flags=0):
@@ -458,3 +459,41 @@ def tolerable_rate_surrogate(circ, crit, P_target, surrogate, p_lo=0.0, p_hi=0.0
     _check(lib.arso_tolerable_rate_surrogate(circ.handle, C.byref(c), P_target, C.byref(o), _stream(stream),
                                              C.byref(r)))
     return r
+
+
+lib.arso_run_batch.argtypes = [C.c_size_t, _vp, _vp, _vp, _vp, _vp, _vp]
+lib.arso_run_batch.restype = C.c_int
+
+
+def run_batch(circuits, error_lists, crits, score_outs, pass_outs=None, stream=None):
+    """One call over many circuits (see include/arso.h, arso_run_batch)."""
+    n = len(circuits)
+    ch = (C.c_void_p * n)(*[c.handle for c in circuits])
+    eh = (C.c_void_p * n)(*[e.handle for e in error_lists])
+    cs = (Criterion * n)()
+    keep = []
+    for i, cr in enumerate(crits):
+        c = cr if isinstance(cr, Criterion) else make_criterion(cr)
+        keep.append(c)
+        cs[i] = c
+    so = (C.c_void_p * n)(*[_ptr(x) for x in score_outs])
+    po = (C.c_void_p * n)(*[_ptr(x) for x in pass_outs]) if pass_outs is not None else None
+    _check(lib.arso_run_batch(n, ch, eh, cs, _stream(stream), so, po))
+
+
+lib.arso_autotune.argtypes = [C.c_uint32, C.POINTER(Gate), C.c_size_t, C.POINTER(Criterion), C.c_double, C.c_uint64,
+                              C.c_uint64, C.POINTER(CompileOpts), _vp, C.POINTER(CompileOpts), _vp, _vp]
+lib.arso_autotune.restype = C.c_int
+
+
+def autotune(n, gates, crit, p, n_traj=64, seed=0, precision=C64, stream=None):
+    """Measured best (tile_qubits, low_qubits) for a circuit; returns (opts dict, per-candidate ms)."""
+    arr, keep = _gates_array(gates)
+    c = crit if isinstance(crit, Criterion) else make_criterion(crit)
+    base = CompileOpts(precision, 0, 0, 0, 0, 0)
+    best = CompileOpts()
+    ms = np.zeros(16)
+    cnt = C.c_uint32()
+    _check(lib.arso_autotune(n, arr, len(gates), C.byref(c), p, n_traj, seed, C.byref(base), _stream(stream),
+                             C.byref(best), ms.ctypes.data, C.byref(cnt)))
+    return {"tile_qubits": best.tile_qubits, "low_qubits": best.low_qubits}, ms[: cnt.value]

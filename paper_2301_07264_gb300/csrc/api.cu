@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <functional>
+#include <map>
 #include <numeric>
 
 #include "kernels.h"
@@ -307,6 +308,19 @@ static PassArgs pass_args(const arso_circuit *c, uint32_t j) {
     return a;
 }
 
+struct GraphKey {
+    int jmin, jmax;
+    uint32_t slots;
+    bool operator<(const GraphKey &o) const {
+        return jmin != o.jmin ? jmin < o.jmin : jmax != o.jmax ? jmax < o.jmax : slots < o.slots;
+    }
+};
+struct GraphCache : std::map<GraphKey, cudaGraphExec_t> {
+    ~GraphCache() {
+        for (auto &kv : *this) cudaGraphExecDestroy(kv.second);
+    }
+};
+
 // Streaming engine over trajectories `ids` of the error list. states_out
 // (non-null) receives final states in the order of `ids` instead of scores.
 static void run_streaming(arso_circuit *c, const arso_error_list *e, const std::vector<uint64_t> &ids,
@@ -351,6 +365,9 @@ static void run_streaming(arso_circuit *c, const arso_error_list *e, const std::
     std::vector<uint32_t> cslot(c->ckpt_pass.begin(), c->ckpt_pass.end());
     Scratch d_cslot(st, cslot.size() * 4);
     h2d(d_cslot.ptr, cslot, st);
+    // captured pass sequences of this call, replayed for batches of the same shape
+    GraphCache graphs;
+    const bool use_graphs = !states_out && c->reg_blocked && !(c->flags & ARSO_OPT_NO_GRAPHS);
     for (size_t b0 = 0; b0 < ids.size(); b0 += B) {
         const size_t nb = std::min<size_t>(B, ids.size() - b0);
         std::vector<uint64_t> st_traj(nb);
@@ -366,6 +383,27 @@ static void run_streaming(arso_circuit *c, const arso_error_list *e, const std::
         h2d(d_slot_traj.ptr, st_traj, st);
         h2d(d_start.ptr, st_start, st);
         h2d(d_end.ptr, st_end, st);
+        double batch_bytes = 0;
+        for (uint32_t j = (uint32_t)jmin; j <= (uint32_t)jmax; ++j)
+            for (size_t i = 0; i < nb; ++i) batch_bytes += (st_start[i] <= (int)j && (int)j <= st_end[i]) ? 2.0 * sb : 0.0;
+        const uint64_t n_launch = (uint64_t)(jmax - jmin + 1) + (states_out ? 0 : 1);
+        const GraphKey key{jmin, jmax, (uint32_t)nb};
+        auto hit = graphs.find(key);
+        if (hit != graphs.end()) {  // replay: the slot tables above are the only inputs that changed
+            {
+                ProfScope ps_(ARSO_K_PASS, batch_bytes, st);
+                ARSO_CUDA(cudaGraphLaunch(hit->second, st));
+            }
+            prof_add_launches(ARSO_K_PASS, n_launch - 1);
+            ARSO_CUDA(cudaStreamSynchronize(st));
+            continue;
+        }
+        const bool capture = use_graphs;
+        if (capture) {
+            if (c->reg_blocked) prepare_pass_rb();
+            ARSO_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            prof_suspend(true);
+        }
         for (uint32_t j = (uint32_t)jmin; j <= (uint32_t)jmax; ++j) {
             PassArgs a = pass_args(c, j);
             a.cache = c->d_cache.ptr;
@@ -387,6 +425,21 @@ static void run_streaming(arso_circuit *c, const arso_error_list *e, const std::
         if (!states_out)
             launch_finish_partials(parts.as<Partial>(), tiles, (uint32_t)nb, d_slot_traj.as<uint64_t>(), crit, d_score,
                                    d_pass, st);
+        if (capture) {
+            prof_suspend(false);
+            cudaGraph_t g = nullptr;
+            ARSO_CUDA(cudaStreamEndCapture(st, &g));
+            cudaGraphExec_t ex = nullptr;
+            const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            ARSO_CUDA(ie);
+            graphs[key] = ex;
+            {
+                ProfScope ps_(ARSO_K_PASS, batch_bytes, st);
+                ARSO_CUDA(cudaGraphLaunch(ex, st));
+            }
+            prof_add_launches(ARSO_K_PASS, n_launch - 1);
+        }
         ARSO_CUDA(cudaStreamSynchronize(st));  // host vectors and slot tables are reused per batch
     }
 }
@@ -743,6 +796,182 @@ arso_status arso_aggregate(const double *score, const uint8_t *pass_flags, uint6
         out[2] = std::sqrt(vs / N);
         out[3] = std::sqrt(vp / N);
         out[4] = (double)n;
+    });
+}
+
+arso_status arso_run_batch(size_t count, arso_circuit *const *circuits, const arso_error_list *const *errors,
+                           const arso_criterion *crits, void *stream, double *const *score_out,
+                           uint8_t *const *pass_out) {
+    return guard([&] {
+        ARSO_REQUIRE(count == 0 || (circuits && errors && crits && score_out), "NULL argument");
+        cudaStream_t st = (cudaStream_t)stream;
+        std::vector<DevCrit> dcs(count);
+        std::vector<std::unique_ptr<Scratch>> tmp;
+        std::vector<double *> d_score(count);
+        std::vector<uint8_t *> d_pass(count);
+        for (size_t i = 0; i < count; ++i) {
+            arso_circuit *c = circuits[i];
+            const arso_error_list *e = errors[i];
+            ARSO_REQUIRE(c && e && score_out[i], "NULL circuit, error list or output");
+            ARSO_REQUIRE(e->circ == c, "error list belongs to another circuit");
+            make_crit(c, &crits[i], dcs[i], st);
+            ensure_cache(c, st);
+            const uint64_t T = std::max<uint64_t>(e->n_traj, 1);
+            if (is_device_ptr(score_out[i])) {
+                d_score[i] = score_out[i];
+            } else {
+                tmp.emplace_back(new Scratch(st, T * 8));
+                d_score[i] = tmp.back()->as<double>();
+            }
+            uint8_t *po = pass_out ? pass_out[i] : nullptr;
+            if (po && is_device_ptr(po)) {
+                d_pass[i] = po;
+            } else if (po) {
+                tmp.emplace_back(new Scratch(st, T));
+                d_pass[i] = tmp.back()->as<uint8_t>();
+            } else {
+                d_pass[i] = nullptr;
+            }
+        }
+        // the register-blocked resident circuits share one persistent launch
+        std::vector<size_t> group;
+        for (size_t i = 0; i < count; ++i) {
+            if (circuits[i]->engine == 0 && circuits[i]->reg_blocked) group.push_back(i);
+            else run_all(circuits[i], errors[i], dcs[i], st, d_score[i], d_pass[i]);
+        }
+        if (!group.empty()) {
+            Scratch refs(st, group.size() * 8);
+            std::vector<BatchCircuit> descs(group.size());
+            std::vector<BatchItem> items;
+            std::vector<uint64_t> ids;
+            double bytes = 0;
+            for (size_t gi = 0; gi < group.size(); ++gi) {
+                const size_t i = group[gi];
+                arso_circuit *c = circuits[i];
+                const arso_error_list *e = errors[i];
+                double *ref = refs.as<double>() + gi;
+                score_into(ref_state_ptr(c), ref_state_ptr(c), (int)c->n, c->precision, dcs[i].d, ref, st);
+                launch_fill_error_free(e->d_first.as<uint32_t>(), e->n_traj, ref, dcs[i].d.threshold, d_score[i],
+                                       d_pass[i], st);
+                BatchCircuit &b = descs[gi];
+                b.n = (int)c->n;
+                b.n_phases = (uint32_t)c->ph_R.size();
+                b.n_ckpt = c->n_ckpt;
+                b.ckpt_every = (uint32_t)c->ckpt_every;
+                b.gates = c->d_gates.as<DGate>();
+                b.mats = c->d_mats.as<float2>();
+                b.ph_gb = c->d_ph_gb.as<uint32_t>();
+                b.ph_R = c->d_ph_R.as<uint32_t>();
+                b.phase_of_pos = c->d_phase_of_pos.as<uint32_t>();
+                b.rpos = c->d_rpos.as<uint8_t>();
+                b.cache = c->d_cache.as<float2>();
+                b.offsets = e->d_offsets.as<uint64_t>();
+                b.keys = e->d_key.as<uint32_t>();
+                b.crit = dcs[i].d;
+                b.score = d_score[i];
+                b.pass_flags = d_pass[i];
+                if (!e->n_traj) continue;
+                std::vector<uint32_t> first(e->n_traj);
+                copy_d2h(first.data(), e->d_first.ptr, e->n_traj * 4, st);
+                ARSO_CUDA(cudaStreamSynchronize(st));
+                std::vector<std::pair<uint32_t, uint64_t>> todo;  // (checkpoint, trajectory)
+                for (uint64_t t = 0; t < e->n_traj; ++t)
+                    if (first[t] != NO_EVENT) todo.emplace_back(c->phase_of_pos[first[t]] / (uint32_t)c->ckpt_every, t);
+                std::sort(todo.begin(), todo.end());
+                const uint32_t per_cta = 1u << (13 - c->n);
+                for (size_t k = 0; k < todo.size(); k += per_cta) {
+                    BatchItem it{};
+                    it.circuit = (uint32_t)gi;
+                    it.count = (uint32_t)std::min<size_t>(per_cta, todo.size() - k);
+                    it.ck = todo[k].first;
+                    it.off = ids.size();
+                    for (size_t q = 0; q < it.count; ++q) ids.push_back(todo[k + q].second);
+                    items.push_back(it);
+                    bytes += (double)it.count * 2.0 * c->state_bytes();
+                }
+            }
+            // longest items first (remaining phases), so the queue drains evenly
+            std::stable_sort(items.begin(), items.end(), [&](const BatchItem &x, const BatchItem &y) {
+                const BatchCircuit &a = descs[x.circuit], &b = descs[y.circuit];
+                return (uint64_t)(a.n_phases - x.ck * a.ckpt_every) > (uint64_t)(b.n_phases - y.ck * b.ckpt_every);
+            });
+            if (!items.empty()) {
+                Scratch d_descs(st, descs.size() * sizeof(BatchCircuit)), d_items(st, items.size() * sizeof(BatchItem));
+                Scratch d_ids(st, ids.size() * 8), d_counter(st, 4);
+                copy_h2d(d_descs.ptr, descs.data(), descs.size() * sizeof(BatchCircuit), st);
+                copy_h2d(d_items.ptr, items.data(), items.size() * sizeof(BatchItem), st);
+                copy_h2d(d_ids.ptr, ids.data(), ids.size() * 8, st);
+                ARSO_CUDA(cudaMemsetAsync(d_counter.ptr, 0, 4, st));
+                launch_batch_resident(d_descs.as<BatchCircuit>(), d_items.as<BatchItem>(), (uint32_t)items.size(),
+                                      d_counter.as<uint32_t>(), d_ids.as<uint64_t>(), bytes, st);
+                ARSO_CUDA(cudaStreamSynchronize(st));
+            }
+        }
+        for (size_t i = 0; i < count; ++i) {
+            const uint64_t T = errors[i]->n_traj;
+            if (!T) continue;
+            if (d_score[i] != score_out[i]) copy_d2h(score_out[i], d_score[i], T * 8, st);
+            if (pass_out && pass_out[i] && d_pass[i] != pass_out[i]) copy_d2h(pass_out[i], d_pass[i], T, st);
+        }
+        ARSO_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+arso_status arso_autotune(uint32_t n_qubits, const arso_gate *gates, size_t n_gates, const arso_criterion *crit,
+                          double p, uint64_t n_traj, uint64_t seed, const arso_compile_opts *base, void *stream,
+                          arso_compile_opts *best, double *ms_out, uint32_t *n_candidates) {
+    return guard([&] {
+        ARSO_REQUIRE(crit && best, "NULL argument");
+        ARSO_REQUIRE(p >= 0 && p <= 1 && n_traj > 0, "need p in [0, 1] and n_traj > 0");
+        cudaStream_t st = (cudaStream_t)stream;
+        arso_compile_opts b0{};
+        if (base) b0 = *base;
+        std::vector<arso_compile_opts> cands;
+        const int rmax = b0.precision == ARSO_C128 ? RESIDENT_MAX_N_C128 : RESIDENT_MAX_N_C64;
+        if ((int)n_qubits <= rmax) {
+            cands.push_back(b0);
+        } else {
+            for (uint32_t t = 10; t <= 14 && t <= n_qubits; ++t)
+                for (uint32_t lq = 3; lq <= 5; ++lq) {
+                    arso_compile_opts o = b0;
+                    o.tile_qubits = t;
+                    o.low_qubits = lq;
+                    cands.push_back(o);
+                }
+        }
+        cudaEvent_t e0, e1;
+        ARSO_CUDA(cudaEventCreate(&e0));
+        ARSO_CUDA(cudaEventCreate(&e1));
+        double best_ms = INFINITY;
+        size_t best_i = 0;
+        for (size_t i = 0; i < cands.size(); ++i) {
+            arso_circuit *c = nullptr;
+            arso_status s1 = arso_compile_circuit(n_qubits, gates, n_gates, &cands[i], &c);
+            if (s1 != ARSO_OK) throw Error(s1, arso_last_error());
+            std::unique_ptr<arso_circuit> hold(c);
+            DevCrit dc;
+            make_crit(c, crit, dc, st);
+            Scratch sc(st, n_traj * 8);
+            double ms = 0;
+            for (int rep = 0; rep < 2; ++rep) {  // the first run builds the prefix cache
+                arso_error_list *raw = nullptr;
+                ARSO_CUDA(cudaEventRecord(e0, st));
+                sample(c, p / 3, p / 3, p / 3, seed, 0, n_traj, st, &raw);
+                std::unique_ptr<arso_error_list> e(raw);
+                run_all(c, e.get(), dc, st, sc.as<double>(), nullptr);
+                ARSO_CUDA(cudaEventRecord(e1, st));
+                ARSO_CUDA(cudaEventSynchronize(e1));
+                float f = 0;
+                ARSO_CUDA(cudaEventElapsedTime(&f, e0, e1));
+                ms = f;
+            }
+            if (ms_out && i < 16) ms_out[i] = ms;
+            if (ms < best_ms) best_ms = ms, best_i = i;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        *best = cands[best_i];
+        if (n_candidates) *n_candidates = (uint32_t)cands.size();
     });
 }
 

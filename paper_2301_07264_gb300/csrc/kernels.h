@@ -87,6 +87,33 @@ struct PassArgs {
 };
 
 void launch_pass_rb(const PassArgs &a, bool last, uint32_t slots, double bytes, cudaStream_t st);
+void prepare_pass_rb();
+
+// Batched resident execution: one persistent launch over (circuit, trajectory
+// block) items of many register-blocked resident circuits (10 <= n <= 13).
+struct BatchCircuit {
+    int n;
+    uint32_t n_phases, n_ckpt, ckpt_every;
+    const DGate *gates;
+    const float2 *mats;
+    const uint32_t *ph_gb, *ph_R, *phase_of_pos;
+    const uint8_t *rpos;
+    const float2 *cache;
+    const uint64_t *offsets;
+    const uint32_t *keys;
+    DCrit crit;
+    double *score;
+    uint8_t *pass_flags;
+};
+struct BatchItem {
+    uint32_t circuit;   // index into the circuit descriptors
+    uint32_t count;     // trajectories in this item (<= 2^(13 - n))
+    uint32_t ck;        // checkpoint every trajectory of the item starts from
+    uint32_t pad;
+    uint64_t off;       // first entry in the trajectory-id array
+};
+void launch_batch_resident(const BatchCircuit *circs, const BatchItem *items, uint32_t n_items, uint32_t *counter,
+                           const uint64_t *ids, double bytes, cudaStream_t st);
 
 void launch_resident(const ResidentArgs &a, bool ideal, int precision, double bytes, cudaStream_t st);
 void launch_pass(const PassArgs &a, bool last, int precision, uint32_t slots, double bytes, cudaStream_t st);

@@ -107,6 +107,7 @@ struct TileCtx {
     uint32_t tpart;        // thread part of the local index
     uint32_t m;            // X mask (stored[j] = state[j ^ m])
     uint32_t gp;           // global phase i^gp
+    uint32_t tid, nthr;    // thread index within the tile's thread group, group size
 };
 
 __device__ __forceinline__ uint32_t reg_pos(const TileCtx &c, uint32_t q) {
@@ -196,7 +197,7 @@ __device__ __forceinline__ void set_phase(TileCtx &c, uint32_t packed, int t) {
     c.rmask = 0;
 #pragma unroll
     for (int b = 0; b < REG_BITS; ++b) c.rmask |= 1u << c.r[b];
-    c.tpart = thread_part(threadIdx.x, c.rmask, t);
+    c.tpart = thread_part(c.tid, c.rmask, t);
 }
 
 // The swizzle is linear over XOR, so the shared-memory slot of register ri is
@@ -238,13 +239,14 @@ __device__ __forceinline__ void remap(float2 (&v)[32], float2 *sm, TileCtx &c, u
 
 // Dense two-qubit gates and SWAP are rare: they run through shared memory on
 // the stored data (U already conjugated by the mask) with runtime indices.
-__device__ __forceinline__ void smem_dense2(float2 *sm, int t, uint32_t q0, uint32_t q1, const float2 *__restrict__ U) {
+__device__ __forceinline__ void smem_dense2(float2 *sm, int t, uint32_t q0, uint32_t q1, const float2 *__restrict__ U,
+                                            uint32_t tid, uint32_t nthr) {
     const uint32_t lo = q0 < q1 ? q0 : q1, hi = q0 < q1 ? q1 : q0;
     const uint32_t m0 = 1u << q0, m1 = 1u << q1;
     float2 M[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) M[k] = U[k];
-    for (uint32_t p = threadIdx.x; p < (1u << (t - 2)); p += blockDim.x) {
+    for (uint32_t p = tid; p < (1u << (t - 2)); p += nthr) {
         const uint32_t i = insert_zero2(p, lo, hi);
         const uint32_t ix[4] = {swz(i), swz(i | m0), swz(i | m1), swz(i | m0 | m1)};
         float2 a[4];
@@ -312,8 +314,8 @@ __device__ __forceinline__ void apply_gate_rb(float2 (&v)[32], TileCtx &c, const
         case GC_DENSE2:
         case GC_SWAP: {
             const uint32_t mab = ((c.m >> g.q0) & 1u) | (((c.m >> g.q1) & 1u) << 1);
-            if (threadIdx.x < 16) {
-                const uint32_t k = threadIdx.x >> 2, l = threadIdx.x & 3u;
+            if (c.tid < 16) {
+                const uint32_t k = c.tid >> 2, l = c.tid & 3u;
                 float2 u;
                 if (g.cls == GC_SWAP) {
                     const uint32_t perm[4] = {0, 2, 1, 3};
@@ -321,12 +323,12 @@ __device__ __forceinline__ void apply_gate_rb(float2 (&v)[32], TileCtx &c, const
                 } else {
                     u = M[4 * (k ^ mab) + (l ^ mab)];
                 }
-                ubuf[threadIdx.x] = u;
+                ubuf[c.tid] = u;
             }
             __syncthreads();
             to_smem(v, sm, c);
             __syncthreads();
-            smem_dense2(sm, t, g.q0, g.q1, ubuf);
+            smem_dense2(sm, t, g.q0, g.q1, ubuf, c.tid, c.nthr);
             __syncthreads();
             from_smem(v, sm, c);
             __syncthreads();
@@ -391,6 +393,8 @@ __global__ void __launch_bounds__(512, 1) pass_rb_kernel(PassArgs a) {
     TileCtx c;
     c.m = 0;
     c.gp = 0;
+    c.tid = threadIdx.x;
+    c.nthr = blockDim.x;
     set_phase(c, load_packed, t);
 
     const uint32_t *ev = nullptr, *ev_end = nullptr;
@@ -459,10 +463,10 @@ __global__ void __launch_bounds__(512, 1) pass_rb_kernel(PassArgs a) {
 // the cached error-free state at the checkpoint (phase boundary) at or before
 // its first error and runs the remaining phases; ckpt_every counts phases.
 
-__device__ __forceinline__ void rb_load_linear(float2 (&v)[32], const float2 *src, int t) {
+__device__ __forceinline__ void rb_load_linear(float2 (&v)[32], const float2 *src, int t, uint32_t tid) {
 #pragma unroll
     for (int hi = 0; hi < 16; ++hi) {
-        const uint32_t j = ((uint32_t)hi << (t - 4)) | (threadIdx.x << 1);
+        const uint32_t j = ((uint32_t)hi << (t - 4)) | (tid << 1);
         const float4 w = __ldg(reinterpret_cast<const float4 *>(src + j));
         v[2 * hi] = make_float2(w.x, w.y);
         v[2 * hi + 1] = make_float2(w.z, w.w);
@@ -480,7 +484,7 @@ __device__ __forceinline__ void rb_store_linear(float2 (&v)[32], float2 *sm, Til
     const uint32_t k2 = 2u * c.gp;
 #pragma unroll
     for (int hi = 0; hi < 16; ++hi) {
-        const uint32_t j = (((uint32_t)hi << (t - 4)) | (threadIdx.x << 1)) ^ (c.m & ~1u);
+        const uint32_t j = (((uint32_t)hi << (t - 4)) | (c.tid << 1)) ^ (c.m & ~1u);
         float2 e = flip0 ? v[2 * hi + 1] : v[2 * hi];
         float2 o = flip0 ? v[2 * hi] : v[2 * hi + 1];
         if (k2) {
@@ -509,6 +513,8 @@ __global__ void __launch_bounds__(512, 1) resident_rb_kernel(ResidentArgs a) {
         TileCtx c;
         c.m = 0;
         c.gp = 0;
+        c.tid = threadIdx.x;
+        c.nthr = blockDim.x;
         set_phase(c, load_packed, t);
         uint32_t cur_packed = load_packed;
         uint32_t ph0 = 0;
@@ -536,7 +542,7 @@ __global__ void __launch_bounds__(512, 1) resident_rb_kernel(ResidentArgs a) {
                 ck = a.phase_of_pos[first] / (uint32_t)a.ckpt_every;
                 ph0 = ck * (uint32_t)a.ckpt_every;
             }
-            rb_load_linear(v, cache + (size_t)ck * N, t);
+            rb_load_linear(v, cache + (size_t)ck * N, t, c.tid);
             ev = a.keys + a.offsets[tr];
             ev_end = a.keys + a.offsets[tr + 1];
         }
@@ -610,21 +616,139 @@ void launch_resident_rb(const ResidentArgs &a, int mode, double bytes, cudaStrea
     ARSO_CUDA(cudaGetLastError());
 }
 
+// --------------------------------------------------------- batched resident ---
+// Persistent CTAs of 256 threads pull (circuit, trajectory block) items from a
+// device counter. A circuit of n qubits needs 2^(n-5) threads per trajectory,
+// so one CTA runs 2^(13-n) trajectories of the same circuit side by side: the
+// sub-groups share the circuit's phase program (uniform barriers) and keep
+// their own registers, shared-memory tile, index mask and error events.
+constexpr int BATCH_THREADS = 256;
+
+__global__ void __launch_bounds__(BATCH_THREADS, 2)
+    batch_resident_kernel(const BatchCircuit *__restrict__ circs, const BatchItem *__restrict__ items, uint32_t n_items,
+                          uint32_t *counter, const uint64_t *__restrict__ ids) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint32_t s_item;
+    __shared__ Partial red[BATCH_THREADS / 32];
+    __shared__ float2 ubuf[8][16];
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1u);
+        __syncthreads();
+        const uint32_t item = s_item;
+        if (item >= n_items) return;
+        const BatchItem it = items[item];
+        const BatchCircuit &C = circs[it.circuit];
+        const int t = C.n;
+        const uint32_t N = 1u << t, gsize = 1u << (t - REG_BITS), sg = threadIdx.x / gsize;
+        float2 *sm = reinterpret_cast<float2 *>(smem_raw) + (size_t)sg * N;
+        const bool active = sg < it.count;
+        const uint64_t tr = ids[it.off + (active ? sg : 0)];
+        const uint32_t load_packed = 0u | ((uint32_t)(t - 4) << 5) | ((uint32_t)(t - 3) << 10) |
+                                     ((uint32_t)(t - 2) << 15) | ((uint32_t)(t - 1) << 20);
+        TileCtx c;
+        c.m = 0;
+        c.gp = 0;
+        c.tid = threadIdx.x % gsize;
+        c.nthr = gsize;
+        set_phase(c, load_packed, t);
+        float2 v[32];
+        rb_load_linear(v, C.cache + (size_t)it.ck * N, t, c.tid);
+        const uint32_t *ev = C.keys + C.offsets[tr];
+        const uint32_t *ev_end = C.keys + C.offsets[tr + 1];
+        uint32_t next = ev < ev_end ? *ev : NO_EVENT;
+        uint32_t cur_packed = load_packed;
+        for (uint32_t ph = it.ck * C.ckpt_every; ph < C.n_phases; ++ph) {
+            const uint32_t R = C.ph_R[ph];
+            if (R != cur_packed) {
+                remap(v, sm, c, R, t);
+                cur_packed = R;
+            }
+            const uint32_t ge = C.ph_gb[ph + 1];
+            for (uint32_t g = C.ph_gb[ph]; g < ge; ++g) {
+                const DGate gate = C.gates[g];
+                apply_gate_rb(v, c, gate, C.rpos[g], C.mats, sm, ubuf[sg], t);
+                while (next != NO_EVENT && ev_pos(next) == g) {
+                    rg_pauli(v, c, ev_slot(next) ? gate.q1 : gate.q0, ev_code(next));
+                    ++ev;
+                    next = ev < ev_end ? *ev : NO_EVENT;
+                }
+            }
+        }
+        if (c.gp) {
+#pragma unroll
+            for (int ri = 0; ri < 32; ++ri) v[ri] = omega_mul(v[ri], 2u * c.gp);
+        }
+        const float2 *ref = C.cache + (size_t)(C.n_ckpt - 1) * N;
+        Partial acc = empty_partial();
+#pragma unroll
+        for (int ri = 0; ri < 32; ++ri) {
+            const uint32_t jj = (c.tpart | reg_part(ri, c.r)) ^ c.m;
+            accumulate(acc, C.crit, v[ri], ref, jj);
+        }
+        // per sub-group reduction: warps reduce by shuffles, the sub-group leader combines its warps
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double a2 = __shfl_down_sync(0xffffffffu, acc.a, o);
+            const double b2 = __shfl_down_sync(0xffffffffu, acc.b, o);
+            const double mp = __shfl_down_sync(0xffffffffu, acc.maxp, o);
+            const unsigned long long mi = __shfl_down_sync(0xffffffffu, acc.idx, o);
+            acc.a += a2;
+            acc.b += b2;
+            argmax_merge(acc.maxp, acc.idx, mp, mi);
+        }
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (c.tid == 0 && active) {
+            Partial s = empty_partial();
+            const uint32_t w0 = (sg * gsize) >> 5, nw = gsize >> 5;
+            for (uint32_t w = w0; w < w0 + nw; ++w) {
+                s.a += red[w].a;
+                s.b += red[w].b;
+                argmax_merge(s.maxp, s.idx, red[w].maxp, red[w].idx);
+            }
+            const double sc = finish_score(C.crit, s);
+            C.score[tr] = sc;
+            if (C.pass_flags) C.pass_flags[tr] = sc >= C.crit.threshold;
+        }
+    }
+}
+
+void launch_batch_resident(const BatchCircuit *circs, const BatchItem *items, uint32_t n_items, uint32_t *counter,
+                           const uint64_t *ids, double bytes, cudaStream_t st) {
+    if (!n_items) return;
+    ProfScope ps_(ARSO_K_RESIDENT, bytes, st);
+    const size_t smem = (size_t(1) << 13) * sizeof(float2);
+    ARSO_CUDA(cudaFuncSetAttribute(batch_resident_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 1, dev = 0, sms = 152;
+    ARSO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_resident_kernel, BATCH_THREADS, smem));
+    ARSO_CUDA(cudaGetDevice(&dev));
+    ARSO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const unsigned grid = (unsigned)std::min<uint64_t>(n_items, (uint64_t)std::max(per_sm, 1) * sms);
+    batch_resident_kernel<<<grid, BATCH_THREADS, smem, st>>>(circs, items, n_items, counter, ids);
+    ARSO_CUDA(cudaGetLastError());
+}
+
+// Raise the dynamic shared-memory limit of both pass variants once, before any
+// launch (and outside stream capture).
+void prepare_pass_rb() {
+    static bool done = false;
+    if (done) return;
+    const int smem = (1 << MAX_TILE_QUBITS) * (int)sizeof(float2);
+    ARSO_CUDA(cudaFuncSetAttribute(pass_rb_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    ARSO_CUDA(cudaFuncSetAttribute(pass_rb_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    done = true;
+}
+
 void launch_pass_rb(const PassArgs &a, bool last, uint32_t slots, double bytes, cudaStream_t st) {
     ProfScope ps_(last && !a.store_last ? ARSO_K_PASS_LAST : ARSO_K_PASS, bytes, st);
+    prepare_pass_rb();
     const uint32_t tiles = 1u << (a.n - a.t);
     const int nt = 1 << (a.t - REG_BITS);
     const size_t smem = (size_t(1) << a.t) * sizeof(float2);
     dim3 grid(tiles, slots);
-    if (last) {
-        if (smem > 48 * 1024)
-            ARSO_CUDA(cudaFuncSetAttribute(pass_rb_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        pass_rb_kernel<true><<<grid, nt, smem, st>>>(a);
-    } else {
-        if (smem > 48 * 1024)
-            ARSO_CUDA(cudaFuncSetAttribute(pass_rb_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        pass_rb_kernel<false><<<grid, nt, smem, st>>>(a);
-    }
+    if (last) pass_rb_kernel<true><<<grid, nt, smem, st>>>(a);
+    else pass_rb_kernel<false><<<grid, nt, smem, st>>>(a);
     ARSO_CUDA(cudaGetLastError());
 }
 

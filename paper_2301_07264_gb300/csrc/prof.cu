@@ -26,6 +26,7 @@ State &state() {
     return s;
 }
 std::atomic<uint64_t> g_launches{0}, g_h2d{0}, g_d2h{0};
+thread_local bool g_suspended = false;
 
 cudaEvent_t take_event(State &s) {
     if (!s.free_events.empty()) {
@@ -58,9 +59,10 @@ void resolve(State &s) {
 }  // namespace
 
 void prof_begin(int kind, double, cudaStream_t st, cudaEvent_t *ev_out) {
+    *ev_out = nullptr;
+    if (g_suspended) return;
     g_launches.fetch_add(1, std::memory_order_relaxed);
     State &s = state();
-    *ev_out = nullptr;
     std::lock_guard<std::mutex> lk(s.mu);
     s.stats[kind].launches += 1;
     if (!s.timing) return;
@@ -82,6 +84,13 @@ void prof_end(int kind, double bytes, cudaStream_t st, cudaEvent_t start) {
 }
 
 void prof_count_h2d(uint64_t b) { g_h2d.fetch_add(b, std::memory_order_relaxed); }
+void prof_suspend(bool on) { g_suspended = on; }
+void prof_add_launches(int kind, uint64_t n) {
+    g_launches.fetch_add(n, std::memory_order_relaxed);
+    State &s = state();
+    std::lock_guard<std::mutex> lk(s.mu);
+    s.stats[kind].launches += n;
+}
 void prof_count_d2h(uint64_t b) { g_d2h.fetch_add(b, std::memory_order_relaxed); }
 
 }  // namespace arso

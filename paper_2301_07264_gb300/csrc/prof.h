@@ -14,6 +14,10 @@ void prof_begin(int kind, double bytes, cudaStream_t st, cudaEvent_t *ev_out);
 void prof_end(int kind, double bytes, cudaStream_t st, cudaEvent_t start);
 void prof_count_h2d(uint64_t bytes);
 void prof_count_d2h(uint64_t bytes);
+// while suspended (stream capture) scopes record nothing
+void prof_suspend(bool on);
+// a replayed graph: count its kernel launches under `kind` and time it as one scope
+void prof_add_launches(int kind, uint64_t n);
 
 struct ProfScope {
     int kind;

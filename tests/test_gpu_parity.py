@@ -442,3 +442,25 @@ def test_grover12_reference_state_unbiased(arso):
     psi = statevector.simulate(circ)
     assert np.max(np.abs(got - psi)) < AMP_TOL_C64
     assert abs(np.vdot(got, got).real - 1.0) < 1e-5
+
+
+def test_graph_replay_equals_direct_launches(arso):
+    """Small batches force many replays of captured pass sequences."""
+    circ = C.brickwork(16, 16, seed=8)
+    kw = dict(tile_qubits=11, max_batch=3)
+    g = arso.compile_circuit(circ.n, circ.gates, **kw)
+    d = arso.compile_circuit(circ.n, circ.gates, flags=arso.OPT_NO_GRAPHS, **kw)
+    T, p = 40, 3e-3
+    sg, sd = np.zeros(T), np.zeros(T)
+    arso.run_trajectories(g, arso.sample_errors(g, p / 3, p / 3, p / 3, 4, 0, T), circ.criterion, sg)
+    arso.run_trajectories(d, arso.sample_errors(d, p / 3, p / 3, p / 3, 4, 0, T), circ.criterion, sd)
+    assert np.array_equal(sg, sd)
+
+
+def test_autotune_returns_a_measured_candidate(arso):
+    circ = C.brickwork(15, 8, seed=2)
+    best, ms = arso.autotune(circ.n, circ.gates, circ.criterion, 1e-3, n_traj=16)
+    assert len(ms) == 15 and np.all(ms > 0)
+    assert 10 <= best["tile_qubits"] <= 14 and 3 <= best["low_qubits"] <= 5
+    k = (best["tile_qubits"] - 10) * 3 + (best["low_qubits"] - 3)
+    assert ms[k] == ms.min()
