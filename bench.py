@@ -343,9 +343,19 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-suffix", action="store_true",
                     help="run every trajectory to the end instead of scoring after its last error")
+    ap.add_argument("--workload", default="brickwork24", choices=["brickwork24", "grover12", "mix256", "search"],
+                    help="brickwork24 is the benchmark line; the others measure the other configurations")
+    ap.add_argument("--search-circuits", type=int, default=8)
+    ap.add_argument("--train-rows", type=int, default=2_000_000)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "brickwork24":
+        from paper_2301_07264_gb300 import bench_workloads
+        line = bench_workloads.run(args)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return 0
     return run_ours(args)
 
 

@@ -1,0 +1,190 @@
+"""Measurements of the workloads other than the default benchmark line
+(used by bench.py --workload ...): the Grover-12 error-rate sweep, the
+256-circuit uneven batch, and the surrogate-bracketed tolerable-rate search.
+Every measured step runs through the C ABI; this module arranges calls."""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+
+
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _kernel_stats(arso):
+    names = (("pass", arso.K_PASS), ("pass_last", arso.K_PASS_LAST), ("resident", arso.K_RESIDENT),
+             ("sample", arso.K_SAMPLE), ("reduce", arso.K_REDUCE), ("other", arso.K_OTHER))
+    out = {}
+    for name, k in names:
+        st = arso.profile_read(k)
+        out[name] = {"launches": st.launches, "ms": st.ms, "GB": st.bytes / 1e9}
+    return out
+
+
+def grover12(args):
+    """Grover (11 search qubits + 1 borrowed), argmax criterion, 16 rates
+    logspace(1e-5, 1e-2); a step runs traj_per_step trajectories at every rate."""
+    import torch
+    from paper_2301_07264_gb300 import arso
+    from workloads import circuits as W
+    circ = W.grover12(0)
+    cc = arso.compile_circuit(circ.n, circ.gates)
+    crit = arso.make_criterion(circ.criterion)
+    rates = np.logspace(-5, -2, 16)
+    per = max(1, args.traj_per_step // 16)
+    score = torch.empty(per, dtype=torch.float64, device="cuda")
+    flags = torch.empty(per, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    res = np.zeros(16)
+
+    def step(k):
+        for i, p in enumerate(rates):
+            e = arso.sample_errors(cc, p / 3, p / 3, p / 3, 0, k * per, per, stream)
+            arso.run_trajectories(cc, e, crit, score, flags, stream)
+            res[i] += arso.aggregate(score, flags, stream)[1]
+
+    for w in range(args.warmup):
+        step(1000 + w)
+    res[:] = 0
+    arso.profile_reset()
+    arso.profile_enable(True)
+    e0, e1 = _events()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(args.steps):
+        step(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    arso.profile_enable(False)
+    sec = e0.elapsed_time(e1) / 1e3
+    total = per * 16 * args.steps
+    info = cc.info()
+    return {"metric": "error-injected trajectories/sec", "value": total / sec, "unit": "traj/s",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "grover12_sweep", "n_qubits": 12, "G": info.G, "L": info.L,
+                       "rates": "16 log-spaced in [1e-5, 1e-2]", "traj_per_rate_per_step": per,
+                       "criterion": "argmax == marked", "engine": "resident (whole state in one CTA)"},
+            "results": {"pass_frac": (res / args.steps).round(4).tolist()},
+            "kernels": _kernel_stats(arso)}
+
+
+def mix256(args):
+    """256 circuits of 8..22 qubits (QFT, Grover, QAOA p=2, adders) at p = 5e-4,
+    2000 trajectories each per step, one arso_run_batch call per step; the
+    streaming circuits use tile shapes picked by arso_autotune (per qubit count)."""
+    import torch
+    from paper_2301_07264_gb300 import arso
+    from workloads import circuits as W
+    mix = W.mix_family(0)
+    p, T = 5e-4, 2000
+    tuned = {}
+    t0 = time.perf_counter()
+    for circ in mix:
+        if circ.n > 13 and circ.n not in tuned:
+            tuned[circ.n], _ = arso.autotune(circ.n, circ.gates, circ.criterion, p * 8, n_traj=64)
+    tune_s = time.perf_counter() - t0
+    ccs = [arso.compile_circuit(c.n, c.gates, **tuned.get(c.n, {})) for c in mix]
+    crits = [c.criterion for c in mix]
+    outs = [torch.empty(T, dtype=torch.float64, device="cuda") for _ in mix]
+    stream = torch.cuda.current_stream()
+
+    def step(k):
+        errs = [arso.sample_errors(cc, p / 3, p / 3, p / 3, 0, k * T, T, stream) for cc in ccs]
+        arso.run_batch(ccs, errs, crits, outs, None, stream)
+
+    for w in range(args.warmup):
+        step(1000 + w)
+    arso.profile_reset()
+    arso.profile_enable(True)
+    e0, e1 = _events()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(args.steps):
+        step(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    arso.profile_enable(False)
+    sec = e0.elapsed_time(e1) / 1e3
+    fams = {f: sum(1 for c in mix if c.family == f) for f in ("qft", "grover", "qaoa", "adder")}
+    return {"metric": "error-injected trajectories/sec", "value": len(mix) * T * args.steps / sec,
+            "unit": "traj/s", "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "mix256_p5e-4", "circuits": len(mix), "families": fams,
+                       "n_range": [min(c.n for c in mix), max(c.n for c in mix)],
+                       "traj_per_circuit": T, "autotuned": {str(k): v for k, v in sorted(tuned.items())},
+                       "autotune_seconds": tune_s},
+            "kernels": _kernel_stats(arso)}
+
+
+def search(args):
+    """Tolerable rate (pass fraction >= 2/3) of unseen QAOA / brickwork circuits:
+    plain Monte Carlo bisection against surrogate bracket + plain verification,
+    both with 20,000 trajectories per probe on the same random numbers."""
+    import torch
+    from paper_2301_07264_gb300 import arso, surrogate_data
+    from workloads import circuits as W
+    rng = np.random.default_rng(1)
+    fam_train = []
+    for k in range(160):
+        n = int(rng.integers(4, 8)) * 2
+        if k % 2:
+            fam_train.append(W.qaoa_maxcut(n, 1000 + k))
+        else:
+            fam_train.append(W.brickwork(n, int(rng.integers(4, 24)), 1000 + k))
+    for c in fam_train:
+        c.criterion = W.Criterion("fidelity", threshold=0.9, aggregate="pass")
+    t0 = time.perf_counter()
+    x, y = surrogate_data.generate(fam_train, args.train_rows, seed=1, lp_lo=-5.0, lp_hi=-1.0, p_points=32)
+    gen_s = time.perf_counter() - t0
+    s = arso.surrogate_create(11)
+    t0 = time.perf_counter()
+    loss = arso.surrogate_train(s, x, y, epochs=4, batch=8192, lr=2e-3, seed=3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    rng = np.random.default_rng(2)
+    evals = []
+    for k in range(args.search_circuits):
+        n = int(rng.integers(6, 8)) * 2
+        c = W.qaoa_maxcut(n, 5000 + k) if k % 2 else W.brickwork(n, int(rng.integers(10, 40)), 5000 + k)
+        evals.append(c)
+    crit = W.Criterion("fidelity", threshold=0.9, aggregate="pass")
+    plain_s = sur_s = 0.0
+    rows = []
+    for c in evals:
+        cc = arso.compile_circuit(c.n, c.gates)
+        arso.tolerable_rate(cc, crit, 2 / 3, n_traj=256, seed=0, mode="mc", rel_tol=0.5, check=False)  # warm cache
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pl = arso.tolerable_rate(cc, crit, 2 / 3, n_traj=20000, seed=0, mode="mc", rel_tol=0.02, p_lo=1e-5,
+                                 p_hi=1e-1, check=False)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        su = arso.tolerable_rate_surrogate(cc, crit, 2 / 3, s, n_traj=20000, seed=0, margin=0.05, p_lo=1e-5, p_hi=1e-1)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        plain_s += t1 - t0
+        sur_s += t2 - t1
+        rows.append({"family": c.family, "n": c.n, "G": c.G, "p_plain": pl.p, "probes_plain": pl.probes,
+                     "p_surrogate": su.p, "probes_surrogate": su.probes, "verified": su.verified,
+                     "rel_err": abs(su.p - pl.p) / pl.p})
+    rel = [r["rel_err"] for r in rows]
+    return {"metric": "tolerable-rate searches/sec", "value": len(evals) / sur_s, "unit": "searches/s",
+            "higher_is_better": True, "dtype": "f32/bf16", "data": "synthetic",
+            "config": {"workload": "surrogate_search", "eval_circuits": len(evals), "eval_qubits": "12-14",
+                       "train_rows": int(x.shape[0]), "train_circuits": len(fam_train), "verify_traj": 20000,
+                       "target": "pass fraction >= 2/3 (fidelity >= 0.9)"},
+            "plain_searches_per_s": len(evals) / plain_s, "speedup": plain_s / sur_s,
+            "rel_err_max": max(rel), "rel_err_mean": float(np.mean(rel)),
+            "verified": sum(r["verified"] for r in rows), "train_loss": loss,
+            "generate_seconds": gen_s, "train_seconds": train_s, "rows": rows}
+
+
+def run(args):
+    import torch
+    torch.cuda.set_device(0)
+    return {"grover12": grover12, "mix256": mix256, "search": search}[args.workload](args)
