@@ -36,16 +36,18 @@ def grover12(args):
     crit = arso.make_criterion(circ.criterion)
     rates = np.logspace(-5, -2, 16)
     per = max(1, args.traj_per_step // 16)
-    score = torch.empty(per, dtype=torch.float64, device="cuda")
-    flags = torch.empty(per, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     res = np.zeros(16)
 
+    scores = [torch.empty(per, dtype=torch.float64, device="cuda") for _ in rates]
+    flag_l = [torch.empty(per, dtype=torch.uint8, device="cuda") for _ in rates]
+
     def step(k):
-        for i, p in enumerate(rates):
-            e = arso.sample_errors(cc, p / 3, p / 3, p / 3, 0, k * per, per, stream)
-            arso.run_trajectories(cc, e, crit, score, flags, stream)
-            res[i] += arso.aggregate(score, flags, stream)[1]
+        # all 16 rates in one persistent launch (arso_run_batch)
+        errs = [arso.sample_errors(cc, p / 3, p / 3, p / 3, 0, k * per, per, stream) for p in rates]
+        arso.run_batch([cc] * len(rates), errs, [crit] * len(rates), scores, flag_l, stream)
+        for i in range(len(rates)):
+            res[i] += arso.aggregate(scores[i], flag_l[i], stream)[1]
 
     for w in range(args.warmup):
         step(1000 + w)
@@ -187,4 +189,5 @@ def search(args):
 def run(args):
     import torch
     torch.cuda.set_device(0)
+    torch.cuda.set_stream(torch.cuda.Stream())
     return {"grover12": grover12, "mix256": mix256, "search": search}[args.workload](args)

@@ -315,6 +315,42 @@ struct GraphKey {
         return jmin != o.jmin ? jmin < o.jmin : jmax != o.jmax ? jmax < o.jmax : slots < o.slots;
     }
 };
+// Stream capture of one batch's launches. If capture cannot start, launches go
+// directly to the stream; if anything throws while capturing, the capture is
+// ended and discarded so the caller's stream is left usable.
+struct CaptureGuard {
+    cudaStream_t st;
+    bool active = false;
+    CaptureGuard(cudaStream_t s, bool want) : st(s) {
+        if (!want) return;
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            active = true;
+            prof_suspend(true);
+        } else {
+            cudaGetLastError();
+        }
+    }
+    cudaGraphExec_t finish() {
+        prof_suspend(false);
+        active = false;
+        cudaGraph_t g = nullptr;
+        ARSO_CUDA(cudaStreamEndCapture(st, &g));
+        cudaGraphExec_t ex = nullptr;
+        const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        ARSO_CUDA(ie);
+        return ex;
+    }
+    ~CaptureGuard() {
+        if (!active) return;
+        prof_suspend(false);
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(st, &g);
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+    }
+};
+
 struct GraphCache : std::map<GraphKey, cudaGraphExec_t> {
     ~GraphCache() {
         for (auto &kv : *this) cudaGraphExecDestroy(kv.second);
@@ -367,7 +403,10 @@ static void run_streaming(arso_circuit *c, const arso_error_list *e, const std::
     h2d(d_cslot.ptr, cslot, st);
     // captured pass sequences of this call, replayed for batches of the same shape
     GraphCache graphs;
-    const bool use_graphs = !states_out && c->reg_blocked && !(c->flags & ARSO_OPT_NO_GRAPHS);
+    // the legacy default stream cannot be captured
+    const bool use_graphs = !states_out && c->reg_blocked && !(c->flags & ARSO_OPT_NO_GRAPHS) && st != nullptr &&
+                            st != cudaStreamLegacy && st != cudaStreamPerThread;
+    if (use_graphs) prepare_pass_rb();
     for (size_t b0 = 0; b0 < ids.size(); b0 += B) {
         const size_t nb = std::min<size_t>(B, ids.size() - b0);
         std::vector<uint64_t> st_traj(nb);
@@ -398,12 +437,7 @@ static void run_streaming(arso_circuit *c, const arso_error_list *e, const std::
             ARSO_CUDA(cudaStreamSynchronize(st));
             continue;
         }
-        const bool capture = use_graphs;
-        if (capture) {
-            if (c->reg_blocked) prepare_pass_rb();
-            ARSO_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-            prof_suspend(true);
-        }
+        CaptureGuard capture(st, use_graphs);
         for (uint32_t j = (uint32_t)jmin; j <= (uint32_t)jmax; ++j) {
             PassArgs a = pass_args(c, j);
             a.cache = c->d_cache.ptr;
@@ -425,14 +459,8 @@ static void run_streaming(arso_circuit *c, const arso_error_list *e, const std::
         if (!states_out)
             launch_finish_partials(parts.as<Partial>(), tiles, (uint32_t)nb, d_slot_traj.as<uint64_t>(), crit, d_score,
                                    d_pass, st);
-        if (capture) {
-            prof_suspend(false);
-            cudaGraph_t g = nullptr;
-            ARSO_CUDA(cudaStreamEndCapture(st, &g));
-            cudaGraphExec_t ex = nullptr;
-            const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
-            cudaGraphDestroy(g);
-            ARSO_CUDA(ie);
+        if (capture.active) {
+            cudaGraphExec_t ex = capture.finish();
             graphs[key] = ex;
             {
                 ProfScope ps_(ARSO_K_PASS, batch_bytes, st);

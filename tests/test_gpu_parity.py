@@ -452,9 +452,14 @@ def test_graph_replay_equals_direct_launches(arso):
     d = arso.compile_circuit(circ.n, circ.gates, flags=arso.OPT_NO_GRAPHS, **kw)
     T, p = 40, 3e-3
     sg, sd = np.zeros(T), np.zeros(T)
-    arso.run_trajectories(g, arso.sample_errors(g, p / 3, p / 3, p / 3, 4, 0, T), circ.criterion, sg)
-    arso.run_trajectories(d, arso.sample_errors(d, p / 3, p / 3, p / 3, 4, 0, T), circ.criterion, sd)
+    st = torch.cuda.Stream()  # the legacy default stream is never captured
+    arso.run_trajectories(g, arso.sample_errors(g, p / 3, p / 3, p / 3, 4, 0, T, st), circ.criterion, sg, stream=st)
+    arso.run_trajectories(d, arso.sample_errors(d, p / 3, p / 3, p / 3, 4, 0, T, st), circ.criterion, sd, stream=st)
     assert np.array_equal(sg, sd)
+    # and the default stream (no capture) gives the same scores
+    s0 = np.zeros(T)
+    arso.run_trajectories(g, arso.sample_errors(g, p / 3, p / 3, p / 3, 4, 0, T), circ.criterion, s0)
+    assert np.array_equal(s0, sd)
 
 
 def test_autotune_returns_a_measured_candidate(arso):
