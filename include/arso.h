@@ -123,6 +123,11 @@ arso_status arso_circuit_get_info(const arso_circuit *c, arso_circuit_info *out)
 arso_status arso_plan_schedule(uint32_t n_qubits, const arso_gate *gates, size_t n_gates,
                                const arso_compile_opts *opts, uint32_t *n_passes, uint32_t capacity,
                                uint32_t *perm, uint32_t *pass_begin, uint64_t *tile_mask);
+/* Host-only: the number of register-bit phases the compile step plans (each
+ * phase boundary inside a pass is one shared-memory transpose of the tile);
+ * 0 when the circuit does not use the register-blocked kernels. */
+arso_status arso_plan_phases(uint32_t n_qubits, const arso_gate *gates, size_t n_gates,
+                             const arso_compile_opts *opts, uint32_t *n_phases);
 
 /* Sample Pauli errors (Sec. IV-B.2): after every gate, each of its qubits
  * independently suffers X, Z or Y with probabilities p_x, p_z, p_y. Trajectory

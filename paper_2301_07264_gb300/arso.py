@@ -497,3 +497,16 @@ def autotune(n, gates, crit, p, n_traj=64, seed=0, precision=C64, stream=None):
     _check(lib.arso_autotune(n, arr, len(gates), C.byref(c), p, n_traj, seed, C.byref(base), _stream(stream),
                              C.byref(best), ms.ctypes.data, C.byref(cnt)))
     return {"tile_qubits": best.tile_qubits, "low_qubits": best.low_qubits}, ms[: cnt.value]
+
+
+lib.arso_plan_phases.argtypes = [C.c_uint32, C.POINTER(Gate), C.c_size_t, C.POINTER(CompileOpts), C.POINTER(C.c_uint32)]
+lib.arso_plan_phases.restype = C.c_int
+
+
+def plan_phases(n, gates, precision=C64, tile_qubits=0, low_qubits=0):
+    """Host-only: number of register-bit phases the compile step plans."""
+    arr, keep = _gates_array(gates)
+    opts = CompileOpts(precision, tile_qubits, low_qubits, 0, 0, 0)
+    out = C.c_uint32()
+    _check(lib.arso_plan_phases(n, arr, len(gates), C.byref(opts), C.byref(out)))
+    return out.value

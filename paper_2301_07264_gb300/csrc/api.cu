@@ -703,6 +703,16 @@ arso_status arso_compile_circuit(uint32_t n_qubits, const arso_gate *gates, size
 
 void arso_circuit_free(arso_circuit *c) { delete c; }
 
+arso_status arso_plan_phases(uint32_t n_qubits, const arso_gate *gates, size_t n_gates,
+                             const arso_compile_opts *opts, uint32_t *n_phases) {
+    return guard([&] {
+        ARSO_REQUIRE(n_phases != nullptr, "n_phases is NULL");
+        arso_circuit c;
+        build_circuit(&c, n_qubits, gates, n_gates, opts);
+        *n_phases = c.reg_blocked ? (uint32_t)c.ph_R.size() : 0u;
+    });
+}
+
 arso_status arso_plan_schedule(uint32_t n_qubits, const arso_gate *gates, size_t n_gates,
                                const arso_compile_opts *opts, uint32_t *n_passes, uint32_t capacity, uint32_t *perm,
                                uint32_t *pass_begin, uint64_t *tile_mask) {

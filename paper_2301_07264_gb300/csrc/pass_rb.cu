@@ -125,21 +125,54 @@ __device__ __forceinline__ void rg_diag1(float2 (&v)[32], const TileCtx &c, uint
     for (int ri = 0; ri < 32; ++ri) v[ri] = cmul(bit_of(ri, pos, mq, th) ? d1 : d0, v[ri]);
 }
 
-// diag(1, e^{i k pi/4}) on tile bit q: branch-free per register
-__device__ __forceinline__ void rg_omega(float2 (&v)[32], const TileCtx &c, uint32_t q, uint32_t k) {
-    const uint32_t pos = reg_pos(c, q), mq = (c.m >> q) & 1u, th = ((c.tpart ^ c.m) >> q) & 1u;
-    if (pos >= REG_BITS && !th) return;
-    const bool odd = k & 1u;
-    const uint32_t qq = (k >> 1) & 3u;  // remaining factor i^qq
-    const bool sw = qq & 1u, nx = qq == 1u || qq == 2u, ny = qq >= 2u;
-#pragma unroll
-    for (int ri = 0; ri < 32; ++ri) {
-        const float2 a = v[ri];
+// diag(1, e^{i k pi/4}) on tile bit q. On a register bit only the 16 registers
+// whose true bit is 1 are touched (two unrolled variants per position); on a
+// thread bit all 32 registers of the threads whose bit is 1.
+struct OmegaOp {
+    bool odd, sw, nx, ny;  // rotate by pi/4, then multiply by i^qq: swap and negate
+    __device__ __forceinline__ explicit OmegaOp(uint32_t k) {
+        odd = k & 1u;
+        const uint32_t qq = (k >> 1) & 3u;
+        sw = qq & 1u;
+        nx = qq == 1u || qq == 2u;
+        ny = qq >= 2u;
+    }
+    __device__ __forceinline__ float2 operator()(float2 a) const {
         const float2 r = odd ? make_float2(mul_rsqrt2(a.x - a.y), mul_rsqrt2(a.x + a.y)) : a;
         float2 o = sw ? make_float2(r.y, r.x) : r;
         o.x = nx ? -o.x : o.x;
         o.y = ny ? -o.y : o.y;
-        v[ri] = bit_of(ri, pos, mq, th) ? o : a;
+        return o;
+    }
+};
+template <int P> __device__ __forceinline__ void rg_omega_half(float2 (&v)[32], const OmegaOp &op, uint32_t want) {
+    if (want) {
+#pragma unroll
+        for (int ri = 0; ri < 32; ++ri)
+            if (ri & (1 << P)) v[ri] = op(v[ri]);
+    } else {
+#pragma unroll
+        for (int ri = 0; ri < 32; ++ri)
+            if (!(ri & (1 << P))) v[ri] = op(v[ri]);
+    }
+}
+__device__ __forceinline__ void rg_omega(float2 (&v)[32], const TileCtx &c, uint32_t q, uint32_t k) {
+    const uint32_t pos = reg_pos(c, q), mq = (c.m >> q) & 1u, th = ((c.tpart ^ c.m) >> q) & 1u;
+    const OmegaOp op(k);
+    if (pos >= REG_BITS) {
+        if (th) {
+#pragma unroll
+            for (int ri = 0; ri < 32; ++ri) v[ri] = op(v[ri]);
+        }
+        return;
+    }
+    const uint32_t want = mq ^ 1u;  // stored bit value whose true bit is 1
+    switch (pos) {
+        case 0: rg_omega_half<0>(v, op, want); break;
+        case 1: rg_omega_half<1>(v, op, want); break;
+        case 2: rg_omega_half<2>(v, op, want); break;
+        case 3: rg_omega_half<3>(v, op, want); break;
+        default: rg_omega_half<4>(v, op, want); break;
     }
 }
 
