@@ -91,6 +91,15 @@ static void upload_circuit(arso_circuit *c) {
                 case GC_DIAG2: for (int i = 0; i < 4; ++i) pool.push_back(h.m[5 * i]); break;
                 default: break;
             }
+            // register kernels: a dense gate whose complex64 entries have the special
+            // unitary form [[a, b], [-conj b, conj a]] exactly runs on a and b alone
+            if (h.cls == GC_DENSE1 && c->reg_blocked) {
+                const std::complex<float> a((float)h.m[0].real(), (float)h.m[0].imag());
+                const std::complex<float> b((float)h.m[1].real(), (float)h.m[1].imag());
+                const std::complex<float> u10((float)h.m[2].real(), (float)h.m[2].imag());
+                const std::complex<float> u11((float)h.m[3].real(), (float)h.m[3].imag());
+                if (u10 == -std::conj(b) && u11 == std::conj(a)) d.cls = GC_SU2;
+            }
             dg[pos] = d;
         }
     }

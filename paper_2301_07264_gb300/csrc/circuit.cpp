@@ -24,6 +24,7 @@
 // attached to the gate they follow, which keeps them correct: a gate moved
 // ahead of gate g never touches g's qubits after g.
 #include <algorithm>
+#include <set>
 #include <cmath>
 #include <cstring>
 
@@ -134,22 +135,88 @@ static void schedule_streaming(arso_circuit *c) {
 }
 
 // Register-bit phases of each pass. A gate that mixes amplitudes needs its
-// mixing qubits among the REG_BITS register bits (dense one- and two-qubit
-// gates: all their qubits; CX: its target); diagonal gates and X act on any
-// bit. Phases are greedy in engine order: when a gate's needs are not met,
-// a new phase starts whose register bits are the needs of the upcoming gates
-// in order of first use, topped up with bits of the current set. Passes start
-// and end in the load/store mapping {0, t-4, t-3, t-2, t-1}, whose thread
-// bits 1..t-5 keep global accesses contiguous.
-static void need_of(const HostGate &h, uint32_t lq0, uint32_t lq1, uint32_t *out, int &k) {
-    k = 0;
+// mixing qubit among the REG_BITS register bits (dense one-qubit gates and H:
+// their qubit; CX: its target); diagonal gates, X, and the dense two-qubit
+// gates and SWAP (run through shared memory) act on any bit. Tile bit 0 is a
+// register bit in every phase (the register kernels pack amplitudes j and
+// j|1 into one FP32x2 register pair).
+//
+// Within a pass the gates may run in any order that respects their qubit
+// dependencies. The planner list-schedules them: with register set R it runs
+// every ready gate whose need is in R, repeatedly; when none is left it picks
+// the next R greedily, one qubit at a time, by the weighted number of gates
+// the closure under R would run. Passes start and end in the load/store
+// mapping {0, t-4, t-3, t-2, t-1}, whose thread bits 1..t-5 keep global
+// accesses contiguous.
+static constexpr uint32_t NO_NEED = 0xFFFFFFFFu;
+
+static uint32_t need_of(const HostGate &h, uint32_t lq0, uint32_t lq1) {
     switch (h.cls) {
-        case GC_DENSE1: case GC_H: out[k++] = lq0; break;
-        // dense two-qubit gates and SWAP run through shared memory: no register needs
-        case GC_CX: out[k++] = lq1; break;
-        default: break;
+        case GC_DENSE1: case GC_H: return lq0;
+        case GC_CX: return lq1;
+        default: return NO_NEED;
     }
 }
+
+// relative cost of a gate in the register kernels (the planner's objective)
+static double gate_weight(const HostGate &h) {
+    switch (h.cls) {
+        case GC_DENSE1: case GC_H: return 1.0;
+        case GC_DENSE2: case GC_SWAP: return 2.0;
+        case GC_DIAG1: case GC_OMEGA: return 0.5;
+        default: return 0.25;
+    }
+}
+
+namespace {
+// Dependency DAG of one pass and a list scheduler with trial closures.
+struct PassScheduler {
+    uint32_t G;
+    std::vector<uint32_t> need;
+    std::vector<double> weight;
+    std::vector<std::vector<uint32_t>> succ;
+    std::vector<uint32_t> indeg;
+    std::set<uint32_t> ready;  // unscheduled gates whose predecessors are all scheduled
+    std::vector<uint32_t> order;
+
+    static bool in(const std::vector<uint32_t> &R, uint32_t q) {
+        return q == NO_NEED || std::find(R.begin(), R.end(), q) != R.end();
+    }
+    // Run every ready gate whose need is in R, repeatedly. With `trial` the
+    // state is restored afterwards and only the weight is returned.
+    double closure(const std::vector<uint32_t> &R, bool trial) {
+        std::vector<std::pair<uint32_t, uint32_t>> undo;  // (gate, old indeg)
+        std::set<uint32_t> rd = ready;
+        double w = 0.0;
+        bool progress = true;
+        while (progress) {
+            progress = false;
+            for (auto it = rd.begin(); it != rd.end();) {
+                const uint32_t g = *it;
+                if (!in(R, need[g])) {
+                    ++it;
+                    continue;
+                }
+                it = rd.erase(it);
+                w += weight[g];
+                if (!trial) order.push_back(g);
+                for (uint32_t s : succ[g]) {
+                    if (trial) undo.emplace_back(s, indeg[s]);
+                    if (--indeg[s] == 0) rd.insert(s);
+                }
+                progress = true;
+                it = rd.begin();  // lowest index first
+            }
+        }
+        if (trial) {
+            for (auto u = undo.rbegin(); u != undo.rend(); ++u) indeg[u->first] = u->second;
+        } else {
+            ready.swap(rd);
+        }
+        return w;
+    }
+};
+}  // namespace
 
 static void plan_phases(arso_circuit *c) {
     const uint32_t t = c->tile_qubits;
@@ -158,56 +225,75 @@ static void plan_phases(arso_circuit *c) {
     c->ph_R.clear();
     c->rpos.assign(c->perm.size(), 0xFF);
     if (!c->reg_blocked) return;
-    const uint32_t load_map[REG_BITS] = {0, t - 4, t - 3, t - 2, t - 1};
+    const std::vector<uint32_t> load_map = {0, t - 4, t - 3, t - 2, t - 1};
     for (Pass &ps : c->passes) {
         std::vector<int> local(c->n, -1);
         for (size_t i = 0; i < ps.tile_qubits.size(); ++i) local[ps.tile_qubits[i]] = (int)i;
         const uint32_t G = ps.ge - ps.gb;
+        PassScheduler S;
+        S.G = G;
+        S.need.resize(G);
+        S.weight.resize(G);
+        S.succ.assign(G, {});
+        S.indeg.assign(G, 0);
+        std::vector<int> last(t, -1);
+        for (uint32_t i = 0; i < G; ++i) {
+            const HostGate &h = c->gates[c->perm[ps.gb + i]];
+            const uint32_t a = (uint32_t)local[h.q0], b = (uint32_t)local[h.q1];
+            S.need[i] = need_of(h, a, b);
+            S.weight[i] = gate_weight(h);
+            const int pa = last[a], pb = h.arity == 2 ? last[b] : -1;
+            if (pa >= 0) S.succ[pa].push_back(i), ++S.indeg[i];
+            if (pb >= 0 && pb != pa) S.succ[pb].push_back(i), ++S.indeg[i];
+            last[a] = (int)i;
+            if (h.arity == 2) last[b] = (int)i;
+        }
+        for (uint32_t i = 0; i < G; ++i)
+            if (!S.indeg[i]) S.ready.insert(i);
+        ps.pb = (uint32_t)c->ph_R.size();
+        std::vector<uint32_t> cur = load_map;
+        std::vector<std::pair<uint32_t, std::vector<uint32_t>>> phases;  // (start in order, R)
+        for (;;) {
+            const size_t before = S.order.size();
+            S.closure(cur, false);
+            if (S.order.size() > before) phases.emplace_back((uint32_t)before, cur);
+            if (S.order.size() == G) break;
+            // next register set: tile bit 0, then greedily the qubit with the largest closure gain
+            std::vector<uint32_t> R{0};
+            while (R.size() < (size_t)REG_BITS) {
+                double best_w = -1.0;
+                uint32_t best_q = 0;
+                for (uint32_t q = 1; q < t; ++q) {
+                    if (std::find(R.begin(), R.end(), q) != R.end()) continue;
+                    std::vector<uint32_t> trial = R;
+                    trial.push_back(q);
+                    const double w = S.closure(trial, true);
+                    if (w > best_w + 1e-12) {
+                        best_w = w;
+                        best_q = q;
+                    }
+                }
+                R.push_back(best_q);
+            }
+            std::sort(R.begin(), R.end());
+            ARSO_REQUIRE(R != cur, "internal: the phase planner made no progress");
+            cur = R;
+        }
+        if (phases.empty()) phases.emplace_back(0u, load_map);
+        // the pass's new engine order
+        std::vector<uint32_t> perm_new(G);
+        for (uint32_t k = 0; k < G; ++k) perm_new[k] = c->perm[ps.gb + S.order[k]];
+        std::copy(perm_new.begin(), perm_new.end(), c->perm.begin() + ps.gb);
         std::vector<uint32_t> lq0(G), lq1(G);
         for (uint32_t i = 0; i < G; ++i) {
             const HostGate &h = c->gates[c->perm[ps.gb + i]];
             lq0[i] = (uint32_t)local[h.q0];
             lq1[i] = (uint32_t)local[h.q1];
         }
-        std::vector<uint32_t> cur(load_map, load_map + REG_BITS);
-        auto fits = [&](uint32_t i) {
-            uint32_t need[2];
-            int k;
-            need_of(c->gates[c->perm[ps.gb + i]], lq0[i], lq1[i], need, k);
-            for (int j = 0; j < k; ++j)
-                if (std::find(cur.begin(), cur.end(), need[j]) == cur.end()) return false;
-            return true;
-        };
-        ps.pb = (uint32_t)c->ph_R.size();
-        uint32_t start = 0;
-        for (uint32_t i = 0; i <= G; ++i) {
-            const bool end = i == G;
-            if (!end && fits(i)) continue;
-            if (i > start || (end && start == 0)) {
-                c->ph_gb.push_back(ps.gb + start);
-                c->ph_R.push_back(pack_rbits(cur.data()));
-            }
-            if (end) break;
-            // new register set: needs of gates i, i+1, ... in order of first use
-            std::vector<uint32_t> nxt;
-            for (uint32_t g = i; g < G; ++g) {
-                uint32_t need[2];
-                int k;
-                need_of(c->gates[c->perm[ps.gb + g]], lq0[g], lq1[g], need, k);
-                std::vector<uint32_t> add;
-                for (int j = 0; j < k; ++j)
-                    if (std::find(nxt.begin(), nxt.end(), need[j]) == nxt.end() &&
-                        std::find(add.begin(), add.end(), need[j]) == add.end())
-                        add.push_back(need[j]);
-                if (nxt.size() + add.size() > (size_t)REG_BITS) break;
-                nxt.insert(nxt.end(), add.begin(), add.end());
-                if (nxt.size() == (size_t)REG_BITS) break;
-            }
-            for (uint32_t b : cur)
-                if (nxt.size() < (size_t)REG_BITS && std::find(nxt.begin(), nxt.end(), b) == nxt.end()) nxt.push_back(b);
-            std::sort(nxt.begin(), nxt.end());
-            cur = nxt;
-            start = i;
+        for (auto &ph : phases) {
+            ARSO_REQUIRE(ph.second[0] == 0, "internal: a register set without tile bit 0");
+            c->ph_gb.push_back(ps.gb + ph.first);
+            c->ph_R.push_back(pack_rbits(ph.second.data()));
         }
         ps.pe = (uint32_t)c->ph_R.size();
         // register positions of each gate's qubits within its phase
@@ -286,12 +372,12 @@ void build_circuit(arso_circuit *c, uint32_t n, const arso_gate *gates, size_t n
         c->low_qubits = lq;
         schedule_streaming(c);
     }
+    plan_phases(c);  // may reorder gates within a pass
     c->pos_of.assign(n_gates, 0);
     for (size_t pos = 0; pos < c->perm.size(); ++pos) c->pos_of[c->perm[pos]] = (uint32_t)pos;
     c->pass_of_pos.assign(n_gates, 0);
     for (size_t p = 0; p < c->passes.size(); ++p)
         for (uint32_t pos = c->passes[p].gb; pos < c->passes[p].ge; ++pos) c->pass_of_pos[pos] = (uint32_t)p;
-    plan_phases(c);
 }
 
 }  // namespace arso

@@ -47,6 +47,7 @@ enum GateClass : uint8_t {
     GC_H = 8,       // Hadamard, 1/sqrt2 applied as a two-float constant (unbiased rounding)
     GC_OMEGA = 9,   // diag(1, e^{i k pi/4}), k in DGate::mat; exact for even k, two-float 1/sqrt2 for odd k
     GC_CZ = 10,     // diag(1, 1, 1, -1)
+    GC_SU2 = 11,    // 2x2 dense of the form [[a, b], [-conj b, conj a]] (register kernels read a and b)
 };
 
 // Register-blocked execution (tiles of >= 2^10 amplitudes): every thread

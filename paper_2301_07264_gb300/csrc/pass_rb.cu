@@ -4,8 +4,11 @@
 // keeps 32 amplitudes in registers. The tile-local index of register ri of
 // thread tid is deposit(ri, R) | deposit(tid, complement of R), where R, the 5
 // "register bits", changes only between phases (a swizzled shared-memory
-// transpose). Within a phase:
-//  * dense one-/two-qubit gates and CX targets act on register bits, entirely
+// transpose). Register bit 0 is always tile bit 0, so registers 2k and 2k+1
+// hold the neighbours j and j|1; they are kept split as two FP32x2 pairs,
+// re[k] = (Re a_j, Re a_j|1) and im[k] = (Im a_j, Im a_j|1), and one packed
+// instruction (FFMA2 / FMUL2 / FADD2) updates both. Within a phase:
+//  * dense one-qubit gates, H and CX targets act on register bits, entirely
 //    in registers;
 //  * diagonal gates (T, S, Z, RZ, P, CZ, CP) act on any bit in place;
 //  * X gates and the X part of Pauli errors never move data: the tile keeps
@@ -26,11 +29,6 @@ namespace arso {
 
 __device__ __forceinline__ uint32_t swz(uint32_t j) { return j ^ (((j >> 4) ^ (j >> 8) ^ (j >> 12)) & 15u); }
 
-__device__ __forceinline__ void unpack_r(uint32_t packed, uint32_t (&r)[REG_BITS]) {
-#pragma unroll
-    for (int b = 0; b < REG_BITS; ++b) r[b] = (packed >> (5 * b)) & 31u;
-}
-
 // tid's bits deposited into the tile bits that are not register bits, ascending
 __device__ __forceinline__ uint32_t thread_part(uint32_t tid, uint32_t rmask, int t) {
     uint32_t out = 0;
@@ -43,55 +41,143 @@ __device__ __forceinline__ uint32_t thread_part(uint32_t tid, uint32_t rmask, in
     return out;
 }
 
+// register bit b of a packed register set
+__device__ __forceinline__ uint32_t rbit(uint32_t packed, int b) { return (packed >> (5 * b)) & 31u; }
+
 // register part of the local index of register ri (ri is a constant after unrolling)
-__device__ __forceinline__ uint32_t reg_part(int ri, const uint32_t (&r)[REG_BITS]) {
+__device__ __forceinline__ uint32_t reg_part(int ri, uint32_t packed) {
     uint32_t o = 0;
 #pragma unroll
     for (int b = 0; b < REG_BITS; ++b)
-        if ((ri >> b) & 1) o |= 1u << r[b];
+        if ((ri >> b) & 1) o |= 1u << rbit(packed, b);
     return o;
 }
 
-// ------------------------------------------------------- register gates ---
-// Code size matters: the whole phase loop must stay resident in the
-// instruction cache, so only dense one-qubit gates, H and CX are specialised
-// per register position (5 copies each); everything else is position-free.
+// ----------------------------------------------------------- amplitudes ---
+struct Amps {
+    float2 re[16], im[16];  // re[k] = (Re of register 2k, Re of register 2k+1)
+};
 
-template <int P>
-__device__ __forceinline__ void rg_dense1(float2 (&v)[32], float2 u00, float2 u01, float2 u10, float2 u11) {
-#pragma unroll
-    for (int ri = 0; ri < 32; ++ri) {
-        if (ri & (1 << P)) continue;
-        const float2 a0 = v[ri], a1 = v[ri | (1 << P)];
-        v[ri] = cmac2(u00, a0, u01, a1);
-        v[ri | (1 << P)] = cmac2(u10, a0, u11, a1);
+__device__ __forceinline__ float2 amp_get(const Amps &a, int ri) {
+    const float2 r = a.re[ri >> 1], i = a.im[ri >> 1];
+    return (ri & 1) ? make_float2(r.y, i.y) : make_float2(r.x, i.x);
+}
+__device__ __forceinline__ void amp_set(Amps &a, int ri, float2 v) {
+    if (ri & 1) {
+        a.re[ri >> 1].y = v.x;
+        a.im[ri >> 1].y = v.y;
+    } else {
+        a.re[ri >> 1].x = v.x;
+        a.im[ri >> 1].x = v.y;
     }
 }
 
-// H on register bit P: (a0, a1) -> ((a0 + a1), (a0 - a1)) / sqrt2; with the
-// qubit's mask bit set the stored data sees X H X: ((a1 - a0), (a0 + a1)) / sqrt2.
-template <int P> __device__ __forceinline__ void rg_h(float2 (&v)[32], uint32_t flip) {
+__device__ __forceinline__ float2 bc2(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 swp2(float2 a) { return make_float2(a.y, a.x); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+// ------------------------------------------------------- register gates ---
+// Code size matters: the whole phase loop must stay resident in the
+// instruction cache, so only dense one-qubit gates, H, phase gates and CZ are
+// specialised per register position; everything else is position-free.
+
+// U on register bit P >= 1: packed registers k and k | 2^(P-1) hold the pairs
+template <int P>
+__device__ __forceinline__ void rg_dense1(Amps &a, float2 u00, float2 u01, float2 u10, float2 u11) {
+    const float2 u00r = bc2(u00.x), u00i = bc2(u00.y), n00i = bc2(-u00.y);
+    const float2 u01r = bc2(u01.x), u01i = bc2(u01.y), n01i = bc2(-u01.y);
+    const float2 u10r = bc2(u10.x), u10i = bc2(u10.y), n10i = bc2(-u10.y);
+    const float2 u11r = bc2(u11.x), u11i = bc2(u11.y), n11i = bc2(-u11.y);
 #pragma unroll
-    for (int ri = 0; ri < 32; ++ri) {
-        if (ri & (1 << P)) continue;
-        const float2 a0 = v[ri], a1 = v[ri | (1 << P)];
-        const float2 s = make_float2(mul_rsqrt2(a0.x + a1.x), mul_rsqrt2(a0.y + a1.y));
-        const float2 d = make_float2(mul_rsqrt2(a0.x - a1.x), mul_rsqrt2(a0.y - a1.y));
-        v[ri] = flip ? cneg(d) : s;
-        v[ri | (1 << P)] = flip ? s : d;
+    for (int k = 0; k < 16; ++k) {
+        if (k & (1 << (P - 1))) continue;
+        const int k1 = k | (1 << (P - 1));
+        const float2 r0 = a.re[k], i0 = a.im[k], r1 = a.re[k1], i1 = a.im[k1];
+        a.re[k] = fma2(n01i, i1, fma2(u01r, r1, fma2(n00i, i0, mul2(u00r, r0))));
+        a.im[k] = fma2(u01i, r1, fma2(u01r, i1, fma2(u00i, r0, mul2(u00r, i0))));
+        a.re[k1] = fma2(n11i, i1, fma2(u11r, r1, fma2(n10i, i0, mul2(u10r, r0))));
+        a.im[k1] = fma2(u11i, r1, fma2(u11r, i1, fma2(u10i, r0, mul2(u10r, i0))));
+    }
+}
+
+// Special unitary U = [[a, b], [-conj b, conj a]] on register bit P >= 1:
+// seven broadcast constants instead of twelve keep the phase loop spill-free.
+template <int P> __device__ __forceinline__ void rg_su2(Amps &a, float2 ua, float2 ub) {
+    const float2 ar = bc2(ua.x), ai = bc2(ua.y), nai = bc2(-ua.y);
+    const float2 br = bc2(ub.x), bi = bc2(ub.y), nbi = bc2(-ub.y), nbr = bc2(-ub.x);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        if (k & (1 << (P - 1))) continue;
+        const int k1 = k | (1 << (P - 1));
+        const float2 r0 = a.re[k], i0 = a.im[k], r1 = a.re[k1], i1 = a.im[k1];
+        a.re[k] = fma2(nbi, i1, fma2(br, r1, fma2(nai, i0, mul2(ar, r0))));
+        a.im[k] = fma2(bi, r1, fma2(br, i1, fma2(ai, r0, mul2(ar, i0))));
+        a.re[k1] = fma2(ai, i1, fma2(ar, r1, fma2(nbi, i0, mul2(nbr, r0))));
+        a.im[k1] = fma2(nai, r1, fma2(ar, i1, fma2(bi, r0, mul2(nbr, i0))));
+    }
+}
+
+// U on register bit 0: the pair sits in the two lanes of one packed register;
+// lane 0 takes (u00, u01) against (a0, a1), lane 1 takes (u11, u10) against (a1, a0).
+__device__ __forceinline__ void rg_dense1_lanes(Amps &a, float2 u00, float2 u01, float2 u10, float2 u11) {
+    const float2 dr = make_float2(u00.x, u11.x), di = make_float2(u00.y, u11.y), ndi = make_float2(-u00.y, -u11.y);
+    const float2 xr = make_float2(u01.x, u10.x), xi = make_float2(u01.y, u10.y), nxi = make_float2(-u01.y, -u10.y);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const float2 r = a.re[k], i = a.im[k], rs = swp2(r), is = swp2(i);
+        a.re[k] = fma2(nxi, is, fma2(xr, rs, fma2(ndi, i, mul2(dr, r))));
+        a.im[k] = fma2(xi, rs, fma2(xr, is, fma2(di, r, mul2(dr, i))));
+    }
+}
+
+// H on register bit P: (a0, a1) -> (a0 + a1, a0 - a1) / sqrt2 with 1/sqrt2
+// applied as the compensated pair hi + lo. FLIP gives (a0 + a1, a1 - a0) /
+// sqrt2, i.e. Z H, which is H on a qubit whose mask bit is set (H X = Z H:
+// the caller then clears the mask bit).
+template <int P, bool FLIP> __device__ __forceinline__ void rg_h(Amps &a) {
+    const float2 hi = bc2(RSQRT2_HI), lo = bc2(RSQRT2_LO), m1 = bc2(-1.f);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        if (k & (1 << (P - 1))) continue;
+        const int k1 = k | (1 << (P - 1));
+        const float2 r0 = a.re[k], i0 = a.im[k], r1 = a.re[k1], i1 = a.im[k1];
+        const float2 sr = add2(r0, r1), si = add2(i0, i1);
+        const float2 dr = FLIP ? fma2(m1, r0, r1) : fma2(m1, r1, r0);
+        const float2 di = FLIP ? fma2(m1, i0, i1) : fma2(m1, i1, i0);
+        a.re[k] = fma2(hi, sr, mul2(lo, sr));
+        a.im[k] = fma2(hi, si, mul2(lo, si));
+        a.re[k1] = fma2(hi, dr, mul2(lo, dr));
+        a.im[k1] = fma2(hi, di, mul2(lo, di));
+    }
+}
+template <int P> __device__ __forceinline__ void rg_h(Amps &a, uint32_t flip) {
+    if (flip) rg_h<P, true>(a);
+    else rg_h<P, false>(a);
+}
+__device__ __forceinline__ void rg_h_lanes(Amps &a, float sg) {
+    const float2 pm = make_float2(1.f, -1.f);
+    const float2 h = make_float2(RSQRT2_HI, sg * RSQRT2_HI), l = make_float2(RSQRT2_LO, sg * RSQRT2_LO);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const float2 tr = fma2(pm, a.re[k], swp2(a.re[k]));  // (a0 + a1, a0 - a1)
+        const float2 ti = fma2(pm, a.im[k], swp2(a.im[k]));
+        a.re[k] = fma2(h, tr, mul2(l, tr));
+        a.im[k] = fma2(h, ti, mul2(l, ti));
     }
 }
 
 // CX on stored data, target register bit P; control is register bit cpos
 // (0..4) or, when cpos == 15, the thread-level bit value cth.
-template <int P> __device__ __forceinline__ void rg_cx(float2 (&v)[32], uint32_t cpos, uint32_t cth) {
+template <int P> __device__ __forceinline__ void rg_cx(Amps &a, uint32_t cpos, uint32_t cth) {
 #pragma unroll
     for (int ri = 0; ri < 32; ++ri) {
         if (ri & (1 << P)) continue;
         const uint32_t ctl = cpos < REG_BITS ? (((uint32_t)ri >> cpos) & 1u) : cth;
-        const float2 a0 = v[ri], a1 = v[ri | (1 << P)];
-        v[ri] = ctl ? a1 : a0;
-        v[ri | (1 << P)] = ctl ? a0 : a1;
+        const float2 a0 = amp_get(a, ri), a1 = amp_get(a, ri | (1 << P));
+        amp_set(a, ri, ctl ? a1 : a0);
+        amp_set(a, ri | (1 << P), ctl ? a0 : a1);
     }
 }
 
@@ -102,77 +188,105 @@ __device__ __forceinline__ uint32_t bit_of(int ri, uint32_t pos, uint32_t mq, ui
 }
 
 struct TileCtx {
-    uint32_t r[REG_BITS];  // register bits of the current phase
-    uint32_t rmask;        // same as a mask
-    uint32_t tpart;        // thread part of the local index
-    uint32_t m;            // X mask (stored[j] = state[j ^ m])
-    uint32_t gp;           // global phase i^gp
-    uint32_t tid, nthr;    // thread index within the tile's thread group, group size
+    uint32_t R;          // register bits of the current phase, 5 bits each (bit 0 of the tile first)
+    uint32_t tpart;      // thread part of the local index
+    uint32_t m;          // X mask (stored[j] = state[j ^ m])
+    uint32_t gp;         // global phase i^gp
+    uint32_t tid, nthr;  // thread index within the tile's thread group, group size
 };
 
 __device__ __forceinline__ uint32_t reg_pos(const TileCtx &c, uint32_t q) {
     uint32_t p = 15;
 #pragma unroll
     for (int b = 0; b < REG_BITS; ++b)
-        if (c.r[b] == q) p = (uint32_t)b;
+        if (rbit(c.R, b) == q) p = (uint32_t)b;
     return p;
 }
+// true value of tile bit q held at thread level
+__device__ __forceinline__ uint32_t thread_bit(const TileCtx &c, uint32_t q) { return ((c.tpart ^ c.m) >> q) & 1u; }
 
-// diag(d0, d1) on tile bit q (true index), any bit
-__device__ __forceinline__ void rg_diag1(float2 (&v)[32], const TileCtx &c, uint32_t q, float2 d0, float2 d1) {
-    const uint32_t pos = reg_pos(c, q), mq = (c.m >> q) & 1u, th = ((c.tpart ^ c.m) >> q) & 1u;
+// diag(d0, d1) on tile bit q (true index) at register position pos (15: thread bit)
+__device__ __forceinline__ void rg_diag1(Amps &a, const TileCtx &c, uint32_t q, uint32_t pos, float2 d0, float2 d1) {
+    const uint32_t mq = (c.m >> q) & 1u, th = thread_bit(c, q);
 #pragma unroll
-    for (int ri = 0; ri < 32; ++ri) v[ri] = cmul(bit_of(ri, pos, mq, th) ? d1 : d0, v[ri]);
+    for (int k = 0; k < 16; ++k) {
+        const uint32_t bx = bit_of(2 * k, pos, mq, th), by = bit_of(2 * k + 1, pos, mq, th);
+        const float2 fr = make_float2(bx ? d1.x : d0.x, by ? d1.x : d0.x);
+        const float2 fi = make_float2(bx ? d1.y : d0.y, by ? d1.y : d0.y);
+        const float2 nfi = make_float2(-fi.x, -fi.y);
+        const float2 r = a.re[k], i = a.im[k];
+        a.re[k] = fma2(nfi, i, mul2(fr, r));
+        a.im[k] = fma2(fi, r, mul2(fr, i));
+    }
 }
 
-// diag(1, e^{i k pi/4}) on tile bit q. On a register bit only the 16 registers
-// whose true bit is 1 are touched (two unrolled variants per position); on a
-// thread bit all 32 registers of the threads whose bit is 1.
-struct OmegaOp {
-    bool odd, sw, nx, ny;  // rotate by pi/4, then multiply by i^qq: swap and negate
-    __device__ __forceinline__ explicit OmegaOp(uint32_t k) {
-        odd = k & 1u;
-        const uint32_t qq = (k >> 1) & 3u;
-        sw = qq & 1u;
-        nx = qq == 1u || qq == 2u;
-        ny = qq >= 2u;
-    }
-    __device__ __forceinline__ float2 operator()(float2 a) const {
-        const float2 r = odd ? make_float2(mul_rsqrt2(a.x - a.y), mul_rsqrt2(a.x + a.y)) : a;
-        float2 o = sw ? make_float2(r.y, r.x) : r;
-        o.x = nx ? -o.x : o.x;
-        o.y = ny ? -o.y : o.y;
-        return o;
-    }
+// diag(1, e^{i k pi/4}) on tile bit q, written per lane as kappa (A + i B)
+// with A, B in {0, +-1} and kappa = 1/sqrt2 (odd k, compensated hi + lo) or 1.
+// (R, I) -> kappa (A R - B I, B R + A I): the products by 0 and +-1 are exact,
+// so lanes with (A, B, hi, lo) = (1, 0, 1, 0) pass through unchanged.
+struct PhaseOp {
+    float2 A, B, nB, H, L;
 };
-template <int P> __device__ __forceinline__ void rg_omega_half(float2 (&v)[32], const OmegaOp &op, uint32_t want) {
+__device__ __forceinline__ void phase_pk(float2 &r, float2 &i, const PhaseOp &o) {
+    float2 t1 = fma2(o.nB, i, mul2(o.A, r));
+    float2 t2 = fma2(o.B, r, mul2(o.A, i));
+    r = fma2(o.H, t1, mul2(o.L, t1));
+    i = fma2(o.H, t2, mul2(o.L, t2));
+}
+__device__ __forceinline__ void omega_ab(uint32_t k, float &A, float &B, float &H, float &L) {
+    const uint32_t q = (k >> 1) & 3u;
+    const float cq = q == 0 ? 1.f : (q == 2 ? -1.f : 0.f), sq = q == 1 ? 1.f : (q == 3 ? -1.f : 0.f);
+    if (k & 1u) {  // i^q (1 + i) / sqrt2
+        A = cq - sq;
+        B = cq + sq;
+        H = RSQRT2_HI;
+        L = RSQRT2_LO;
+    } else {
+        A = cq;
+        B = sq;
+        H = 1.f;
+        L = 0.f;
+    }
+}
+template <int P> __device__ __forceinline__ void rg_omega_half(Amps &a, const PhaseOp &op, uint32_t want) {
     if (want) {
 #pragma unroll
-        for (int ri = 0; ri < 32; ++ri)
-            if (ri & (1 << P)) v[ri] = op(v[ri]);
+        for (int k = 0; k < 16; ++k)
+            if (k & (1 << (P - 1))) phase_pk(a.re[k], a.im[k], op);
     } else {
 #pragma unroll
-        for (int ri = 0; ri < 32; ++ri)
-            if (!(ri & (1 << P))) v[ri] = op(v[ri]);
+        for (int k = 0; k < 16; ++k)
+            if (!(k & (1 << (P - 1)))) phase_pk(a.re[k], a.im[k], op);
     }
 }
-__device__ __forceinline__ void rg_omega(float2 (&v)[32], const TileCtx &c, uint32_t q, uint32_t k) {
-    const uint32_t pos = reg_pos(c, q), mq = (c.m >> q) & 1u, th = ((c.tpart ^ c.m) >> q) & 1u;
-    const OmegaOp op(k);
+__device__ __forceinline__ void rg_omega(Amps &a, const TileCtx &c, uint32_t q, uint32_t pos, uint32_t k) {
+    float A, B, H, L;
+    omega_ab(k, A, B, H, L);
     if (pos >= REG_BITS) {
-        if (th) {
+        if (thread_bit(c, q)) {
+            const PhaseOp op{bc2(A), bc2(B), bc2(-B), bc2(H), bc2(L)};
 #pragma unroll
-            for (int ri = 0; ri < 32; ++ri) v[ri] = op(v[ri]);
+            for (int kk = 0; kk < 16; ++kk) phase_pk(a.re[kk], a.im[kk], op);
         }
         return;
     }
-    const uint32_t want = mq ^ 1u;  // stored bit value whose true bit is 1
+    const uint32_t want = ((c.m >> q) & 1u) ^ 1u;  // stored bit value whose true bit is 1
+    if (pos == 0) {
+        // lane `want` of every packed register
+        const PhaseOp op = want ? PhaseOp{make_float2(1.f, A), make_float2(0.f, B), make_float2(0.f, -B),
+                                          make_float2(1.f, H), make_float2(0.f, L)}
+                                : PhaseOp{make_float2(A, 1.f), make_float2(B, 0.f), make_float2(-B, 0.f),
+                                          make_float2(H, 1.f), make_float2(L, 0.f)};
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) phase_pk(a.re[kk], a.im[kk], op);
+        return;
+    }
+    const PhaseOp op{bc2(A), bc2(B), bc2(-B), bc2(H), bc2(L)};
     switch (pos) {
-        case 0: rg_omega_half<0>(v, op, want); break;
-        case 1: rg_omega_half<1>(v, op, want); break;
-        case 2: rg_omega_half<2>(v, op, want); break;
-        case 3: rg_omega_half<3>(v, op, want); break;
-        default: rg_omega_half<4>(v, op, want); break;
+        case 1: rg_omega_half<1>(a, op, want); break;
+        case 2: rg_omega_half<2>(a, op, want); break;
+        case 3: rg_omega_half<3>(a, op, want); break;
+        default: rg_omega_half<4>(a, op, want); break;
     }
 }
 
@@ -183,97 +297,204 @@ __device__ __forceinline__ uint32_t reg_pattern(uint32_t pos) {
 __device__ __forceinline__ uint32_t bit_mask(const TileCtx &c, uint32_t q) {
     const uint32_t pos = reg_pos(c, q);
     if (pos < REG_BITS) return ((c.m >> q) & 1u) ? ~reg_pattern(pos) : reg_pattern(pos);
-    return (((c.tpart ^ c.m) >> q) & 1u) ? 0xFFFFFFFFu : 0u;
+    return thread_bit(c, q) ? 0xFFFFFFFFu : 0u;
 }
+__device__ __forceinline__ uint32_t sign_bit(uint32_t mask, int ri) { return (mask << (31 - ri)) & 0x80000000u; }
 // negate the registers selected by mask: flip the sign bits
-__device__ __forceinline__ void negate_masked(float2 (&v)[32], uint32_t mask) {
+__device__ __forceinline__ void negate_masked(Amps &a, uint32_t mask) {
 #pragma unroll
-    for (int ri = 0; ri < 32; ++ri) {
-        const uint32_t sgn = (mask << (31 - ri)) & 0x80000000u;
-        v[ri].x = __uint_as_float(__float_as_uint(v[ri].x) ^ sgn);
-        v[ri].y = __uint_as_float(__float_as_uint(v[ri].y) ^ sgn);
+    for (int k = 0; k < 16; ++k) {
+        const uint32_t sx = sign_bit(mask, 2 * k), sy = sign_bit(mask, 2 * k + 1);
+        a.re[k].x = __uint_as_float(__float_as_uint(a.re[k].x) ^ sx);
+        a.im[k].x = __uint_as_float(__float_as_uint(a.im[k].x) ^ sx);
+        a.re[k].y = __uint_as_float(__float_as_uint(a.re[k].y) ^ sy);
+        a.im[k].y = __uint_as_float(__float_as_uint(a.im[k].y) ^ sy);
     }
 }
 
-__device__ __forceinline__ void rg_cz(float2 (&v)[32], const TileCtx &c, uint32_t qa, uint32_t qb) {
-    const uint32_t mask = bit_mask(c, qa) & bit_mask(c, qb);
-    if (mask) negate_masked(v, mask);
+// CZ: negate the registers whose stored bits at positions PA and PB equal
+// (WA, WB). Both bits in registers: 8 of the 32 amplitudes, fixed at compile
+// time (40 variants); packed registers are negated with one FMUL2 by (-1, -1)
+// or (-1, 1) per plane.
+template <int PA, int PB, int WA, int WB> __device__ __forceinline__ void neg_quarter(Amps &a) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const bool nx = ((((2 * k) >> PA) & 1) == WA) && ((((2 * k) >> PB) & 1) == WB);
+        const bool ny = ((((2 * k + 1) >> PA) & 1) == WA) && ((((2 * k + 1) >> PB) & 1) == WB);
+        if (!nx && !ny) continue;
+        const float2 s = make_float2(nx ? -1.f : 1.f, ny ? -1.f : 1.f);
+        a.re[k] = mul2(s, a.re[k]);
+        a.im[k] = mul2(s, a.im[k]);
+    }
 }
+template <int P, int W> __device__ __forceinline__ void neg_half(Amps &a) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const bool nx = (((2 * k) >> P) & 1) == W, ny = (((2 * k + 1) >> P) & 1) == W;
+        if (!nx && !ny) continue;
+        const float2 s = make_float2(nx ? -1.f : 1.f, ny ? -1.f : 1.f);
+        a.re[k] = mul2(s, a.re[k]);
+        a.im[k] = mul2(s, a.im[k]);
+    }
+}
+__host__ __device__ constexpr int cz_pa(int pp) { return pp < 4 ? 0 : pp < 7 ? 1 : pp < 9 ? 2 : 3; }
+__host__ __device__ constexpr int cz_pb(int pp) {
+    return pp < 4 ? pp + 1 : pp < 7 ? pp - 2 : pp < 9 ? pp - 4 : 4;
+}
+template <int IDX> __device__ __forceinline__ void cz_case(Amps &a) {
+    neg_quarter<cz_pa(IDX >> 2), cz_pb(IDX >> 2), (IDX >> 1) & 1, IDX & 1>(a);
+}
+#define ARSO_CZ4(i)                                      \
+    case 4 * (i): cz_case<4 * (i)>(a); break;            \
+    case 4 * (i) + 1: cz_case<4 * (i) + 1>(a); break;    \
+    case 4 * (i) + 2: cz_case<4 * (i) + 2>(a); break;    \
+    case 4 * (i) + 3: cz_case<4 * (i) + 3>(a); break;
 
-__device__ __forceinline__ void rg_diag2(float2 (&v)[32], const TileCtx &c, uint32_t qa, uint32_t qb,
+__device__ __forceinline__ void rg_cz(Amps &a, const TileCtx &c, uint32_t qa, uint32_t qb, uint32_t pa, uint32_t pb) {
+    uint32_t wa = ((c.m >> qa) & 1u) ^ 1u, wb = ((c.m >> qb) & 1u) ^ 1u;  // stored values whose true bit is 1
+    if (pa < REG_BITS && pb < REG_BITS) {
+        if (pa > pb) {
+            const uint32_t tp = pa, tw = wa;
+            pa = pb;
+            wa = wb;
+            pb = tp;
+            wb = tw;
+        }
+        // pair index of (pa < pb) in (0,1),(0,2),(0,3),(0,4),(1,2),(1,3),(1,4),(2,3),(2,4),(3,4)
+        const uint32_t pp = pa == 0 ? pb - 1 : pa == 1 ? pb + 2 : pa == 2 ? pb + 4 : 9;
+        switch (pp * 4 + wa * 2 + wb) {
+            ARSO_CZ4(0) ARSO_CZ4(1) ARSO_CZ4(2) ARSO_CZ4(3) ARSO_CZ4(4)
+            ARSO_CZ4(5) ARSO_CZ4(6) ARSO_CZ4(7) ARSO_CZ4(8) ARSO_CZ4(9)
+            default: break;
+        }
+        return;
+    }
+    if (pa < REG_BITS || pb < REG_BITS) {
+        const uint32_t p = pa < REG_BITS ? pa : pb, w = pa < REG_BITS ? wa : wb;
+        if (!thread_bit(c, pa < REG_BITS ? qb : qa)) return;
+        switch (p * 2 + w) {
+            case 0: neg_half<0, 0>(a); break;
+            case 1: neg_half<0, 1>(a); break;
+            case 2: neg_half<1, 0>(a); break;
+            case 3: neg_half<1, 1>(a); break;
+            case 4: neg_half<2, 0>(a); break;
+            case 5: neg_half<2, 1>(a); break;
+            case 6: neg_half<3, 0>(a); break;
+            case 7: neg_half<3, 1>(a); break;
+            case 8: neg_half<4, 0>(a); break;
+            default: neg_half<4, 1>(a); break;
+        }
+        return;
+    }
+    if (thread_bit(c, qa) && thread_bit(c, qb)) {
+        const float2 m1 = bc2(-1.f);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            a.re[k] = mul2(m1, a.re[k]);
+            a.im[k] = mul2(m1, a.im[k]);
+        }
+    }
+}
+#undef ARSO_CZ4
+
+__device__ __forceinline__ void rg_diag2(Amps &a, const TileCtx &c, uint32_t qa, uint32_t qb,
                                          const float2 *__restrict__ d) {
-    const uint32_t pa = reg_pos(c, qa), ma = (c.m >> qa) & 1u, ta = ((c.tpart ^ c.m) >> qa) & 1u;
-    const uint32_t pb = reg_pos(c, qb), mb = (c.m >> qb) & 1u, tb = ((c.tpart ^ c.m) >> qb) & 1u;
+    const uint32_t pa = reg_pos(c, qa), ma = (c.m >> qa) & 1u, ta = thread_bit(c, qa);
+    const uint32_t pb = reg_pos(c, qb), mb = (c.m >> qb) & 1u, tb = thread_bit(c, qb);
     const float2 d0 = d[0], d1 = d[1], d2 = d[2], d3 = d[3];
 #pragma unroll
     for (int ri = 0; ri < 32; ++ri) {
         const uint32_t k = bit_of(ri, pa, ma, ta) | (bit_of(ri, pb, mb, tb) << 1);
         const float2 f = k == 0 ? d0 : (k == 1 ? d1 : (k == 2 ? d2 : d3));
-        v[ri] = cmul(f, v[ri]);
+        amp_set(a, ri, cmul(f, amp_get(a, ri)));
     }
 }
 
 // Pauli error on tile bit q of the true state (Eq. (2)): Z -> phase -1 on
 // bit q; X -> index mask; Y = i X Z.
-__device__ __forceinline__ void rg_pauli(float2 (&v)[32], TileCtx &c, uint32_t q, uint32_t code) {
+__device__ __forceinline__ void rg_pauli(Amps &a, TileCtx &c, uint32_t q, uint32_t code) {
     if (code & 2u) {  // Z part (Z or Y): negate where bit q of the true index is 1
         const uint32_t mask = bit_mask(c, q);
-        if (mask) negate_masked(v, mask);
+        if (mask) negate_masked(a, mask);
     }
     if (code & 1u) c.m ^= 1u << q;          // X part (X or Y)
     if (code == 3u) c.gp = (c.gp + 1u) & 3u;  // Y = i X Z
 }
 
+// multiply every amplitude by i^gp (exact) and reset gp
+__device__ __forceinline__ void apply_global_phase(Amps &a, TileCtx &c) {
+    if (!c.gp) return;
+    const float2 A = bc2(c.gp == 2 ? -1.f : (c.gp == 0 ? 1.f : 0.f)), B = bc2(c.gp == 1 ? 1.f : (c.gp == 3 ? -1.f : 0.f));
+    const float2 nB = make_float2(-B.x, -B.y);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const float2 r = a.re[k], i = a.im[k];
+        a.re[k] = fma2(nB, i, mul2(A, r));
+        a.im[k] = fma2(B, r, mul2(A, i));
+    }
+    c.gp = 0;
+}
+
 // stored index -> tile-local index bits for the load/store mapping
 __device__ __forceinline__ void set_phase(TileCtx &c, uint32_t packed, int t) {
-    unpack_r(packed, c.r);
-    c.rmask = 0;
+    c.R = packed;
+    uint32_t rmask = 0;
 #pragma unroll
-    for (int b = 0; b < REG_BITS; ++b) c.rmask |= 1u << c.r[b];
-    c.tpart = thread_part(c.tid, c.rmask, t);
+    for (int b = 0; b < REG_BITS; ++b) rmask |= 1u << rbit(packed, b);
+    c.tpart = thread_part(c.tid, rmask, t);
 }
 
-// The swizzle is linear over XOR, so the shared-memory slot of register ri is
-// swz(tpart) ^ (XOR of swz(1 << r[b]) over the set bits b of ri); walking the
-// registers in Gray-code order costs one XOR per register.
-__host__ __device__ constexpr int ctz5(int x) { return x & 1 ? 0 : x & 2 ? 1 : x & 4 ? 2 : x & 8 ? 3 : 4; }
+// Shared memory holds a tile as two planes of packed neighbour pairs:
+// plane_re[swz(J)] = (Re a_2J, Re a_2J+1) and plane_im likewise, plane_im =
+// plane_re + 2^(t-1). The swizzle is linear over XOR, so the slot of packed
+// register k is swz(tpart >> 1) ^ (XOR of swz(2^(r[b]-1)) over the set bits
+// b-1 of k); walking the registers in Gray-code order costs one XOR each.
+__host__ __device__ constexpr int ctz4(int x) { return x & 1 ? 0 : x & 2 ? 1 : x & 4 ? 2 : 3; }
 
-__device__ __forceinline__ void smem_basis(const TileCtx &c, uint32_t &base, uint32_t (&sw)[REG_BITS]) {
-    base = swz(c.tpart);
+__device__ __forceinline__ void smem_basis(const TileCtx &c, uint32_t &base, uint32_t (&sw)[REG_BITS - 1]) {
+    base = swz(c.tpart >> 1);
 #pragma unroll
-    for (int b = 0; b < REG_BITS; ++b) sw[b] = swz(1u << c.r[b]);
+    for (int b = 1; b < REG_BITS; ++b) sw[b - 1] = swz(1u << (rbit(c.R, b) - 1));
 }
-__device__ __forceinline__ void to_smem(const float2 (&v)[32], float2 *sm, const TileCtx &c) {
-    uint32_t idx, sw[REG_BITS];
+__device__ __forceinline__ void to_smem(const Amps &a, float2 *sm, const TileCtx &c, int t) {
+    uint32_t idx, sw[REG_BITS - 1];
     smem_basis(c, idx, sw);
+    float2 *pim = sm + (1u << (t - 1));
 #pragma unroll
-    for (int k = 0; k < 32; ++k) {
-        sm[idx] = v[k ^ (k >> 1)];
-        if (k < 31) idx ^= sw[ctz5(k + 1)];
+    for (int kk = 0; kk < 16; ++kk) {
+        const int k = kk ^ (kk >> 1);
+        sm[idx] = a.re[k];
+        pim[idx] = a.im[k];
+        if (kk < 15) idx ^= sw[ctz4(kk + 1)];
     }
 }
-__device__ __forceinline__ void from_smem(float2 (&v)[32], const float2 *sm, const TileCtx &c) {
-    uint32_t idx, sw[REG_BITS];
+__device__ __forceinline__ void from_smem(Amps &a, const float2 *sm, const TileCtx &c, int t) {
+    uint32_t idx, sw[REG_BITS - 1];
     smem_basis(c, idx, sw);
+    const float2 *pim = sm + (1u << (t - 1));
 #pragma unroll
-    for (int k = 0; k < 32; ++k) {
-        v[k ^ (k >> 1)] = sm[idx];
-        if (k < 31) idx ^= sw[ctz5(k + 1)];
+    for (int kk = 0; kk < 16; ++kk) {
+        const int k = kk ^ (kk >> 1);
+        a.re[k] = sm[idx];
+        a.im[k] = pim[idx];
+        if (kk < 15) idx ^= sw[ctz4(kk + 1)];
     }
 }
 
-__device__ __forceinline__ void remap(float2 (&v)[32], float2 *sm, TileCtx &c, uint32_t packed, int t) {
+__device__ __forceinline__ void remap(Amps &a, float2 *sm, TileCtx &c, uint32_t packed, int t) {
     __syncthreads();
-    to_smem(v, sm, c);
+    to_smem(a, sm, c, t);
     set_phase(c, packed, t);
     __syncthreads();
-    from_smem(v, sm, c);
+    from_smem(a, sm, c, t);
 }
 
 // Dense two-qubit gates and SWAP are rare: they run through shared memory on
 // the stored data (U already conjugated by the mask) with runtime indices.
 __device__ __forceinline__ void smem_dense2(float2 *sm, int t, uint32_t q0, uint32_t q1, const float2 *__restrict__ U,
                                             uint32_t tid, uint32_t nthr) {
+    float *pre = reinterpret_cast<float *>(sm);
+    float *pim = reinterpret_cast<float *>(sm + (1u << (t - 1)));
     const uint32_t lo = q0 < q1 ? q0 : q1, hi = q0 < q1 ? q1 : q0;
     const uint32_t m0 = 1u << q0, m1 = 1u << q1;
     float2 M[16];
@@ -281,65 +502,83 @@ __device__ __forceinline__ void smem_dense2(float2 *sm, int t, uint32_t q0, uint
     for (int k = 0; k < 16; ++k) M[k] = U[k];
     for (uint32_t p = tid; p < (1u << (t - 2)); p += nthr) {
         const uint32_t i = insert_zero2(p, lo, hi);
-        const uint32_t ix[4] = {swz(i), swz(i | m0), swz(i | m1), swz(i | m0 | m1)};
-        float2 a[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) a[k] = sm[ix[k]];
+        const uint32_t jx[4] = {i, i | m0, i | m1, i | m0 | m1};
+        uint32_t ix[4];
+        float2 v[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            float2 acc = cmac2(M[4 * k], a[0], M[4 * k + 1], a[1]);
-            const float2 acc2 = cmac2(M[4 * k + 2], a[2], M[4 * k + 3], a[3]);
-            acc.x += acc2.x;
-            acc.y += acc2.y;
-            sm[ix[k]] = acc;
+            ix[k] = 2u * swz(jx[k] >> 1) + (jx[k] & 1u);
+            v[k] = make_float2(pre[ix[k]], pim[ix[k]]);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float2 acc = cmac2(M[4 * k], v[0], M[4 * k + 1], v[1]);
+            const float2 acc2 = cmac2(M[4 * k + 2], v[2], M[4 * k + 3], v[3]);
+            pre[ix[k]] = acc.x + acc2.x;
+            pim[ix[k]] = acc.y + acc2.y;
         }
     }
 }
 
-__device__ __forceinline__ void apply_gate_rb(float2 (&v)[32], TileCtx &c, const DGate &g, uint8_t rp,
+__device__ __forceinline__ void apply_gate_rb(Amps &a, TileCtx &c, const DGate &g, uint8_t rp,
                                               const float2 *__restrict__ mats, float2 *sm, float2 *ubuf, int t) {
     const uint32_t p0 = rp & 15u, p1 = rp >> 4;
     const float2 *M = mats + g.mat;
     switch (g.cls) {
         case GC_H: {
+            // with the qubit's mask bit set: H X = Z H, so apply Z H and clear the bit
             const uint32_t flip = (c.m >> g.q0) & 1u;
             switch (p0) {
-                case 0: rg_h<0>(v, flip); break;
-                case 1: rg_h<1>(v, flip); break;
-                case 2: rg_h<2>(v, flip); break;
-                case 3: rg_h<3>(v, flip); break;
-                default: rg_h<4>(v, flip); break;
+                case 0: rg_h_lanes(a, flip ? -1.f : 1.f); break;
+                case 1: rg_h<1>(a, flip); break;
+                case 2: rg_h<2>(a, flip); break;
+                case 3: rg_h<3>(a, flip); break;
+                default: rg_h<4>(a, flip); break;
             }
+            c.m &= ~(1u << g.q0);
             break;
         }
         case GC_DENSE1: {
             // with the qubit's mask bit set the stored data sees X U X = [[u11, u10], [u01, u00]]
             const uint32_t flip = (c.m >> g.q0) & 1u;
-            const float2 u00 = flip ? M[3] : M[0], u01 = flip ? M[2] : M[1];
-            const float2 u10 = flip ? M[1] : M[2], u11 = flip ? M[0] : M[3];
+            const float2 u00 = M[flip ? 3 : 0], u01 = M[flip ? 2 : 1];
+            const float2 u10 = M[flip ? 1 : 2], u11 = M[flip ? 0 : 3];
             switch (p0) {
-                case 0: rg_dense1<0>(v, u00, u01, u10, u11); break;
-                case 1: rg_dense1<1>(v, u00, u01, u10, u11); break;
-                case 2: rg_dense1<2>(v, u00, u01, u10, u11); break;
-                case 3: rg_dense1<3>(v, u00, u01, u10, u11); break;
-                default: rg_dense1<4>(v, u00, u01, u10, u11); break;
+                case 0: rg_dense1_lanes(a, u00, u01, u10, u11); break;
+                case 1: rg_dense1<1>(a, u00, u01, u10, u11); break;
+                case 2: rg_dense1<2>(a, u00, u01, u10, u11); break;
+                case 3: rg_dense1<3>(a, u00, u01, u10, u11); break;
+                default: rg_dense1<4>(a, u00, u01, u10, u11); break;
             }
             break;
         }
-        case GC_DIAG1: rg_diag1(v, c, g.q0, M[0], M[1]); break;
-        case GC_OMEGA: rg_omega(v, c, g.q0, g.mat); break;
+        case GC_SU2: {
+            // X U X = [[conj a, -conj b], [b, a]]: the same form with (u11, u10)
+            const uint32_t flip = (c.m >> g.q0) & 1u;
+            const float2 ua = M[flip ? 3 : 0], ub = M[flip ? 2 : 1];
+            switch (p0) {
+                case 0: rg_dense1_lanes(a, ua, ub, make_float2(-ub.x, ub.y), make_float2(ua.x, -ua.y)); break;
+                case 1: rg_su2<1>(a, ua, ub); break;
+                case 2: rg_su2<2>(a, ua, ub); break;
+                case 3: rg_su2<3>(a, ua, ub); break;
+                default: rg_su2<4>(a, ua, ub); break;
+            }
+            break;
+        }
+        case GC_DIAG1: rg_diag1(a, c, g.q0, p0, M[0], M[1]); break;
+        case GC_OMEGA: rg_omega(a, c, g.q0, p0, g.mat); break;
         case GC_X: c.m ^= 1u << g.q0; break;
-        case GC_CZ: rg_cz(v, c, g.q0, g.q1); break;
-        case GC_DIAG2: rg_diag2(v, c, g.q0, g.q1, M); break;
+        case GC_CZ: rg_cz(a, c, g.q0, g.q1, p0, p1); break;
+        case GC_DIAG2: rg_diag2(a, c, g.q0, g.q1, M); break;
         case GC_CX: {
             // CX X^m = X^{m'} CX with m' = m ^ (target bit if the control bit is in m)
             const uint32_t cth = (c.tpart >> g.q0) & 1u;
             switch (p1) {
-                case 0: rg_cx<0>(v, p0, cth); break;
-                case 1: rg_cx<1>(v, p0, cth); break;
-                case 2: rg_cx<2>(v, p0, cth); break;
-                case 3: rg_cx<3>(v, p0, cth); break;
-                default: rg_cx<4>(v, p0, cth); break;
+                case 0: rg_cx<0>(a, p0, cth); break;
+                case 1: rg_cx<1>(a, p0, cth); break;
+                case 2: rg_cx<2>(a, p0, cth); break;
+                case 3: rg_cx<3>(a, p0, cth); break;
+                default: rg_cx<4>(a, p0, cth); break;
             }
             if ((c.m >> g.q0) & 1u) c.m ^= 1u << g.q1;
             break;
@@ -359,11 +598,11 @@ __device__ __forceinline__ void apply_gate_rb(float2 (&v)[32], TileCtx &c, const
                 ubuf[c.tid] = u;
             }
             __syncthreads();
-            to_smem(v, sm, c);
+            to_smem(a, sm, c, t);
             __syncthreads();
             smem_dense2(sm, t, g.q0, g.q1, ubuf, c.tid, c.nthr);
             __syncthreads();
-            from_smem(v, sm, c);
+            from_smem(a, sm, c, t);
             __syncthreads();
             // SWAP X^m = X^{m with bits q0, q1 exchanged} SWAP
             if (g.cls == GC_SWAP && (((c.m >> g.q0) ^ (c.m >> g.q1)) & 1u)) c.m ^= (1u << g.q0) | (1u << g.q1);
@@ -373,55 +612,88 @@ __device__ __forceinline__ void apply_gate_rb(float2 (&v)[32], TileCtx &c, const
     }
 }
 
+// Gates [g, ge) of one phase with the Pauli events that fall inside them.
+// The inner loop runs up to and including the next event's gate without
+// touching the event state, which stays out of the hot registers.
+__device__ __forceinline__ void run_gates(Amps &v, TileCtx &c, uint32_t g, uint32_t ge, const DGate *__restrict__ gates,
+                                          const uint8_t *__restrict__ rpos, const float2 *__restrict__ mats,
+                                          float2 *sm, float2 *ubuf, int t, const uint32_t *&ev,
+                                          const uint32_t *ev_end, uint32_t &next) {
+    while (g < ge) {
+        const uint32_t np = next == NO_EVENT ? ge : ev_pos(next);
+        const uint32_t stop = np < ge ? np + 1 : ge;
+        for (; g < stop; ++g) apply_gate_rb(v, c, gates[g], rpos[g], mats, sm, ubuf, t);
+        if (np >= ge) break;
+        const DGate gate = gates[np];
+        while (next != NO_EVENT && ev_pos(next) == np) {
+            rg_pauli(v, c, ev_slot(next) ? gate.q1 : gate.q0, ev_code(next));
+            ++ev;
+            next = ev < ev_end ? *ev : NO_EVENT;
+        }
+    }
+}
+
+// global offset of the tile's first amplitude: the tile index deposited into
+// the global bits outside the tile
+__device__ __forceinline__ uint64_t tile_base(uint64_t rest_mask, uint64_t tile) {
+    uint64_t base = 0;
+    for (uint64_t mm = rest_mask; mm; mm &= mm - 1) {
+        if (tile & 1) base |= mm & (~mm + 1);
+        tile >>= 1;
+    }
+    return base;
+}
+
+// The phase loop holds the 64 amplitude registers; everything needed only
+// before or after it (addresses, slot data) is recomputed there instead of
+// being kept live.
 template <bool LAST>
 __global__ void __launch_bounds__(512, 1) pass_rb_kernel(PassArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *sm = reinterpret_cast<float2 *>(smem_raw);
     __shared__ Partial red[32];
     __shared__ float2 ubuf[16];
-    const int t = a.t, cl = a.c;
+    const int t = a.t;
     const uint32_t slot = blockIdx.y;
     const uint64_t N = 1ull << a.n;
-    int start, end = 0;
-    uint64_t tr = 0;
-    const float2 *src;
-    float2 *dst;
-    if (a.ideal) {
-        start = 0;
-        src = static_cast<const float2 *>(a.ideal_src);
-        dst = static_cast<float2 *>(a.ideal_dst);
-    } else {
-        start = a.start_pass[slot];
-        end = a.end_pass[slot];
-        if (a.pass < start || a.pass > end) return;
-        tr = a.slot_traj[slot];
-        float2 *mine = static_cast<float2 *>(a.work) + (size_t)slot * N;
-        src = a.pass == start ? static_cast<const float2 *>(a.cache) + (size_t)a.cache_slot[start] * N : mine;
-        dst = mine;
-    }
-    // tile base: deposit the tile index into the non-tile global bits
-    uint64_t base = 0;
-    {
-        uint64_t tile = blockIdx.x;
-        for (uint64_t mm = a.rest_mask; mm; mm &= mm - 1) {
-            if (tile & 1) base |= mm & (~mm + 1);
-            tile >>= 1;
-        }
-    }
-    const uint32_t *offs = a.offs;
-    const uint32_t cmask = (1u << cl) - 1u;
-    auto gidx = [&](uint32_t j) -> uint64_t { return base + offs[j >> cl] + (j & cmask); };
+    const uint32_t cmask = (1u << a.c) - 1u;
+    auto gidx = [&](uint64_t base, uint32_t j) -> uint64_t { return base + a.offs[j >> a.c] + (j & cmask); };
 
     // load mapping R = {0, t-4, ..., t-1}: register ri = b0 | hi << 1 holds j = hi << (t-4) | tid << 1 | b0
     const uint32_t load_packed = 0u | ((uint32_t)(t - 4) << 5) | ((uint32_t)(t - 3) << 10) |
                                  ((uint32_t)(t - 2) << 15) | ((uint32_t)(t - 1) << 20);
-    float2 v[32];
+    Amps v;
+    const uint32_t *ev = nullptr, *ev_end = nullptr;
+    {
+        const float2 *src;
+        if (a.ideal) {
+            src = static_cast<const float2 *>(a.ideal_src);
+        } else {
+            const int start = a.start_pass[slot];
+            if (a.pass < start || a.pass > a.end_pass[slot]) return;
+            src = a.pass == start ? static_cast<const float2 *>(a.cache) + (size_t)a.cache_slot[start] * N
+                                  : static_cast<const float2 *>(a.work) + (size_t)slot * N;
+            // this pass's events: binary search for the first key at or after the pass's first gate
+            const uint64_t tr = a.slot_traj[slot];
+            const uint32_t *lo = a.keys + a.offsets[tr];
+            const uint32_t *hi = a.keys + a.offsets[tr + 1];
+            ev_end = hi;
+            const uint32_t key_lo = a.gb << 3;
+            while (lo < hi) {
+                const uint32_t *mid = lo + (hi - lo) / 2;
+                if (*mid < key_lo) lo = mid + 1;
+                else hi = mid;
+            }
+            ev = lo;
+        }
+        const uint64_t base = tile_base(a.rest_mask, blockIdx.x);
 #pragma unroll
-    for (int hi = 0; hi < 16; ++hi) {
-        const uint32_t j = ((uint32_t)hi << (t - 4)) | (threadIdx.x << 1);
-        const float4 w = __ldg(reinterpret_cast<const float4 *>(src + gidx(j)));
-        v[2 * hi] = make_float2(w.x, w.y);
-        v[2 * hi + 1] = make_float2(w.z, w.w);
+        for (int hi = 0; hi < 16; ++hi) {
+            const uint32_t j = ((uint32_t)hi << (t - 4)) | (threadIdx.x << 1);
+            const float4 w = __ldg(reinterpret_cast<const float4 *>(src + gidx(base, j)));
+            v.re[hi] = make_float2(w.x, w.z);
+            v.im[hi] = make_float2(w.y, w.w);
+        }
     }
     TileCtx c;
     c.m = 0;
@@ -430,64 +702,35 @@ __global__ void __launch_bounds__(512, 1) pass_rb_kernel(PassArgs a) {
     c.nthr = blockDim.x;
     set_phase(c, load_packed, t);
 
-    const uint32_t *ev = nullptr, *ev_end = nullptr;
-    if (!a.ideal) {
-        const uint32_t *lo = a.keys + a.offsets[tr];
-        const uint32_t *hi = a.keys + a.offsets[tr + 1];
-        const uint32_t key_lo = a.gb << 3;
-        while (lo < hi) {
-            const uint32_t *mid = lo + (hi - lo) / 2;
-            if (*mid < key_lo) lo = mid + 1;
-            else hi = mid;
-        }
-        ev = lo;
-        ev_end = a.keys + a.offsets[tr + 1];
-    }
-    uint32_t next = ev && ev < ev_end ? *ev : NO_EVENT;
+    uint32_t next = ev < ev_end ? *ev : NO_EVENT;
     const float2 *mats = static_cast<const float2 *>(a.mats);
-    uint32_t cur_packed = load_packed;
     for (uint32_t ph = a.pb; ph < a.pe; ++ph) {
         const uint32_t R = a.ph_R[ph];
-        if (R != cur_packed) {
-            remap(v, sm, c, R, t);
-            cur_packed = R;
-        }
-        const uint32_t ge = a.ph_gb[ph + 1];
-        for (uint32_t g = a.ph_gb[ph]; g < ge; ++g) {
-            const DGate gate = a.gates[g];
-            apply_gate_rb(v, c, gate, a.rpos[g], mats, sm, ubuf, t);
-            while (next != NO_EVENT && ev_pos(next) == g) {
-                rg_pauli(v, c, ev_slot(next) ? gate.q1 : gate.q0, ev_code(next));
-                ++ev;
-                next = ev < ev_end ? *ev : NO_EVENT;
-            }
-        }
+        if (R != c.R) remap(v, sm, c, R, t);
+        run_gates(v, c, a.ph_gb[ph], a.ph_gb[ph + 1], a.gates, a.rpos, mats, sm, ubuf, t, ev, ev_end, next);
     }
-    // global phase i^gp
-    if (c.gp) {
-#pragma unroll
-        for (int ri = 0; ri < 32; ++ri) v[ri] = omega_mul(v[ri], 2u * c.gp);
-    }
-    if (!a.ideal && !a.store_last && a.pass == end) {
-        const float2 *ref = static_cast<const float2 *>(a.cache) + (size_t)a.cache_slot[end + 1] * N;
+    apply_global_phase(v, c);  // global phase i^gp
+    const uint64_t base = tile_base(a.rest_mask, blockIdx.x);
+    if (!a.ideal && !a.store_last && a.pass == a.end_pass[slot]) {
+        const float2 *ref = static_cast<const float2 *>(a.cache) + (size_t)a.cache_slot[a.pass + 1] * N;
         Partial acc = empty_partial();
 #pragma unroll
         for (int ri = 0; ri < 32; ++ri) {
-            const uint32_t jj = (c.tpart | reg_part(ri, c.r)) ^ c.m;
-            accumulate(acc, a.crit, v[ri], ref, gidx(jj));
+            const uint32_t jj = (c.tpart | reg_part(ri, c.R)) ^ c.m;
+            accumulate(acc, a.crit, amp_get(v, ri), ref, gidx(base, jj));
         }
         acc = block_reduce_partial(acc, red);
         if (threadIdx.x == 0) a.partials[(size_t)slot * gridDim.x + blockIdx.x] = acc;
         return;
     }
-    if (cur_packed != load_packed) remap(v, sm, c, load_packed, t);
+    if (c.R != load_packed) remap(v, sm, c, load_packed, t);
+    float2 *dst = a.ideal ? static_cast<float2 *>(a.ideal_dst) : static_cast<float2 *>(a.work) + (size_t)slot * N;
     const uint32_t flip0 = c.m & 1u;
 #pragma unroll
     for (int hi = 0; hi < 16; ++hi) {
         const uint32_t j = (((uint32_t)hi << (t - 4)) | (threadIdx.x << 1)) ^ (c.m & ~1u);
-        const float2 e = flip0 ? v[2 * hi + 1] : v[2 * hi];
-        const float2 o = flip0 ? v[2 * hi] : v[2 * hi + 1];
-        reinterpret_cast<float4 *>(dst + gidx(j))[0] = make_float4(e.x, e.y, o.x, o.y);
+        const float2 r = flip0 ? swp2(v.re[hi]) : v.re[hi], i = flip0 ? swp2(v.im[hi]) : v.im[hi];
+        reinterpret_cast<float4 *>(dst + gidx(base, j))[0] = make_float4(r.x, i.x, r.y, i.y);
     }
 }
 
@@ -496,35 +739,27 @@ __global__ void __launch_bounds__(512, 1) pass_rb_kernel(PassArgs a) {
 // the cached error-free state at the checkpoint (phase boundary) at or before
 // its first error and runs the remaining phases; ckpt_every counts phases.
 
-__device__ __forceinline__ void rb_load_linear(float2 (&v)[32], const float2 *src, int t, uint32_t tid) {
+__device__ __forceinline__ void rb_load_linear(Amps &v, const float2 *src, int t, uint32_t tid) {
 #pragma unroll
     for (int hi = 0; hi < 16; ++hi) {
         const uint32_t j = ((uint32_t)hi << (t - 4)) | (tid << 1);
         const float4 w = __ldg(reinterpret_cast<const float4 *>(src + j));
-        v[2 * hi] = make_float2(w.x, w.y);
-        v[2 * hi + 1] = make_float2(w.z, w.w);
+        v.re[hi] = make_float2(w.x, w.z);
+        v.im[hi] = make_float2(w.y, w.w);
     }
 }
 
 // store the true state (mask and global phase applied); leaves v in the load mapping
-__device__ __forceinline__ void rb_store_linear(float2 (&v)[32], float2 *sm, TileCtx &c, uint32_t &cur_packed,
-                                                uint32_t load_packed, float2 *dst, int t) {
-    if (cur_packed != load_packed) {
-        remap(v, sm, c, load_packed, t);
-        cur_packed = load_packed;
-    }
+__device__ __forceinline__ void rb_store_linear(Amps &v, float2 *sm, TileCtx &c, uint32_t load_packed, float2 *dst,
+                                                int t) {
+    if (c.R != load_packed) remap(v, sm, c, load_packed, t);
+    apply_global_phase(v, c);
     const uint32_t flip0 = c.m & 1u;
-    const uint32_t k2 = 2u * c.gp;
 #pragma unroll
     for (int hi = 0; hi < 16; ++hi) {
         const uint32_t j = (((uint32_t)hi << (t - 4)) | (c.tid << 1)) ^ (c.m & ~1u);
-        float2 e = flip0 ? v[2 * hi + 1] : v[2 * hi];
-        float2 o = flip0 ? v[2 * hi] : v[2 * hi + 1];
-        if (k2) {
-            e = omega_mul(e, k2);
-            o = omega_mul(o, k2);
-        }
-        reinterpret_cast<float4 *>(dst + j)[0] = make_float4(e.x, e.y, o.x, o.y);
+        const float2 r = flip0 ? swp2(v.re[hi]) : v.re[hi], i = flip0 ? swp2(v.im[hi]) : v.im[hi];
+        reinterpret_cast<float4 *>(dst + j)[0] = make_float4(r.x, i.x, r.y, i.y);
     }
 }
 
@@ -542,21 +777,20 @@ __global__ void __launch_bounds__(512, 1) resident_rb_kernel(ResidentArgs a) {
                                  ((uint32_t)(t - 2) << 15) | ((uint32_t)(t - 1) << 20);
     const uint64_t count = MODE == 2 ? 1 : a.count;
     for (uint64_t b = blockIdx.x; b < count; b += gridDim.x) {
-        float2 v[32];
+        Amps v;
         TileCtx c;
         c.m = 0;
         c.gp = 0;
         c.tid = threadIdx.x;
         c.nthr = blockDim.x;
         set_phase(c, load_packed, t);
-        uint32_t cur_packed = load_packed;
         uint32_t ph0 = 0;
         const uint32_t *ev = nullptr, *ev_end = nullptr;
         uint64_t tr = 0;
         if (MODE == 2) {
 #pragma unroll
-            for (int ri = 0; ri < 32; ++ri) v[ri] = make_float2(0.f, 0.f);
-            if (threadIdx.x == 0) v[0] = make_float2(1.f, 0.f);
+            for (int k = 0; k < 16; ++k) v.re[k] = v.im[k] = make_float2(0.f, 0.f);
+            if (threadIdx.x == 0) v.re[0].x = 1.f;
         } else {
             tr = a.first_traj + b;
             const uint32_t first = a.first[tr];
@@ -583,40 +817,25 @@ __global__ void __launch_bounds__(512, 1) resident_rb_kernel(ResidentArgs a) {
         for (uint32_t ph = ph0; ph < a.n_phases; ++ph) {
             if (MODE == 2 && ph % (uint32_t)a.ckpt_every == 0) {
                 float2 *dst = const_cast<float2 *>(cache) + (size_t)(ph / (uint32_t)a.ckpt_every) * N;
-                rb_store_linear(v, sm, c, cur_packed, load_packed, dst, t);
+                rb_store_linear(v, sm, c, load_packed, dst, t);
             }
             const uint32_t R = a.ph_R[ph];
-            if (R != cur_packed) {
-                remap(v, sm, c, R, t);
-                cur_packed = R;
-            }
-            const uint32_t ge = a.ph_gb[ph + 1];
-            for (uint32_t g = a.ph_gb[ph]; g < ge; ++g) {
-                const DGate gate = a.gates[g];
-                apply_gate_rb(v, c, gate, a.rpos[g], mats, sm, ubuf, t);
-                while (next != NO_EVENT && ev_pos(next) == g) {
-                    rg_pauli(v, c, ev_slot(next) ? gate.q1 : gate.q0, ev_code(next));
-                    ++ev;
-                    next = ev < ev_end ? *ev : NO_EVENT;
-                }
-            }
+            if (R != c.R) remap(v, sm, c, R, t);
+            run_gates(v, c, a.ph_gb[ph], a.ph_gb[ph + 1], a.gates, a.rpos, mats, sm, ubuf, t, ev, ev_end, next);
         }
         if (MODE == 2) {
-            rb_store_linear(v, sm, c, cur_packed, load_packed, const_cast<float2 *>(cache) + (size_t)(a.n_ckpt - 1) * N,
+            rb_store_linear(v, sm, c, load_packed, const_cast<float2 *>(cache) + (size_t)(a.n_ckpt - 1) * N,
                             t);
         } else if (MODE == 1) {
-            rb_store_linear(v, sm, c, cur_packed, load_packed, static_cast<float2 *>(a.states_out) + (size_t)b * N, t);
+            rb_store_linear(v, sm, c, load_packed, static_cast<float2 *>(a.states_out) + (size_t)b * N, t);
         } else {
-            if (c.gp) {
-#pragma unroll
-                for (int ri = 0; ri < 32; ++ri) v[ri] = omega_mul(v[ri], 2u * c.gp);
-            }
+            apply_global_phase(v, c);
             const float2 *ref = cache + (size_t)(a.n_ckpt - 1) * N;
             Partial acc = empty_partial();
 #pragma unroll
             for (int ri = 0; ri < 32; ++ri) {
-                const uint32_t jj = (c.tpart | reg_part(ri, c.r)) ^ c.m;
-                accumulate(acc, a.crit, v[ri], ref, jj);
+                const uint32_t jj = (c.tpart | reg_part(ri, c.R)) ^ c.m;
+                accumulate(acc, a.crit, amp_get(v, ri), ref, jj);
             }
             acc = block_reduce_partial(acc, red);
             if (threadIdx.x == 0) {
@@ -685,39 +904,23 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2)
         c.tid = threadIdx.x % gsize;
         c.nthr = gsize;
         set_phase(c, load_packed, t);
-        float2 v[32];
+        Amps v;
         rb_load_linear(v, C.cache + (size_t)it.ck * N, t, c.tid);
         const uint32_t *ev = C.keys + C.offsets[tr];
         const uint32_t *ev_end = C.keys + C.offsets[tr + 1];
         uint32_t next = ev < ev_end ? *ev : NO_EVENT;
-        uint32_t cur_packed = load_packed;
         for (uint32_t ph = it.ck * C.ckpt_every; ph < C.n_phases; ++ph) {
             const uint32_t R = C.ph_R[ph];
-            if (R != cur_packed) {
-                remap(v, sm, c, R, t);
-                cur_packed = R;
-            }
-            const uint32_t ge = C.ph_gb[ph + 1];
-            for (uint32_t g = C.ph_gb[ph]; g < ge; ++g) {
-                const DGate gate = C.gates[g];
-                apply_gate_rb(v, c, gate, C.rpos[g], C.mats, sm, ubuf[sg], t);
-                while (next != NO_EVENT && ev_pos(next) == g) {
-                    rg_pauli(v, c, ev_slot(next) ? gate.q1 : gate.q0, ev_code(next));
-                    ++ev;
-                    next = ev < ev_end ? *ev : NO_EVENT;
-                }
-            }
+            if (R != c.R) remap(v, sm, c, R, t);
+            run_gates(v, c, C.ph_gb[ph], C.ph_gb[ph + 1], C.gates, C.rpos, C.mats, sm, ubuf[sg], t, ev, ev_end, next);
         }
-        if (c.gp) {
-#pragma unroll
-            for (int ri = 0; ri < 32; ++ri) v[ri] = omega_mul(v[ri], 2u * c.gp);
-        }
+        apply_global_phase(v, c);
         const float2 *ref = C.cache + (size_t)(C.n_ckpt - 1) * N;
         Partial acc = empty_partial();
 #pragma unroll
         for (int ri = 0; ri < 32; ++ri) {
-            const uint32_t jj = (c.tpart | reg_part(ri, c.r)) ^ c.m;
-            accumulate(acc, C.crit, v[ri], ref, jj);
+            const uint32_t jj = (c.tpart | reg_part(ri, c.R)) ^ c.m;
+            accumulate(acc, C.crit, amp_get(v, ri), ref, jj);
         }
         // per sub-group reduction: warps reduce by shuffles, the sub-group leader combines its warps
 #pragma unroll

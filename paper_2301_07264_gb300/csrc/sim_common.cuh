@@ -72,7 +72,8 @@ template <typename T>
 __device__ __forceinline__ void tile_gate(T *s, int t, const DGate &g, const T *__restrict__ M) {
     const uint32_t nt = blockDim.x, tid = threadIdx.x;
     switch (g.cls) {
-        case GC_DENSE1: {
+        case GC_DENSE1:
+        case GC_SU2: {
             const T u00 = M[0], u01 = M[1], u10 = M[2], u11 = M[3];
             const uint32_t b = g.q0, bit = 1u << b;
             for (uint32_t p = tid; p < (1u << (t - 1)); p += nt) {
