@@ -151,9 +151,24 @@ static void upload_circuit(arso_circuit *c) {
         c->d_ph_R.ensure(std::max<size_t>(c->ph_R.size(), 1) * 4);
         if (!c->ph_R.empty())
             ARSO_CUDA(cudaMemcpy(c->d_ph_R.ptr, c->ph_R.data(), c->ph_R.size() * 4, cudaMemcpyHostToDevice));
-        c->d_rpos.ensure(std::max<size_t>(c->rpos.size(), 1));
-        if (!c->rpos.empty())
-            ARSO_CUDA(cudaMemcpy(c->d_rpos.ptr, c->rpos.data(), c->rpos.size(), cudaMemcpyHostToDevice));
+        std::vector<RegOp> ops(std::max<size_t>(dg.size(), 1));
+        for (size_t pos = 0; pos < c->rpos.size(); ++pos) {
+            const DGate &d = dg[pos];
+            RegOp &o = ops[pos];
+            o.w0 = (uint32_t)d.cls | (uint32_t)(c->rpos[pos] & 15u) << 8 | (uint32_t)(c->rpos[pos] >> 4) << 12 |
+                   (uint32_t)d.q0 << 16 | (uint32_t)d.q1 << 24;
+            o.aux = d.mat;
+            const HostGate &h = c->gates[c->perm[pos]];
+            if (d.cls == GC_SU2) {
+                o.c0 = make_float2((float)h.m[0].real(), (float)h.m[0].imag());
+                o.c1 = make_float2((float)h.m[1].real(), (float)h.m[1].imag());
+            } else if (d.cls == GC_DIAG1) {
+                o.c0 = make_float2((float)h.m[0].real(), (float)h.m[0].imag());
+                o.c1 = make_float2((float)h.m[3].real(), (float)h.m[3].imag());
+            }
+        }
+        c->d_rops.ensure(ops.size() * sizeof(RegOp));
+        ARSO_CUDA(cudaMemcpy(c->d_rops.ptr, ops.data(), ops.size() * sizeof(RegOp), cudaMemcpyHostToDevice));
         c->d_phase_of_pos.ensure(std::max<size_t>(c->phase_of_pos.size(), 1) * 4);
         if (!c->phase_of_pos.empty())
             ARSO_CUDA(cudaMemcpy(c->d_phase_of_pos.ptr, c->phase_of_pos.data(), c->phase_of_pos.size() * 4,
@@ -175,7 +190,7 @@ static ResidentArgs resident_args(const arso_circuit *c) {
         a.n_phases = (uint32_t)c->ph_R.size();
         a.ph_gb = c->d_ph_gb.as<uint32_t>();
         a.ph_R = c->d_ph_R.as<uint32_t>();
-        a.rpos = c->d_rpos.as<uint8_t>();
+        a.rops = c->d_rops.as<RegOp>();
         a.phase_of_pos = c->d_phase_of_pos.as<uint32_t>();
     }
     return a;
@@ -195,7 +210,7 @@ static void run_pass(const arso_circuit *c, const PassArgs &a, bool last, uint32
         b.pe = c->passes[a.pass].pe;
         b.ph_gb = c->d_ph_gb.as<uint32_t>();
         b.ph_R = c->d_ph_R.as<uint32_t>();
-        b.rpos = c->d_rpos.as<uint8_t>();
+        b.rops = c->d_rops.as<RegOp>();
         launch_pass_rb(b, last, slots, bytes, st);
     } else {
         launch_pass(a, last, c->precision, slots, bytes, st);
@@ -910,7 +925,7 @@ arso_status arso_run_batch(size_t count, arso_circuit *const *circuits, const ar
                 b.ph_gb = c->d_ph_gb.as<uint32_t>();
                 b.ph_R = c->d_ph_R.as<uint32_t>();
                 b.phase_of_pos = c->d_phase_of_pos.as<uint32_t>();
-                b.rpos = c->d_rpos.as<uint8_t>();
+                b.rops = c->d_rops.as<RegOp>();
                 b.cache = c->d_cache.as<float2>();
                 b.offsets = e->d_offsets.as<uint64_t>();
                 b.keys = e->d_key.as<uint32_t>();

@@ -290,10 +290,14 @@ static void plan_phases(arso_circuit *c) {
             lq0[i] = (uint32_t)local[h.q0];
             lq1[i] = (uint32_t)local[h.q1];
         }
-        for (auto &ph : phases) {
-            ARSO_REQUIRE(ph.second[0] == 0, "internal: a register set without tile bit 0");
-            c->ph_gb.push_back(ps.gb + ph.first);
-            c->ph_R.push_back(pack_rbits(ph.second.data()));
+        // phases longer than MAX_PHASE_OPS gates continue with the same register set
+        for (size_t k = 0; k < phases.size(); ++k) {
+            ARSO_REQUIRE(phases[k].second[0] == 0, "internal: a register set without tile bit 0");
+            const uint32_t end = k + 1 < phases.size() ? phases[k + 1].first : G;
+            for (uint32_t b = phases[k].first; b < end || b == phases[k].first; b += MAX_PHASE_OPS) {
+                c->ph_gb.push_back(ps.gb + b);
+                c->ph_R.push_back(pack_rbits(phases[k].second.data()));
+            }
         }
         ps.pe = (uint32_t)c->ph_R.size();
         // register positions of each gate's qubits within its phase

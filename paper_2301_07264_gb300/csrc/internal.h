@@ -57,6 +57,9 @@ enum GateClass : uint8_t {
 // diagonal gates, X gates and Pauli errors act on any bit.
 constexpr int REG_BITS = 5;
 constexpr int RB_MIN_TILE = 10;                   // 32 threads x 32 amplitudes
+// gates per phase at most: the register kernels stage a phase's gate records
+// in shared memory (double-buffered: the next phase's copy overlaps this one)
+constexpr int MAX_PHASE_OPS = 64;
 inline uint32_t pack_rbits(const uint32_t *p) {   // 5 local bit positions, 5 bits each
     uint32_t r = 0;
     for (int b = 0; b < REG_BITS; ++b) r |= p[b] << (5 * b);
@@ -77,6 +80,19 @@ struct DGate {
     uint8_t q0, q1;
     uint8_t arity;
     uint32_t mat;   // offset (in complex entries) into the matrix pool
+};
+
+// One gate as the register-blocked kernels see it: everything in one 32-byte
+// record (two 16-byte loads, no dependent second load for the common gates).
+//   w0  = cls | p0 << 8 | p1 << 12 | q0 << 16 | q1 << 24, with p0/p1 the
+//         register positions of q0/q1 in the gate's phase (15: thread bit)
+//   aux = matrix-pool offset (dense and two-qubit diagonal gates) or the
+//         exponent k of GC_OMEGA
+//   c0, c1 = inline constants: (a, b) of GC_SU2, (d0, d1) of GC_DIAG1
+struct __align__(16) RegOp {
+    uint32_t w0, aux;
+    float2 c0, c1;
+    uint32_t pad[2];
 };
 
 // An event in engine order: (gate position << 3) | (slot << 2) | pauli code.
@@ -160,7 +176,7 @@ struct arso_circuit {
     arso::DeviceBuffer d_mats;              // complex<float> or complex<double> pool
     arso::DeviceBuffer d_loc_key;           // location -> (pos << 1) | slot
     arso::DeviceBuffer d_pass_of_pos;       // uint32 per engine position
-    arso::DeviceBuffer d_ph_gb, d_ph_R, d_rpos, d_phase_of_pos;
+    arso::DeviceBuffer d_ph_gb, d_ph_R, d_rops, d_phase_of_pos;
     // prefix cache
     bool cache_ready = false;
     uint64_t ckpt_every = 1;                // resident: gates between checkpoints

@@ -46,7 +46,7 @@ struct ResidentArgs {
     // register-blocked execution: checkpoints sit at phase boundaries
     uint32_t n_phases;
     const uint32_t *ph_gb, *ph_R;
-    const uint8_t *rpos;
+    const RegOp *rops;
     const uint32_t *phase_of_pos;  // gate position -> phase
 };
 
@@ -83,7 +83,7 @@ struct PassArgs {
     uint32_t pb, pe;             // phases of this pass
     const uint32_t *ph_gb;       // phase -> first engine position (with sentinel)
     const uint32_t *ph_R;        // phase -> packed register bits
-    const uint8_t *rpos;         // engine position -> register positions of q0 | q1 << 4
+    const RegOp *rops;           // engine position -> register-kernel gate record
 };
 
 void launch_pass_rb(const PassArgs &a, bool last, uint32_t slots, double bytes, cudaStream_t st);
@@ -97,7 +97,7 @@ struct BatchCircuit {
     const DGate *gates;
     const float2 *mats;
     const uint32_t *ph_gb, *ph_R, *phase_of_pos;
-    const uint8_t *rpos;
+    const RegOp *rops;
     const float2 *cache;
     const uint64_t *offsets;
     const uint32_t *keys;

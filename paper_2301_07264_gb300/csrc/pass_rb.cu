@@ -520,14 +520,15 @@ __device__ __forceinline__ void smem_dense2(float2 *sm, int t, uint32_t q0, uint
     }
 }
 
-__device__ __forceinline__ void apply_gate_rb(Amps &a, TileCtx &c, const DGate &g, uint8_t rp,
-                                              const float2 *__restrict__ mats, float2 *sm, float2 *ubuf, int t) {
-    const uint32_t p0 = rp & 15u, p1 = rp >> 4;
-    const float2 *M = mats + g.mat;
-    switch (g.cls) {
+__device__ __forceinline__ void apply_op(Amps &a, TileCtx &c, const RegOp &op, const float2 *__restrict__ mats,
+                                         float2 *sm, float2 *ubuf, int t) {
+    const uint32_t cls = op.w0 & 255u, p0 = (op.w0 >> 8) & 15u, p1 = (op.w0 >> 12) & 15u;
+    const uint32_t q0 = (op.w0 >> 16) & 255u, q1 = op.w0 >> 24;
+    const float2 *M = mats + op.aux;
+    switch (cls) {
         case GC_H: {
             // with the qubit's mask bit set: H X = Z H, so apply Z H and clear the bit
-            const uint32_t flip = (c.m >> g.q0) & 1u;
+            const uint32_t flip = (c.m >> q0) & 1u;
             switch (p0) {
                 case 0: rg_h_lanes(a, flip ? -1.f : 1.f); break;
                 case 1: rg_h<1>(a, flip); break;
@@ -535,12 +536,12 @@ __device__ __forceinline__ void apply_gate_rb(Amps &a, TileCtx &c, const DGate &
                 case 3: rg_h<3>(a, flip); break;
                 default: rg_h<4>(a, flip); break;
             }
-            c.m &= ~(1u << g.q0);
+            c.m &= ~(1u << q0);
             break;
         }
         case GC_DENSE1: {
             // with the qubit's mask bit set the stored data sees X U X = [[u11, u10], [u01, u00]]
-            const uint32_t flip = (c.m >> g.q0) & 1u;
+            const uint32_t flip = (c.m >> q0) & 1u;
             const float2 u00 = M[flip ? 3 : 0], u01 = M[flip ? 2 : 1];
             const float2 u10 = M[flip ? 1 : 2], u11 = M[flip ? 0 : 3];
             switch (p0) {
@@ -554,8 +555,9 @@ __device__ __forceinline__ void apply_gate_rb(Amps &a, TileCtx &c, const DGate &
         }
         case GC_SU2: {
             // X U X = [[conj a, -conj b], [b, a]]: the same form with (u11, u10)
-            const uint32_t flip = (c.m >> g.q0) & 1u;
-            const float2 ua = M[flip ? 3 : 0], ub = M[flip ? 2 : 1];
+            const uint32_t flip = (c.m >> q0) & 1u;
+            const float2 ua = flip ? make_float2(op.c0.x, -op.c0.y) : op.c0;
+            const float2 ub = flip ? make_float2(-op.c1.x, op.c1.y) : op.c1;
             switch (p0) {
                 case 0: rg_dense1_lanes(a, ua, ub, make_float2(-ub.x, ub.y), make_float2(ua.x, -ua.y)); break;
                 case 1: rg_su2<1>(a, ua, ub); break;
@@ -565,14 +567,14 @@ __device__ __forceinline__ void apply_gate_rb(Amps &a, TileCtx &c, const DGate &
             }
             break;
         }
-        case GC_DIAG1: rg_diag1(a, c, g.q0, p0, M[0], M[1]); break;
-        case GC_OMEGA: rg_omega(a, c, g.q0, p0, g.mat); break;
-        case GC_X: c.m ^= 1u << g.q0; break;
-        case GC_CZ: rg_cz(a, c, g.q0, g.q1, p0, p1); break;
-        case GC_DIAG2: rg_diag2(a, c, g.q0, g.q1, M); break;
+        case GC_DIAG1: rg_diag1(a, c, q0, p0, op.c0, op.c1); break;
+        case GC_OMEGA: rg_omega(a, c, q0, p0, op.aux); break;
+        case GC_X: c.m ^= 1u << q0; break;
+        case GC_CZ: rg_cz(a, c, q0, q1, p0, p1); break;
+        case GC_DIAG2: rg_diag2(a, c, q0, q1, M); break;
         case GC_CX: {
             // CX X^m = X^{m'} CX with m' = m ^ (target bit if the control bit is in m)
-            const uint32_t cth = (c.tpart >> g.q0) & 1u;
+            const uint32_t cth = (c.tpart >> q0) & 1u;
             switch (p1) {
                 case 0: rg_cx<0>(a, p0, cth); break;
                 case 1: rg_cx<1>(a, p0, cth); break;
@@ -580,16 +582,16 @@ __device__ __forceinline__ void apply_gate_rb(Amps &a, TileCtx &c, const DGate &
                 case 3: rg_cx<3>(a, p0, cth); break;
                 default: rg_cx<4>(a, p0, cth); break;
             }
-            if ((c.m >> g.q0) & 1u) c.m ^= 1u << g.q1;
+            if ((c.m >> q0) & 1u) c.m ^= 1u << q1;
             break;
         }
         case GC_DENSE2:
         case GC_SWAP: {
-            const uint32_t mab = ((c.m >> g.q0) & 1u) | (((c.m >> g.q1) & 1u) << 1);
+            const uint32_t mab = ((c.m >> q0) & 1u) | (((c.m >> q1) & 1u) << 1);
             if (c.tid < 16) {
                 const uint32_t k = c.tid >> 2, l = c.tid & 3u;
                 float2 u;
-                if (g.cls == GC_SWAP) {
+                if (cls == GC_SWAP) {
                     const uint32_t perm[4] = {0, 2, 1, 3};
                     u = make_float2(perm[k] == l ? 1.f : 0.f, 0.f);
                 } else {
@@ -600,37 +602,55 @@ __device__ __forceinline__ void apply_gate_rb(Amps &a, TileCtx &c, const DGate &
             __syncthreads();
             to_smem(a, sm, c, t);
             __syncthreads();
-            smem_dense2(sm, t, g.q0, g.q1, ubuf, c.tid, c.nthr);
+            smem_dense2(sm, t, q0, q1, ubuf, c.tid, c.nthr);
             __syncthreads();
             from_smem(a, sm, c, t);
             __syncthreads();
             // SWAP X^m = X^{m with bits q0, q1 exchanged} SWAP
-            if (g.cls == GC_SWAP && (((c.m >> g.q0) ^ (c.m >> g.q1)) & 1u)) c.m ^= (1u << g.q0) | (1u << g.q1);
+            if (cls == GC_SWAP && (((c.m >> q0) ^ (c.m >> q1)) & 1u)) c.m ^= (1u << q0) | (1u << q1);
             break;
         }
         default: break;
     }
 }
 
-// Gates [g, ge) of one phase with the Pauli events that fall inside them.
-// The inner loop runs up to and including the next event's gate without
-// touching the event state, which stays out of the hot registers.
-__device__ __forceinline__ void run_gates(Amps &v, TileCtx &c, uint32_t g, uint32_t ge, const DGate *__restrict__ gates,
-                                          const uint8_t *__restrict__ rpos, const float2 *__restrict__ mats,
-                                          float2 *sm, float2 *ubuf, int t, const uint32_t *&ev,
-                                          const uint32_t *ev_end, uint32_t &next) {
+// Gates [g, ge) of one phase with the Pauli events that fall inside them;
+// ops[0] is the record of gate g0 (the phase's first gate). The inner loop
+// runs up to and including the next event's gate without touching the event
+// state, which stays out of the hot registers.
+__device__ __forceinline__ void run_gates(Amps &v, TileCtx &c, uint32_t g, uint32_t ge, const RegOp *ops, uint32_t g0,
+                                          const float2 *__restrict__ mats, float2 *sm, float2 *ubuf, int t,
+                                          const uint32_t *&ev, const uint32_t *ev_end, uint32_t &next) {
     while (g < ge) {
         const uint32_t np = next == NO_EVENT ? ge : ev_pos(next);
         const uint32_t stop = np < ge ? np + 1 : ge;
-        for (; g < stop; ++g) apply_gate_rb(v, c, gates[g], rpos[g], mats, sm, ubuf, t);
+        for (; g < stop; ++g) apply_op(v, c, ops[g - g0], mats, sm, ubuf, t);
         if (np >= ge) break;
-        const DGate gate = gates[np];
+        const uint32_t w0 = ops[np - g0].w0;
         while (next != NO_EVENT && ev_pos(next) == np) {
-            rg_pauli(v, c, ev_slot(next) ? gate.q1 : gate.q0, ev_code(next));
+            rg_pauli(v, c, ev_slot(next) ? (w0 >> 24) : ((w0 >> 16) & 255u), ev_code(next));
             ++ev;
             next = ev < ev_end ? *ev : NO_EVENT;
         }
     }
+}
+
+// A phase's gate records are staged in shared memory: stage_ops starts
+// cp.async copies of the next phase's records (at most MAX_PHASE_OPS, 16 bytes
+// per copy) while the current phase runs; stage_wait waits for this thread's
+// copies and syncs the CTA, after which the staged records are visible to all
+// threads and the other buffer is free again.
+__device__ __forceinline__ void stage_ops(RegOp *dst, const RegOp *src, uint32_t n, uint32_t tid, uint32_t nthr) {
+    n = n < (uint32_t)MAX_PHASE_OPS ? n : (uint32_t)MAX_PHASE_OPS;
+    const char *s = reinterpret_cast<const char *>(src);
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    for (uint32_t i = tid; i < 2 * n; i += nthr)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d + 16 * i), "l"(s + 16 * i) : "memory");
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void stage_wait() {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
 }
 
 // global offset of the tile's first amplitude: the tile index deposited into
@@ -653,6 +673,7 @@ __global__ void __launch_bounds__(512, 1) pass_rb_kernel(PassArgs a) {
     float2 *sm = reinterpret_cast<float2 *>(smem_raw);
     __shared__ Partial red[32];
     __shared__ float2 ubuf[16];
+    __shared__ RegOp s_ops[2][MAX_PHASE_OPS];
     const int t = a.t;
     const uint32_t slot = blockIdx.y;
     const uint64_t N = 1ull << a.n;
@@ -704,10 +725,18 @@ __global__ void __launch_bounds__(512, 1) pass_rb_kernel(PassArgs a) {
 
     uint32_t next = ev < ev_end ? *ev : NO_EVENT;
     const float2 *mats = static_cast<const float2 *>(a.mats);
+    if (a.pb < a.pe)
+        stage_ops(s_ops[0], a.rops + a.ph_gb[a.pb], a.ph_gb[a.pb + 1] - a.ph_gb[a.pb], threadIdx.x, blockDim.x);
     for (uint32_t ph = a.pb; ph < a.pe; ++ph) {
+        const uint32_t buf = (ph - a.pb) & 1u;
+        stage_wait();
+        if (ph + 1 < a.pe)
+            stage_ops(s_ops[buf ^ 1u], a.rops + a.ph_gb[ph + 1], a.ph_gb[ph + 2] - a.ph_gb[ph + 1], threadIdx.x,
+                      blockDim.x);
         const uint32_t R = a.ph_R[ph];
         if (R != c.R) remap(v, sm, c, R, t);
-        run_gates(v, c, a.ph_gb[ph], a.ph_gb[ph + 1], a.gates, a.rpos, mats, sm, ubuf, t, ev, ev_end, next);
+        const uint32_t g0 = a.ph_gb[ph];
+        run_gates(v, c, g0, a.ph_gb[ph + 1], s_ops[buf], g0, mats, sm, ubuf, t, ev, ev_end, next);
     }
     apply_global_phase(v, c);  // global phase i^gp
     const uint64_t base = tile_base(a.rest_mask, blockIdx.x);
@@ -769,6 +798,7 @@ __global__ void __launch_bounds__(512, 1) resident_rb_kernel(ResidentArgs a) {
     float2 *sm = reinterpret_cast<float2 *>(smem_raw);
     __shared__ Partial red[32];
     __shared__ float2 ubuf[16];
+    __shared__ RegOp s_ops[2][MAX_PHASE_OPS];
     const int t = a.n;
     const uint32_t N = 1u << t;
     const float2 *cache = static_cast<const float2 *>(a.cache);
@@ -814,14 +844,22 @@ __global__ void __launch_bounds__(512, 1) resident_rb_kernel(ResidentArgs a) {
             ev_end = a.keys + a.offsets[tr + 1];
         }
         uint32_t next = ev && ev < ev_end ? *ev : NO_EVENT;
+        if (ph0 < a.n_phases)
+            stage_ops(s_ops[0], a.rops + a.ph_gb[ph0], a.ph_gb[ph0 + 1] - a.ph_gb[ph0], threadIdx.x, blockDim.x);
         for (uint32_t ph = ph0; ph < a.n_phases; ++ph) {
+            const uint32_t buf = (ph - ph0) & 1u;
+            stage_wait();
+            if (ph + 1 < a.n_phases)
+                stage_ops(s_ops[buf ^ 1u], a.rops + a.ph_gb[ph + 1], a.ph_gb[ph + 2] - a.ph_gb[ph + 1], threadIdx.x,
+                          blockDim.x);
             if (MODE == 2 && ph % (uint32_t)a.ckpt_every == 0) {
                 float2 *dst = const_cast<float2 *>(cache) + (size_t)(ph / (uint32_t)a.ckpt_every) * N;
                 rb_store_linear(v, sm, c, load_packed, dst, t);
             }
             const uint32_t R = a.ph_R[ph];
             if (R != c.R) remap(v, sm, c, R, t);
-            run_gates(v, c, a.ph_gb[ph], a.ph_gb[ph + 1], a.gates, a.rpos, mats, sm, ubuf, t, ev, ev_end, next);
+            const uint32_t g0 = a.ph_gb[ph];
+            run_gates(v, c, g0, a.ph_gb[ph + 1], s_ops[buf], g0, mats, sm, ubuf, t, ev, ev_end, next);
         }
         if (MODE == 2) {
             rb_store_linear(v, sm, c, load_packed, const_cast<float2 *>(cache) + (size_t)(a.n_ckpt - 1) * N,
@@ -883,6 +921,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2)
     __shared__ uint32_t s_item;
     __shared__ Partial red[BATCH_THREADS / 32];
     __shared__ float2 ubuf[8][16];
+    __shared__ RegOp s_ops[2][MAX_PHASE_OPS];
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_item = atomicAdd(counter, 1u);
@@ -909,10 +948,19 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2)
         const uint32_t *ev = C.keys + C.offsets[tr];
         const uint32_t *ev_end = C.keys + C.offsets[tr + 1];
         uint32_t next = ev < ev_end ? *ev : NO_EVENT;
-        for (uint32_t ph = it.ck * C.ckpt_every; ph < C.n_phases; ++ph) {
+        const uint32_t ph0 = it.ck * C.ckpt_every;
+        if (ph0 < C.n_phases)
+            stage_ops(s_ops[0], C.rops + C.ph_gb[ph0], C.ph_gb[ph0 + 1] - C.ph_gb[ph0], threadIdx.x, BATCH_THREADS);
+        for (uint32_t ph = ph0; ph < C.n_phases; ++ph) {
+            const uint32_t buf = (ph - ph0) & 1u;
+            stage_wait();
+            if (ph + 1 < C.n_phases)
+                stage_ops(s_ops[buf ^ 1u], C.rops + C.ph_gb[ph + 1], C.ph_gb[ph + 2] - C.ph_gb[ph + 1], threadIdx.x,
+                          BATCH_THREADS);
             const uint32_t R = C.ph_R[ph];
             if (R != c.R) remap(v, sm, c, R, t);
-            run_gates(v, c, C.ph_gb[ph], C.ph_gb[ph + 1], C.gates, C.rpos, C.mats, sm, ubuf[sg], t, ev, ev_end, next);
+            const uint32_t g0 = C.ph_gb[ph];
+            run_gates(v, c, g0, C.ph_gb[ph + 1], s_ops[buf], g0, C.mats, sm, ubuf[sg], t, ev, ev_end, next);
         }
         apply_global_phase(v, c);
         const float2 *ref = C.cache + (size_t)(C.n_ckpt - 1) * N;

@@ -85,6 +85,7 @@ def test_resident_circuits_plan_one_pass(arso):
 
 def test_phase_planner_counts(arso):
     # the list-scheduling planner: brickwork-24 at 13-qubit tiles needs at most
-    # 160 register-set phases for 1420 gates, Grover-12 at most 820 for 60,771
+    # 160 phases for 1420 gates; Grover-12's 60,771 gates need at least
+    # ceil(60,771 / 64) phases of at most 64 gates, and at most 1,310
     assert arso.plan_phases(24, C.brickwork24(0).gates, tile_qubits=13) <= 160
-    assert arso.plan_phases(12, C.grover12(0).gates) <= 820
+    assert 950 <= arso.plan_phases(12, C.grover12(0).gates) <= 1310
