@@ -358,6 +358,11 @@ arso_status arso_score_state_noalloc(uint32_t n_qubits, const void *amps, const 
  * around every kernel launch and accumulates, per kernel family, the number
  * of launches, their summed device time and the algorithmic bytes they move
  * (the reads and writes the algorithm requires, not cache-level traffic).
+ * Streaming passes also count algorithmic flops: per amplitude and gate, 14
+ * for a dense one-qubit gate (2x2 complex matrix-vector product), 30 for a
+ * dense two-qubit gate, 6 for a diagonal gate, 4 for H, 2 for an odd power
+ * of the T phase and 0 for permutations and sign flips (X, CX, SWAP, CZ, Z,
+ * S), times the amplitudes each launch sweeps.
  * Launch and host<->device transfer counters run whether or not timing is
  * enabled. Process-wide, thread-safe; reading resolves pending events. */
 enum {
@@ -373,6 +378,8 @@ typedef struct {
     uint64_t launches;
     double ms;              /* summed device time (timing enabled only) */
     double bytes;           /* summed algorithmic bytes (timing enabled only) */
+    double flops;           /* summed algorithmic FP32 flops of the register-blocked streaming
+                               passes (timing enabled only; 0 for other kernels) */
 } arso_kernel_stats;
 arso_status arso_profile_enable(int on);
 arso_status arso_profile_reset(void);

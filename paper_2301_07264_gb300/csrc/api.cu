@@ -201,9 +201,11 @@ static void launch_resident_any(const arso_circuit *c, const ResidentArgs &a, in
     else launch_resident(a, mode == 2, c->precision, bytes, st);
 }
 
-// streaming pass launch: register-blocked kernel when the schedule has phases
-static void run_pass(const arso_circuit *c, const PassArgs &a, bool last, uint32_t slots, double bytes,
+// streaming pass launch: register-blocked kernel when the schedule has phases.
+// sweeps = how many states the launch reads and writes once (active slots).
+static void run_pass(const arso_circuit *c, const PassArgs &a, bool last, uint32_t slots, double sweeps,
                      cudaStream_t st) {
+    const double bytes = 2.0 * (double)c->state_bytes() * sweeps;
     if (c->reg_blocked) {
         PassArgs b = a;
         b.pb = c->passes[a.pass].pb;
@@ -211,7 +213,7 @@ static void run_pass(const arso_circuit *c, const PassArgs &a, bool last, uint32
         b.ph_gb = c->d_ph_gb.as<uint32_t>();
         b.ph_R = c->d_ph_R.as<uint32_t>();
         b.rops = c->d_rops.as<RegOp>();
-        launch_pass_rb(b, last, slots, bytes, st);
+        launch_pass_rb(b, last, slots, bytes, st, c->passes[a.pass].flops_per_amp * std::ldexp(sweeps, (int)c->n));
     } else {
         launch_pass(a, last, c->precision, slots, bytes, st);
     }
@@ -262,7 +264,7 @@ static void ensure_cache(arso_circuit *c, cudaStream_t st) {
             a.ideal = 1;
             a.ideal_src = c->ckpt_pass[j] != NO_EVENT ? base + (size_t)c->ckpt_pass[j] * sb : work.ptr;
             a.ideal_dst = c->ckpt_pass[j + 1] != NO_EVENT ? base + (size_t)c->ckpt_pass[j + 1] * sb : work.ptr;
-            run_pass(c, a, false, 1, 2.0 * sb, st);
+            run_pass(c, a, false, 1, 1.0, st);
         }
     }
     ARSO_CUDA(cudaStreamSynchronize(st));
@@ -446,15 +448,19 @@ static void run_streaming(arso_circuit *c, const arso_error_list *e, const std::
         h2d(d_slot_traj.ptr, st_traj, st);
         h2d(d_start.ptr, st_start, st);
         h2d(d_end.ptr, st_end, st);
-        double batch_bytes = 0;
+        double batch_bytes = 0, batch_flops = 0;
         for (uint32_t j = (uint32_t)jmin; j <= (uint32_t)jmax; ++j)
-            for (size_t i = 0; i < nb; ++i) batch_bytes += (st_start[i] <= (int)j && (int)j <= st_end[i]) ? 2.0 * sb : 0.0;
+            for (size_t i = 0; i < nb; ++i)
+                if (st_start[i] <= (int)j && (int)j <= st_end[i]) {
+                    batch_bytes += 2.0 * sb;
+                    batch_flops += c->reg_blocked ? c->passes[j].flops_per_amp * std::ldexp(1.0, (int)c->n) : 0.0;
+                }
         const uint64_t n_launch = (uint64_t)(jmax - jmin + 1) + (states_out ? 0 : 1);
         const GraphKey key{jmin, jmax, (uint32_t)nb};
         auto hit = graphs.find(key);
         if (hit != graphs.end()) {  // replay: the slot tables above are the only inputs that changed
             {
-                ProfScope ps_(ARSO_K_PASS, batch_bytes, st);
+                ProfScope ps_(ARSO_K_PASS, batch_bytes, st, batch_flops);
                 ARSO_CUDA(cudaGraphLaunch(hit->second, st));
             }
             prof_add_launches(ARSO_K_PASS, n_launch - 1);
@@ -478,7 +484,7 @@ static void run_streaming(arso_circuit *c, const arso_error_list *e, const std::
             a.store_last = states_out ? 1 : 0;
             uint32_t active = 0;
             for (size_t i = 0; i < nb; ++i) active += st_start[i] <= (int)j && (int)j <= st_end[i];
-            run_pass(c, a, j == P - 1, (uint32_t)nb, 2.0 * (double)sb * active, st);
+            run_pass(c, a, j == P - 1, (uint32_t)nb, (double)active, st);
         }
         if (!states_out)
             launch_finish_partials(parts.as<Partial>(), tiles, (uint32_t)nb, d_slot_traj.as<uint64_t>(), crit, d_score,
@@ -487,7 +493,7 @@ static void run_streaming(arso_circuit *c, const arso_error_list *e, const std::
             cudaGraphExec_t ex = capture.finish();
             graphs[key] = ex;
             {
-                ProfScope ps_(ARSO_K_PASS, batch_bytes, st);
+                ProfScope ps_(ARSO_K_PASS, batch_bytes, st, batch_flops);
                 ARSO_CUDA(cudaGraphLaunch(ex, st));
             }
             prof_add_launches(ARSO_K_PASS, n_launch - 1);

@@ -218,6 +218,18 @@ struct PassScheduler {
 };
 }  // namespace
 
+// algorithmic FP32 flops per amplitude of one gate (see the tracing section of arso.h)
+static double gate_flops(const HostGate &h) {
+    switch (h.cls) {
+        case GC_DENSE1: return 14.0;
+        case GC_DENSE2: return 30.0;
+        case GC_DIAG1: case GC_DIAG2: return 6.0;
+        case GC_H: return 4.0;
+        case GC_OMEGA: return (h.omega_k & 1u) ? 2.0 : 0.0;
+        default: return 0.0;
+    }
+}
+
 static void plan_phases(arso_circuit *c) {
     const uint32_t t = c->tile_qubits;
     c->reg_blocked = c->precision == ARSO_C64 && t >= (uint32_t)RB_MIN_TILE;
@@ -314,6 +326,10 @@ static void plan_phases(arso_circuit *c) {
                 c->rpos[pos] = (uint8_t)(p0 | (p1 << 4));
             }
         }
+    }
+    for (Pass &ps : c->passes) {
+        ps.flops_per_amp = 0.0;
+        for (uint32_t pos = ps.gb; pos < ps.ge; ++pos) ps.flops_per_amp += gate_flops(c->gates[c->perm[pos]]);
     }
     c->ph_gb.push_back(c->passes.empty() ? 0 : c->passes.back().ge);  // sentinel
     c->phase_of_pos.assign(c->perm.size(), 0);

@@ -121,6 +121,7 @@ struct Pass {
     uint32_t gb, ge;                   // gate range in engine order
     std::vector<uint32_t> tile_qubits; // sorted global qubits, tile-local bit i -> tile_qubits[i]
     uint32_t pb = 0, pe = 0;           // register-blocked phases [pb, pe)
+    double flops_per_amp = 0.0;        // algorithmic FP32 flops per amplitude of one sweep
 };
 
 struct Criterion {

@@ -86,7 +86,7 @@ struct PassArgs {
     const RegOp *rops;           // engine position -> register-kernel gate record
 };
 
-void launch_pass_rb(const PassArgs &a, bool last, uint32_t slots, double bytes, cudaStream_t st);
+void launch_pass_rb(const PassArgs &a, bool last, uint32_t slots, double bytes, cudaStream_t st, double flops = 0.0);
 void prepare_pass_rb();
 
 // Batched resident execution: one persistent launch over (circuit, trajectory

@@ -481,8 +481,11 @@ __device__ __forceinline__ void from_smem(Amps &a, const float2 *sm, const TileC
     }
 }
 
+// SYNCED: the caller has just synced the CTA after the last shared-memory
+// read (a phase start), so the first barrier is not needed.
+template <bool SYNCED = false>
 __device__ __forceinline__ void remap(Amps &a, float2 *sm, TileCtx &c, uint32_t packed, int t) {
-    __syncthreads();
+    if (!SYNCED) __syncthreads();
     to_smem(a, sm, c, t);
     set_phase(c, packed, t);
     __syncthreads();
@@ -734,7 +737,7 @@ __global__ void __launch_bounds__(512, 1) pass_rb_kernel(PassArgs a) {
             stage_ops(s_ops[buf ^ 1u], a.rops + a.ph_gb[ph + 1], a.ph_gb[ph + 2] - a.ph_gb[ph + 1], threadIdx.x,
                       blockDim.x);
         const uint32_t R = a.ph_R[ph];
-        if (R != c.R) remap(v, sm, c, R, t);
+        if (R != c.R) remap<true>(v, sm, c, R, t);
         const uint32_t g0 = a.ph_gb[ph];
         run_gates(v, c, g0, a.ph_gb[ph + 1], s_ops[buf], g0, mats, sm, ubuf, t, ev, ev_end, next);
     }
@@ -857,7 +860,7 @@ __global__ void __launch_bounds__(512, 1) resident_rb_kernel(ResidentArgs a) {
                 rb_store_linear(v, sm, c, load_packed, dst, t);
             }
             const uint32_t R = a.ph_R[ph];
-            if (R != c.R) remap(v, sm, c, R, t);
+            if (R != c.R) remap<MODE != 2>(v, sm, c, R, t);
             const uint32_t g0 = a.ph_gb[ph];
             run_gates(v, c, g0, a.ph_gb[ph + 1], s_ops[buf], g0, mats, sm, ubuf, t, ev, ev_end, next);
         }
@@ -958,7 +961,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2)
                 stage_ops(s_ops[buf ^ 1u], C.rops + C.ph_gb[ph + 1], C.ph_gb[ph + 2] - C.ph_gb[ph + 1], threadIdx.x,
                           BATCH_THREADS);
             const uint32_t R = C.ph_R[ph];
-            if (R != c.R) remap(v, sm, c, R, t);
+            if (R != c.R) remap<true>(v, sm, c, R, t);
             const uint32_t g0 = C.ph_gb[ph];
             run_gates(v, c, g0, C.ph_gb[ph + 1], s_ops[buf], g0, C.mats, sm, ubuf[sg], t, ev, ev_end, next);
         }
@@ -1024,8 +1027,8 @@ void prepare_pass_rb() {
     done = true;
 }
 
-void launch_pass_rb(const PassArgs &a, bool last, uint32_t slots, double bytes, cudaStream_t st) {
-    ProfScope ps_(last && !a.store_last ? ARSO_K_PASS_LAST : ARSO_K_PASS, bytes, st);
+void launch_pass_rb(const PassArgs &a, bool last, uint32_t slots, double bytes, cudaStream_t st, double flops) {
+    ProfScope ps_(last && !a.store_last ? ARSO_K_PASS_LAST : ARSO_K_PASS, bytes, st, flops);
     prepare_pass_rb();
     const uint32_t tiles = 1u << (a.n - a.t);
     const int nt = 1 << (a.t - REG_BITS);

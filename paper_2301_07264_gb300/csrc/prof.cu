@@ -11,7 +11,7 @@ namespace arso {
 namespace {
 struct Pending {
     int kind;
-    double bytes;
+    double bytes, flops;
     cudaEvent_t a, b;
 };
 struct State {
@@ -48,6 +48,7 @@ void resolve(State &s) {
         if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
             s.stats[p.kind].ms += ms;
             s.stats[p.kind].bytes += p.bytes;
+            s.stats[p.kind].flops += p.flops;
         } else {
             cudaGetLastError();
         }
@@ -70,13 +71,13 @@ void prof_begin(int kind, double, cudaStream_t st, cudaEvent_t *ev_out) {
     if (e && cudaEventRecord(e, st) == cudaSuccess) *ev_out = e;
 }
 
-void prof_end(int kind, double bytes, cudaStream_t st, cudaEvent_t start) {
+void prof_end(int kind, double bytes, cudaStream_t st, cudaEvent_t start, double flops) {
     if (!start) return;
     State &s = state();
     std::lock_guard<std::mutex> lk(s.mu);
     cudaEvent_t e = take_event(s);
     if (e && cudaEventRecord(e, st) == cudaSuccess) {
-        s.pending.push_back(Pending{kind, bytes, start, e});
+        s.pending.push_back(Pending{kind, bytes, flops, start, e});
         if (s.pending.size() > 4096) resolve(s);
     } else {
         s.free_events.push_back(start);
