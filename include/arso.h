@@ -264,7 +264,14 @@ typedef struct {
     const arso_surrogate *surrogate; /* NULL = plain search */
     const float *features;  /* surrogate inputs for this circuit (32 floats), with `surrogate` */
     double surrogate_margin;/* verify bracket half-width in log10 p (default 0.15) */
+    uint32_t flags;         /* ARSO_SEARCH_NO_REUSE: simulate every trajectory of every probe */
 } arso_search_opts;
+/* Probes of one search draw the same random numbers, so the error sets of a
+ * trajectory are nested in p; a trajectory with as many events at p as at an
+ * earlier probe has the same events and its score is reused (exact). The
+ * reuse applies to the register-blocked resident engine and the streaming
+ * engine. */
+#define ARSO_SEARCH_NO_REUSE 1u
 typedef struct {
     double p, lo, hi, value_lo, value_hi;
     uint32_t probes;        /* plain-simulator probes */

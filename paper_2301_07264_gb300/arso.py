@@ -73,7 +73,8 @@ class Result(C.Structure):
 class SearchOpts(C.Structure):
     _fields_ = [("p_lo", C.c_double), ("p_hi", C.c_double), ("rel_tol", C.c_double), ("n_traj", C.c_uint64),
                 ("seed", C.c_uint64), ("max_probes", C.c_uint32), ("mode", C.c_uint32),
-                ("surrogate", C.c_void_p), ("features", C.POINTER(C.c_float)), ("surrogate_margin", C.c_double)]
+                ("surrogate", C.c_void_p), ("features", C.POINTER(C.c_float)), ("surrogate_margin", C.c_double),
+                ("flags", C.c_uint32)]
 
 
 class RateResult(C.Structure):
@@ -335,10 +336,14 @@ def success_prob(circ, crit, p, mode="auto", n_traj=1000, seed=0, stream=None) -
     return r
 
 
+SEARCH_NO_REUSE = 1
+
+
 def tolerable_rate(circ, crit, P_target, p_lo=0.0, p_hi=0.0, rel_tol=0.0, n_traj=0, seed=0, max_probes=0,
-                   mode="auto", stream=None, check=True) -> RateResult:
+                   mode="auto", stream=None, check=True, reuse=True) -> RateResult:
     c = crit if isinstance(crit, Criterion) else make_criterion(crit)
-    o = SearchOpts(p_lo, p_hi, rel_tol, n_traj, seed, max_probes, MODE[mode], None, None, 0.0)
+    o = SearchOpts(p_lo, p_hi, rel_tol, n_traj, seed, max_probes, MODE[mode], None, None, 0.0,
+                   0 if reuse else SEARCH_NO_REUSE)
     r = RateResult()
     st = lib.arso_tolerable_rate(circ.handle, C.byref(c), P_target, C.byref(o), _stream(stream), C.byref(r))
     if check:
@@ -452,9 +457,10 @@ def surrogate_grads(s, x, y, stream=None):
 
 
 def tolerable_rate_surrogate(circ, crit, P_target, surrogate, p_lo=0.0, p_hi=0.0, n_traj=0, seed=0, margin=0.0,
-                             rel_tol=0.0, max_probes=0, stream=None) -> RateResult:
+                             rel_tol=0.0, max_probes=0, stream=None, reuse=True) -> RateResult:
     c = crit if isinstance(crit, Criterion) else make_criterion(crit)
-    o = SearchOpts(p_lo, p_hi, rel_tol, n_traj, seed, max_probes, MODE["mc"], surrogate.handle, None, margin)
+    o = SearchOpts(p_lo, p_hi, rel_tol, n_traj, seed, max_probes, MODE["mc"], surrogate.handle, None, margin,
+                   0 if reuse else SEARCH_NO_REUSE)
     r = RateResult()
     _check(lib.arso_tolerable_rate_surrogate(circ.handle, C.byref(c), P_target, C.byref(o), _stream(stream),
                                              C.byref(r)))

@@ -651,6 +651,120 @@ static McOut mc_run(arso_circuit *c, const DevCrit &dc, double p, uint64_t n_tra
     return o;
 }
 
+// Probes of one search share (seed, n_traj) and draw the same random numbers:
+// a trajectory's error set at p is contained in its set at any p' > p (the
+// error test compares one draw with a threshold increasing in p, and with
+// p_X = p_Z = p_Y the type cut points do not depend on p). So a trajectory
+// with as many events at p as at an earlier probe has exactly that probe's
+// events, and its score there is reused; only the others are simulated.
+struct ProbeMemo {
+    struct Rec {
+        double p;
+        std::vector<uint32_t> count;
+        std::vector<double> score;
+        std::vector<uint8_t> pass;
+    };
+    std::vector<Rec> recs;
+    bool enabled = true;
+};
+
+static bool memo_supported(const arso_circuit *c) { return c->engine == 1 || c->reg_blocked; }
+
+static McOut mc_run_memo(arso_circuit *c, const DevCrit &dc, double p, uint64_t n_traj, uint64_t seed, cudaStream_t st,
+                         ProbeMemo *memo) {
+    if (!memo || !memo->enabled || !memo_supported(c) || n_traj == 0) return mc_run(c, dc, p, n_traj, seed, st);
+    arso_error_list *raw = nullptr;
+    sample(c, p / 3, p / 3, p / 3, seed, 0, n_traj, st, &raw);
+    std::unique_ptr<arso_error_list> e(raw);
+    ensure_cache(c, st);
+    std::vector<uint64_t> off(n_traj + 1);
+    copy_d2h(off.data(), e->d_offsets.ptr, (n_traj + 1) * 8, st);
+    Scratch ref(st, sizeof(double));
+    score_into(ref_state_ptr(c), ref_state_ptr(c), (int)c->n, c->precision, dc.d, ref.as<double>(), st);
+    double ref_h = 0.0;
+    copy_d2h(&ref_h, ref.ptr, 8, st);
+    ARSO_CUDA(cudaStreamSynchronize(st));
+    ProbeMemo::Rec rec;
+    rec.p = p;
+    rec.count.resize(n_traj);
+    rec.score.resize(n_traj);
+    rec.pass.resize(n_traj);
+    // the nearest earlier probes below and above p
+    const ProbeMemo::Rec *below = nullptr, *above = nullptr;
+    for (const ProbeMemo::Rec &r : memo->recs) {
+        if (r.count.size() != n_traj) continue;
+        if (r.p <= p && (!below || r.p > below->p)) below = &r;
+        if (r.p >= p && (!above || r.p < above->p)) above = &r;
+    }
+    std::vector<uint64_t> ids;
+    for (uint64_t t = 0; t < n_traj; ++t) {
+        const uint32_t k = (uint32_t)(off[t + 1] - off[t]);
+        rec.count[t] = k;
+        const ProbeMemo::Rec *from = nullptr;
+        if (k == 0) {
+            rec.score[t] = ref_h;
+            rec.pass[t] = ref_h >= dc.d.threshold;
+            continue;
+        }
+        if (below && below->count[t] == k) from = below;
+        else if (above && above->count[t] == k) from = above;
+        if (from) {
+            rec.score[t] = from->score[t];
+            rec.pass[t] = from->pass[t];
+        } else {
+            ids.push_back(t);
+        }
+    }
+    if (!ids.empty()) {
+        Scratch sc(st, n_traj * 8), pf(st, n_traj);
+        if (c->engine == 0) {
+            Scratch d_ids(st, ids.size() * 8);
+            copy_h2d(d_ids.ptr, ids.data(), ids.size() * 8, st);
+            ResidentArgs a = resident_args(c);
+            a.first_traj = 0;
+            a.count = ids.size();
+            a.ids = d_ids.as<uint64_t>();
+            a.offsets = e->d_offsets.as<uint64_t>();
+            a.keys = e->d_key.as<uint32_t>();
+            a.first = e->d_first.as<uint32_t>();
+            a.crit = dc.d;
+            a.ref_score = ref.as<double>();
+            a.score = sc.as<double>();
+            a.pass_flags = pf.as<uint8_t>();
+            launch_resident_rb(a, 0, (double)ids.size() * c->state_bytes(), st);
+        } else {
+            std::vector<uint32_t> first(n_traj), last(n_traj), fp, lp;
+            copy_d2h(first.data(), e->d_first.ptr, n_traj * 4, st);
+            copy_d2h(last.data(), e->d_last.ptr, n_traj * 4, st);
+            ARSO_CUDA(cudaStreamSynchronize(st));
+            for (uint64_t t : ids) fp.push_back(first[t]), lp.push_back(last[t]);
+            run_streaming(c, e.get(), ids, fp, lp, dc.d, sc.as<double>(), pf.as<uint8_t>(), nullptr, st);
+        }
+        std::vector<double> sh(n_traj);
+        std::vector<uint8_t> ph(n_traj);
+        copy_d2h(sh.data(), sc.ptr, n_traj * 8, st);
+        copy_d2h(ph.data(), pf.ptr, n_traj, st);
+        ARSO_CUDA(cudaStreamSynchronize(st));
+        for (uint64_t t : ids) rec.score[t] = sh[t], rec.pass[t] = ph[t];
+    }
+    double s1 = 0.0, s2 = 0.0, np = 0.0;
+    for (uint64_t t = 0; t < n_traj; ++t) {
+        s1 += rec.score[t];
+        s2 += rec.score[t] * rec.score[t];
+        np += rec.pass[t];
+    }
+    memo->recs.push_back(std::move(rec));
+    McOut o{};
+    const double N = (double)n_traj;
+    o.mean = s1 / N;
+    o.pass_frac = np / N;
+    const double var_s = n_traj > 1 ? std::max(0.0, (s2 - s1 * s1 / N) / (N - 1)) : 0.0;
+    const double var_p = n_traj > 1 ? std::max(0.0, (np - np * np / N) / (N - 1)) : 0.0;
+    o.sd_mean = std::sqrt(var_s / N);
+    o.sd_pass = std::sqrt(var_p / N);
+    return o;
+}
+
 // Exhaustive single-error analysis: values per location and per type
 // (Eq. (3)); P[4] = {P_R, P_X, P_Z, P_Y} for the given aggregate.
 static void exhaustive(arso_circuit *c, const DevCrit &dc, cudaStream_t st, double *P, std::vector<double> *per_loc_mean,
@@ -1180,8 +1294,10 @@ arso_status arso_tolerable_rate(const arso_circuit *cc, const arso_criterion *cr
             }
         }
         out->mode_used = 1;
+        ProbeMemo memo;
+        memo.enabled = !(o.flags & ARSO_SEARCH_NO_REUSE);
         auto f = [&](double p) {
-            const McOut m = mc_run(c, dc, p, nt, o.seed, st);
+            const McOut m = mc_run_memo(c, dc, p, nt, o.seed, st, &memo);
             ++out->probes;
             return dc.aggregate == ARSO_AGG_MEAN ? m.mean : m.pass_frac;
         };
@@ -1257,8 +1373,10 @@ arso_status arso_tolerable_rate_surrogate(const arso_circuit *cc, const arso_cri
             lp_s = a + (b - a) * ((i0 - 1) + fr) / (K - 1);
         }
         // 2. verify the bracket with plain trajectories (common random numbers)
+        ProbeMemo memo;
+        memo.enabled = !(opts->flags & ARSO_SEARCH_NO_REUSE);
         auto probe = [&](double p) {
-            const McOut m = mc_run(c, dc, p, nt, opts->seed, st);
+            const McOut m = mc_run_memo(c, dc, p, nt, opts->seed, st, &memo);
             ++out->probes;
             return m.pass_frac;
         };

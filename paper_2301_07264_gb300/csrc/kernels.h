@@ -33,8 +33,10 @@ struct ResidentArgs {
     const void *cache;           // n_ckpt states; entry c = after gates [0, c*every); last = psi_R
     uint64_t ckpt_every;
     uint32_t n_ckpt;
-    // trajectories [first_traj, first_traj + count) of the error list
+    // trajectories [first_traj, first_traj + count) of the error list, or, with
+    // ids (register-blocked kernel only), the trajectories ids[0 .. count)
     uint64_t first_traj, count;
+    const uint64_t *ids;
     const uint64_t *offsets;
     const uint32_t *keys;
     const uint32_t *first;       // per trajectory: engine position of the first event or NO_EVENT

@@ -825,7 +825,7 @@ __global__ void __launch_bounds__(512, 1) resident_rb_kernel(ResidentArgs a) {
             for (int k = 0; k < 16; ++k) v.re[k] = v.im[k] = make_float2(0.f, 0.f);
             if (threadIdx.x == 0) v.re[0].x = 1.f;
         } else {
-            tr = a.first_traj + b;
+            tr = a.ids ? a.ids[b] : a.first_traj + b;
             const uint32_t first = a.first[tr];
             if (MODE == 0 && first == NO_EVENT) {
                 if (threadIdx.x == 0) {

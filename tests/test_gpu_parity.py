@@ -469,3 +469,29 @@ def test_autotune_returns_a_measured_candidate(arso):
     assert 10 <= best["tile_qubits"] <= 14 and 3 <= best["low_qubits"] <= 5
     k = (best["tile_qubits"] - 10) * 3 + (best["low_qubits"] - 3)
     assert ms[k] == ms.min()
+
+
+@pytest.mark.parametrize("n,depth", [(12, 20), (14, 12)])
+def test_search_probe_reuse_is_exact(arso, n, depth):
+    # probes of one search share their random numbers, so a trajectory with as
+    # many events as at an earlier probe has the same events: reusing its score
+    # must give exactly the search that simulates every trajectory (12 qubits:
+    # resident engine, 14: streaming engine), with fewer amplitudes swept
+    circ = C.brickwork(n, depth, 11)
+    crit = C.Criterion("fidelity", threshold=0.9, aggregate="pass")
+    cc = arso.compile_circuit(circ.n, circ.gates)
+    kw = dict(n_traj=2000, seed=5, mode="mc", rel_tol=0.05, p_lo=1e-5, p_hi=1e-1)
+    swept = {}
+    res = {}
+    for reuse in (False, True):
+        arso.profile_reset()
+        arso.profile_enable(True)
+        res[reuse] = arso.tolerable_rate(cc, crit, 2 / 3, reuse=reuse, **kw)
+        arso.profile_enable(False)
+        swept[reuse] = sum(arso.profile_read(k).bytes for k in (arso.K_PASS, arso.K_PASS_LAST, arso.K_RESIDENT))
+    a, b = res[False], res[True]
+    assert a.converged and b.converged
+    assert a.probes == b.probes and a.lo == b.lo and a.hi == b.hi
+    assert a.value_lo == b.value_lo and a.value_hi == b.value_hi
+    assert abs(a.p - b.p) <= 1e-12 * a.p
+    assert swept[True] < 0.8 * swept[False]
