@@ -349,7 +349,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--traj-per-step", type=int, default=1000)
+    ap.add_argument("--traj-per-step", type=int, default=None,
+                    help="default 1000 (brickwork24), 4096 (grover12: 256 per rate, several waves of the "
+                         "persistent launch)")
     ap.add_argument("--tile", type=int, default=0, help="tile qubits (0 = library default)")
     ap.add_argument("--cache-gb", type=float, default=0.0, help="prefix-cache budget (0 = library default)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -361,6 +363,8 @@ def main():
     ap.add_argument("--search-circuits", type=int, default=8)
     ap.add_argument("--train-rows", type=int, default=2_000_000)
     args = ap.parse_args()
+    if args.traj_per_step is None:
+        args.traj_per_step = 4096 if args.workload == "grover12" else 1000
     if args.impl == "reference":
         return run_reference(args)
     if args.workload != "brickwork24":
