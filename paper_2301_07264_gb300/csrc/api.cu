@@ -68,6 +68,38 @@ template <typename T> static void h2d(void *dst, const std::vector<T> &v, cudaSt
 }
 
 // ------------------------------------------------------------ upload -------
+// op code and mask-adjustment fields of a register-kernel gate record
+static uint32_t reg_opcode(uint32_t cls, uint32_t p0, uint32_t p1) {
+    auto enc = [](uint32_t opc, uint32_t sa, uint32_t sb, uint32_t xa, uint32_t xb) {
+        return opc | sa << 8 | sb << 10 | xa << 12 | xb << 13;
+    };
+    const uint32_t R = (uint32_t)REG_BITS;
+    switch (cls) {
+        case GC_SU2: return enc(OP_SU2 + p0, 0, 0, 0, 0);
+        case GC_DENSE1: return enc(OP_DENSE1 + p0, 0, 0, 0, 0);
+        case GC_H: return enc(OP_H + 2 * p0, 1, 0, 0, 0);  // + flip = bit q0 of m
+        case GC_CZ: {
+            if (p0 < R && p1 < R) {
+                const uint32_t lo = std::min(p0, p1), hi = std::max(p0, p1);
+                const uint32_t pp = lo == 0 ? hi - 1 : lo == 1 ? hi + 2 : lo == 2 ? hi + 4 : 9;
+                // want = 1 ^ mask bit; the lower position carries weight 2
+                return p0 < p1 ? enc(OP_CZ_RR + 4 * pp, 2, 1, 1, 1) : enc(OP_CZ_RR + 4 * pp, 1, 2, 1, 1);
+            }
+            if (p0 < R) return enc(OP_CZ_RT + 2 * p0, 1, 0, 1, 0);
+            if (p1 < R) return enc(OP_CZ_RT + 2 * p1, 0, 1, 0, 1);
+            return enc(OP_CZ_TT, 0, 0, 0, 0);
+        }
+        case GC_X: return enc(OP_X, 0, 0, 0, 0);
+        case GC_OMEGA: return enc(OP_OMEGA, 0, 0, 0, 0);
+        case GC_DIAG1: return enc(OP_DIAG1, 0, 0, 0, 0);
+        case GC_DIAG2: return enc(OP_DIAG2, 0, 0, 0, 0);
+        case GC_CX: return enc(OP_CX + std::min(p1, R - 1), 0, 0, 0, 0);
+        case GC_DENSE2: return enc(OP_DENSE2, 0, 0, 0, 0);
+        case GC_SWAP: return enc(OP_SWAP, 0, 0, 0, 0);
+        default: return enc(OP_NOP, 0, 0, 0, 0);
+    }
+}
+
 static void upload_circuit(arso_circuit *c) {
     const size_t G = c->gates.size();
     std::vector<DGate> dg(std::max<size_t>(G, 1));
@@ -159,6 +191,7 @@ static void upload_circuit(arso_circuit *c) {
                    (uint32_t)d.q0 << 16 | (uint32_t)d.q1 << 24;
             o.aux = d.mat;
             const HostGate &h = c->gates[c->perm[pos]];
+            o.pad[0] = reg_opcode(d.cls, c->rpos[pos] & 15u, c->rpos[pos] >> 4);
             if (d.cls == GC_SU2) {
                 o.c0 = make_float2((float)h.m[0].real(), (float)h.m[0].imag());
                 o.c1 = make_float2((float)h.m[1].real(), (float)h.m[1].imag());

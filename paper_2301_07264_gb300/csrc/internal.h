@@ -95,6 +95,28 @@ struct __align__(16) RegOp {
     uint32_t pad[2];
 };
 
+// Register-kernel op codes (RegOp::pad[0] bits 0-7): the gate class with its
+// register positions resolved on the host, so the kernel dispatches once.
+// Mask-dependent variants follow their base code: the kernel adds
+// sa * (bit q0 of m ^ xa) + sb * (bit q1 of m ^ xb), with sa (bits 8-9),
+// sb (bits 10-11), xa (bit 12), xb (bit 13) of pad[0].
+enum RegOpCode : uint32_t {
+    OP_SU2 = 0,      // + register position 0..4 (0: the packed lanes)
+    OP_DENSE1 = 5,   // + position
+    OP_H = 10,       // + 2 * position + mask bit of q0
+    OP_CZ_RR = 20,   // + 4 * pair index of (lower, higher) position + 2 * want(lower) + want(higher)
+    OP_CZ_RT = 60,   // + 2 * register position + want(register qubit); the other qubit is a thread bit
+    OP_CZ_TT = 70,   // both qubits thread bits
+    OP_X = 71,
+    OP_OMEGA = 72,
+    OP_DIAG1 = 73,
+    OP_DIAG2 = 74,
+    OP_CX = 75,      // + target position
+    OP_DENSE2 = 80,
+    OP_SWAP = 81,
+    OP_NOP = 82,
+};
+
 // An event in engine order: (gate position << 3) | (slot << 2) | pauli code.
 __host__ __device__ inline uint32_t ev_pos(uint32_t e) { return e >> 3; }
 __host__ __device__ inline uint32_t ev_slot(uint32_t e) { return (e >> 2) & 1u; }

@@ -523,78 +523,89 @@ __device__ __forceinline__ void smem_dense2(float2 *sm, int t, uint32_t q0, uint
     }
 }
 
+// One dispatch per gate: the host resolved class and register positions into
+// an op code; the mask-dependent variants (H on a flipped qubit, the CZ sign
+// pattern) are selected by adding the relevant mask bits.
+#define ARSO_CASE_P(BASE, CALL) \
+    case BASE + 1: CALL(1); break; \
+    case BASE + 2: CALL(2); break; \
+    case BASE + 3: CALL(3); break; \
+    case BASE + 4: CALL(4); break;
+#define ARSO_CZ_CASE(i) case OP_CZ_RR + (i): cz_case<(i)>(a); break;
+#define ARSO_CZ_CASE4(i) ARSO_CZ_CASE(4 * (i)) ARSO_CZ_CASE(4 * (i) + 1) ARSO_CZ_CASE(4 * (i) + 2) ARSO_CZ_CASE(4 * (i) + 3)
+
 __device__ __forceinline__ void apply_op(Amps &a, TileCtx &c, const RegOp &op, const float2 *__restrict__ mats,
                                          float2 *sm, float2 *ubuf, int t) {
-    const uint32_t cls = op.w0 & 255u, p0 = (op.w0 >> 8) & 15u, p1 = (op.w0 >> 12) & 15u;
+    const uint32_t p0 = (op.w0 >> 8) & 15u, p1 = (op.w0 >> 12) & 15u;
     const uint32_t q0 = (op.w0 >> 16) & 255u, q1 = op.w0 >> 24;
+    const uint32_t x = op.pad[0];
+    const uint32_t ba = ((c.m >> q0) ^ (x >> 12)) & 1u, bb = ((c.m >> q1) ^ (x >> 13)) & 1u;
+    const uint32_t code = (x & 255u) + ba * ((x >> 8) & 3u) + bb * ((x >> 10) & 3u);
+    const uint32_t flip = (c.m >> q0) & 1u;
     const float2 *M = mats + op.aux;
-    switch (cls) {
-        case GC_H: {
-            // with the qubit's mask bit set: H X = Z H, so apply Z H and clear the bit
-            const uint32_t flip = (c.m >> q0) & 1u;
-            switch (p0) {
-                case 0: rg_h_lanes(a, flip ? -1.f : 1.f); break;
-                case 1: rg_h<1>(a, flip); break;
-                case 2: rg_h<2>(a, flip); break;
-                case 3: rg_h<3>(a, flip); break;
-                default: rg_h<4>(a, flip); break;
+    // X U X for the qubit's mask bit: for SU(2) [[conj a, -conj b], [b, a]], the same form
+    const float2 ua = flip ? make_float2(op.c0.x, -op.c0.y) : op.c0;
+    const float2 ub = flip ? make_float2(-op.c1.x, op.c1.y) : op.c1;
+#define ARSO_SU2(P) rg_su2<P>(a, ua, ub)
+#define ARSO_D1(P) rg_dense1<P>(a, M[flip ? 3 : 0], M[flip ? 2 : 1], M[flip ? 1 : 2], M[flip ? 0 : 3])
+#define ARSO_CX(P) rg_cx<P>(a, p0, (c.tpart >> q0) & 1u)
+    switch (code) {
+        case OP_SU2: rg_dense1_lanes(a, ua, ub, make_float2(-ub.x, ub.y), make_float2(ua.x, -ua.y)); break;
+        ARSO_CASE_P(OP_SU2, ARSO_SU2)
+        case OP_DENSE1: rg_dense1_lanes(a, M[flip ? 3 : 0], M[flip ? 2 : 1], M[flip ? 1 : 2], M[flip ? 0 : 3]); break;
+        ARSO_CASE_P(OP_DENSE1, ARSO_D1)
+        // H on a flipped qubit: H X = Z H, so apply Z H and clear the mask bit
+        case OP_H: rg_h_lanes(a, 1.f); break;
+        case OP_H + 1: rg_h_lanes(a, -1.f); c.m &= ~(1u << q0); break;
+        case OP_H + 2: rg_h<1, false>(a); break;
+        case OP_H + 3: rg_h<1, true>(a); c.m &= ~(1u << q0); break;
+        case OP_H + 4: rg_h<2, false>(a); break;
+        case OP_H + 5: rg_h<2, true>(a); c.m &= ~(1u << q0); break;
+        case OP_H + 6: rg_h<3, false>(a); break;
+        case OP_H + 7: rg_h<3, true>(a); c.m &= ~(1u << q0); break;
+        case OP_H + 8: rg_h<4, false>(a); break;
+        case OP_H + 9: rg_h<4, true>(a); c.m &= ~(1u << q0); break;
+        ARSO_CZ_CASE4(0) ARSO_CZ_CASE4(1) ARSO_CZ_CASE4(2) ARSO_CZ_CASE4(3) ARSO_CZ_CASE4(4)
+        ARSO_CZ_CASE4(5) ARSO_CZ_CASE4(6) ARSO_CZ_CASE4(7) ARSO_CZ_CASE4(8) ARSO_CZ_CASE4(9)
+        // one register qubit: negate its want half where the thread-level qubit is 1
+        case OP_CZ_RT + 0: if (thread_bit(c, p0 < REG_BITS ? q1 : q0)) neg_half<0, 0>(a); break;
+        case OP_CZ_RT + 1: if (thread_bit(c, p0 < REG_BITS ? q1 : q0)) neg_half<0, 1>(a); break;
+        case OP_CZ_RT + 2: if (thread_bit(c, p0 < REG_BITS ? q1 : q0)) neg_half<1, 0>(a); break;
+        case OP_CZ_RT + 3: if (thread_bit(c, p0 < REG_BITS ? q1 : q0)) neg_half<1, 1>(a); break;
+        case OP_CZ_RT + 4: if (thread_bit(c, p0 < REG_BITS ? q1 : q0)) neg_half<2, 0>(a); break;
+        case OP_CZ_RT + 5: if (thread_bit(c, p0 < REG_BITS ? q1 : q0)) neg_half<2, 1>(a); break;
+        case OP_CZ_RT + 6: if (thread_bit(c, p0 < REG_BITS ? q1 : q0)) neg_half<3, 0>(a); break;
+        case OP_CZ_RT + 7: if (thread_bit(c, p0 < REG_BITS ? q1 : q0)) neg_half<3, 1>(a); break;
+        case OP_CZ_RT + 8: if (thread_bit(c, p0 < REG_BITS ? q1 : q0)) neg_half<4, 0>(a); break;
+        case OP_CZ_RT + 9: if (thread_bit(c, p0 < REG_BITS ? q1 : q0)) neg_half<4, 1>(a); break;
+        case OP_CZ_TT:
+            if (thread_bit(c, q0) && thread_bit(c, q1)) {
+                const float2 m1 = bc2(-1.f);
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    a.re[k] = mul2(m1, a.re[k]);
+                    a.im[k] = mul2(m1, a.im[k]);
+                }
             }
-            c.m &= ~(1u << q0);
             break;
-        }
-        case GC_DENSE1: {
-            // with the qubit's mask bit set the stored data sees X U X = [[u11, u10], [u01, u00]]
-            const uint32_t flip = (c.m >> q0) & 1u;
-            const float2 u00 = M[flip ? 3 : 0], u01 = M[flip ? 2 : 1];
-            const float2 u10 = M[flip ? 1 : 2], u11 = M[flip ? 0 : 3];
-            switch (p0) {
-                case 0: rg_dense1_lanes(a, u00, u01, u10, u11); break;
-                case 1: rg_dense1<1>(a, u00, u01, u10, u11); break;
-                case 2: rg_dense1<2>(a, u00, u01, u10, u11); break;
-                case 3: rg_dense1<3>(a, u00, u01, u10, u11); break;
-                default: rg_dense1<4>(a, u00, u01, u10, u11); break;
-            }
-            break;
-        }
-        case GC_SU2: {
-            // X U X = [[conj a, -conj b], [b, a]]: the same form with (u11, u10)
-            const uint32_t flip = (c.m >> q0) & 1u;
-            const float2 ua = flip ? make_float2(op.c0.x, -op.c0.y) : op.c0;
-            const float2 ub = flip ? make_float2(-op.c1.x, op.c1.y) : op.c1;
-            switch (p0) {
-                case 0: rg_dense1_lanes(a, ua, ub, make_float2(-ub.x, ub.y), make_float2(ua.x, -ua.y)); break;
-                case 1: rg_su2<1>(a, ua, ub); break;
-                case 2: rg_su2<2>(a, ua, ub); break;
-                case 3: rg_su2<3>(a, ua, ub); break;
-                default: rg_su2<4>(a, ua, ub); break;
-            }
-            break;
-        }
-        case GC_DIAG1: rg_diag1(a, c, q0, p0, op.c0, op.c1); break;
-        case GC_OMEGA: rg_omega(a, c, q0, p0, op.aux); break;
-        case GC_X: c.m ^= 1u << q0; break;
-        case GC_CZ: rg_cz(a, c, q0, q1, p0, p1); break;
-        case GC_DIAG2: rg_diag2(a, c, q0, q1, M); break;
-        case GC_CX: {
-            // CX X^m = X^{m'} CX with m' = m ^ (target bit if the control bit is in m)
-            const uint32_t cth = (c.tpart >> q0) & 1u;
-            switch (p1) {
-                case 0: rg_cx<0>(a, p0, cth); break;
-                case 1: rg_cx<1>(a, p0, cth); break;
-                case 2: rg_cx<2>(a, p0, cth); break;
-                case 3: rg_cx<3>(a, p0, cth); break;
-                default: rg_cx<4>(a, p0, cth); break;
-            }
-            if ((c.m >> q0) & 1u) c.m ^= 1u << q1;
-            break;
-        }
-        case GC_DENSE2:
-        case GC_SWAP: {
+        case OP_X: c.m ^= 1u << q0; break;
+        case OP_OMEGA: rg_omega(a, c, q0, p0, op.aux); break;
+        case OP_DIAG1: rg_diag1(a, c, q0, p0, op.c0, op.c1); break;
+        case OP_DIAG2: rg_diag2(a, c, q0, q1, M); break;
+        // CX X^m = X^{m'} CX with m' = m ^ (target bit if the control bit is in m)
+        case OP_CX: ARSO_CX(0); if (flip) c.m ^= 1u << q1; break;
+        case OP_CX + 1: ARSO_CX(1); if (flip) c.m ^= 1u << q1; break;
+        case OP_CX + 2: ARSO_CX(2); if (flip) c.m ^= 1u << q1; break;
+        case OP_CX + 3: ARSO_CX(3); if (flip) c.m ^= 1u << q1; break;
+        case OP_CX + 4: ARSO_CX(4); if (flip) c.m ^= 1u << q1; break;
+        case OP_DENSE2:
+        case OP_SWAP: {
+            const bool swap = code == OP_SWAP;
             const uint32_t mab = ((c.m >> q0) & 1u) | (((c.m >> q1) & 1u) << 1);
             if (c.tid < 16) {
                 const uint32_t k = c.tid >> 2, l = c.tid & 3u;
                 float2 u;
-                if (cls == GC_SWAP) {
+                if (swap) {
                     const uint32_t perm[4] = {0, 2, 1, 3};
                     u = make_float2(perm[k] == l ? 1.f : 0.f, 0.f);
                 } else {
@@ -610,12 +621,18 @@ __device__ __forceinline__ void apply_op(Amps &a, TileCtx &c, const RegOp &op, c
             from_smem(a, sm, c, t);
             __syncthreads();
             // SWAP X^m = X^{m with bits q0, q1 exchanged} SWAP
-            if (cls == GC_SWAP && (((c.m >> q0) ^ (c.m >> q1)) & 1u)) c.m ^= (1u << q0) | (1u << q1);
+            if (swap && (((c.m >> q0) ^ (c.m >> q1)) & 1u)) c.m ^= (1u << q0) | (1u << q1);
             break;
         }
         default: break;
     }
+#undef ARSO_SU2
+#undef ARSO_D1
+#undef ARSO_CX
 }
+#undef ARSO_CASE_P
+#undef ARSO_CZ_CASE
+#undef ARSO_CZ_CASE4
 
 // Gates [g, ge) of one phase with the Pauli events that fall inside them;
 // ops[0] is the record of gate g0 (the phase's first gate). The inner loop
