@@ -144,10 +144,10 @@ static void schedule_streaming(arso_circuit *c) {
 // Within a pass the gates may run in any order that respects their qubit
 // dependencies. The planner list-schedules them: with register set R it runs
 // every ready gate whose need is in R, repeatedly; when none is left it picks
-// the next R greedily, one qubit at a time, by the weighted number of gates
-// the closure under R would run. Passes start and end in the load/store
-// mapping {0, t-4, t-3, t-2, t-1}, whose thread bits 1..t-5 keep global
-// accesses contiguous.
+// the next R among all sets of tile bit 0 and four other tile bits by the
+// weighted number of gates the closure under R would run. Passes start and
+// end in the load/store mapping {0, t-4, t-3, t-2, t-1}, whose thread bits
+// 1..t-5 keep global accesses contiguous.
 static constexpr uint32_t NO_NEED = 0xFFFFFFFFu;
 
 static uint32_t need_of(const HostGate &h, uint32_t lq0, uint32_t lq1) {
@@ -270,23 +270,19 @@ static void plan_phases(arso_circuit *c) {
             S.closure(cur, false);
             if (S.order.size() > before) phases.emplace_back((uint32_t)before, cur);
             if (S.order.size() == G) break;
-            // next register set: tile bit 0, then greedily the qubit with the largest closure gain
-            std::vector<uint32_t> R{0};
-            while (R.size() < (size_t)REG_BITS) {
-                double best_w = -1.0;
-                uint32_t best_q = 0;
-                for (uint32_t q = 1; q < t; ++q) {
-                    if (std::find(R.begin(), R.end(), q) != R.end()) continue;
-                    std::vector<uint32_t> trial = R;
-                    trial.push_back(q);
-                    const double w = S.closure(trial, true);
-                    if (w > best_w + 1e-12) {
-                        best_w = w;
-                        best_q = q;
-                    }
-                }
-                R.push_back(best_q);
-            }
+            // next register set: tile bit 0 and the 4 other tile bits whose closure runs
+            // the largest weight of gates (all C(t-1, 4) sets are tried; ties keep the first)
+            std::vector<uint32_t> R{0, 1, 2, 3, 4}, best;
+            double best_w = -1.0;
+            for (uint32_t a = 1; a < t; ++a)
+                for (uint32_t b = a + 1; b < t; ++b)
+                    for (uint32_t d = b + 1; d < t; ++d)
+                        for (uint32_t e = d + 1; e < t; ++e) {
+                            R[1] = a, R[2] = b, R[3] = d, R[4] = e;
+                            const double w = S.closure(R, true);
+                            if (w > best_w + 1e-12) best_w = w, best = R;
+                        }
+            R = best;
             std::sort(R.begin(), R.end());
             ARSO_REQUIRE(R != cur, "internal: the phase planner made no progress");
             cur = R;

@@ -544,13 +544,17 @@ __device__ __forceinline__ void apply_op(Amps &a, TileCtx &c, const RegOp &op, c
     const uint32_t flip = (c.m >> q0) & 1u;
     const float2 *M = mats + op.aux;
     // X U X for the qubit's mask bit: for SU(2) [[conj a, -conj b], [b, a]], the same form
-    const float2 ua = flip ? make_float2(op.c0.x, -op.c0.y) : op.c0;
-    const float2 ub = flip ? make_float2(-op.c1.x, op.c1.y) : op.c1;
-#define ARSO_SU2(P) rg_su2<P>(a, ua, ub)
+#define ARSO_UA (flip ? make_float2(op.c0.x, -op.c0.y) : op.c0)
+#define ARSO_UB (flip ? make_float2(-op.c1.x, op.c1.y) : op.c1)
+#define ARSO_SU2(P) rg_su2<P>(a, ARSO_UA, ARSO_UB)
 #define ARSO_D1(P) rg_dense1<P>(a, M[flip ? 3 : 0], M[flip ? 2 : 1], M[flip ? 1 : 2], M[flip ? 0 : 3])
 #define ARSO_CX(P) rg_cx<P>(a, p0, (c.tpart >> q0) & 1u)
     switch (code) {
-        case OP_SU2: rg_dense1_lanes(a, ua, ub, make_float2(-ub.x, ub.y), make_float2(ua.x, -ua.y)); break;
+        case OP_SU2: {
+            const float2 ua = ARSO_UA, ub = ARSO_UB;
+            rg_dense1_lanes(a, ua, ub, make_float2(-ub.x, ub.y), make_float2(ua.x, -ua.y));
+            break;
+        }
         ARSO_CASE_P(OP_SU2, ARSO_SU2)
         case OP_DENSE1: rg_dense1_lanes(a, M[flip ? 3 : 0], M[flip ? 2 : 1], M[flip ? 1 : 2], M[flip ? 0 : 3]); break;
         ARSO_CASE_P(OP_DENSE1, ARSO_D1)
@@ -626,6 +630,8 @@ __device__ __forceinline__ void apply_op(Amps &a, TileCtx &c, const RegOp &op, c
         }
         default: break;
     }
+#undef ARSO_UA
+#undef ARSO_UB
 #undef ARSO_SU2
 #undef ARSO_D1
 #undef ARSO_CX
