@@ -344,58 +344,6 @@ __host__ __device__ constexpr int cz_pb(int pp) {
 template <int IDX> __device__ __forceinline__ void cz_case(Amps &a) {
     neg_quarter<cz_pa(IDX >> 2), cz_pb(IDX >> 2), (IDX >> 1) & 1, IDX & 1>(a);
 }
-#define ARSO_CZ4(i)                                      \
-    case 4 * (i): cz_case<4 * (i)>(a); break;            \
-    case 4 * (i) + 1: cz_case<4 * (i) + 1>(a); break;    \
-    case 4 * (i) + 2: cz_case<4 * (i) + 2>(a); break;    \
-    case 4 * (i) + 3: cz_case<4 * (i) + 3>(a); break;
-
-__device__ __forceinline__ void rg_cz(Amps &a, const TileCtx &c, uint32_t qa, uint32_t qb, uint32_t pa, uint32_t pb) {
-    uint32_t wa = ((c.m >> qa) & 1u) ^ 1u, wb = ((c.m >> qb) & 1u) ^ 1u;  // stored values whose true bit is 1
-    if (pa < REG_BITS && pb < REG_BITS) {
-        if (pa > pb) {
-            const uint32_t tp = pa, tw = wa;
-            pa = pb;
-            wa = wb;
-            pb = tp;
-            wb = tw;
-        }
-        // pair index of (pa < pb) in (0,1),(0,2),(0,3),(0,4),(1,2),(1,3),(1,4),(2,3),(2,4),(3,4)
-        const uint32_t pp = pa == 0 ? pb - 1 : pa == 1 ? pb + 2 : pa == 2 ? pb + 4 : 9;
-        switch (pp * 4 + wa * 2 + wb) {
-            ARSO_CZ4(0) ARSO_CZ4(1) ARSO_CZ4(2) ARSO_CZ4(3) ARSO_CZ4(4)
-            ARSO_CZ4(5) ARSO_CZ4(6) ARSO_CZ4(7) ARSO_CZ4(8) ARSO_CZ4(9)
-            default: break;
-        }
-        return;
-    }
-    if (pa < REG_BITS || pb < REG_BITS) {
-        const uint32_t p = pa < REG_BITS ? pa : pb, w = pa < REG_BITS ? wa : wb;
-        if (!thread_bit(c, pa < REG_BITS ? qb : qa)) return;
-        switch (p * 2 + w) {
-            case 0: neg_half<0, 0>(a); break;
-            case 1: neg_half<0, 1>(a); break;
-            case 2: neg_half<1, 0>(a); break;
-            case 3: neg_half<1, 1>(a); break;
-            case 4: neg_half<2, 0>(a); break;
-            case 5: neg_half<2, 1>(a); break;
-            case 6: neg_half<3, 0>(a); break;
-            case 7: neg_half<3, 1>(a); break;
-            case 8: neg_half<4, 0>(a); break;
-            default: neg_half<4, 1>(a); break;
-        }
-        return;
-    }
-    if (thread_bit(c, qa) && thread_bit(c, qb)) {
-        const float2 m1 = bc2(-1.f);
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            a.re[k] = mul2(m1, a.re[k]);
-            a.im[k] = mul2(m1, a.im[k]);
-        }
-    }
-}
-#undef ARSO_CZ4
 
 __device__ __forceinline__ void rg_diag2(Amps &a, const TileCtx &c, uint32_t qa, uint32_t qb,
                                          const float2 *__restrict__ d) {
@@ -523,66 +471,18 @@ __device__ __forceinline__ void smem_dense2(float2 *sm, int t, uint32_t q0, uint
     }
 }
 
-// One dispatch per gate: the host resolved class and register positions into
-// an op code; the mask-dependent variants (H on a flipped qubit, the CZ sign
-// pattern) are selected by adding the relevant mask bits.
-#define ARSO_CASE_P(BASE, CALL) \
-    case BASE + 1: CALL(1); break; \
-    case BASE + 2: CALL(2); break; \
-    case BASE + 3: CALL(3); break; \
-    case BASE + 4: CALL(4); break;
+// CZ from the host-resolved code: pair of register positions, or one
+// register position and a thread bit; the mask bits of the qubits select the
+// sign pattern (want = 1 ^ mask bit).
 #define ARSO_CZ_CASE(i) case OP_CZ_RR + (i): cz_case<(i)>(a); break;
 #define ARSO_CZ_CASE4(i) ARSO_CZ_CASE(4 * (i)) ARSO_CZ_CASE(4 * (i) + 1) ARSO_CZ_CASE(4 * (i) + 2) ARSO_CZ_CASE(4 * (i) + 3)
-
-__device__ __forceinline__ void apply_op(Amps &a, TileCtx &c, const RegOp &op, const float2 *__restrict__ mats,
-                                         float2 *sm, float2 *ubuf, int t) {
-    const uint32_t p0 = (op.w0 >> 8) & 15u, p1 = (op.w0 >> 12) & 15u;
-    const uint32_t q0 = (op.w0 >> 16) & 255u, q1 = op.w0 >> 24;
+__device__ __forceinline__ void rg_cz_code(Amps &a, const TileCtx &c, const RegOp &op, uint32_t q0, uint32_t q1,
+                                           uint32_t p0) {
     const uint32_t x = op.pad[0];
     const uint32_t ba = ((c.m >> q0) ^ (x >> 12)) & 1u, bb = ((c.m >> q1) ^ (x >> 13)) & 1u;
     const uint32_t code = (x & 255u) + ba * ((x >> 8) & 3u) + bb * ((x >> 10) & 3u);
-    const uint32_t flip = (c.m >> q0) & 1u;
-    const float2 *M = mats + op.aux;
-    // X U X for the qubit's mask bit: for SU(2) [[conj a, -conj b], [b, a]], the same form
-#define ARSO_UA (flip ? make_float2(op.c0.x, -op.c0.y) : op.c0)
-#define ARSO_UB (flip ? make_float2(-op.c1.x, op.c1.y) : op.c1)
-#define ARSO_SU2(P) rg_su2<P>(a, ARSO_UA, ARSO_UB)
-#define ARSO_D1(P) rg_dense1<P>(a, M[flip ? 3 : 0], M[flip ? 2 : 1], M[flip ? 1 : 2], M[flip ? 0 : 3])
-#define ARSO_CX(P) rg_cx<P>(a, p0, (c.tpart >> q0) & 1u)
-    switch (code) {
-        case OP_SU2: {
-            const float2 ua = ARSO_UA, ub = ARSO_UB;
-            rg_dense1_lanes(a, ua, ub, make_float2(-ub.x, ub.y), make_float2(ua.x, -ua.y));
-            break;
-        }
-        ARSO_CASE_P(OP_SU2, ARSO_SU2)
-        case OP_DENSE1: rg_dense1_lanes(a, M[flip ? 3 : 0], M[flip ? 2 : 1], M[flip ? 1 : 2], M[flip ? 0 : 3]); break;
-        ARSO_CASE_P(OP_DENSE1, ARSO_D1)
-        // H on a flipped qubit: H X = Z H, so apply Z H and clear the mask bit
-        case OP_H: rg_h_lanes(a, 1.f); break;
-        case OP_H + 1: rg_h_lanes(a, -1.f); c.m &= ~(1u << q0); break;
-        case OP_H + 2: rg_h<1, false>(a); break;
-        case OP_H + 3: rg_h<1, true>(a); c.m &= ~(1u << q0); break;
-        case OP_H + 4: rg_h<2, false>(a); break;
-        case OP_H + 5: rg_h<2, true>(a); c.m &= ~(1u << q0); break;
-        case OP_H + 6: rg_h<3, false>(a); break;
-        case OP_H + 7: rg_h<3, true>(a); c.m &= ~(1u << q0); break;
-        case OP_H + 8: rg_h<4, false>(a); break;
-        case OP_H + 9: rg_h<4, true>(a); c.m &= ~(1u << q0); break;
-        ARSO_CZ_CASE4(0) ARSO_CZ_CASE4(1) ARSO_CZ_CASE4(2) ARSO_CZ_CASE4(3) ARSO_CZ_CASE4(4)
-        ARSO_CZ_CASE4(5) ARSO_CZ_CASE4(6) ARSO_CZ_CASE4(7) ARSO_CZ_CASE4(8) ARSO_CZ_CASE4(9)
-        // one register qubit: negate its want half where the thread-level qubit is 1
-        case OP_CZ_RT + 0: if (thread_bit(c, p0 < REG_BITS ? q1 : q0)) neg_half<0, 0>(a); break;
-        case OP_CZ_RT + 1: if (thread_bit(c, p0 < REG_BITS ? q1 : q0)) neg_half<0, 1>(a); break;
-        case OP_CZ_RT + 2: if (thread_bit(c, p0 < REG_BITS ? q1 : q0)) neg_half<1, 0>(a); break;
-        case OP_CZ_RT + 3: if (thread_bit(c, p0 < REG_BITS ? q1 : q0)) neg_half<1, 1>(a); break;
-        case OP_CZ_RT + 4: if (thread_bit(c, p0 < REG_BITS ? q1 : q0)) neg_half<2, 0>(a); break;
-        case OP_CZ_RT + 5: if (thread_bit(c, p0 < REG_BITS ? q1 : q0)) neg_half<2, 1>(a); break;
-        case OP_CZ_RT + 6: if (thread_bit(c, p0 < REG_BITS ? q1 : q0)) neg_half<3, 0>(a); break;
-        case OP_CZ_RT + 7: if (thread_bit(c, p0 < REG_BITS ? q1 : q0)) neg_half<3, 1>(a); break;
-        case OP_CZ_RT + 8: if (thread_bit(c, p0 < REG_BITS ? q1 : q0)) neg_half<4, 0>(a); break;
-        case OP_CZ_RT + 9: if (thread_bit(c, p0 < REG_BITS ? q1 : q0)) neg_half<4, 1>(a); break;
-        case OP_CZ_TT:
+    if (code >= (uint32_t)OP_CZ_RT) {
+        if (code == (uint32_t)OP_CZ_TT) {
             if (thread_bit(c, q0) && thread_bit(c, q1)) {
                 const float2 m1 = bc2(-1.f);
 #pragma unroll
@@ -591,20 +491,89 @@ __device__ __forceinline__ void apply_op(Amps &a, TileCtx &c, const RegOp &op, c
                     a.im[k] = mul2(m1, a.im[k]);
                 }
             }
+            return;
+        }
+        if (!thread_bit(c, p0 < REG_BITS ? q1 : q0)) return;
+        switch (code - OP_CZ_RT) {
+            case 0: neg_half<0, 0>(a); break;
+            case 1: neg_half<0, 1>(a); break;
+            case 2: neg_half<1, 0>(a); break;
+            case 3: neg_half<1, 1>(a); break;
+            case 4: neg_half<2, 0>(a); break;
+            case 5: neg_half<2, 1>(a); break;
+            case 6: neg_half<3, 0>(a); break;
+            case 7: neg_half<3, 1>(a); break;
+            case 8: neg_half<4, 0>(a); break;
+            default: neg_half<4, 1>(a); break;
+        }
+        return;
+    }
+    switch (code) {
+        ARSO_CZ_CASE4(0) ARSO_CZ_CASE4(1) ARSO_CZ_CASE4(2) ARSO_CZ_CASE4(3) ARSO_CZ_CASE4(4)
+        ARSO_CZ_CASE4(5) ARSO_CZ_CASE4(6) ARSO_CZ_CASE4(7) ARSO_CZ_CASE4(8) ARSO_CZ_CASE4(9)
+        default: break;
+    }
+}
+#undef ARSO_CZ_CASE
+#undef ARSO_CZ_CASE4
+
+// One dispatch per gate on the host-resolved base op code (class and
+// register positions); mask-dependent details (H on a flipped qubit, the CZ
+// sign pattern) are resolved inside the case, so cheap gates pay no extra
+// decoding.
+#define ARSO_P4(BASE, CALL) \
+    case BASE + 1: CALL(1); break; \
+    case BASE + 2: CALL(2); break; \
+    case BASE + 3: CALL(3); break; \
+    case BASE + 4: CALL(4); break;
+__device__ __forceinline__ void apply_op(Amps &a, TileCtx &c, const RegOp &op, const float2 *__restrict__ mats,
+                                         float2 *sm, float2 *ubuf, int t) {
+    const uint32_t p0 = (op.w0 >> 8) & 15u, p1 = (op.w0 >> 12) & 15u;
+    const uint32_t q0 = (op.w0 >> 16) & 255u, q1 = op.w0 >> 24;
+    const float2 *M = mats + op.aux;
+    // X U X for the qubit's mask bit: for SU(2) [[conj a, -conj b], [b, a]], the same form;
+    // for a general U [[u11, u10], [u01, u00]]
+#define ARSO_FLIP ((c.m >> q0) & 1u)
+#define ARSO_UA (ARSO_FLIP ? make_float2(op.c0.x, -op.c0.y) : op.c0)
+#define ARSO_UB (ARSO_FLIP ? make_float2(-op.c1.x, op.c1.y) : op.c1)
+#define ARSO_SU2(P) rg_su2<P>(a, ARSO_UA, ARSO_UB)
+#define ARSO_D1(P) \
+    rg_dense1<P>(a, M[ARSO_FLIP ? 3 : 0], M[ARSO_FLIP ? 2 : 1], M[ARSO_FLIP ? 1 : 2], M[ARSO_FLIP ? 0 : 3])
+    // H on a flipped qubit: H X = Z H, so apply Z H and clear the mask bit
+#define ARSO_H(P) rg_h<P>(a, ARSO_FLIP); c.m &= ~(1u << q0)
+    // CX X^m = X^{m'} CX with m' = m ^ (target bit if the control bit is in m)
+#define ARSO_CX(P) rg_cx<P>(a, p0, (c.tpart >> q0) & 1u); if (ARSO_FLIP) c.m ^= 1u << q1
+    switch (op.pad[0] & 255u) {
+        case OP_SU2: {
+            const float2 ua = ARSO_UA, ub = ARSO_UB;
+            rg_dense1_lanes(a, ua, ub, make_float2(-ub.x, ub.y), make_float2(ua.x, -ua.y));
             break;
+        }
+        ARSO_P4(OP_SU2, ARSO_SU2)
+        case OP_DENSE1: {
+            const uint32_t f = ARSO_FLIP;
+            rg_dense1_lanes(a, M[f ? 3 : 0], M[f ? 2 : 1], M[f ? 1 : 2], M[f ? 0 : 3]);
+            break;
+        }
+        ARSO_P4(OP_DENSE1, ARSO_D1)
+        case OP_H: rg_h_lanes(a, ARSO_FLIP ? -1.f : 1.f); c.m &= ~(1u << q0); break;
+        case OP_H + 2: ARSO_H(1); break;
+        case OP_H + 4: ARSO_H(2); break;
+        case OP_H + 6: ARSO_H(3); break;
+        case OP_H + 8: ARSO_H(4); break;
+        case OP_CZ_RR + 0: case OP_CZ_RR + 4: case OP_CZ_RR + 8: case OP_CZ_RR + 12: case OP_CZ_RR + 16:
+        case OP_CZ_RR + 20: case OP_CZ_RR + 24: case OP_CZ_RR + 28: case OP_CZ_RR + 32: case OP_CZ_RR + 36:
+        case OP_CZ_RT + 0: case OP_CZ_RT + 2: case OP_CZ_RT + 4: case OP_CZ_RT + 6: case OP_CZ_RT + 8:
+        case OP_CZ_TT: rg_cz_code(a, c, op, q0, q1, p0); break;
         case OP_X: c.m ^= 1u << q0; break;
         case OP_OMEGA: rg_omega(a, c, q0, p0, op.aux); break;
         case OP_DIAG1: rg_diag1(a, c, q0, p0, op.c0, op.c1); break;
         case OP_DIAG2: rg_diag2(a, c, q0, q1, M); break;
-        // CX X^m = X^{m'} CX with m' = m ^ (target bit if the control bit is in m)
-        case OP_CX: ARSO_CX(0); if (flip) c.m ^= 1u << q1; break;
-        case OP_CX + 1: ARSO_CX(1); if (flip) c.m ^= 1u << q1; break;
-        case OP_CX + 2: ARSO_CX(2); if (flip) c.m ^= 1u << q1; break;
-        case OP_CX + 3: ARSO_CX(3); if (flip) c.m ^= 1u << q1; break;
-        case OP_CX + 4: ARSO_CX(4); if (flip) c.m ^= 1u << q1; break;
+        case OP_CX: ARSO_CX(0); break;
+        ARSO_P4(OP_CX, ARSO_CX)
         case OP_DENSE2:
         case OP_SWAP: {
-            const bool swap = code == OP_SWAP;
+            const bool swap = (op.pad[0] & 255u) == OP_SWAP;
             const uint32_t mab = ((c.m >> q0) & 1u) | (((c.m >> q1) & 1u) << 1);
             if (c.tid < 16) {
                 const uint32_t k = c.tid >> 2, l = c.tid & 3u;
@@ -630,15 +599,15 @@ __device__ __forceinline__ void apply_op(Amps &a, TileCtx &c, const RegOp &op, c
         }
         default: break;
     }
+#undef ARSO_FLIP
 #undef ARSO_UA
 #undef ARSO_UB
 #undef ARSO_SU2
 #undef ARSO_D1
+#undef ARSO_H
 #undef ARSO_CX
 }
-#undef ARSO_CASE_P
-#undef ARSO_CZ_CASE
-#undef ARSO_CZ_CASE4
+#undef ARSO_P4
 
 // Gates [g, ge) of one phase with the Pauli events that fall inside them;
 // ops[0] is the record of gate g0 (the phase's first gate). The inner loop
