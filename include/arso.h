@@ -205,8 +205,8 @@ arso_status arso_run_batch(size_t count, arso_circuit *const *circuits, const ar
 
 /* Autotune the fused-pass schedule of a circuit by measurement: for each
  * candidate (tile_qubits in 10..14, low_qubits in 3..5) compile the circuit,
- * time n_traj trajectories at uniform rate p (CUDA events on `stream`,
- * after one warm-up run that also builds the prefix cache) and return the
+ * time n_traj trajectories at uniform rate p (CUDA events on `stream`; best
+ * of three runs after one warm-up run that also builds the prefix cache) and return the
  * fastest options in *best (precision and the other fields copied from
  * `base`, which may be NULL). ms_out (optional, capacity 16) receives each
  * candidate's time in candidate order, tile-major; *n_candidates their number.
