@@ -86,7 +86,14 @@ typedef struct {
 /* The streaming engine records each batch's pass launches into a CUDA graph
  * (keyed by the batch's pass range and slot count) and replays it for later
  * batches of the same shape; this flag launches every pass directly. */
-enum { ARSO_OPT_NO_SUFFIX_REUSE = 1, ARSO_OPT_NO_GRAPHS = 2 };
+/* Exhaustive single-error analysis (Sec. IV-B.1) for the fidelity criterion
+ * takes every single-error score from one error-free sweep: the state with
+ * error P on qubit q after gate g has fidelity <psi_g|P|psi_g>^2 with psi_R,
+ * because the rest of the circuit is unitary and maps psi_g to psi_R. The
+ * sweep keeps the state in one CTA (resident circuits) or in HBM (streaming
+ * complex64 circuits, one gate and one expectation per launch). This flag
+ * simulates the 3L single-error trajectories instead (for comparisons). */
+enum { ARSO_OPT_NO_SUFFIX_REUSE = 1, ARSO_OPT_NO_GRAPHS = 2, ARSO_OPT_NO_FAST_EXHAUSTIVE = 4 };
 
 typedef struct arso_circuit arso_circuit;
 typedef struct arso_error_list arso_error_list;

@@ -198,6 +198,7 @@ def _gates_array(gates):
 
 OPT_NO_SUFFIX_REUSE = 1
 OPT_NO_GRAPHS = 2
+OPT_NO_FAST_EXHAUSTIVE = 4
 
 
 def compile_circuit(n, gates, precision=C64, tile_qubits=0, low_qubits=0, max_batch=0, cache_bytes=0, flags=0):

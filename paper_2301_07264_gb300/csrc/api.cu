@@ -800,8 +800,91 @@ static McOut mc_run_memo(arso_circuit *c, const DevCrit &dc, double p, uint64_t 
 
 // Exhaustive single-error analysis: values per location and per type
 // (Eq. (3)); P[4] = {P_R, P_X, P_Z, P_Y} for the given aggregate.
+// Fidelity of every single-error state from one error-free sweep: the state
+// with error P on qubit q after gate g scores <psi_g|P|psi_g>^2 (the rest of the
+// circuit maps psi_g to psi_R). Scores in the exhaustive order (X block, Z
+// block, Y block, each in location order). Returns false where the sweep is
+// not available (streaming complex128), leaving the trajectory route.
+static bool single_error_fidelities(arso_circuit *c, cudaStream_t st, std::vector<double> &s) {
+    const uint64_t L = c->L, G = c->gates.size();
+    if (c->engine != 0 && c->precision != ARSO_C64) return false;
+    std::vector<double> xyz(3 * std::max<uint64_t>(L, 1));
+    if (L) {
+        std::vector<uint32_t> first(G);
+        for (uint64_t l = L; l-- > 0;) first[c->loc_gate[l]] = (uint32_t)l;
+        Scratch d_out(st, 3 * L * 8);
+        if (c->engine == 0) {
+            std::vector<uint32_t> fl(G);
+            for (uint64_t pos = 0; pos < G; ++pos) fl[pos] = first[c->perm[pos]];
+            Scratch d_fl(st, G * 4);
+            copy_h2d(d_fl.ptr, fl.data(), G * 4, st);
+            launch_expect_resident(c->d_gates.as<DGate>(), c->d_mats.ptr, (uint32_t)G, (int)c->n, c->precision,
+                                   d_fl.as<uint32_t>(), d_out.as<double>(), st);
+            copy_d2h(xyz.data(), d_out.ptr, 3 * L * 8, st);
+            ARSO_CUDA(cudaStreamSynchronize(st));
+        } else {
+            // complex64 state in HBM, one gate and one expectation per launch, in engine order
+            const int n = (int)c->n;
+            Scratch psi(st, c->state_bytes()), part(st, 3 * (size_t)expect_hbm_blocks(n) * 8);
+            launch_init_zero_state(psi.ptr, n, ARSO_C64, st);
+            for (uint64_t pos = 0; pos < G; ++pos) {
+                const HostGate &h = c->gates[c->perm[pos]];
+                if (h.cls != GC_NOP) {
+                    DGate d{};
+                    d.cls = h.cls == GC_H ? (uint8_t)GC_DENSE1
+                          : h.cls == GC_OMEGA ? (uint8_t)GC_DIAG1 : h.cls == GC_CZ ? (uint8_t)GC_DIAG2 : h.cls;
+                    d.arity = (uint8_t)h.arity;
+                    d.q0 = (uint8_t)h.q0;
+                    d.q1 = (uint8_t)h.q1;
+                    M16 m{};
+                    if (h.arity == 1 && d.cls == GC_DIAG1) {
+                        m.m[0] = make_float2((float)h.m[0].real(), (float)h.m[0].imag());
+                        m.m[1] = make_float2((float)h.m[3].real(), (float)h.m[3].imag());
+                    } else {
+                        for (int i = 0; i < (h.arity == 1 ? 4 : 16); ++i)
+                            m.m[i] = make_float2((float)h.m[i].real(), (float)h.m[i].imag());
+                    }
+                    launch_gate_pairs(psi.as<float2>(), n, d, m, st);
+                }
+                const uint32_t l0 = first[c->perm[pos]];
+                for (int j = 0; j < h.arity; ++j)
+                    launch_expect_hbm(psi.as<float2>(), n, j ? h.q1 : h.q0, part.as<double>(),
+                                      d_out.as<double>() + 3 * (size_t)(l0 + j), st);
+            }
+            copy_d2h(xyz.data(), d_out.ptr, 3 * L * 8, st);
+            ARSO_CUDA(cudaStreamSynchronize(st));
+        }
+    }
+    s.assign(3 * L, 0.0);
+    for (uint64_t l = 0; l < L; ++l)
+        for (int k = 0; k < 3; ++k) s[k * L + l] = xyz[3 * l + k] * xyz[3 * l + k];  // X, Z, Y blocks
+    return true;
+}
+
+static void exhaustive_by_trajectories(arso_circuit *c, const DevCrit &dc, cudaStream_t st, std::vector<double> &s,
+                                       std::vector<uint8_t> &f);
+static void exhaustive_finish(arso_circuit *c, const DevCrit &dc, cudaStream_t st, const std::vector<double> &s,
+                              const std::vector<uint8_t> &f, double *P, std::vector<double> *per_loc_mean,
+                              std::vector<double> *per_loc_pass, double *P_pass);
+
 static void exhaustive(arso_circuit *c, const DevCrit &dc, cudaStream_t st, double *P, std::vector<double> *per_loc_mean,
                        std::vector<double> *per_loc_pass, double *P_pass) {
+    const uint64_t L = c->L;
+    const uint64_t T = 3 * L;
+    std::vector<double> s(T);
+    std::vector<uint8_t> f(T);
+    if (dc.d.kind == ARSO_CRIT_FIDELITY && !(c->flags & ARSO_OPT_NO_FAST_EXHAUSTIVE) &&
+        single_error_fidelities(c, st, s)) {
+        for (uint64_t i = 0; i < T; ++i) f[i] = s[i] >= dc.d.threshold;
+    } else {
+        exhaustive_by_trajectories(c, dc, st, s, f);
+    }
+    exhaustive_finish(c, dc, st, s, f, P, per_loc_mean, per_loc_pass, P_pass);
+}
+
+// Every single-error state simulated as a trajectory with one event.
+static void exhaustive_by_trajectories(arso_circuit *c, const DevCrit &dc, cudaStream_t st, std::vector<double> &s,
+                                       std::vector<uint8_t> &f) {
     const uint64_t L = c->L;
     const uint64_t T = 3 * L;
     std::vector<uint64_t> off(T + 1);
@@ -817,12 +900,21 @@ static void exhaustive(arso_circuit *c, const DevCrit &dc, cudaStream_t st, doub
     std::unique_ptr<arso_error_list> e(raw);
     Scratch sc(st, std::max<uint64_t>(T, 1) * 8), pf(st, std::max<uint64_t>(T, 1));
     run_all(c, e.get(), dc, st, sc.as<double>(), pf.as<uint8_t>());
-    std::vector<double> s(T);
-    std::vector<uint8_t> f(T);
+    s.assign(T, 0.0);
+    f.assign(T, 0);
     if (T) {
         copy_d2h(s.data(), sc.ptr, T * 8, st);
         copy_d2h(f.data(), pf.ptr, T, st);
     }
+    ARSO_CUDA(cudaStreamSynchronize(st));
+}
+
+static void exhaustive_finish(arso_circuit *c, const DevCrit &dc, cudaStream_t st, const std::vector<double> &s,
+                              const std::vector<uint8_t> &f, double *P, std::vector<double> *per_loc_mean,
+                              std::vector<double> *per_loc_pass, double *P_pass) {
+    const uint64_t L = c->L;
+    const uint64_t T = 3 * L;
+    ensure_cache(c, st);
     // reference value
     Scratch ref(st, 8);
     score_into(ref_state_ptr(c), ref_state_ptr(c), (int)c->n, c->precision, dc.d, ref.as<double>(), st);

@@ -473,4 +473,131 @@ void launch_init_zero_state(void *psi, int n, int precision, cudaStream_t st) {
     ARSO_CUDA(cudaGetLastError());
 }
 
+
+// ------------------------------------------- single-error fidelity values ---
+// For the fidelity criterion the final state with one Pauli error P on qubit q
+// after gate g scores |<psi_g|P|psi_g>|^2 (the rest of the circuit is unitary
+// and maps psi_g to psi_R), so the exhaustive analysis needs only the Pauli
+// expectations <X_q>, <Z_q>, <Y_q> of the error-free state after every gate.
+// Per pair (a0, a1) along bit q: Z contributes |a0|^2 - |a1|^2, X
+// 2 Re(conj(a0) a1), Y 2 Im(conj(a0) a1). FP64 accumulation.
+template <typename T>
+__device__ __forceinline__ void pauli_terms(T a0, T a1, double &x, double &z, double &y) {
+    const double r0 = a0.x, i0 = a0.y, r1 = a1.x, i1 = a1.y;
+    z += r0 * r0 + i0 * i0 - r1 * r1 - i1 * i1;
+    x += 2.0 * (r0 * r1 + i0 * i1);
+    y += 2.0 * (r0 * i1 - i0 * r1);
+}
+
+// block-wide sum of three doubles; every thread gets the result
+__device__ __forceinline__ void block_sum3(double &x, double &z, double &y, double (*red)[32]) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_down_sync(0xffffffffu, x, o);
+        z += __shfl_down_sync(0xffffffffu, z, o);
+        y += __shfl_down_sync(0xffffffffu, y, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) red[0][warp] = x, red[1][warp] = z, red[2][warp] = y;
+    __syncthreads();
+    x = z = y = 0.0;
+    for (int w = 0; w < nw; ++w) x += red[0][w], z += red[1][w], y += red[2][w];
+}
+
+// Whole state in one CTA's shared memory: apply the gates in engine order and
+// write (<X>, <Z>, <Y>) of each gate's qubits after it to out[3 * location].
+template <typename T>
+__global__ void expect_resident_kernel(const DGate *__restrict__ gates, const T *__restrict__ mats, uint32_t G, int n,
+                                       const uint32_t *__restrict__ first_loc, double *__restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[3][32];
+    T *s = reinterpret_cast<T *>(smem_raw);
+    const uint32_t N = 1u << n;
+    for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) {
+        T z;
+        z.x = i == 0 ? 1 : 0;
+        z.y = 0;
+        s[i] = z;
+    }
+    __syncthreads();
+    for (uint32_t pos = 0; pos < G; ++pos) {
+        const DGate g = gates[pos];
+        tile_gate(s, n, g, mats + g.mat);
+        __syncthreads();
+        for (int j = 0; j < g.arity; ++j) {
+            const uint32_t q = j ? g.q1 : g.q0, bit = 1u << q;
+            double x = 0.0, z = 0.0, y = 0.0;
+            for (uint32_t p = threadIdx.x; p < N / 2; p += blockDim.x) {
+                const uint32_t i0 = insert_zero(p, q);
+                pauli_terms(s[i0], s[i0 | bit], x, z, y);
+            }
+            block_sum3(x, z, y, red);
+            if (threadIdx.x == 0) {
+                double *o = out + 3 * (size_t)(first_loc[pos] + j);
+                o[0] = x;
+                o[1] = z;
+                o[2] = y;
+            }
+        }
+    }
+}
+
+void launch_expect_resident(const DGate *gates, const void *mats, uint32_t G, int n, int precision,
+                            const uint32_t *first_loc, double *out, cudaStream_t st) {
+    const size_t smem = (size_t(1) << n) * (precision == ARSO_C64 ? 8 : 16);
+    ProfScope ps_(ARSO_K_OTHER, 0.0, st);
+    if (precision == ARSO_C64) {
+        if (smem > 48 * 1024)
+            ARSO_CUDA(cudaFuncSetAttribute(expect_resident_kernel<float2>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        expect_resident_kernel<float2><<<1, 512, smem, st>>>(gates, static_cast<const float2 *>(mats), G, n,
+                                                             first_loc, out);
+    } else {
+        if (smem > 48 * 1024)
+            ARSO_CUDA(cudaFuncSetAttribute(expect_resident_kernel<double2>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        expect_resident_kernel<double2><<<1, 512, smem, st>>>(gates, static_cast<const double2 *>(mats), G, n,
+                                                              first_loc, out);
+    }
+    ARSO_CUDA(cudaGetLastError());
+}
+
+// The same expectations for a complex64 state in HBM: per-block partial sums,
+// then one thread adds the blocks in order (deterministic).
+__global__ void expect_partials_kernel(const float2 *__restrict__ psi, int n, uint32_t q, double *partials) {
+    __shared__ double red[3][32];
+    const uint64_t half = 1ull << (n - 1), bit = 1ull << q, lo = bit - 1;
+    double x = 0.0, z = 0.0, y = 0.0;
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < half; p += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t i0 = ((p & ~lo) << 1) | (p & lo);
+        pauli_terms(psi[i0], psi[i0 | bit], x, z, y);
+    }
+    block_sum3(x, z, y, red);
+    if (threadIdx.x == 0) {
+        partials[3 * blockIdx.x] = x;
+        partials[3 * blockIdx.x + 1] = z;
+        partials[3 * blockIdx.x + 2] = y;
+    }
+}
+__global__ void expect_finish_kernel(const double *partials, uint32_t blocks, double *out3) {
+    double x = 0.0, z = 0.0, y = 0.0;
+    for (uint32_t b = 0; b < blocks; ++b) x += partials[3 * b], z += partials[3 * b + 1], y += partials[3 * b + 2];
+    out3[0] = x;
+    out3[1] = z;
+    out3[2] = y;
+}
+
+uint32_t expect_hbm_blocks(int n) {
+    return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(((1ull << (n - 1)) + 255) / 256, 152ull * 8));
+}
+
+void launch_expect_hbm(const float2 *psi, int n, uint32_t q, double *partials, double *out3, cudaStream_t st) {
+    const uint32_t blocks = expect_hbm_blocks(n);
+    ProfScope ps_(ARSO_K_REDUCE, 8.0 * (double)(1ull << n), st);
+    expect_partials_kernel<<<blocks, 256, 0, st>>>(psi, n, q, partials);
+    expect_finish_kernel<<<1, 1, 0, st>>>(partials, blocks, out3);
+    ARSO_CUDA(cudaGetLastError());
+}
+
 }  // namespace arso

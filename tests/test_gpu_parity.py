@@ -495,3 +495,36 @@ def test_search_probe_reuse_is_exact(arso, n, depth):
     assert a.value_lo == b.value_lo and a.value_hi == b.value_hi
     assert abs(a.p - b.p) <= 1e-12 * a.p
     assert swept[True] < 0.8 * swept[False]
+
+
+@pytest.mark.parametrize("case", ["resident_c64", "resident_c128", "streaming_c64"])
+def test_fast_exhaustive_matches_single_error_trajectories(arso, case):
+    # the error-free sweep of Pauli expectations (fidelity = <psi_g|P|psi_g>^2)
+    # against simulating every single-error state as a trajectory
+    if case == "resident_c64":
+        circ, kw, tol = C.brickwork(12, 10, 3), {}, AMP_TOL_C64
+    elif case == "resident_c128":
+        circ, kw, tol = C.qft4_0101(), {"precision": arso.C128}, AMP_TOL_C128
+    else:
+        circ, kw, tol = C.brickwork(14, 8, 4), {"tile_qubits": 10}, AMP_TOL_C64
+    crit = C.Criterion("fidelity", threshold=0.9, aggregate="mean")
+    fast = arso.compile_circuit(circ.n, circ.gates, **kw)
+    slow = arso.compile_circuit(circ.n, circ.gates, flags=arso.OPT_NO_FAST_EXHAUSTIVE, **kw)
+    Pf, per_f = arso.exhaustive(fast, crit)
+    Ps, per_s = arso.exhaustive(slow, crit)
+    assert per_f.shape == (3 * circ.L,)
+    assert np.max(np.abs(per_f - per_s)) < 10 * tol
+    assert np.max(np.abs(Pf - Ps)) < 10 * tol
+
+
+def test_fast_exhaustive_streaming_matches_oracle(arso):
+    circ = C.brickwork(14, 4, 5)
+    crit = C.Criterion("fidelity", threshold=0.5, aggregate="mean")
+    circ.criterion = crit
+    cc = arso.compile_circuit(circ.n, circ.gates, tile_qubits=10)
+    P, per = arso.exhaustive(cc, crit)
+    a = ox.analyse(circ)
+    assert abs(P[0] - a["P_R"]) < SCORE_TOL
+    for k, e in enumerate(("X", "Z", "Y")):
+        assert abs(P[1 + k] - a["P_e"][e]) < SCORE_TOL
+        assert np.max(np.abs(per[k * circ.L:(k + 1) * circ.L] - a["per_location"][e])) < SCORE_TOL
