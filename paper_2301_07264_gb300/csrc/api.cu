@@ -814,12 +814,22 @@ static bool single_error_fidelities(arso_circuit *c, cudaStream_t st, std::vecto
         for (uint64_t l = L; l-- > 0;) first[c->loc_gate[l]] = (uint32_t)l;
         Scratch d_out(st, 3 * L * 8);
         if (c->engine == 0) {
+            // one CTA per segment between cached checkpoints (every ckpt_every gates,
+            // or phases when register-blocked), all segments in parallel
+            ensure_cache(c, st);
+            const uint64_t units = c->reg_blocked ? c->ph_R.size() : G;
+            std::vector<uint32_t> seg;
+            for (uint64_t u = 0; u < units; u += c->ckpt_every)
+                seg.push_back(c->reg_blocked ? c->ph_gb[u] : (uint32_t)u);
+            seg.push_back((uint32_t)G);
             std::vector<uint32_t> fl(G);
             for (uint64_t pos = 0; pos < G; ++pos) fl[pos] = first[c->perm[pos]];
-            Scratch d_fl(st, G * 4);
+            Scratch d_fl(st, G * 4), d_seg(st, seg.size() * 4);
             copy_h2d(d_fl.ptr, fl.data(), G * 4, st);
-            launch_expect_resident(c->d_gates.as<DGate>(), c->d_mats.ptr, (uint32_t)G, (int)c->n, c->precision,
-                                   d_fl.as<uint32_t>(), d_out.as<double>(), st);
+            copy_h2d(d_seg.ptr, seg.data(), seg.size() * 4, st);
+            launch_expect_resident(c->d_gates.as<DGate>(), c->d_mats.ptr, (int)c->n, c->precision, c->d_cache.ptr,
+                                   d_seg.as<uint32_t>(), (uint32_t)(seg.size() - 1), d_fl.as<uint32_t>(),
+                                   d_out.as<double>(), st);
             copy_d2h(xyz.data(), d_out.ptr, 3 * L * 8, st);
             ARSO_CUDA(cudaStreamSynchronize(st));
         } else {

@@ -132,10 +132,12 @@ uint32_t launch_score_partials(const void *psi, const void *ref, int n, int prec
                                Partial *partials, uint32_t max_blocks, cudaStream_t st);
 void launch_init_zero_state(void *psi, int n, int precision, cudaStream_t st);
 // Pauli expectations (<X_q>, <Z_q>, <Y_q>) of the error-free state after each
-// gate: whole state in one CTA (resident circuits; out[3 * location + k]) or a
+// gate: resident circuits run one CTA per cached checkpoint segment
+// (engine positions seg_pos[b] .. seg_pos[b + 1]; out[3 * location + k]), or a
 // complex64 state in HBM (one qubit per launch; partials: 3 * expect_hbm_blocks(n)).
-void launch_expect_resident(const DGate *gates, const void *mats, uint32_t G, int n, int precision,
-                            const uint32_t *first_loc, double *out, cudaStream_t st);
+void launch_expect_resident(const DGate *gates, const void *mats, int n, int precision, const void *ckpt,
+                            const uint32_t *seg_pos, uint32_t n_seg, const uint32_t *first_loc, double *out,
+                            cudaStream_t st);
 uint32_t expect_hbm_blocks(int n);
 void launch_expect_hbm(const float2 *psi, int n, uint32_t q, double *partials, double *out3, cudaStream_t st);
 

@@ -505,23 +505,23 @@ __device__ __forceinline__ void block_sum3(double &x, double &z, double &y, doub
     for (int w = 0; w < nw; ++w) x += red[0][w], z += red[1][w], y += red[2][w];
 }
 
-// Whole state in one CTA's shared memory: apply the gates in engine order and
-// write (<X>, <Z>, <Y>) of each gate's qubits after it to out[3 * location].
+// Whole state in one CTA's shared memory: CTA b starts from cached error-free
+// checkpoint b (engine position seg_pos[b]), applies the gates up to
+// seg_pos[b + 1] in engine order and writes (<X>, <Z>, <Y>) of each gate's
+// qubits after it to out[3 * location]; the segments run in parallel.
 template <typename T>
-__global__ void expect_resident_kernel(const DGate *__restrict__ gates, const T *__restrict__ mats, uint32_t G, int n,
+__global__ void expect_resident_kernel(const DGate *__restrict__ gates, const T *__restrict__ mats, int n,
+                                       const T *__restrict__ ckpt, const uint32_t *__restrict__ seg_pos,
                                        const uint32_t *__restrict__ first_loc, double *__restrict__ out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[3][32];
     T *s = reinterpret_cast<T *>(smem_raw);
     const uint32_t N = 1u << n;
-    for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) {
-        T z;
-        z.x = i == 0 ? 1 : 0;
-        z.y = 0;
-        s[i] = z;
-    }
+    const T *src = ckpt + (size_t)blockIdx.x * N;
+    for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) s[i] = src[i];
     __syncthreads();
-    for (uint32_t pos = 0; pos < G; ++pos) {
+    const uint32_t pe = seg_pos[blockIdx.x + 1];
+    for (uint32_t pos = seg_pos[blockIdx.x]; pos < pe; ++pos) {
         const DGate g = gates[pos];
         tile_gate(s, n, g, mats + g.mat);
         __syncthreads();
@@ -543,22 +543,26 @@ __global__ void expect_resident_kernel(const DGate *__restrict__ gates, const T 
     }
 }
 
-void launch_expect_resident(const DGate *gates, const void *mats, uint32_t G, int n, int precision,
-                            const uint32_t *first_loc, double *out, cudaStream_t st) {
+void launch_expect_resident(const DGate *gates, const void *mats, int n, int precision, const void *ckpt,
+                            const uint32_t *seg_pos, uint32_t n_seg, const uint32_t *first_loc, double *out,
+                            cudaStream_t st) {
+    if (!n_seg) return;
     const size_t smem = (size_t(1) << n) * (precision == ARSO_C64 ? 8 : 16);
-    ProfScope ps_(ARSO_K_OTHER, 0.0, st);
+    ProfScope ps_(ARSO_K_OTHER, (double)n_seg * smem, st);
     if (precision == ARSO_C64) {
         if (smem > 48 * 1024)
             ARSO_CUDA(cudaFuncSetAttribute(expect_resident_kernel<float2>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        expect_resident_kernel<float2><<<1, 512, smem, st>>>(gates, static_cast<const float2 *>(mats), G, n,
-                                                             first_loc, out);
+        expect_resident_kernel<float2><<<n_seg, 512, smem, st>>>(gates, static_cast<const float2 *>(mats), n,
+                                                                 static_cast<const float2 *>(ckpt), seg_pos,
+                                                                 first_loc, out);
     } else {
         if (smem > 48 * 1024)
             ARSO_CUDA(cudaFuncSetAttribute(expect_resident_kernel<double2>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        expect_resident_kernel<double2><<<1, 512, smem, st>>>(gates, static_cast<const double2 *>(mats), G, n,
-                                                              first_loc, out);
+        expect_resident_kernel<double2><<<n_seg, 512, smem, st>>>(gates, static_cast<const double2 *>(mats), n,
+                                                                  static_cast<const double2 *>(ckpt), seg_pos,
+                                                                  first_loc, out);
     }
     ARSO_CUDA(cudaGetLastError());
 }
