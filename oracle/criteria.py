@@ -25,3 +25,11 @@ def score(crit, psi, psi_ref=None):
 
 def passes(crit, s):
     return s >= crit.threshold
+
+
+def heavy_outputs(psi_ref):
+    """Heavy outputs of a quantum-volume circuit (Cross et al. 2019, the
+    success measure the paper's QV evaluation uses): the basis states whose
+    ideal probability exceeds the median of the ideal output distribution."""
+    probs = np.abs(np.asarray(psi_ref)) ** 2
+    return np.flatnonzero(probs > np.median(probs)).astype(np.uint64)

@@ -216,8 +216,63 @@ def exhaustive(args):
             "rows": rows}
 
 
+def qv(args):
+    """Quantum-volume circuits scored by their heavy-output probability (the
+    paper's QV evaluation: binning on the heavy outputs, averaged over 200
+    random circuits per data point): 200 circuits at each of 8, 12 and 16
+    qubits, p = 1e-3, 500 trajectories per circuit, one arso_run_batch call per
+    size and step. The heavy sets come from the library's error-free states."""
+    import torch
+    from paper_2301_07264_gb300 import arso
+    from workloads import circuits as W
+    sizes, per_size, T, p = (8, 12, 16), 200, 500, 1e-3
+    groups = []
+    for n in sizes:
+        ccs, crits = [], []
+        ref = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+        for k in range(per_size):
+            circ = W.quantum_volume(n, 10_000 * n + k)
+            cc = arso.compile_circuit(n, circ.gates)
+            arso.reference_state(cc, ref)
+            probs = (ref.abs() ** 2).double().cpu().numpy()
+            heavy = np.flatnonzero(probs > np.median(probs)).astype(np.uint64)
+            ccs.append(cc)
+            crits.append(W.Criterion("binning", basis_set=heavy.tolist(), threshold=2 / 3, aggregate="mean"))
+        outs = [torch.empty(T, dtype=torch.float64, device="cuda") for _ in ccs]
+        groups.append((n, ccs, crits, outs))
+    stream = torch.cuda.current_stream()
+
+    def step(k):
+        for n, ccs, crits, outs in groups:
+            errs = [arso.sample_errors(cc, p / 3, p / 3, p / 3, 0, k * T, T, stream) for cc in ccs]
+            arso.run_batch(ccs, errs, crits, outs, None, stream)
+
+    for w in range(args.warmup):
+        step(1000 + w)
+    hop = {n: [] for n in sizes}
+    e0, e1 = _events()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(args.steps):
+        step(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    for n, ccs, crits, outs in groups:
+        hop[n] = [float(o.mean().item()) for o in outs]
+    total = len(sizes) * per_size * T * args.steps
+    return {"metric": "error-injected trajectories/sec", "value": total / sec, "unit": "traj/s",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "quantum_volume_heavy_output", "sizes": list(sizes), "circuits_per_size": per_size,
+                       "traj_per_circuit": T, "p": p, "criterion": "binning on heavy outputs (mean)"},
+            "results": {str(n): {"mean_heavy_output_probability": float(np.mean(hop[n])),
+                                 "circuits_above_2/3": int(np.sum(np.asarray(hop[n]) > 2 / 3))} for n in sizes},
+            "kernels": _kernel_stats(arso)}
+
+
 def run(args):
     import torch
     torch.cuda.set_device(0)
     torch.cuda.set_stream(torch.cuda.Stream())
-    return {"grover12": grover12, "mix256": mix256, "search": search, "exhaustive": exhaustive}[args.workload](args)
+    return {"grover12": grover12, "mix256": mix256, "search": search, "exhaustive": exhaustive, "qv": qv}[args.workload](args)

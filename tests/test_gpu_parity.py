@@ -528,3 +528,21 @@ def test_fast_exhaustive_streaming_matches_oracle(arso):
     for k, e in enumerate(("X", "Z", "Y")):
         assert abs(P[1 + k] - a["P_e"][e]) < SCORE_TOL
         assert np.max(np.abs(per[k * circ.L:(k + 1) * circ.L] - a["per_location"][e])) < SCORE_TOL
+
+
+@pytest.mark.parametrize("n,kw", [(10, {}), (14, {"tile_qubits": 10})])
+def test_quantum_volume_heavy_output_scores(arso, n, kw):
+    # QV circuits (Haar U(4) layers, dense two-qubit gates) scored by binning on
+    # the heavy outputs of their ideal distribution, per trajectory against the oracle
+    circ = C.quantum_volume(n, 7)
+    heavy = criteria.heavy_outputs(statevector.simulate(circ, []))
+    crit = C.Criterion("binning", basis_set=heavy.tolist(), threshold=2 / 3, aggregate="mean")
+    cc = arso.compile_circuit(n, circ.gates, **kw)
+    T, p = 6, 3e-2
+    errs = arso.sample_errors(cc, p / 3, p / 3, p / 3, 5, 0, T)
+    got = np.zeros(T)
+    arso.run_trajectories(cc, errs, crit, got)
+    lists = sampling.sample(5, 0, T, circ.L, p / 3, p / 3, p / 3)
+    for t in range(T):
+        want = criteria.score(crit, statevector.simulate(circ, lists[t]))
+        assert abs(got[t] - want) < SCORE_TOL

@@ -441,3 +441,24 @@ def test_pins_catch_a_transposed_cx():
     expect = np.zeros(8, dtype=complex)
     expect[0] = expect[-1] = 1 / math.sqrt(2)
     assert np.max(np.abs(psi - expect)) > 0.1
+
+
+def test_heavy_outputs_of_quantum_volume_circuits():
+    # the heavy set is the upper half of the ideal distribution: 2^(n-1)
+    # outcomes; a uniform state puts exactly 1/2 on it; for random QV circuits
+    # the ideal heavy-output probability approaches (1 + ln 2) / 2 = 0.847
+    # (Porter-Thomas statistics, Aaronson & Chen 2017), already near it at n = 6
+    hops = []
+    for s in range(40):
+        circ = C.quantum_volume(6, s)
+        assert circ.G == 18 and all(g.name == "U2" for g in circ.gates)
+        psi = statevector.simulate(circ, [])
+        assert abs(np.linalg.norm(psi) - 1) < 1e-12
+        heavy = criteria.heavy_outputs(psi)
+        assert len(heavy) == 32
+        crit = C.Criterion("binning", basis_set=heavy.tolist(), threshold=2 / 3)
+        hops.append(criteria.score(crit, psi))
+        uniform = np.full(64, 1 / 8, dtype=np.complex128)
+        assert abs(criteria.score(crit, uniform) - 0.5) < 1e-12
+    assert 0.80 < np.mean(hops) < 0.90
+    assert min(hops) > 0.5

@@ -231,6 +231,30 @@ def haar_su2(rng: np.random.Generator) -> np.ndarray:
     return np.array([[a + 1j * b, c + 1j * d], [-c + 1j * d, a - 1j * b]], dtype=np.complex128)
 
 
+def haar_u4(rng: np.random.Generator) -> np.ndarray:
+    """Haar-random U(4): QR of a complex Gaussian matrix, with the phases of R's
+    diagonal moved into Q (Mezzadri 2007)."""
+    z = rng.standard_normal((4, 4)) + 1j * rng.standard_normal((4, 4))
+    qm, r = np.linalg.qr(z)
+    return (qm * (np.diag(r) / np.abs(np.diag(r)))).astype(np.complex128)
+
+
+def quantum_volume(n: int, seed: int) -> Circuit:
+    """Quantum-volume model circuit (Cross et al. 2019): n layers; each layer
+    pairs the qubits by a random permutation and applies a Haar U(4) to every
+    pair (an odd qubit out idles). The criterion is binning on the heavy
+    outputs, the basis states whose ideal probability exceeds the median; that
+    set depends on the ideal output distribution, so whoever runs the circuit
+    fills in ``criterion.basis_set`` from its error-free state."""
+    rng = np.random.default_rng(seed)
+    gates = []
+    for _ in range(n):
+        perm = rng.permutation(n)
+        for k in range(n // 2):
+            gates.append(_g("U2", int(perm[2 * k]), int(perm[2 * k + 1]), matrix=haar_u4(rng)))
+    return Circuit(n, gates, "qv", Criterion("binning", threshold=2 / 3, aggregate="mean"), {"seed": seed})
+
+
 def brickwork(n: int, depth: int, seed: int, threshold: float = 0.9) -> Circuit:
     """Per layer: Haar SU(2) on every qubit, then CZ on (0,1),(2,3),... in even
     layers and (1,2),(3,4),... in odd layers (open chain)."""
@@ -346,10 +370,7 @@ def random_circuit(n: int, G: int, seed: int, two_qubit_frac: float = 0.4) -> Ci
             if name == "CP":
                 gates.append(_g(name, a, b, params=(rng.uniform(-math.pi, math.pi),)))
             elif name == "U2":
-                z = rng.standard_normal((4, 4)) + 1j * rng.standard_normal((4, 4))
-                qm, r = np.linalg.qr(z)
-                qm = qm * (np.diag(r) / np.abs(np.diag(r)))
-                gates.append(_g(name, a, b, matrix=qm.astype(np.complex128)))
+                gates.append(_g(name, a, b, matrix=haar_u4(rng)))
             else:
                 gates.append(_g(name, a, b))
         else:
