@@ -358,7 +358,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-suffix", action="store_true",
                     help="run every trajectory to the end instead of scoring after its last error")
-    ap.add_argument("--workload", default="brickwork24", choices=["brickwork24", "grover12", "mix256", "search", "exhaustive", "qv"],
+    ap.add_argument("--workload", default="brickwork24", choices=["brickwork24", "grover12", "mix256", "search", "exhaustive", "qv", "families"],
                     help="brickwork24 is the benchmark line; the others measure the other configurations")
     ap.add_argument("--search-circuits", type=int, default=8)
     ap.add_argument("--train-rows", type=int, default=2_000_000)

@@ -271,8 +271,61 @@ def qv(args):
             "kernels": _kernel_stats(arso)}
 
 
+def families(args):
+    """Tolerable error rate (target success 0.66, the paper's figure) of the
+    paper's circuit families at several sizes, through the library's Fig. 3
+    flow (exhaustive analysis, then Eq. (5) or Monte Carlo bisection), then
+    per family least-squares fits of p* linear in 1 / G (through the origin,
+    and with an intercept) and the extrapolation of the first to a 56-qubit
+    instance of the family (the paper's quantum-advantage regime)."""
+    import torch
+    from paper_2301_07264_gb300 import arso
+    from workloads import circuits as W
+    P_target = 0.66
+    fams = {
+        "bv": (lambda n: W.bernstein_vazirani(n, (1 << (n - 1)) - 1 - (n % 3)), (6, 8, 10, 12, 14, 16)),
+        "hlf": (lambda n: W.hidden_linear_function(n, 100 + n), (6, 8, 10, 12, 14, 16)),
+        "ryrz": (lambda n: W.ryrz_ansatz(n, 1, 200 + n), (6, 8, 10, 12, 14, 16)),
+        "qft": (lambda n: W.qft_basis(n, int(("10" * n)[:n], 2)), (6, 8, 10, 12, 14, 16)),
+        "adder": (lambda n: W.cuccaro_adder((n - 2) // 2, 5 % (1 << ((n - 2) // 2)), 3), (6, 8, 10, 12, 14, 16)),
+        "uccsd": (lambda n: W.uccsd_ansatz(n, n // 2, 300 + n), (4, 6, 8, 10)),
+    }
+    rows, fits = [], {}
+    t0 = time.perf_counter()
+    for name, (make, sizes) in fams.items():
+        Gs, ps = [], []
+        for n in sizes:
+            circ = make(n)
+            crit = W.Criterion(circ.criterion.kind, target=circ.criterion.target, threshold=circ.criterion.threshold,
+                               aggregate="mean")
+            cc = arso.compile_circuit(circ.n, circ.gates)
+            r = arso.tolerable_rate(cc, crit, P_target, n_traj=4000, seed=0, rel_tol=0.05, p_lo=1e-7, p_hi=0.3,
+                                    check=False)
+            rows.append({"family": name, "n": n, "G": circ.G, "L": circ.L, "p_tol": r.p, "probes": r.probes,
+                         "mode": "Eq. (5)" if r.mode_used == 0 else "Monte Carlo", "p_tol_times_G": r.p * circ.G})
+            Gs.append(circ.G)
+            ps.append(r.p)
+        # p* = b / G (proportional, the extrapolation) and p* = a + b / G (with intercept)
+        g_inv, pv = 1.0 / np.asarray(Gs, dtype=float), np.asarray(ps)
+        b0 = float(g_inv @ pv / (g_inv @ g_inv))
+        A = np.stack([np.ones(len(Gs)), g_inv], axis=1)
+        coef, *_ = np.linalg.lstsq(A, pv, rcond=None)
+        G56 = make(56).G
+        fits[name] = {"b": b0, "mse": float(np.mean((b0 * g_inv - pv) ** 2)),
+                      "affine_a": float(coef[0]), "affine_b": float(coef[1]),
+                      "affine_mse": float(np.mean((A @ coef - pv) ** 2)),
+                      "G_56": G56, "p_tol_56_extrapolated": b0 / G56}
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    return {"metric": "tolerable-rate searches/sec", "value": len(rows) / sec, "unit": "searches/s",
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "families_tolerable_rate", "target": P_target, "n_traj": 4000, "rel_tol": 0.05},
+            "all_below_one_error": all(r["p_tol_times_G"] < 1.0 for r in rows),
+            "fits": fits, "rows": rows}
+
+
 def run(args):
     import torch
     torch.cuda.set_device(0)
     torch.cuda.set_stream(torch.cuda.Stream())
-    return {"grover12": grover12, "mix256": mix256, "search": search, "exhaustive": exhaustive, "qv": qv}[args.workload](args)
+    return {"grover12": grover12, "mix256": mix256, "search": search, "exhaustive": exhaustive, "qv": qv, "families": families}[args.workload](args)

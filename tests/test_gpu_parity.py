@@ -546,3 +546,29 @@ def test_quantum_volume_heavy_output_scores(arso, n, kw):
     for t in range(T):
         want = criteria.score(crit, statevector.simulate(circ, lists[t]))
         assert abs(got[t] - want) < SCORE_TOL
+
+
+@pytest.mark.parametrize("family", ["bv", "hlf", "ryrz", "uccsd", "ryrz_streaming"])
+def test_paper_families_scores(arso, family):
+    # the paper's remaining circuit families, per trajectory against the oracle
+    kw = {}
+    if family == "bv":
+        circ = C.bernstein_vazirani(11, 0b1011001101)
+    elif family == "hlf":
+        circ = C.hidden_linear_function(10, 2)
+    elif family == "ryrz":
+        circ = C.ryrz_ansatz(10, 3, 4)
+    elif family == "uccsd":
+        circ = C.uccsd_ansatz(8, 4, 5)
+    else:
+        circ, kw = C.ryrz_ansatz(14, 2, 6), {"tile_qubits": 10}
+    cc = arso.compile_circuit(circ.n, circ.gates, **kw)
+    T, p = 5, 1e-2
+    errs = arso.sample_errors(cc, p / 3, p / 3, p / 3, 9, 0, T)
+    got = np.zeros(T)
+    arso.run_trajectories(cc, errs, circ.criterion, got)
+    ref = statevector.simulate(circ, [])
+    lists = sampling.sample(9, 0, T, circ.L, p / 3, p / 3, p / 3)
+    for t in range(T):
+        want = criteria.score(circ.criterion, statevector.simulate(circ, lists[t]), ref)
+        assert abs(got[t] - want) < SCORE_TOL

@@ -462,3 +462,26 @@ def test_heavy_outputs_of_quantum_volume_circuits():
         assert abs(criteria.score(crit, uniform) - 0.5) < 1e-12
     assert 0.80 < np.mean(hops) < 0.90
     assert min(hops) > 0.5
+
+
+def test_paper_families_closed_forms():
+    # BV: the closing H gates map the data qubits to |secret> and the ancilla to |1>
+    for n, secret in ((5, 0b1011), (8, 0b1100101)):
+        circ = C.bernstein_vazirani(n, secret)
+        psi = statevector.simulate(circ, [])
+        assert abs(abs(psi[circ.criterion.target]) ** 2 - 1) < 1e-12
+    # HLF is a Clifford circuit: its output distribution is uniform on a support of size 2^k
+    for seed in range(4):
+        pr = np.abs(statevector.simulate(C.hidden_linear_function(7, seed), [])) ** 2
+        nz = pr[pr > 1e-12]
+        assert abs(nz.sum() - 1) < 1e-12 and np.allclose(nz, nz[0], atol=1e-12)
+        assert len(nz) & (len(nz) - 1) == 0
+    # RYRZ: depth layers of 2n rotations and n-1 CX, plus a final rotation layer
+    circ = C.ryrz_ansatz(6, 3, 1)
+    assert circ.G == 3 * (2 * 6 + 5) + 2 * 6
+    # UCCSD: every excitation conserves the number of occupied orbitals
+    circ = C.uccsd_ansatz(8, 4, 2)
+    psi = statevector.simulate(circ, [])
+    weight = np.array([bin(i).count("1") for i in range(1 << 8)])
+    assert np.sum(np.abs(psi[weight != 4]) ** 2) < 1e-20
+    assert abs(np.linalg.norm(psi) - 1) < 1e-12

@@ -305,11 +305,119 @@ def qaoa_maxcut(n: int, seed: int, layers: int = 2, threshold: float = 0.5) -> C
                    {"edges": edges, "gammas": gammas.tolist(), "betas": betas.tolist()})
 
 
+def bernstein_vazirani(n: int, secret: int) -> Circuit:
+    """Bernstein-Vazirani with CX gates (the paper's BV family): n - 1 data
+    qubits and the ancilla n - 1 prepared in |->; the oracle is a CX from every
+    data qubit whose secret bit is 1 onto the ancilla. Closing H gates leave
+    |secret> on the data qubits and |1> on the ancilla: one correct outcome."""
+    anc = n - 1
+    gates = [_g("X", anc)] + [_g("H", q) for q in range(n)]
+    gates += [_g("CX", q, anc) for q in range(n - 1) if (secret >> q) & 1]
+    gates += [_g("H", q) for q in range(n)]
+    target = (secret & ((1 << (n - 1)) - 1)) | (1 << anc)
+    return Circuit(n, gates, "bv", Criterion("outcome", target=target, threshold=0.5, aggregate="mean"),
+                   {"secret": secret})
+
+
+def hidden_linear_function(n: int, seed: int, edge_prob: float = 0.5) -> Circuit:
+    """Hidden linear function circuit (Bravyi, Gosset, Koenig 2018): H on every
+    qubit, CZ on the edges of a random graph (the symmetric part of the
+    quadratic form), S on a random subset (its diagonal), H on every qubit.
+    Its outputs are spread uniformly over a subspace, so it is scored by
+    fidelity (the paper's choice for circuits without a single correct outcome)."""
+    rng = np.random.default_rng(seed)
+    gates = [_g("H", q) for q in range(n)]
+    for u in range(n):
+        for v in range(u + 1, n):
+            if rng.random() < edge_prob:
+                gates.append(_g("CZ", u, v))
+    gates += [_g("S", q) for q in range(n) if rng.random() < 0.5]
+    gates += [_g("H", q) for q in range(n)]
+    return Circuit(n, gates, "hlf", Criterion("fidelity", threshold=0.5, aggregate="mean"), {"seed": seed})
+
+
+def ryrz_ansatz(n: int, depth: int, seed: int) -> Circuit:
+    """Hardware-efficient RY-RZ ansatz: a layer of RY and RZ rotations with
+    random angles on every qubit, then a CX chain (q, q+1), repeated depth
+    times, and a final rotation layer. Scored by fidelity."""
+    rng = np.random.default_rng(seed)
+    gates = []
+
+    def rot():
+        out = []
+        for q in range(n):
+            out.append(_g("RY", q, params=(rng.uniform(-math.pi, math.pi),)))
+            out.append(_g("RZ", q, params=(rng.uniform(-math.pi, math.pi),)))
+        return out
+
+    for _ in range(depth):
+        gates += rot()
+        gates += [_g("CX", q, q + 1) for q in range(n - 1)]
+    gates += rot()
+    return Circuit(n, gates, "ryrz", Criterion("fidelity", threshold=0.5, aggregate="mean"), {"depth": depth})
+
+
+def _pauli_exp(string: dict, theta: float) -> list:
+    """exp(-i theta/2 P) for a Pauli string {qubit: "X"|"Y"|"Z"}: basis change to
+    Z (H for X, RX(pi/2) for Y), a CX ladder that collects the parity on the
+    last qubit, RZ(theta), the ladder reversed and the basis change undone."""
+    qs = sorted(string)
+    pre, post = [], []
+    for q in qs:
+        if string[q] == "X":
+            pre.append(_g("H", q))
+            post.append(_g("H", q))
+        elif string[q] == "Y":
+            pre.append(_g("RX", q, params=(math.pi / 2,)))
+            post.append(_g("RX", q, params=(-math.pi / 2,)))
+    ladder = [_g("CX", qs[i], qs[i + 1]) for i in range(len(qs) - 1)]
+    return pre + ladder + [_g("RZ", qs[-1], params=(theta,))] + ladder[::-1] + post
+
+
+def uccsd_ansatz(n: int, electrons: int, seed: int, max_doubles: int = 6) -> Circuit:
+    """UCCSD-style ansatz in the Jordan-Wigner encoding: X gates load the
+    Hartree-Fock state (the first `electrons` orbitals occupied), then every
+    single excitation i -> a and up to max_doubles double excitations
+    (i, j) -> (a, b) with random amplitudes, each as its Pauli-string
+    exponentials (2 strings per single, 8 per double) with Z strings on the
+    orbitals in between. Every excitation conserves the number of occupied
+    orbitals. Scored by fidelity."""
+    rng = np.random.default_rng(seed)
+    occ, vir = list(range(electrons)), list(range(electrons, n))
+    gates = [_g("X", q) for q in occ]
+
+    def strings(ops):
+        # ops: sorted list of (qubit, X|Y); the Jordan-Wigner Z string fills the gaps
+        lo, hi = ops[0][0], ops[-1][0]
+        st = {q: "Z" for q in range(lo, hi + 1)}
+        for q, p in ops:
+            st[q] = p
+        return st
+
+    for i in occ:
+        for a in vir:
+            t = rng.uniform(-0.5, 0.5)
+            gates += _pauli_exp(strings([(i, "X"), (a, "Y")]), t)
+            gates += _pauli_exp(strings([(i, "Y"), (a, "X")]), -t)
+    doubles = [(i, j, a, b) for i in occ for j in occ if j > i for a in vir for b in vir if b > a]
+    rng.shuffle(doubles)
+    for (i, j, a, b) in doubles[:max_doubles]:
+        t = rng.uniform(-0.5, 0.5)
+        for k, combo in enumerate(("XXXY", "XXYX", "XYYY", "YXYY", "XYXX", "YXXX", "YYXY", "YYYX")):
+            sign = 1.0 if k < 4 else -1.0
+            ops = sorted(zip((i, j, a, b), combo))
+            gates += _pauli_exp(strings(ops), sign * t / 4)
+    return Circuit(n, gates, "uccsd", Criterion("fidelity", threshold=0.5, aggregate="mean"),
+                   {"electrons": electrons})
+
+
 def cuccaro_adder(bits: int, a: int, b: int) -> Circuit:
     """Ripple-carry adder (Cuccaro, Draper, Kutin, Moulton 2004) on 2*bits+2
     qubits: [c0, b0, a0, b1, a1, ..., z]. Operands are loaded by X gates;
     Toffolis are in Clifford+T. Scored by the probability of the outcome that
     holds b <- a+b (low bits), z <- carry, a unchanged."""
+    if a >> bits or b >> bits:
+        raise ValueError(f"operands must fit in {bits} bits")
     n = 2 * bits + 2
     c0 = 0
     bq = [1 + 2 * i for i in range(bits)]
