@@ -28,9 +28,6 @@ static_assert(N_PARAMS == ARSO_SURROGATE_PARAMS, "parameter layout");
 // B(k, n) = B[k * sbk + n * sbn]; epilogue: + bias[n], relu, or * (mask > 0).
 enum { EPI_NONE = 0, EPI_BIAS_RELU = 1, EPI_BIAS = 2, EPI_RELU_MASK = 3 };
 
-template <typename TA, typename TB> struct Ld {
-    __device__ static float a(const TA *p) { return (float)*p; }
-};
 __device__ __forceinline__ float ldf(const float *p) { return *p; }
 __device__ __forceinline__ float ldf(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
 
