@@ -572,3 +572,22 @@ def test_paper_families_scores(arso, family):
     for t in range(T):
         want = criteria.score(circ.criterion, statevector.simulate(circ, lists[t]), ref)
         assert abs(got[t] - want) < SCORE_TOL
+
+
+@pytest.mark.parametrize("n,kw", [(12, {}), (16, {"tile_qubits": 12})])
+def test_split_trajectory_ranges_are_bit_identical(arso, n, kw):
+    # the sharding contract on one GPU: error draws depend only on (seed,
+    # trajectory id, location), so scoring [0, T) in one call or as two ranks'
+    # contiguous ranges gives the same score for every trajectory, bit for bit
+    circ = C.brickwork(n, 12, 21)
+    crit = C.Criterion("fidelity", threshold=0.9, aggregate="pass")
+    cc = arso.compile_circuit(circ.n, circ.gates, **kw)
+    T, p, seed = 600, 2e-3, 13
+    whole = np.zeros(T)
+    arso.run_trajectories(cc, arso.sample_errors(cc, p / 3, p / 3, p / 3, seed, 0, T), crit, whole)
+    parts = []
+    for begin, count in ((0, 257), (257, T - 257)):
+        s = np.zeros(count)
+        arso.run_trajectories(cc, arso.sample_errors(cc, p / 3, p / 3, p / 3, seed, begin, count), crit, s)
+        parts.append(s)
+    assert np.array_equal(np.concatenate(parts), whole)
