@@ -528,7 +528,7 @@ __device__ __forceinline__ void rg_cz_code(Amps &a, const TileCtx &c, const RegO
     case BASE + 4: CALL(4); break;
 __device__ __forceinline__ void apply_op(Amps &a, TileCtx &c, const RegOp &op, const float2 *__restrict__ mats,
                                          float2 *sm, float2 *ubuf, int t) {
-    const uint32_t p0 = (op.w0 >> 8) & 15u, p1 = (op.w0 >> 12) & 15u;
+    const uint32_t p0 = (op.w0 >> 8) & 15u;
     const uint32_t q0 = (op.w0 >> 16) & 255u, q1 = op.w0 >> 24;
     const float2 *M = mats + op.aux;
     // X U X for the qubit's mask bit: for SU(2) [[conj a, -conj b], [b, a]], the same form;
@@ -540,7 +540,7 @@ __device__ __forceinline__ void apply_op(Amps &a, TileCtx &c, const RegOp &op, c
 #define ARSO_D1(P) \
     rg_dense1<P>(a, M[ARSO_FLIP ? 3 : 0], M[ARSO_FLIP ? 2 : 1], M[ARSO_FLIP ? 1 : 2], M[ARSO_FLIP ? 0 : 3])
     // H on a flipped qubit: H X = Z H, so apply Z H and clear the mask bit
-#define ARSO_H(P) rg_h<P>(a, ARSO_FLIP); c.m &= ~(1u << q0)
+#define ARSO_HADAMARD(P) rg_h<P>(a, ARSO_FLIP); c.m &= ~(1u << q0)
     // CX X^m = X^{m'} CX with m' = m ^ (target bit if the control bit is in m)
 #define ARSO_CX(P) rg_cx<P>(a, p0, (c.tpart >> q0) & 1u); if (ARSO_FLIP) c.m ^= 1u << q1
     switch (op.pad[0] & 255u) {
@@ -557,10 +557,10 @@ __device__ __forceinline__ void apply_op(Amps &a, TileCtx &c, const RegOp &op, c
         }
         ARSO_P4(OP_DENSE1, ARSO_D1)
         case OP_H: rg_h_lanes(a, ARSO_FLIP ? -1.f : 1.f); c.m &= ~(1u << q0); break;
-        case OP_H + 2: ARSO_H(1); break;
-        case OP_H + 4: ARSO_H(2); break;
-        case OP_H + 6: ARSO_H(3); break;
-        case OP_H + 8: ARSO_H(4); break;
+        case OP_H + 2: ARSO_HADAMARD(1); break;
+        case OP_H + 4: ARSO_HADAMARD(2); break;
+        case OP_H + 6: ARSO_HADAMARD(3); break;
+        case OP_H + 8: ARSO_HADAMARD(4); break;
         case OP_CZ_RR + 0: case OP_CZ_RR + 4: case OP_CZ_RR + 8: case OP_CZ_RR + 12: case OP_CZ_RR + 16:
         case OP_CZ_RR + 20: case OP_CZ_RR + 24: case OP_CZ_RR + 28: case OP_CZ_RR + 32: case OP_CZ_RR + 36:
         case OP_CZ_RT + 0: case OP_CZ_RT + 2: case OP_CZ_RT + 4: case OP_CZ_RT + 6: case OP_CZ_RT + 8:
@@ -604,7 +604,7 @@ __device__ __forceinline__ void apply_op(Amps &a, TileCtx &c, const RegOp &op, c
 #undef ARSO_UB
 #undef ARSO_SU2
 #undef ARSO_D1
-#undef ARSO_H
+#undef ARSO_HADAMARD
 #undef ARSO_CX
 }
 #undef ARSO_P4
