@@ -569,14 +569,20 @@ void launch_expect_resident(const DGate *gates, const void *mats, int n, int pre
 
 // The same expectations for a complex64 state in HBM: per-block partial sums,
 // then one thread adds the blocks in order (deterministic).
+// Each thread sums its few pairs in FP32 (GB300's FP64 rate is a small
+// fraction of FP32); the block and grid sums are FP64.
 __global__ void expect_partials_kernel(const float2 *__restrict__ psi, int n, uint32_t q, double *partials) {
     __shared__ double red[3][32];
     const uint64_t half = 1ull << (n - 1), bit = 1ull << q, lo = bit - 1;
-    double x = 0.0, z = 0.0, y = 0.0;
+    float xf = 0.f, zf = 0.f, yf = 0.f;
     for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < half; p += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t i0 = ((p & ~lo) << 1) | (p & lo);
-        pauli_terms(psi[i0], psi[i0 | bit], x, z, y);
+        const float2 a0 = psi[i0], a1 = psi[i0 | bit];
+        zf += a0.x * a0.x + a0.y * a0.y - a1.x * a1.x - a1.y * a1.y;
+        xf += 2.f * (a0.x * a1.x + a0.y * a1.y);
+        yf += 2.f * (a0.x * a1.y - a0.y * a1.x);
     }
+    double x = xf, z = zf, y = yf;
     block_sum3(x, z, y, red);
     if (threadIdx.x == 0) {
         partials[3 * blockIdx.x] = x;
