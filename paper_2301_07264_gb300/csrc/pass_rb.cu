@@ -648,6 +648,39 @@ __device__ __forceinline__ void stage_wait() {
     __syncthreads();
 }
 
+// Criterion partial of one thread's 32 amplitudes (true index of register ri:
+// (tpart | register part) ^ m, mapped to memory by idx). Fidelity overlaps and
+// outcome/binning probabilities are summed over the 32 registers in FP32 and
+// then added to the FP64 partial (GB300's FP64 rate is a small fraction of its
+// FP32 rate; the block and trajectory sums stay FP64); argmax compares FP64
+// probabilities amplitude by amplitude.
+template <class Index>
+__device__ __forceinline__ void score_registers(Partial &acc, const DCrit &crit, const Amps &v, const TileCtx &c,
+                                                const float2 *__restrict__ ref, Index idx) {
+    if (crit.kind == ARSO_CRIT_ARGMAX) {
+#pragma unroll
+        for (int ri = 0; ri < 32; ++ri) accumulate(acc, crit, amp_get(v, ri), ref, idx((c.tpart | reg_part(ri, c.R)) ^ c.m));
+        return;
+    }
+    float fa = 0.f, fb = 0.f;
+#pragma unroll
+    for (int ri = 0; ri < 32; ++ri) {
+        const uint64_t gi = idx((c.tpart | reg_part(ri, c.R)) ^ c.m);
+        const float2 x = amp_get(v, ri);
+        if (crit.kind == ARSO_CRIT_FIDELITY) {
+            const float2 r = ref[gi];
+            fa = fmaf(r.x, x.x, fmaf(r.y, x.y, fa));
+            fb = fmaf(r.x, x.y, fmaf(-r.y, x.x, fb));
+        } else {
+            const bool in = crit.kind == ARSO_CRIT_OUTCOME ? gi == crit.target
+                                                            : ((crit.bitmap[gi >> 5] >> (gi & 31)) & 1u) != 0;
+            if (in) fa = fmaf(x.x, x.x, fmaf(x.y, x.y, fa));
+        }
+    }
+    acc.a += (double)fa;
+    acc.b += (double)fb;
+}
+
 // global offset of the tile's first amplitude: the tile index deposited into
 // the global bits outside the tile
 __device__ __forceinline__ uint64_t tile_base(uint64_t rest_mask, uint64_t tile) {
@@ -738,11 +771,7 @@ __global__ void __launch_bounds__(512, 1) pass_rb_kernel(PassArgs a) {
     if (!a.ideal && !a.store_last && a.pass == a.end_pass[slot]) {
         const float2 *ref = static_cast<const float2 *>(a.cache) + (size_t)a.cache_slot[a.pass + 1] * N;
         Partial acc = empty_partial();
-#pragma unroll
-        for (int ri = 0; ri < 32; ++ri) {
-            const uint32_t jj = (c.tpart | reg_part(ri, c.R)) ^ c.m;
-            accumulate(acc, a.crit, amp_get(v, ri), ref, gidx(base, jj));
-        }
+        score_registers(acc, a.crit, v, c, ref, [&](uint32_t j) { return gidx(base, j); });
         acc = block_reduce_partial(acc, red);
         if (threadIdx.x == 0) a.partials[(size_t)slot * gridDim.x + blockIdx.x] = acc;
         return;
@@ -865,11 +894,7 @@ __global__ void __launch_bounds__(512, 1) resident_rb_kernel(ResidentArgs a) {
             apply_global_phase(v, c);
             const float2 *ref = cache + (size_t)(a.n_ckpt - 1) * N;
             Partial acc = empty_partial();
-#pragma unroll
-            for (int ri = 0; ri < 32; ++ri) {
-                const uint32_t jj = (c.tpart | reg_part(ri, c.R)) ^ c.m;
-                accumulate(acc, a.crit, amp_get(v, ri), ref, jj);
-            }
+            score_registers(acc, a.crit, v, c, ref, [](uint32_t j) { return (uint64_t)j; });
             acc = block_reduce_partial(acc, red);
             if (threadIdx.x == 0) {
                 const double sc = finish_score(a.crit, acc);
@@ -960,11 +985,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2)
         apply_global_phase(v, c);
         const float2 *ref = C.cache + (size_t)(C.n_ckpt - 1) * N;
         Partial acc = empty_partial();
-#pragma unroll
-        for (int ri = 0; ri < 32; ++ri) {
-            const uint32_t jj = (c.tpart | reg_part(ri, c.R)) ^ c.m;
-            accumulate(acc, C.crit, amp_get(v, ri), ref, jj);
-        }
+        score_registers(acc, C.crit, v, c, ref, [](uint32_t j) { return (uint64_t)j; });
         // per sub-group reduction: warps reduce by shuffles, the sub-group leader combines its warps
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
