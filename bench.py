@@ -14,6 +14,13 @@ folded Pauli errors, fused fidelity reduction and aggregation.
 Prints ONE JSON line (rank 0). Under torchrun every rank runs its own
 trajectory range (weak scaling, no collective on the data path); the time is
 the max over ranks after a barrier.
+
+Other configurations (--workload): grover12 (Grover, 11 search qubits + 1
+borrowed, 16 rates, argmax), mix256 (256 uneven circuits of 8-22 qubits with
+autotuned tiles), search (surrogate-bracketed vs plain tolerable-rate search),
+exhaustive (single-error analysis by one sweep vs by trajectories), qv
+(quantum-volume heavy-output probability), families (tolerable rate of the
+paper's circuit families, 1/G fits and the 56-qubit extrapolation).
 """
 from __future__ import annotations
 
