@@ -154,6 +154,21 @@ def errored_fraction(L):
     return sum(1.0 - (1.0 - p) ** L for p in P_RATES) / len(P_RATES)
 
 
+def grover_cpu_baseline(seconds):
+    """The FP64 oracle on the Grover-12 sweep, bounded: the first gates of one
+    trajectory's simulation; a trajectory with an error simulates all G gates
+    (the GPU path restarts from a cached prefix; the oracle does not)."""
+    from workloads import circuits as C
+    circ = C.grover12(0)
+    rates = [10 ** (-5 + 3 * i / 15) for i in range(16)]
+    frac = sum(1.0 - (1.0 - p) ** circ.L for p in rates) / len(rates)
+    sg, g = oracle_sample(circ, seconds=seconds)
+    return {"value": 1.0 / (frac * circ.G * sg), "unit": "traj/s", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 numpy oracle simulate() of the first {g} gates of one Grover-12 trajectory "
+                      f"({sg * 1e6:.1f} us/gate, single-threaded); traj/s = 1 / (errored fraction {frac:.3f} x "
+                      f"G {circ.G} x sec/gate)"}
+
+
 def run_reference(args):
     """--impl reference: the FP64 CPU oracle timed on this host's cores."""
     ws, rank, _ = _dist()
@@ -378,6 +393,8 @@ def main():
         from paper_2301_07264_gb300 import bench_workloads
         line = bench_workloads.run(args)
         if line is not None:
+            if args.workload == "grover12" and not args.no_cpu_baseline:
+                line["cpu_baseline"] = grover_cpu_baseline(args.cpu_seconds)
             print(json.dumps(line), flush=True)
         return 0
     return run_ours(args)
