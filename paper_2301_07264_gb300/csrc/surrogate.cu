@@ -15,6 +15,7 @@
 
 #include "kernels.h"
 #include "prof.h"
+#include "umma.cuh"
 
 namespace arso {
 
@@ -24,53 +25,373 @@ constexpr size_t OFF_W1 = 0, OFF_B1 = OFF_W1 + IN * HID, OFF_W2 = OFF_B1 + HID, 
 static_assert(N_PARAMS == ARSO_SURROGATE_PARAMS, "parameter layout");
 
 // ------------------------------------------------------------------ GEMM ---
-// C[m, n] = epi( sum_k A(m, k) B(k, n) ), A(m, k) = A[m * sam + k * sak],
-// B(k, n) = B[k * sbk + n * sbn]; epilogue: + bias[n], relu, or * (mask > 0).
-enum { EPI_NONE = 0, EPI_BIAS_RELU = 1, EPI_BIAS = 2, EPI_RELU_MASK = 3 };
+// C[m, n] = epi( sum_k A(m, k) B(n, k) ) on the tensor cores (tcgen05, kind::f16):
+// one CTA per 128 x 128 output tile, FP32 accumulator in tensor memory, K in
+// blocks of 64 staged through two shared-memory buffers. Operands are read with
+// element strides, A(m, k) = A[m * sr + k * sk], and converted on the way into
+// shared memory: a bfloat16 operand goes in as it is; an FP32 operand is split
+// into bfloat16 terms x = x0 + x1 + x2 + r, x0 = bf16(x), x1 = bf16(x - x0),
+// x2 = bf16(x - x0 - x1), |r| <= 2^-27 |x|. Products of bfloat16 are exact in
+// FP32 and the tile accumulates the terms A_i B_j with i + j <= 2 (three against
+// bfloat16 weights, six for two FP32 operands); each dropped term is below about
+// 2^-24 of its product, so the result is an FP32 product up to the accumulation.
+// With gridDim.z > 1 each z takes one K chunk and writes its partial tile to
+// C + z * M * ldc; splitk_sum_kernel adds the chunks in a fixed order.
+enum { EPI_NONE = 0, EPI_BIAS_RELU = 1, EPI_RELU_MASK = 3 };
 
-__device__ __forceinline__ float ldf(const float *p) { return *p; }
-__device__ __forceinline__ float ldf(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+constexpr int GM_BM = 128, GM_BN = 128, GM_BK = 64, GM_THREADS = 256;
+constexpr int GM_NT = HID / GM_BN;  // output tiles across a hidden layer (partial logits)
+constexpr int GM_A_BYTES = GM_BM * GM_BK * 2, GM_B_BYTES = GM_BN * GM_BK * 2;
+constexpr int GM_STAGE_BYTES = 2 * GM_A_BYTES + 2 * GM_B_BYTES;  // two planes of A and two of B
+constexpr int GM_TILE_BYTES = 2 * GM_STAGE_BYTES;
+constexpr int GM_SMEM = GM_TILE_BYTES + 64 + 2 * GM_BM * 4;     // + barriers, tmem slot, logit halves
+constexpr uint32_t GM_IDESC = idesc_bf16_f32(GM_BM, GM_BN);
 
-template <typename TA, typename TB>
-__global__ void gemm_kernel(int M, int N, int K, const TA *__restrict__ A, long sam, long sak, const TB *__restrict__ B,
-                            long sbk, long sbn, float *__restrict__ C, int epi, const TB *__restrict__ bias,
-                            const float *__restrict__ mask) {
-    __shared__ float As[16][17], Bs[16][17];
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int m = blockIdx.y * 16 + ty, n = blockIdx.x * 16 + tx;
-    float acc = 0.f;
-    for (int k0 = 0; k0 < K; k0 += 16) {
-        const int ka = k0 + tx, kb = k0 + ty;
-        As[ty][tx] = (m < M && ka < K) ? ldf(A + (long)m * sam + (long)ka * sak) : 0.f;
-        Bs[ty][tx] = (kb < K && n < N) ? ldf(B + (long)kb * sbk + (long)n * sbn) : 0.f;
-        __syncthreads();
+struct GemmOperand {
+    const void *p;
+    long sr, sk;  // element strides along the row (m or n) and along k
+    int bf16;     // 1: bfloat16 elements, 0: FP32 (split into hi + lo)
+};
+
+struct GemmArgs {
+    int M, N, K, k_chunk;
+    GemmOperand a, b;
+    float *C;  // NULL: no store (the fused logit is the only output)
+    long ldc;
+    int epi;
+    const __nv_bfloat16 *bias;
+    const float *mask;
+    long ldm;
+    const __nv_bfloat16 *w3;  // EPI_BIAS_RELU: z[blockIdx.x * M + m] = sum over this tile's n of relu(...)[m, n] w3[n]
+    float *z;
+    unsigned *err;
+};
+
+__device__ unsigned g_gemm_err;
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
+           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
+}
+
+// Stage rows [r0, r0 + R) x k [k0, k0 + 64) of an operand (zero outside
+// rows < r_end, k < k_end) as `terms` bfloat16 planes (1 for a bfloat16 operand).
+// Shared layout of a plane: 16-byte unit (r, kc) holds k = 8 kc .. 8 kc + 7 of row r
+// at unit ((r / 8) * 8 + kc) * 8 + r % 8, so each 8 x 8 core matrix is 128
+// contiguous bytes, K-adjacent core matrices are 128 bytes apart and row groups 1024.
+__device__ __forceinline__ float bf16_bits_to_float(uint32_t packed, int half) {
+    return __uint_as_float(((packed >> (16 * half)) & 0xFFFFu) << 16);
+}
+
+template <int R>
+__device__ __forceinline__ void stage_operand(const GemmOperand &o, int r0, int r_end, int k0, int k_end, int terms,
+                                              uint4 *p0, uint4 *p1, uint4 *p2) {
+    constexpr int UNITS = R * 8 / GM_THREADS;  // 16-byte units per thread
+    const bool rows_contiguous = o.sr == 1 && o.sk != 1;
+    // vector path: rows contiguous in k and 16-byte aligned, whole 8-element chunks
+    const bool vec = o.sk == 1 && (o.sr & (o.bf16 ? 7 : 3)) == 0 && ((uintptr_t)o.p & 15) == 0;
+    float v[UNITS][8];
+    int idx[UNITS];
+    // issue every load of the block first, then convert: the loads overlap in flight
 #pragma unroll
-        for (int kk = 0; kk < 16; ++kk) acc = fmaf(As[ty][kk], Bs[kk][tx], acc);
+    for (int j = 0; j < UNITS; ++j) {
+        const int u = threadIdx.x + j * GM_THREADS;
+        int r, kc;
+        if (rows_contiguous) {  // a warp reads 32 consecutive rows at each k
+            r = u % R;
+            kc = u / R;
+        } else {  // eight consecutive rows per quarter warp, k chunks across the warp
+            r = (u & 7) | ((u >> 6) << 3);
+            kc = (u >> 3) & 7;
+        }
+        idx[j] = ((r >> 3) * 8 + kc) * 8 + (r & 7);
+        const int gr = r0 + r, gk = k0 + kc * 8;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[j][i] = 0.f;
+        if (gr >= r_end) continue;
+        const long base = (long)gr * o.sr;
+        if (vec && o.bf16 && gk + 8 <= k_end) {
+            const uint4 x = __ldg(reinterpret_cast<const uint4 *>(static_cast<const __nv_bfloat16 *>(o.p) + base + gk));
+            const uint32_t xw[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[j][i] = bf16_bits_to_float(xw[i >> 1], i & 1);
+        } else if (vec && gk + 8 <= k_end) {
+            const float4 *q = reinterpret_cast<const float4 *>(static_cast<const float *>(o.p) + base + gk);
+            const float4 x0 = __ldg(q), x1 = __ldg(q + 1);
+            v[j][0] = x0.x, v[j][1] = x0.y, v[j][2] = x0.z, v[j][3] = x0.w;
+            v[j][4] = x1.x, v[j][5] = x1.y, v[j][6] = x1.z, v[j][7] = x1.w;
+        } else if (o.bf16) {
+            const __nv_bfloat16 *p = static_cast<const __nv_bfloat16 *>(o.p);
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (gk + i < k_end) v[j][i] = __bfloat162float(p[base + (long)(gk + i) * o.sk]);
+        } else {
+            const float *p = static_cast<const float *>(o.p);
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (gk + i < k_end) v[j][i] = __ldg(p + base + (long)(gk + i) * o.sk);
+        }
+    }
+    uint4 *planes[3] = {p0, p1, p2};
+#pragma unroll
+    for (int j = 0; j < UNITS; ++j) {
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            if (t >= terms) break;
+            uint4 q;
+            q.x = pack_bf16(v[j][0], v[j][1]);
+            q.y = pack_bf16(v[j][2], v[j][3]);
+            q.z = pack_bf16(v[j][4], v[j][5]);
+            q.w = pack_bf16(v[j][6], v[j][7]);
+            planes[t][idx[j]] = q;
+            const uint32_t qw[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[j][i] -= bf16_bits_to_float(qw[i >> 1], i & 1);  // exact in FP32
+        }
+    }
+}
+
+__global__ void __launch_bounds__(GM_THREADS, 1) umma_gemm_kernel(GemmArgs a) {
+    extern __shared__ __align__(1024) uint8_t gm_smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(gm_smem + GM_TILE_BYTES);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(gm_smem + GM_TILE_BYTES + 16);
+    float *s_z = reinterpret_cast<float *>(gm_smem + GM_TILE_BYTES + 64);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * GM_BM, n0 = blockIdx.x * GM_BN;
+    const int kz0 = blockIdx.z * a.k_chunk, kz1 = min(a.K, kz0 + a.k_chunk);
+    const int nkb = (kz1 - kz0 + GM_BK - 1) / GM_BK;
+
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) tmem_alloc(tmem_slot, GM_BN);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    // bfloat16 terms per operand (1: a bfloat16 operand, 3: FP32); two FP32 operands
+    // take six planes and a single buffer, the other cases two buffers
+    const int ta = a.a.bf16 ? 1 : 3, tb = a.b.bf16 ? 1 : 3;
+    const int nst = (ta == 3 && tb == 3) ? 1 : 2;
+    uint32_t parity[2] = {0u, 0u};
+    bool pending[2] = {false, false};
+    bool bad = false;
+    for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % nst;
+        if (pending[s]) {  // the MMAs of block kb - nst read this buffer
+            bad |= !mbar_wait_bounded(bar + s, parity[s]);
+            parity[s] ^= 1u;
+            pending[s] = false;
+        }
+        if (__syncthreads_or(bad)) {
+            bad = true;
+            break;
+        }
+        uint8_t *st = gm_smem + s * GM_STAGE_BYTES;
+        uint4 *pa[3], *pb[3];
+        if (nst == 2) {  // per buffer: A0 | A1 | B0 | B1, with A2 in B1's place when B is bfloat16
+            pa[0] = reinterpret_cast<uint4 *>(st);
+            pa[1] = reinterpret_cast<uint4 *>(st + GM_A_BYTES);
+            pb[0] = reinterpret_cast<uint4 *>(st + 2 * GM_A_BYTES);
+            pb[1] = pa[2] = reinterpret_cast<uint4 *>(st + 2 * GM_A_BYTES + GM_B_BYTES);
+            pb[2] = nullptr;
+        } else {  // one buffer: A0 | A1 | A2 | B0 | B1 | B2
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                pa[t] = reinterpret_cast<uint4 *>(st + t * GM_A_BYTES);
+                pb[t] = reinterpret_cast<uint4 *>(st + 3 * GM_A_BYTES + t * GM_B_BYTES);
+            }
+        }
+        const int k0 = kz0 + kb * GM_BK;
+        stage_operand<GM_BM>(a.a, m0, a.M, k0, kz1, ta, pa[0], pa[1], pa[2]);
+        stage_operand<GM_BN>(a.b, n0, a.N, k0, kz1, tb, pb[0], pb[1], pb[2]);
+        fence_proxy_async_smem();
         __syncthreads();
+        if (threadIdx.x == 0) {
+            tc_fence_after();
+            uint32_t sa[3], sb[3];
+#pragma unroll
+            for (int t = 0; t < 3; ++t) sa[t] = smem_u32(pa[t]), sb[t] = smem_u32(pb[t]);
+#pragma unroll 1
+            for (int k = 0; k < GM_BK / 16; ++k) {  // 16 k per MMA: two core matrices along K
+                const uint32_t off = k * 256;
+                // the terms A_i B_j with i + j <= 2, largest first
+                for (int i = 0; i < ta; ++i)
+                    for (int j = 0; j < tb && i + j <= 2; ++j)
+                        umma_bf16(tmem, smem_desc_kmajor(sa[i] + off, 128, 1024),
+                                  smem_desc_kmajor(sb[j] + off, 128, 1024), GM_IDESC,
+                                  (kb > 0 || k > 0 || i > 0 || j > 0) ? 1u : 0u);
+            }
+            umma_commit(bar + s);
+        }
+        pending[s] = true;
     }
-    if (m < M && n < N) {
-        if (epi == EPI_BIAS_RELU) acc = fmaxf(acc + ldf(bias + n), 0.f);
-        else if (epi == EPI_BIAS) acc += ldf(bias + n);
-        else if (epi == EPI_RELU_MASK) acc = mask[(long)m * N + n] > 0.f ? acc : 0.f;
-        C[(long)m * N + n] = acc;
+    for (int s = 0; s < 2; ++s)
+        if (pending[s]) {
+            bad |= !mbar_wait_bounded(bar + s, parity[s]);
+            parity[s] ^= 1u;
+        }
+    bad = __syncthreads_or(bad) || nkb == 0;
+    tc_fence_after();
+
+    if (!bad) {
+        // warp w reads lanes (rows) 32 (w mod 4) .. +31 and column half w / 4; each
+        // 32 x 32 chunk turns through a padded tile in the (now idle) operand buffers
+        // so that a warp stores, and reads the mask, one row segment at a time
+        const int q = warp & 3, h = warp >> 2;
+        const int mw = m0 + q * 32;
+        float *C = a.C ? a.C + (size_t)blockIdx.z * a.M * a.ldc : nullptr;
+        float(*T)[33] = reinterpret_cast<float(*)[33]>(gm_smem + warp * (32 * 33 * 4));
+        float zacc = 0.f;
+#pragma unroll 1
+        for (int c = 0; c < GM_BN / 64; ++c) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * (GM_BN / 2) + c * 32), v);
+            const int nb = n0 + h * (GM_BN / 2) + c * 32;
+            if (a.epi == EPI_BIAS_RELU) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    if (nb + j >= a.N) break;
+                    v[j] = fmaxf(v[j] + __bfloat162float(a.bias[nb + j]), 0.f);
+                    if (a.z) zacc = fmaf(v[j], __bfloat162float(a.w3[nb + j]), zacc);
+                }
+            }
+            if (!C) continue;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) T[lane][j] = v[j];
+            __syncwarp();
+            const int n = nb + lane;
+            if (n < a.N) {
+#pragma unroll 4
+                for (int r = 0; r < 32; ++r) {
+                    const int m = mw + r;
+                    if (m >= a.M) break;
+                    float x = T[r][lane];
+                    if (a.epi == EPI_RELU_MASK) x = a.mask[(size_t)m * a.ldm + n] > 0.f ? x : 0.f;
+                    C[(size_t)m * a.ldc + n] = x;
+                }
+            }
+            __syncwarp();
+        }
+        if (a.z) {
+            s_z[h * GM_BM + q * 32 + lane] = zacc;
+            __syncthreads();
+            if (threadIdx.x < GM_BM && m0 + (int)threadIdx.x < a.M)
+                a.z[(size_t)blockIdx.x * a.M + m0 + threadIdx.x] = s_z[threadIdx.x] + s_z[GM_BM + threadIdx.x];
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_free(tmem, GM_BN);
+    }
+    if (bad && nkb > 0 && threadIdx.x == 0) atomicOr(a.err ? a.err : &g_gemm_err, 1u);
+}
+
+// out[i] = sum over z in order of part[z * n + i]
+__global__ void splitk_sum_kernel(const float *__restrict__ part, int splits, size_t n, float *out) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int z = 0; z < splits; ++z) s += part[(size_t)z * n + i];
+        out[i] = s;
     }
 }
 
-template <typename TA, typename TB>
-static void gemm(int M, int N, int K, const TA *A, long sam, long sak, const TB *B, long sbk, long sbn, float *C, int epi,
-                 const TB *bias, const float *mask, cudaStream_t st) {
-    dim3 block(16, 16), grid((N + 15) / 16, (M + 15) / 16);
-    gemm_kernel<TA, TB><<<grid, block, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, epi, bias, mask);
+struct GemmScratch {
+    DeviceBuffer part;
+};
+
+// C = epi(A B^T) for the operands above; K > GM_SPLIT_K is split across CTAs
+// (weight gradients, K = batch rows) and reduced in a fixed order.
+constexpr int GM_SPLIT_K = 512;
+
+static void umma_gemm(int M, int N, int K, GemmOperand A, GemmOperand B, float *C, long ldc, int epi,
+                      const __nv_bfloat16 *bias, const float *mask, long ldm, const __nv_bfloat16 *w3, float *z,
+                      GemmScratch *scratch, cudaStream_t st) {
+    static uint64_t attr_set = 0;  // one bit per device
+    int dev = 0;
+    ARSO_CUDA(cudaGetDevice(&dev));
+    if (dev >= 64 || !(attr_set >> dev & 1)) {
+        ARSO_CUDA(cudaFuncSetAttribute(umma_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, GM_SMEM));
+        if (dev < 64) attr_set |= 1ull << dev;
+    }
+    if (A.bf16 && !B.bf16) throw Error(ARSO_EINVAL, "tensor-core GEMM: a bfloat16 A needs a bfloat16 B");
+    GemmArgs g{};
+    g.M = M, g.N = N, g.K = K, g.a = A, g.b = B, g.ldc = ldc, g.epi = epi, g.bias = bias, g.mask = mask, g.ldm = ldm;
+    g.w3 = w3, g.z = z, g.err = nullptr;
+    int splits = 1;
+    g.k_chunk = K;
+    if (K > GM_SPLIT_K && scratch) {
+        g.k_chunk = std::max(256, ((K + 63) / 64 + 63) / 64 * 64);  // 256-row chunks, at most about 64 of them
+        splits = (K + g.k_chunk - 1) / g.k_chunk;
+        scratch->part.ensure((size_t)splits * M * N * sizeof(float));
+        g.C = scratch->part.as<float>();
+        g.ldc = N;
+    } else {
+        g.C = C;
+    }
+    dim3 grid((N + GM_BN - 1) / GM_BN, (M + GM_BM - 1) / GM_BM, splits);
+    umma_gemm_kernel<<<grid, GM_THREADS, GM_SMEM, st>>>(g);
     ARSO_CUDA(cudaGetLastError());
+    if (splits > 1) {
+        if (ldc != N) throw Error(ARSO_EINVAL, "split-K output must be dense");
+        const size_t n = (size_t)M * N;
+        splitk_sum_kernel<<<(unsigned)std::min<size_t>((n + 255) / 256, 1024), 256, 0, st>>>(g.C, splits, n, C);
+        ARSO_CUDA(cudaGetLastError());
+    }
 }
 
-// column sums: out[n] = sum_m X[m, n] (bias gradients)
-__global__ void colsum_kernel(const float *__restrict__ X, int M, int N, float *out) {
+// raise ARSO_ETIMEOUT if a GEMM gave up waiting on its tensor-core work (call after a sync)
+static void check_gemm_err() {
+    unsigned e = 0;
+    ARSO_CUDA(cudaMemcpyFromSymbol(&e, g_gemm_err, sizeof(e)));
+    if (e) {
+        const unsigned zero = 0;
+        ARSO_CUDA(cudaMemcpyToSymbol(g_gemm_err, &zero, sizeof(zero)));
+        throw Error(ARSO_ETIMEOUT, "tensor-core GEMM: a bounded wait on its MMAs gave up");
+    }
+}
+
+// Column sums out[n] = sum_m w[m] X[m, n] (w = NULL: 1), in two fixed-order stages:
+// each block sums a 64-row chunk per column, then the chunks are added in order.
+constexpr int CS_ROWS = 64;
+__global__ void colsum_partial_kernel(const float *__restrict__ X, const float *__restrict__ w, int M, int N,
+                                      float *part) {
+    const int n = threadIdx.x + blockIdx.y * blockDim.x;
+    if (n >= N) return;
+    const int r0 = blockIdx.x * CS_ROWS, r1 = min(M, r0 + CS_ROWS);
+    float s = 0.f;
+    for (int r = r0; r < r1; ++r) s = fmaf(X[(size_t)r * N + n], w ? w[r] : 1.f, s);
+    part[(size_t)blockIdx.x * N + n] = s;
+}
+
+__global__ void colsum_finish_kernel(const float *__restrict__ part, int chunks, int N, float *out) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     float s = 0.f;
-    for (int m = 0; m < M; ++m) s += X[(long)m * N + n];
+    for (int c = 0; c < chunks; ++c) s += part[(size_t)c * N + n];
     out[n] = s;
+}
+
+static void colsum(const float *X, const float *w, int M, int N, float *out, DeviceBuffer &part, cudaStream_t st) {
+    const int chunks = (M + CS_ROWS - 1) / CS_ROWS;
+    part.ensure((size_t)chunks * N * sizeof(float));
+    const int bx = std::min(N, 256);
+    colsum_partial_kernel<<<dim3(chunks, (N + bx - 1) / bx), bx, 0, st>>>(X, w, M, N, part.as<float>());
+    colsum_finish_kernel<<<(N + 255) / 256, 256, 0, st>>>(part.as<float>(), chunks, N, out);
+    ARSO_CUDA(cudaGetLastError());
+}
+
+// dh2[i, k] = dz[i] w3[k] where h2[i, k] > 0, else 0
+__global__ void dh2_kernel(const float *__restrict__ dz, const __nv_bfloat16 *__restrict__ w3,
+                           const float *__restrict__ h2, int rows, float *dh2) {
+    const size_t n = (size_t)rows * HID;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dh2[i] = h2[i] > 0.f ? dz[i / HID] * __bfloat162float(w3[i % HID]) : 0.f;
 }
 
 // gather and standardise a batch: xb[i, c] = (x[idx[i], c] - mean[c]) / sd[c]
@@ -82,14 +403,23 @@ __global__ void gather_norm_kernel(const float *__restrict__ x, const uint32_t *
     xb[(long)i * IN + c] = (x[r * IN + c] - norm[c]) / norm[IN + c];
 }
 
+// logit of row i: the output tiles' partial sums, in order, plus the output bias
+__device__ __forceinline__ float logit(const float *__restrict__ zp, int rows, const __nv_bfloat16 *b3, int i) {
+    float z = zp[i];
+#pragma unroll
+    for (int t = 1; t < GM_NT; ++t) z += zp[(size_t)t * rows + i];
+    return z + __bfloat162float(*b3);
+}
+
 // logit gradient of the mean BCE: dz = (sigmoid(z) - y) / B; loss += softplus(z) - y z
-__global__ void bce_kernel(const float *__restrict__ z, const float *__restrict__ y, const uint32_t *__restrict__ idx,
-                           uint64_t base, int rows, float inv_b, float *dz, double *loss_sum) {
+__global__ void bce_kernel(const float *__restrict__ zp, const __nv_bfloat16 *b3, const float *__restrict__ y,
+                           const uint32_t *__restrict__ idx, uint64_t base, int rows, float inv_b, float *dz,
+                           double *loss_sum) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double l = 0.0;
     if (i < rows) {
         const uint64_t r = idx ? idx[base + i] : base + i;
-        const float zi = z[i], yi = y[r];
+        const float zi = logit(zp, rows, b3, i), yi = y[r];
         const float s = 1.f / (1.f + __expf(-zi));
         dz[i] = (s - yi) * inv_b;
         l = (double)(fmaxf(zi, 0.f) + log1pf(__expf(-fabsf(zi))) - yi * zi);
@@ -99,9 +429,9 @@ __global__ void bce_kernel(const float *__restrict__ z, const float *__restrict_
     if ((threadIdx.x & 31) == 0 && l != 0.0) atomicAdd(loss_sum, l);
 }
 
-__global__ void sigmoid_kernel(const float *__restrict__ z, int n, float *out) {
+__global__ void sigmoid_kernel(const float *__restrict__ zp, const __nv_bfloat16 *b3, int n, float *out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = 1.f / (1.f + __expf(-z[i]));
+    if (i < n) out[i] = 1.f / (1.f + __expf(-logit(zp, n, b3, i)));
 }
 
 // Adam (Kingma & Ba 2015) on the FP32 masters; refresh the bfloat16 copies
@@ -162,14 +492,15 @@ struct arso_surrogate {
 namespace arso {
 
 struct Activations {
-    DeviceBuffer xb, h1, h2, z, dz, dh1, dh2, lsum;
+    DeviceBuffer xb, h1, h2, z, dz, dh1, dh2, lsum, cs_part;
+    GemmScratch gs;
     int cap = 0;
     void ensure(int rows) {
         if (rows <= cap) return;
         xb.ensure((size_t)rows * IN * 4);
         h1.ensure((size_t)rows * HID * 4);
         h2.ensure((size_t)rows * HID * 4);
-        z.ensure((size_t)rows * 4);
+        z.ensure((size_t)rows * GM_NT * 4);  // partial logits, one row of them per output tile
         dz.ensure((size_t)rows * 4);
         dh1.ensure((size_t)rows * HID * 4);
         dh2.ensure((size_t)rows * HID * 4);
@@ -186,39 +517,36 @@ static void upload_norm(arso_surrogate *s) {
     ARSO_CUDA(cudaMemcpy(s->norm.ptr, h, sizeof(h), cudaMemcpyHostToDevice));
 }
 
-// forward of `rows` gathered rows: xb -> h1 -> h2 -> z (logits)
-static void mlp_forward(const arso_surrogate *s, Activations &a, int rows, cudaStream_t st) {
+// forward of `rows` gathered rows: xb -> h1 -> h2 -> z (logits); the output layer
+// is fused into the second GEMM's epilogue (keep_h2 = false: h2 is not stored)
+static void mlp_forward(const arso_surrogate *s, Activations &a, int rows, bool keep_h2, cudaStream_t st) {
     const __nv_bfloat16 *w = s->w16.as<__nv_bfloat16>();
-    gemm<float, __nv_bfloat16>(rows, HID, IN, a.xb.as<float>(), IN, 1, w + OFF_W1, HID, 1, a.h1.as<float>(),
-                               EPI_BIAS_RELU, w + OFF_B1, nullptr, st);
-    gemm<float, __nv_bfloat16>(rows, HID, HID, a.h1.as<float>(), HID, 1, w + OFF_W2, HID, 1, a.h2.as<float>(),
-                               EPI_BIAS_RELU, w + OFF_B2, nullptr, st);
-    gemm<float, __nv_bfloat16>(rows, 1, HID, a.h2.as<float>(), HID, 1, w + OFF_W3, 1, 1, a.z.as<float>(), EPI_BIAS,
-                               w + OFF_B3, nullptr, st);
+    umma_gemm(rows, HID, IN, {a.xb.ptr, IN, 1, 0}, {w + OFF_W1, 1, HID, 1}, a.h1.as<float>(), HID, EPI_BIAS_RELU,
+              w + OFF_B1, nullptr, 0, nullptr, nullptr, nullptr, st);
+    umma_gemm(rows, HID, HID, {a.h1.ptr, HID, 1, 0}, {w + OFF_W2, 1, HID, 1}, keep_h2 ? a.h2.as<float>() : nullptr,
+              HID, EPI_BIAS_RELU, w + OFF_B2, nullptr, 0, w + OFF_W3, a.z.as<float>(), nullptr, st);
 }
 
 // gradients of the mean BCE into s->g (FP32) given a.dz
 static void mlp_backward(const arso_surrogate *s, Activations &a, int rows, float *g, cudaStream_t st) {
     const __nv_bfloat16 *w = s->w16.as<__nv_bfloat16>();
     // dW3[k] = sum_i h2[i,k] dz[i]; db3 = sum_i dz[i]
-    gemm<float, float>(HID, 1, rows, a.h2.as<float>(), 1, HID, a.dz.as<float>(), 1, 1, g + OFF_W3, EPI_NONE, nullptr,
-                       nullptr, st);
-    colsum_kernel<<<1, 32, 0, st>>>(a.dz.as<float>(), rows, 1, g + OFF_B3);
+    colsum(a.h2.as<float>(), a.dz.as<float>(), rows, HID, g + OFF_W3, a.cs_part, st);
+    colsum(a.dz.as<float>(), nullptr, rows, 1, g + OFF_B3, a.cs_part, st);
     // dh2[i,k] = dz[i] W3[k] (h2 > 0)
-    gemm<float, __nv_bfloat16>(rows, HID, 1, a.dz.as<float>(), 1, 1, w + OFF_W3, 1, 1, a.dh2.as<float>(),
-                               EPI_RELU_MASK, nullptr, a.h2.as<float>(), st);
-    // dW2 = h1^T dh2; db2 = colsum dh2
-    gemm<float, float>(HID, HID, rows, a.h1.as<float>(), 1, HID, a.dh2.as<float>(), HID, 1, g + OFF_W2, EPI_NONE,
-                       nullptr, nullptr, st);
-    colsum_kernel<<<(HID + 127) / 128, 128, 0, st>>>(a.dh2.as<float>(), rows, HID, g + OFF_B2);
-    // dh1 = dh2 W2^T (h1 > 0)
-    gemm<float, __nv_bfloat16>(rows, HID, HID, a.dh2.as<float>(), HID, 1, w + OFF_W2, 1, HID, a.dh1.as<float>(),
-                               EPI_RELU_MASK, nullptr, a.h1.as<float>(), st);
-    // dW1 = xb^T dh1; db1 = colsum dh1
-    gemm<float, float>(IN, HID, rows, a.xb.as<float>(), 1, IN, a.dh1.as<float>(), HID, 1, g + OFF_W1, EPI_NONE,
-                       nullptr, nullptr, st);
-    colsum_kernel<<<(HID + 127) / 128, 128, 0, st>>>(a.dh1.as<float>(), rows, HID, g + OFF_B1);
+    dh2_kernel<<<1024, 256, 0, st>>>(a.dz.as<float>(), w + OFF_W3, a.h2.as<float>(), rows, a.dh2.as<float>());
     ARSO_CUDA(cudaGetLastError());
+    // dW2[i, j] = sum_b h1[b, i] dh2[b, j]; db2 = colsum dh2
+    umma_gemm(HID, HID, rows, {a.h1.ptr, 1, HID, 0}, {a.dh2.ptr, 1, HID, 0}, g + OFF_W2, HID, EPI_NONE, nullptr,
+              nullptr, 0, nullptr, nullptr, &a.gs, st);
+    colsum(a.dh2.as<float>(), nullptr, rows, HID, g + OFF_B2, a.cs_part, st);
+    // dh1 = dh2 W2^T (h1 > 0)
+    umma_gemm(rows, HID, HID, {a.dh2.ptr, HID, 1, 0}, {w + OFF_W2, HID, 1, 1}, a.dh1.as<float>(), HID, EPI_RELU_MASK,
+              nullptr, a.h1.as<float>(), HID, nullptr, nullptr, nullptr, st);
+    // dW1[i, j] = sum_b xb[b, i] dh1[b, j]; db1 = colsum dh1
+    umma_gemm(IN, HID, rows, {a.xb.ptr, 1, IN, 0}, {a.dh1.ptr, 1, HID, 0}, g + OFF_W1, HID, EPI_NONE, nullptr,
+              nullptr, 0, nullptr, nullptr, &a.gs, st);
+    colsum(a.dh1.as<float>(), nullptr, rows, HID, g + OFF_B1, a.cs_part, st);
 }
 
 static void refresh_bf16(arso_surrogate *s, cudaStream_t st) {
@@ -338,9 +666,9 @@ arso_status arso_surrogate_grads(const arso_surrogate *s, const float *x, const 
         a.ensure((int)n);
         ProfScope ps_(ARSO_K_OTHER, 0.0, st);
         gather_norm_kernel<<<(unsigned)n, 64, 0, st>>>(x, nullptr, 0, (int)n, s->norm.as<float>(), a.xb.as<float>());
-        mlp_forward(s, a, (int)n, st);
+        mlp_forward(s, a, (int)n, true, st);
         ARSO_CUDA(cudaMemsetAsync(a.lsum.ptr, 0, 8, st));
-        bce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a.z.as<float>(), y, nullptr, 0, (int)n, 1.f / (float)n,
+        bce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a.z.as<float>(), s->w16.as<__nv_bfloat16>() + OFF_B3, y, nullptr, 0, (int)n, 1.f / (float)n,
                                                                 a.dz.as<float>(), a.lsum.as<double>());
         DeviceBuffer g;
         g.ensure(N_PARAMS * 4);
@@ -349,6 +677,7 @@ arso_status arso_surrogate_grads(const arso_surrogate *s, const float *x, const 
         double l = 0;
         ARSO_CUDA(cudaMemcpyAsync(&l, a.lsum.ptr, 8, cudaMemcpyDeviceToHost, st));
         ARSO_CUDA(cudaStreamSynchronize(st));
+        check_gemm_err();
         if (loss_out) *loss_out = l / (double)n;
         return ARSO_OK;
     } catch (const Error &e) {
@@ -383,8 +712,8 @@ arso_status arso_surrogate_train(arso_surrogate *s, const float *x, const float 
                 ProfScope ps_(ARSO_K_OTHER, 0.0, st);
                 gather_norm_kernel<<<rows, 64, 0, st>>>(x, d_idx.as<uint32_t>(), b0, rows, s->norm.as<float>(),
                                                         a.xb.as<float>());
-                mlp_forward(s, a, rows, st);
-                bce_kernel<<<(rows + 255) / 256, 256, 0, st>>>(a.z.as<float>(), y, d_idx.as<uint32_t>(), b0, rows,
+                mlp_forward(s, a, rows, true, st);
+                bce_kernel<<<(rows + 255) / 256, 256, 0, st>>>(a.z.as<float>(), s->w16.as<__nv_bfloat16>() + OFF_B3, y, d_idx.as<uint32_t>(), b0, rows,
                                                               1.f / (float)rows, a.dz.as<float>(), a.lsum.as<double>());
                 mlp_backward(s, a, rows, s->g.as<float>(), st);
                 s->t += 1;
@@ -396,6 +725,7 @@ arso_status arso_surrogate_train(arso_surrogate *s, const float *x, const float 
             }
             ARSO_CUDA(cudaMemcpyAsync(&last, a.lsum.ptr, 8, cudaMemcpyDeviceToHost, st));
             ARSO_CUDA(cudaStreamSynchronize(st));
+            check_gemm_err();
         }
         if (loss_out) *loss_out = last / (double)n;
         return ARSO_OK;
@@ -416,11 +746,13 @@ arso_status arso_surrogate_predict(const arso_surrogate *s, const float *x, uint
             const int rows = (int)std::min<uint64_t>(chunk, n - b0);
             ProfScope ps_(ARSO_K_OTHER, 0.0, st);
             gather_norm_kernel<<<rows, 64, 0, st>>>(x, nullptr, b0, rows, s->norm.as<float>(), a.xb.as<float>());
-            mlp_forward(s, a, rows, st);
-            sigmoid_kernel<<<(rows + 255) / 256, 256, 0, st>>>(a.z.as<float>(), rows, out + b0);
+            mlp_forward(s, a, rows, false, st);
+            sigmoid_kernel<<<(rows + 255) / 256, 256, 0, st>>>(a.z.as<float>(), s->w16.as<__nv_bfloat16>() + OFF_B3, rows,
+                                                              out + b0);
             ARSO_CUDA(cudaGetLastError());
         }
         ARSO_CUDA(cudaStreamSynchronize(st));
+        check_gemm_err();
         return ARSO_OK;
     } catch (const Error &e) {
         set_last_error(e.what());
