@@ -332,9 +332,10 @@ arso_status arso_surrogate_grads(const arso_surrogate *s, const float *x, const 
  * log10 p on the surrogate's prediction for the circuit's features, take the
  * bracket [p_s 10^-m, p_s 10^m] (m = opts->surrogate_margin), verify it with
  * opts->n_traj plain trajectories at each end (values straddle P_target),
- * widen it by 10^(2m) per side while it fails (at most 3 times), and answer by
- * log-linear interpolation inside the verified bracket. If it cannot be
- * verified, fall back to arso_tolerable_rate's Monte Carlo search. */
+ * widen it by 10^(2m) per side while it fails (at most 3 times), narrow a
+ * widened bracket back to width 10^(2m) with plain probes (at most 6), and
+ * answer by log-linear interpolation inside the verified bracket. If it cannot
+ * be verified, fall back to arso_tolerable_rate's Monte Carlo search. */
 arso_status arso_tolerable_rate_surrogate(const arso_circuit *c, const arso_criterion *crit, double P_target,
                                           const arso_search_opts *opts, void *stream, arso_rate_result *out);
 
@@ -386,14 +387,16 @@ enum {
     ARSO_K_SAMPLE = 3,      /* Philox error sampling (count + fill) */
     ARSO_K_REDUCE = 4,      /* criterion partials, finish, sums */
     ARSO_K_OTHER = 5,       /* bookkeeping kernels (scan, sort, fill, init) */
-    ARSO_K_COUNT = 6
+    ARSO_K_GEMM = 6,        /* surrogate MLP GEMMs on the tensor cores */
+    ARSO_K_COUNT = 7
 };
 typedef struct {
     uint64_t launches;
     double ms;              /* summed device time (timing enabled only) */
     double bytes;           /* summed algorithmic bytes (timing enabled only) */
-    double flops;           /* summed algorithmic FP32 flops of the register-blocked streaming
-                               passes (timing enabled only; 0 for other kernels) */
+    double flops;           /* summed algorithmic flops (timing enabled only): FP32 flops of the
+                               register-blocked streaming passes, and 2 M N K per M x N x K
+                               surrogate GEMM; 0 for other kernels */
 } arso_kernel_stats;
 arso_status arso_profile_enable(int on);
 arso_status arso_profile_reset(void);

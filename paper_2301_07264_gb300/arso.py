@@ -288,7 +288,7 @@ class KernelStats(C.Structure):
     _fields_ = [("launches", C.c_uint64), ("ms", C.c_double), ("bytes", C.c_double), ("flops", C.c_double)]
 
 
-K_PASS, K_PASS_LAST, K_RESIDENT, K_SAMPLE, K_REDUCE, K_OTHER = range(6)
+K_PASS, K_PASS_LAST, K_RESIDENT, K_SAMPLE, K_REDUCE, K_OTHER, K_GEMM = range(7)
 
 
 def profile_enable(on=True):

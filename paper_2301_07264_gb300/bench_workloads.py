@@ -17,7 +17,7 @@ def _events():
 
 def _kernel_stats(arso):
     names = (("pass", arso.K_PASS), ("pass_last", arso.K_PASS_LAST), ("resident", arso.K_RESIDENT),
-             ("sample", arso.K_SAMPLE), ("reduce", arso.K_REDUCE), ("other", arso.K_OTHER))
+             ("sample", arso.K_SAMPLE), ("reduce", arso.K_REDUCE), ("other", arso.K_OTHER), ("gemm", arso.K_GEMM))
     out = {}
     for name, k in names:
         st = arso.profile_read(k)
@@ -148,6 +148,26 @@ def search(args):
     loss = arso.surrogate_train(s, x, y, epochs=4, batch=8192, lr=2e-3, seed=3)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
+    # the tensor-core GEMMs' share of one profiled training epoch (a fresh network, so the
+    # timed run above is undisturbed): per-launch CUDA events on the library's stream
+    probe = arso.surrogate_create(12)
+    m = min(int(x.shape[0]), 262144)
+    arso.profile_reset()
+    arso.profile_enable(True)
+    arso.surrogate_train(probe, x[:m], y[:m], epochs=1, batch=8192, lr=2e-3, seed=3)
+    torch.cuda.synchronize()
+    arso.profile_enable(False)
+    ks = {name: arso.profile_read(k) for name, k in (("gemm", arso.K_GEMM), ("reduce", arso.K_REDUCE),
+                                                    ("other", arso.K_OTHER))}
+    total_ms = sum(v.ms for v in ks.values())
+    gemm = ks["gemm"]
+    train_info = {"rows": int(x.shape[0]), "epochs": 4, "batch": 8192, "seconds": train_s,
+                  "rows_per_s": 4 * int(x.shape[0]) / train_s,
+                  "profiled_rows": m,
+                  "gemm": {"kernel": "umma_gemm_kernel (tcgen05 kind::f16, TMEM accumulator)",
+                           "launches": gemm.launches, "ms": gemm.ms, "share": gemm.ms / total_ms if total_ms else None,
+                           "useful_tflops": gemm.flops / gemm.ms / 1e9 if gemm.ms else None},
+                  "reduce_ms": ks["reduce"].ms, "other_ms": ks["other"].ms}
     rng = np.random.default_rng(2)
     evals = []
     for k in range(args.search_circuits):
@@ -183,7 +203,7 @@ def search(args):
             "plain_searches_per_s": len(evals) / plain_s, "speedup": plain_s / sur_s,
             "rel_err_max": max(rel), "rel_err_mean": float(np.mean(rel)),
             "verified": sum(r["verified"] for r in rows), "train_loss": loss,
-            "generate_seconds": gen_s, "train_seconds": train_s, "rows": rows}
+            "generate_seconds": gen_s, "train_seconds": train_s, "surrogate_train": train_info, "rows": rows}
 
 
 def exhaustive(args):

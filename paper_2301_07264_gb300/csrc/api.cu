@@ -1522,6 +1522,18 @@ arso_status arso_tolerable_rate_surrogate(const arso_circuit *cc, const arso_cri
             if (v_hi >= P_target && hi < p_hi) hi = std::min(p_hi, hi * std::pow(10.0, 2 * margin)), v_hi = probe(hi);
         }
         if (v_lo >= P_target && v_hi < P_target) {
+            // a widened bracket (the surrogate missed by more than the margin) is narrowed
+            // back to the nominal width 2 margin with plain probes, each placed at the
+            // log-linear interpolation point kept inside the middle 60% of the bracket,
+            // so the final interpolation spans no more than a nominal bracket
+            for (int r = 0; r < 6 && std::log10(hi / lo) > 2 * margin * (1 + 1e-9); ++r) {
+                const double w = std::log10(hi / lo);
+                const double fr = std::min(0.8, std::max(0.2, (v_lo - P_target) / (v_lo - v_hi)));
+                const double pm = std::pow(10.0, std::log10(lo) + fr * w);
+                const double vm = probe(pm);
+                if (vm >= P_target) lo = pm, v_lo = vm;
+                else hi = pm, v_hi = vm;
+            }
             out->verified = 1;
             out->converged = 1;
             out->lo = lo;

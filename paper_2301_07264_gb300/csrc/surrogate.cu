@@ -36,15 +36,17 @@ static_assert(N_PARAMS == ARSO_SURROGATE_PARAMS, "parameter layout");
 // bfloat16 weights, six for two FP32 operands); each dropped term is below about
 // 2^-24 of its product, so the result is an FP32 product up to the accumulation.
 // With gridDim.z > 1 each z takes one K chunk and writes its partial tile to
-// C + z * M * ldc; splitk_sum_kernel adds the chunks in a fixed order.
+// C + z * M * ldc.
 enum { EPI_NONE = 0, EPI_BIAS_RELU = 1, EPI_RELU_MASK = 3 };
 
-constexpr int GM_BM = 128, GM_BN = 128, GM_BK = 64, GM_THREADS = 256;
+constexpr int GM_BM = 128, GM_BN = 128, GM_BK = 64, GM_THREADS = 512;
+constexpr int GM_WG = GM_THREADS / 128;  // warps sharing each 32-row lane quarter (column groups)
+static_assert(GM_BN == GM_WG * 32, "one 32-column chunk per warp in the epilogue");
 constexpr int GM_NT = HID / GM_BN;  // output tiles across a hidden layer (partial logits)
 constexpr int GM_A_BYTES = GM_BM * GM_BK * 2, GM_B_BYTES = GM_BN * GM_BK * 2;
 constexpr int GM_STAGE_BYTES = 2 * GM_A_BYTES + 2 * GM_B_BYTES;  // two planes of A and two of B
 constexpr int GM_TILE_BYTES = 2 * GM_STAGE_BYTES;
-constexpr int GM_SMEM = GM_TILE_BYTES + 64 + 2 * GM_BM * 4;     // + barriers, tmem slot, logit halves
+constexpr int GM_SMEM = GM_TILE_BYTES + 64 + GM_WG * GM_BM * 4;  // + barriers, tmem slot, logit parts
 constexpr uint32_t GM_IDESC = idesc_bf16_f32(GM_BM, GM_BN);
 
 struct GemmOperand {
@@ -64,6 +66,7 @@ struct GemmArgs {
     long ldm;
     const __nv_bfloat16 *w3;  // EPI_BIAS_RELU: z[blockIdx.x * M + m] = sum over this tile's n of relu(...)[m, n] w3[n]
     float *z;
+    float *colsum;  // EPI_RELU_MASK: colsum[blockIdx.y * N + n] = sum of the tile's rows of column n
     unsigned *err;
 };
 
@@ -83,28 +86,34 @@ __device__ __forceinline__ float bf16_bits_to_float(uint32_t packed, int half) {
     return __uint_as_float(((packed >> (16 * half)) & 0xFFFFu) << 16);
 }
 
-template <int R>
-__device__ __forceinline__ void stage_operand(const GemmOperand &o, int r0, int r_end, int k0, int k_end, int terms,
-                                              uint4 *p0, uint4 *p1, uint4 *p2) {
-    constexpr int UNITS = R * 8 / GM_THREADS;  // 16-byte units per thread
-    const bool rows_contiguous = o.sr == 1 && o.sk != 1;
+constexpr int GM_UNITS = GM_BM * 8 / GM_THREADS;  // 16-byte shared-memory units per thread and operand
+static_assert(GM_BM == GM_BN, "both operand tiles stage the same number of units");
+
+// unit j of this thread: row r and k chunk kc of the tile
+__device__ __forceinline__ void unit_of(bool rows_contiguous, int j, int &r, int &kc) {
+    const int u = threadIdx.x + j * GM_THREADS;
+    if (rows_contiguous) {  // a warp reads 32 consecutive rows at each k
+        r = u % GM_BM;
+        kc = u / GM_BM;
+    } else {  // eight consecutive rows per quarter warp, k chunks across the warp
+        r = (u & 7) | ((u >> 6) << 3);
+        kc = (u >> 3) & 7;
+    }
+}
+
+__device__ __forceinline__ bool rows_contiguous(const GemmOperand &o) { return o.sr == 1 && o.sk != 1; }
+
+// Read this thread's units of rows [r0, r0 + 128) x k [k0, k0 + 64) into registers
+// (zero outside rows < r_end, k < k_end); every load is issued before any is used.
+__device__ __forceinline__ void load_operand(const GemmOperand &o, int r0, int r_end, int k0, int k_end,
+                                             float (&v)[GM_UNITS][8]) {
+    const bool rc = rows_contiguous(o);
     // vector path: rows contiguous in k and 16-byte aligned, whole 8-element chunks
     const bool vec = o.sk == 1 && (o.sr & (o.bf16 ? 7 : 3)) == 0 && ((uintptr_t)o.p & 15) == 0;
-    float v[UNITS][8];
-    int idx[UNITS];
-    // issue every load of the block first, then convert: the loads overlap in flight
 #pragma unroll
-    for (int j = 0; j < UNITS; ++j) {
-        const int u = threadIdx.x + j * GM_THREADS;
+    for (int j = 0; j < GM_UNITS; ++j) {
         int r, kc;
-        if (rows_contiguous) {  // a warp reads 32 consecutive rows at each k
-            r = u % R;
-            kc = u / R;
-        } else {  // eight consecutive rows per quarter warp, k chunks across the warp
-            r = (u & 7) | ((u >> 6) << 3);
-            kc = (u >> 3) & 7;
-        }
-        idx[j] = ((r >> 3) * 8 + kc) * 8 + (r & 7);
+        unit_of(rc, j, r, kc);
         const int gr = r0 + r, gk = k0 + kc * 8;
 #pragma unroll
         for (int i = 0; i < 8; ++i) v[j][i] = 0.f;
@@ -132,21 +141,36 @@ __device__ __forceinline__ void stage_operand(const GemmOperand &o, int r0, int 
                 if (gk + i < k_end) v[j][i] = __ldg(p + base + (long)(gk + i) * o.sk);
         }
     }
+}
+
+// Write the registers of load_operand as `terms` bfloat16 planes (1 for a bfloat16
+// operand). Shared layout of a plane: 16-byte unit (r, kc) holds k = 8 kc .. 8 kc + 7
+// of row r at unit ((r / 8) * 8 + kc) * 8 + r % 8, so each 8 x 8 core matrix is 128
+// contiguous bytes, K-adjacent core matrices are 128 bytes apart and row groups 1024.
+__device__ __forceinline__ void store_operand(const GemmOperand &o, float (&v)[GM_UNITS][8], int terms, uint4 *p0,
+                                              uint4 *p1, uint4 *p2) {
+    const bool rc = rows_contiguous(o);
     uint4 *planes[3] = {p0, p1, p2};
 #pragma unroll
-    for (int j = 0; j < UNITS; ++j) {
+    for (int j = 0; j < GM_UNITS; ++j) {
+        int r, kc;
+        unit_of(rc, j, r, kc);
+        const int idx = ((r >> 3) * 8 + kc) * 8 + (r & 7);
+        float x[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = v[j][i];
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
             if (t >= terms) break;
             uint4 q;
-            q.x = pack_bf16(v[j][0], v[j][1]);
-            q.y = pack_bf16(v[j][2], v[j][3]);
-            q.z = pack_bf16(v[j][4], v[j][5]);
-            q.w = pack_bf16(v[j][6], v[j][7]);
-            planes[t][idx[j]] = q;
+            q.x = pack_bf16(x[0], x[1]);
+            q.y = pack_bf16(x[2], x[3]);
+            q.z = pack_bf16(x[4], x[5]);
+            q.w = pack_bf16(x[6], x[7]);
+            planes[t][idx] = q;
             const uint32_t qw[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-            for (int i = 0; i < 8; ++i) v[j][i] -= bf16_bits_to_float(qw[i >> 1], i & 1);  // exact in FP32
+            for (int i = 0; i < 8; ++i) x[i] -= bf16_bits_to_float(qw[i >> 1], i & 1);  // exact in FP32
         }
     }
 }
@@ -205,9 +229,14 @@ __global__ void __launch_bounds__(GM_THREADS, 1) umma_gemm_kernel(GemmArgs a) {
                 pb[t] = reinterpret_cast<uint4 *>(st + 3 * GM_A_BYTES + t * GM_B_BYTES);
             }
         }
-        const int k0 = kz0 + kb * GM_BK;
-        stage_operand<GM_BM>(a.a, m0, a.M, k0, kz1, ta, pa[0], pa[1], pa[2]);
-        stage_operand<GM_BN>(a.b, n0, a.N, k0, kz1, tb, pb[0], pb[1], pb[2]);
+        {
+            float va[GM_UNITS][8], vb[GM_UNITS][8];
+            const int k0 = kz0 + kb * GM_BK;
+            load_operand(a.a, m0, a.M, k0, kz1, va);
+            load_operand(a.b, n0, a.N, k0, kz1, vb);
+            store_operand(a.a, va, ta, pa[0], pa[1], pa[2]);
+            store_operand(a.b, vb, tb, pb[0], pb[1], pb[2]);
+        }
         fence_proxy_async_smem();
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -238,49 +267,64 @@ __global__ void __launch_bounds__(GM_THREADS, 1) umma_gemm_kernel(GemmArgs a) {
     tc_fence_after();
 
     if (!bad) {
-        // warp w reads lanes (rows) 32 (w mod 4) .. +31 and column half w / 4; each
-        // 32 x 32 chunk turns through a padded tile in the (now idle) operand buffers
-        // so that a warp stores, and reads the mask, one row segment at a time
+        // warp w reads lanes (rows) 32 (w mod 4) .. +31 and the 32 columns of group w / 4;
+        // the 32 x 32 chunk turns through a padded tile in the (now idle) operand buffers
+        // so that each store, and each mask read, is one row segment of the warp
         const int q = warp & 3, h = warp >> 2;
-        const int mw = m0 + q * 32;
-        float *C = a.C ? a.C + (size_t)blockIdx.z * a.M * a.ldc : nullptr;
-        float(*T)[33] = reinterpret_cast<float(*)[33]>(gm_smem + warp * (32 * 33 * 4));
-        float zacc = 0.f;
-#pragma unroll 1
-        for (int c = 0; c < GM_BN / 64; ++c) {
-            float v[32];
-            tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * (GM_BN / 2) + c * 32), v);
-            const int nb = n0 + h * (GM_BN / 2) + c * 32;
-            if (a.epi == EPI_BIAS_RELU) {
+        const int mw = m0 + q * 32, nb = n0 + h * 32, n = nb + lane;
+        float mk[32];
+        if (a.epi == EPI_RELU_MASK) {  // all 32 mask loads in flight before the first use
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    if (nb + j >= a.N) break;
-                    v[j] = fmaxf(v[j] + __bfloat162float(a.bias[nb + j]), 0.f);
-                    if (a.z) zacc = fmaf(v[j], __bfloat162float(a.w3[nb + j]), zacc);
-                }
+            for (int r = 0; r < 32; ++r)
+                mk[r] = (n < a.N && mw + r < a.M) ? __ldg(a.mask + (size_t)(mw + r) * a.ldm + n) : 0.f;
+        }
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * 32), v);
+        float zacc = 0.f;
+        if (a.epi == EPI_BIAS_RELU) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                if (nb + j >= a.N) break;
+                v[j] = fmaxf(v[j] + __bfloat162float(a.bias[nb + j]), 0.f);
+                if (a.z) zacc = fmaf(v[j], __bfloat162float(a.w3[nb + j]), zacc);
             }
-            if (!C) continue;
+        }
+        float *C = a.C ? a.C + (size_t)blockIdx.z * a.M * a.ldc : nullptr;
+        if (C) {
+            float(*T)[33] = reinterpret_cast<float(*)[33]>(gm_smem + warp * (32 * 33 * 4));
 #pragma unroll
             for (int j = 0; j < 32; ++j) T[lane][j] = v[j];
             __syncwarp();
-            const int n = nb + lane;
+            float cs = 0.f;
             if (n < a.N) {
-#pragma unroll 4
+#pragma unroll
                 for (int r = 0; r < 32; ++r) {
-                    const int m = mw + r;
-                    if (m >= a.M) break;
-                    float x = T[r][lane];
-                    if (a.epi == EPI_RELU_MASK) x = a.mask[(size_t)m * a.ldm + n] > 0.f ? x : 0.f;
-                    C[(size_t)m * a.ldc + n] = x;
+                    if (mw + r < a.M) {
+                        float x = T[r][lane];
+                        if (a.epi == EPI_RELU_MASK) x = mk[r] > 0.f ? x : 0.f;
+                        C[(size_t)(mw + r) * a.ldc + n] = x;
+                        cs += x;
+                    }
                 }
             }
-            __syncwarp();
+            if (a.colsum) {  // the four row quarters of each column, added in order
+                s_z[h * GM_BM + q * 32 + lane] = cs;
+                __syncthreads();
+                if (q == 0 && n < a.N) {
+                    const float *c4 = s_z + h * GM_BM + lane;
+                    a.colsum[(size_t)blockIdx.y * a.N + n] = ((c4[0] + c4[32]) + c4[64]) + c4[96];
+                }
+            }
         }
         if (a.z) {
             s_z[h * GM_BM + q * 32 + lane] = zacc;
             __syncthreads();
-            if (threadIdx.x < GM_BM && m0 + (int)threadIdx.x < a.M)
-                a.z[(size_t)blockIdx.x * a.M + m0 + threadIdx.x] = s_z[threadIdx.x] + s_z[GM_BM + threadIdx.x];
+            if (threadIdx.x < GM_BM && m0 + (int)threadIdx.x < a.M) {
+                float zs = s_z[threadIdx.x];
+#pragma unroll
+                for (int g = 1; g < GM_WG; ++g) zs += s_z[g * GM_BM + threadIdx.x];
+                a.z[(size_t)blockIdx.x * a.M + m0 + threadIdx.x] = zs;
+            }
         }
     }
     tc_fence_before();
@@ -292,26 +336,13 @@ __global__ void __launch_bounds__(GM_THREADS, 1) umma_gemm_kernel(GemmArgs a) {
     if (bad && nkb > 0 && threadIdx.x == 0) atomicOr(a.err ? a.err : &g_gemm_err, 1u);
 }
 
-// out[i] = sum over z in order of part[z * n + i]
-__global__ void splitk_sum_kernel(const float *__restrict__ part, int splits, size_t n, float *out) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        float s = 0.f;
-        for (int z = 0; z < splits; ++z) s += part[(size_t)z * n + i];
-        out[i] = s;
-    }
-}
-
-struct GemmScratch {
-    DeviceBuffer part;
-};
-
-// C = epi(A B^T) for the operands above; K > GM_SPLIT_K is split across CTAs
-// (weight gradients, K = batch rows) and reduced in a fixed order.
-constexpr int GM_SPLIT_K = 512;
-
-static void umma_gemm(int M, int N, int K, GemmOperand A, GemmOperand B, float *C, long ldc, int epi,
-                      const __nv_bfloat16 *bias, const float *mask, long ldm, const __nv_bfloat16 *w3, float *z,
-                      GemmScratch *scratch, cudaStream_t st) {
+// C = epi(A B^T) for the operands above. With `part` set (weight gradients, K =
+// batch rows) the K range is cut into chunks of at least 256 rows, at most about 64
+// of them, and chunk z writes its M x N partial to part + z * M * N; the caller adds
+// the chunks in order (grad_finish_kernel). Returns the number of chunks.
+static int umma_gemm(int M, int N, int K, GemmOperand A, GemmOperand B, float *C, long ldc, int epi,
+                     const __nv_bfloat16 *bias, const float *mask, long ldm, const __nv_bfloat16 *w3, float *z,
+                     float *colsum, DeviceBuffer *part, cudaStream_t st) {
     static uint64_t attr_set = 0;  // one bit per device
     int dev = 0;
     ARSO_CUDA(cudaGetDevice(&dev));
@@ -322,27 +353,24 @@ static void umma_gemm(int M, int N, int K, GemmOperand A, GemmOperand B, float *
     if (A.bf16 && !B.bf16) throw Error(ARSO_EINVAL, "tensor-core GEMM: a bfloat16 A needs a bfloat16 B");
     GemmArgs g{};
     g.M = M, g.N = N, g.K = K, g.a = A, g.b = B, g.ldc = ldc, g.epi = epi, g.bias = bias, g.mask = mask, g.ldm = ldm;
-    g.w3 = w3, g.z = z, g.err = nullptr;
+    g.w3 = w3, g.z = z, g.colsum = colsum, g.err = nullptr;
     int splits = 1;
     g.k_chunk = K;
-    if (K > GM_SPLIT_K && scratch) {
-        g.k_chunk = std::max(256, ((K + 63) / 64 + 63) / 64 * 64);  // 256-row chunks, at most about 64 of them
+    g.C = C;
+    if (part) {
+        g.k_chunk = std::max(256, ((K + 63) / 64 + 63) / 64 * 64);
         splits = (K + g.k_chunk - 1) / g.k_chunk;
-        scratch->part.ensure((size_t)splits * M * N * sizeof(float));
-        g.C = scratch->part.as<float>();
+        part->ensure((size_t)splits * M * N * sizeof(float));
+        g.C = part->as<float>();
         g.ldc = N;
-    } else {
-        g.C = C;
     }
     dim3 grid((N + GM_BN - 1) / GM_BN, (M + GM_BM - 1) / GM_BM, splits);
+    const double bytes = (double)M * K * (A.bf16 ? 2 : 4) + (double)N * K * (B.bf16 ? 2 : 4) +
+                         (double)M * N * 4 * splits * (g.C ? 1 : 0) + (mask ? (double)M * N * 4 : 0.0);
+    ProfScope ps_(ARSO_K_GEMM, bytes, st, 2.0 * M * N * K);
     umma_gemm_kernel<<<grid, GM_THREADS, GM_SMEM, st>>>(g);
     ARSO_CUDA(cudaGetLastError());
-    if (splits > 1) {
-        if (ldc != N) throw Error(ARSO_EINVAL, "split-K output must be dense");
-        const size_t n = (size_t)M * N;
-        splitk_sum_kernel<<<(unsigned)std::min<size_t>((n + 255) / 256, 1024), 256, 0, st>>>(g.C, splits, n, C);
-        ARSO_CUDA(cudaGetLastError());
-    }
+    return splits;
 }
 
 // raise ARSO_ETIMEOUT if a GEMM gave up waiting on its tensor-core work (call after a sync)
@@ -356,42 +384,51 @@ static void check_gemm_err() {
     }
 }
 
-// Column sums out[n] = sum_m w[m] X[m, n] (w = NULL: 1), in two fixed-order stages:
-// each block sums a 64-row chunk per column, then the chunks are added in order.
-constexpr int CS_ROWS = 64;
-__global__ void colsum_partial_kernel(const float *__restrict__ X, const float *__restrict__ w, int M, int N,
-                                      float *part) {
-    const int n = threadIdx.x + blockIdx.y * blockDim.x;
-    if (n >= N) return;
-    const int r0 = blockIdx.x * CS_ROWS, r1 = min(M, r0 + CS_ROWS);
-    float s = 0.f;
-    for (int r = r0; r < r1; ++r) s = fmaf(X[(size_t)r * N + n], w ? w[r] : 1.f, s);
-    part[(size_t)blockIdx.x * N + n] = s;
+// Output-layer backward over a chunk of DH2_ROWS rows per block, one thread per
+// hidden unit k: dh2[i, k] = dz[i] w3[k] where h2[i, k] > 0 (else 0), and the chunk's
+// partial sums of db2[k] = sum_i dh2[i, k], dW3[k] = sum_i h2[i, k] dz[i] and
+// db3 = sum_i dz[i].
+constexpr int DH2_ROWS = 64;
+__global__ void __launch_bounds__(HID) dh2_kernel(const float *__restrict__ dz, const __nv_bfloat16 *__restrict__ w3,
+                                                  const float *__restrict__ h2, int rows, float *dh2, float *p_b2,
+                                                  float *p_w3, float *p_b3) {
+    const int k = threadIdx.x, c = blockIdx.x;
+    const int r0 = c * DH2_ROWS, r1 = min(rows, r0 + DH2_ROWS);
+    const float w = __bfloat162float(w3[k]);
+    float sb = 0.f, sw = 0.f, sz = 0.f;
+#pragma unroll 8
+    for (int r = r0; r < r1; ++r) {
+        const float d = dz[r], h = h2[(size_t)r * HID + k];
+        const float g = h > 0.f ? d * w : 0.f;
+        dh2[(size_t)r * HID + k] = g;
+        sb += g;
+        sw = fmaf(h, d, sw);
+        sz += d;
+    }
+    p_b2[(size_t)c * HID + k] = sb;
+    p_w3[(size_t)c * HID + k] = sw;
+    if (k == 0) p_b3[c] = sz;
 }
 
-__global__ void colsum_finish_kernel(const float *__restrict__ part, int chunks, int N, float *out) {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
-    float s = 0.f;
-    for (int c = 0; c < chunks; ++c) s += part[(size_t)c * N + n];
-    out[n] = s;
-}
+// Where each parameter block's gradient partials are: count partial arrays of the
+// block's size, `stride` floats apart, summed in order into g.
+struct GradParts {
+    const float *src[6];
+    int count[6];
+};
 
-static void colsum(const float *X, const float *w, int M, int N, float *out, DeviceBuffer &part, cudaStream_t st) {
-    const int chunks = (M + CS_ROWS - 1) / CS_ROWS;
-    part.ensure((size_t)chunks * N * sizeof(float));
-    const int bx = std::min(N, 256);
-    colsum_partial_kernel<<<dim3(chunks, (N + bx - 1) / bx), bx, 0, st>>>(X, w, M, N, part.as<float>());
-    colsum_finish_kernel<<<(N + 255) / 256, 256, 0, st>>>(part.as<float>(), chunks, N, out);
-    ARSO_CUDA(cudaGetLastError());
-}
-
-// dh2[i, k] = dz[i] w3[k] where h2[i, k] > 0, else 0
-__global__ void dh2_kernel(const float *__restrict__ dz, const __nv_bfloat16 *__restrict__ w3,
-                           const float *__restrict__ h2, int rows, float *dh2) {
-    const size_t n = (size_t)rows * HID;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        dh2[i] = h2[i] > 0.f ? dz[i / HID] * __bfloat162float(w3[i % HID]) : 0.f;
+__global__ void grad_finish_kernel(GradParts p, float *__restrict__ g) {
+    const size_t off[7] = {OFF_W1, OFF_B1, OFF_W2, OFF_B2, OFF_W3, OFF_B3, N_PARAMS};
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N_PARAMS; i += (size_t)gridDim.x * blockDim.x) {
+        int b = 0;
+        while (i >= off[b + 1]) ++b;
+        const size_t j = i - off[b], stride = off[b + 1] - off[b];
+        const float *src = p.src[b];
+        float s = 0.f;
+#pragma unroll 8
+        for (int c = 0; c < p.count[b]; ++c) s += src[c * stride + j];
+        g[i] = s;
+    }
 }
 
 // gather and standardise a batch: xb[i, c] = (x[idx[i], c] - mean[c]) / sd[c]
@@ -492,8 +529,8 @@ struct arso_surrogate {
 namespace arso {
 
 struct Activations {
-    DeviceBuffer xb, h1, h2, z, dz, dh1, dh2, lsum, cs_part;
-    GemmScratch gs;
+    DeviceBuffer xb, h1, h2, z, dz, dh1, dh2, lsum;
+    DeviceBuffer pw1, pb1, pw2, pb2, pw3, pb3;  // gradient partials, summed by grad_finish_kernel
     int cap = 0;
     void ensure(int rows) {
         if (rows <= cap) return;
@@ -504,6 +541,11 @@ struct Activations {
         dz.ensure((size_t)rows * 4);
         dh1.ensure((size_t)rows * HID * 4);
         dh2.ensure((size_t)rows * HID * 4);
+        const size_t chunks = (rows + DH2_ROWS - 1) / DH2_ROWS, tiles = (size_t)(rows + GM_BM - 1) / GM_BM;
+        pb1.ensure(tiles * HID * 4);
+        pb2.ensure(chunks * HID * 4);
+        pw3.ensure(chunks * HID * 4);
+        pb3.ensure(chunks * 4);
         lsum.ensure(8);
         cap = rows;
     }
@@ -522,34 +564,58 @@ static void upload_norm(arso_surrogate *s) {
 static void mlp_forward(const arso_surrogate *s, Activations &a, int rows, bool keep_h2, cudaStream_t st) {
     const __nv_bfloat16 *w = s->w16.as<__nv_bfloat16>();
     umma_gemm(rows, HID, IN, {a.xb.ptr, IN, 1, 0}, {w + OFF_W1, 1, HID, 1}, a.h1.as<float>(), HID, EPI_BIAS_RELU,
-              w + OFF_B1, nullptr, 0, nullptr, nullptr, nullptr, st);
+              w + OFF_B1, nullptr, 0, nullptr, nullptr, nullptr, nullptr, st);
     umma_gemm(rows, HID, HID, {a.h1.ptr, HID, 1, 0}, {w + OFF_W2, 1, HID, 1}, keep_h2 ? a.h2.as<float>() : nullptr,
-              HID, EPI_BIAS_RELU, w + OFF_B2, nullptr, 0, w + OFF_W3, a.z.as<float>(), nullptr, st);
+              HID, EPI_BIAS_RELU, w + OFF_B2, nullptr, 0, w + OFF_W3, a.z.as<float>(), nullptr, nullptr, st);
 }
 
-// gradients of the mean BCE into s->g (FP32) given a.dz
+// gradients of the mean BCE into g (FP32) given a.dz: every parameter block is
+// accumulated as partial sums (over batch chunks) that one kernel adds in order
 static void mlp_backward(const arso_surrogate *s, Activations &a, int rows, float *g, cudaStream_t st) {
     const __nv_bfloat16 *w = s->w16.as<__nv_bfloat16>();
-    // dW3[k] = sum_i h2[i,k] dz[i]; db3 = sum_i dz[i]
-    colsum(a.h2.as<float>(), a.dz.as<float>(), rows, HID, g + OFF_W3, a.cs_part, st);
-    colsum(a.dz.as<float>(), nullptr, rows, 1, g + OFF_B3, a.cs_part, st);
-    // dh2[i,k] = dz[i] W3[k] (h2 > 0)
-    dh2_kernel<<<1024, 256, 0, st>>>(a.dz.as<float>(), w + OFF_W3, a.h2.as<float>(), rows, a.dh2.as<float>());
-    ARSO_CUDA(cudaGetLastError());
-    // dW2[i, j] = sum_b h1[b, i] dh2[b, j]; db2 = colsum dh2
-    umma_gemm(HID, HID, rows, {a.h1.ptr, 1, HID, 0}, {a.dh2.ptr, 1, HID, 0}, g + OFF_W2, HID, EPI_NONE, nullptr,
-              nullptr, 0, nullptr, nullptr, &a.gs, st);
-    colsum(a.dh2.as<float>(), nullptr, rows, HID, g + OFF_B2, a.cs_part, st);
-    // dh1 = dh2 W2^T (h1 > 0)
+    const int chunks = (rows + DH2_ROWS - 1) / DH2_ROWS, tiles = (rows + GM_BM - 1) / GM_BM;
+    {   // dh2 = dz W3^T (h2 > 0); partials of db2, dW3, db3
+        ProfScope ps_(ARSO_K_OTHER, (double)rows * HID * 8 + (double)rows * 4, st);
+        dh2_kernel<<<chunks, HID, 0, st>>>(a.dz.as<float>(), w + OFF_W3, a.h2.as<float>(), rows, a.dh2.as<float>(),
+                                           a.pb2.as<float>(), a.pw3.as<float>(), a.pb3.as<float>());
+        ARSO_CUDA(cudaGetLastError());
+    }
+    // dW2[i, j] = sum_b h1[b, i] dh2[b, j]
+    const int s2 = umma_gemm(HID, HID, rows, {a.h1.ptr, 1, HID, 0}, {a.dh2.ptr, 1, HID, 0}, nullptr, HID, EPI_NONE,
+                             nullptr, nullptr, 0, nullptr, nullptr, nullptr, &a.pw2, st);
+    // dh1 = dh2 W2^T (h1 > 0), with the partials of db1 = sum_b dh1[b, :]
     umma_gemm(rows, HID, HID, {a.dh2.ptr, HID, 1, 0}, {w + OFF_W2, HID, 1, 1}, a.dh1.as<float>(), HID, EPI_RELU_MASK,
-              nullptr, a.h1.as<float>(), HID, nullptr, nullptr, nullptr, st);
-    // dW1[i, j] = sum_b xb[b, i] dh1[b, j]; db1 = colsum dh1
-    umma_gemm(IN, HID, rows, {a.xb.ptr, 1, IN, 0}, {a.dh1.ptr, 1, HID, 0}, g + OFF_W1, HID, EPI_NONE, nullptr,
-              nullptr, 0, nullptr, nullptr, &a.gs, st);
-    colsum(a.dh1.as<float>(), nullptr, rows, HID, g + OFF_B1, a.cs_part, st);
+              nullptr, a.h1.as<float>(), HID, nullptr, nullptr, a.pb1.as<float>(), nullptr, st);
+    // dW1[i, j] = sum_b xb[b, i] dh1[b, j]
+    const int s1 = umma_gemm(IN, HID, rows, {a.xb.ptr, 1, IN, 0}, {a.dh1.ptr, 1, HID, 0}, nullptr, HID, EPI_NONE,
+                             nullptr, nullptr, 0, nullptr, nullptr, nullptr, &a.pw1, st);
+    GradParts p{{a.pw1.as<float>(), a.pb1.as<float>(), a.pw2.as<float>(), a.pb2.as<float>(), a.pw3.as<float>(),
+                 a.pb3.as<float>()},
+                {s1, tiles, s2, chunks, chunks, chunks}};
+    const double parts = (double)s1 * IN * HID + (double)tiles * HID + (double)s2 * HID * HID +
+                         (double)chunks * (2 * HID + 1);
+    ProfScope ps_(ARSO_K_REDUCE, (parts + N_PARAMS) * 4, st);
+    grad_finish_kernel<<<(N_PARAMS + 255) / 256, 256, 0, st>>>(p, g);
+    ARSO_CUDA(cudaGetLastError());
+}
+
+static void gather(const float *x, const uint32_t *idx, uint64_t base, int rows, const arso_surrogate *s,
+                   Activations &a, cudaStream_t st) {
+    ProfScope ps_(ARSO_K_OTHER, (double)rows * IN * 8, st);
+    gather_norm_kernel<<<rows, 64, 0, st>>>(x, idx, base, rows, s->norm.as<float>(), a.xb.as<float>());
+    ARSO_CUDA(cudaGetLastError());
+}
+
+static void bce(const arso_surrogate *s, Activations &a, const float *y, const uint32_t *idx, uint64_t base, int rows,
+                cudaStream_t st) {
+    ProfScope ps_(ARSO_K_REDUCE, (double)rows * (GM_NT * 4 + 12), st);
+    bce_kernel<<<(rows + 255) / 256, 256, 0, st>>>(a.z.as<float>(), s->w16.as<__nv_bfloat16>() + OFF_B3, y, idx, base,
+                                                  rows, 1.f / (float)rows, a.dz.as<float>(), a.lsum.as<double>());
+    ARSO_CUDA(cudaGetLastError());
 }
 
 static void refresh_bf16(arso_surrogate *s, cudaStream_t st) {
+    ProfScope ps_(ARSO_K_OTHER, N_PARAMS * 6.0, st);
     to_bf16_kernel<<<64, 256, 0, st>>>(s->w.as<float>(), s->w16.as<__nv_bfloat16>(), N_PARAMS);
     ARSO_CUDA(cudaGetLastError());
 }
@@ -558,8 +624,11 @@ static void ensure_norm(arso_surrogate *s, const float *x, uint64_t n, cudaStrea
     if (s->norm_set) return;
     DeviceBuffer mom;
     mom.ensure(2 * IN * sizeof(double));
-    moments_kernel<<<IN, 256, 0, st>>>(x, n, mom.as<double>());
-    ARSO_CUDA(cudaGetLastError());
+    {
+        ProfScope ps_(ARSO_K_REDUCE, (double)n * IN * 4, st);
+        moments_kernel<<<IN, 256, 0, st>>>(x, n, mom.as<double>());
+        ARSO_CUDA(cudaGetLastError());
+    }
     double h[2 * IN];
     ARSO_CUDA(cudaMemcpyAsync(h, mom.ptr, sizeof(h), cudaMemcpyDeviceToHost, st));
     ARSO_CUDA(cudaStreamSynchronize(st));
@@ -664,12 +733,10 @@ arso_status arso_surrogate_grads(const arso_surrogate *s, const float *x, const 
         cudaStream_t st = (cudaStream_t)stream;
         Activations a;
         a.ensure((int)n);
-        ProfScope ps_(ARSO_K_OTHER, 0.0, st);
-        gather_norm_kernel<<<(unsigned)n, 64, 0, st>>>(x, nullptr, 0, (int)n, s->norm.as<float>(), a.xb.as<float>());
+        gather(x, nullptr, 0, (int)n, s, a, st);
         mlp_forward(s, a, (int)n, true, st);
         ARSO_CUDA(cudaMemsetAsync(a.lsum.ptr, 0, 8, st));
-        bce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a.z.as<float>(), s->w16.as<__nv_bfloat16>() + OFF_B3, y, nullptr, 0, (int)n, 1.f / (float)n,
-                                                                a.dz.as<float>(), a.lsum.as<double>());
+        bce(s, a, y, nullptr, 0, (int)n, st);
         DeviceBuffer g;
         g.ensure(N_PARAMS * 4);
         mlp_backward(s, a, (int)n, g.as<float>(), st);
@@ -709,15 +776,13 @@ arso_status arso_surrogate_train(arso_surrogate *s, const float *x, const float 
             ARSO_CUDA(cudaMemsetAsync(a.lsum.ptr, 0, 8, st));
             for (uint64_t b0 = 0; b0 < n; b0 += batch) {
                 const int rows = (int)std::min<uint64_t>(batch, n - b0);
-                ProfScope ps_(ARSO_K_OTHER, 0.0, st);
-                gather_norm_kernel<<<rows, 64, 0, st>>>(x, d_idx.as<uint32_t>(), b0, rows, s->norm.as<float>(),
-                                                        a.xb.as<float>());
+                gather(x, d_idx.as<uint32_t>(), b0, rows, s, a, st);
                 mlp_forward(s, a, rows, true, st);
-                bce_kernel<<<(rows + 255) / 256, 256, 0, st>>>(a.z.as<float>(), s->w16.as<__nv_bfloat16>() + OFF_B3, y, d_idx.as<uint32_t>(), b0, rows,
-                                                              1.f / (float)rows, a.dz.as<float>(), a.lsum.as<double>());
+                bce(s, a, y, d_idx.as<uint32_t>(), b0, rows, st);
                 mlp_backward(s, a, rows, s->g.as<float>(), st);
                 s->t += 1;
                 const float c1 = 1.f - (float)std::pow(0.9, (double)s->t), c2 = 1.f - (float)std::pow(0.999, (double)s->t);
+                ProfScope ps_(ARSO_K_OTHER, N_PARAMS * 22.0, st);
                 adam_kernel<<<152, 256, 0, st>>>(s->w.as<float>(), s->w16.as<__nv_bfloat16>(), s->g.as<float>(),
                                                  s->m.as<float>(), s->v.as<float>(), N_PARAMS, (float)lr, 0.9f, 0.999f,
                                                  1e-8f, c1, c2);
@@ -744,9 +809,9 @@ arso_status arso_surrogate_predict(const arso_surrogate *s, const float *x, uint
         a.ensure((int)std::min<uint64_t>(n, chunk));
         for (uint64_t b0 = 0; b0 < n; b0 += chunk) {
             const int rows = (int)std::min<uint64_t>(chunk, n - b0);
-            ProfScope ps_(ARSO_K_OTHER, 0.0, st);
-            gather_norm_kernel<<<rows, 64, 0, st>>>(x, nullptr, b0, rows, s->norm.as<float>(), a.xb.as<float>());
+            gather(x, nullptr, b0, rows, s, a, st);
             mlp_forward(s, a, rows, false, st);
+            ProfScope ps_(ARSO_K_OTHER, (double)rows * (GM_NT * 4 + 4), st);
             sigmoid_kernel<<<(rows + 255) / 256, 256, 0, st>>>(a.z.as<float>(), s->w16.as<__nv_bfloat16>() + OFF_B3, rows,
                                                               out + b0);
             ARSO_CUDA(cudaGetLastError());
