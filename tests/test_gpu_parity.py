@@ -413,7 +413,7 @@ def test_brickwork24_full_size_launch(arso):
         psi = statevector.simulate(circ, ev)
         assert torch.max(torch.abs(out[0].cpu() - torch.from_numpy(psi))).item() < AMP_TOL_C64
     full = C.brickwork24(0)
-    cc = arso.compile_circuit(24, full.gates, tile_qubits=14)
+    cc = arso.compile_circuit(24, full.gates)  # the benchmark's tile shape
     T = 64
     p = 1e-3
     errs = arso.sample_errors(cc, p / 3, p / 3, p / 3, 0, 0, T)
@@ -429,6 +429,59 @@ def test_brickwork24_full_size_launch(arso):
     arso.trajectory_states(cc, errs, 0, 2, states)
     norms = torch.sum(torch.abs(states.to(torch.complex128)) ** 2, dim=1).cpu().numpy()
     assert np.all(np.abs(norms - 1.0) < 1e-4)
+
+
+@pytest.fixture(scope="module")
+def brickwork24_single_errors():
+    """Oracle fidelities of brickwork-24 trajectories whose errors all follow one of
+    the first 63 gates. For a Pauli P after gate g the rest of the circuit U is
+    unitary and psi_R = U psi_g, so the fidelity is |<psi_g|P|psi_g>|^2; with P1
+    after g1 and P2 after g2 it is |<psi_g2|P2 V P1|psi_g1>|^2, V the gates between.
+    Locations: X after the SU(2) gate 40, Y after gate 44, Y on the first qubit of
+    the CZ gate 60, Z on the second qubit of the CZ gate 62, and X at 40 with Z at 62."""
+    full = C.brickwork24(0)
+    n = full.n
+    table = statevector.location_table(full)
+    gates_of = {g: [l for l, (gg, _) in enumerate(table) if gg == g] for g in (40, 44, 60, 62)}
+    x40, y44, y60, z62 = ((gates_of[40][0], 1), (gates_of[44][0], 3), (gates_of[60][0], 3), (gates_of[62][1], 2))
+    cases = [[x40], [y44], [y60], [z62], [x40, z62]]
+    psi = statevector.zero_state(n)
+    snap = {}
+    for g in range(63):
+        statevector.apply_gate(psi, n, full.gates[g])
+        if g in gates_of:
+            snap[g] = psi.copy()
+
+    def pauli(state, ev):
+        out = state.copy()
+        statevector.apply_pauli(out, n, table[ev[0]][1], ev[1])
+        return out
+
+    def single(ev):
+        g = table[ev[0]][0]
+        return abs(np.vdot(snap[g], pauli(snap[g], ev))) ** 2
+
+    expected = [single(x40), single(y44), single(y60), single(z62)]
+    branch = pauli(snap[40], x40)
+    for g in range(41, 63):
+        statevector.apply_gate(branch, n, full.gates[g])
+    expected.append(abs(np.vdot(snap[62], pauli(branch, z62))) ** 2)
+    return full, cases, np.array(expected)
+
+
+@pytest.mark.parametrize("suffix_reuse", [True, False])
+def test_brickwork24_full_depth_against_oracle(arso, brickwork24_single_errors, suffix_reuse):
+    """Brickwork-24 depth 40 in the benchmark's launch configuration (default tile,
+    prefix cache): the GPU runs these trajectories through every pass after the
+    first error (suffix reuse off) or stops after the last error's pass and scores
+    against the cached error-free state there (on, as in the benchmark)."""
+    full, cases, expected = brickwork24_single_errors
+    assert np.all((expected[:4] > 0.05) & (expected[:4] < 0.95))  # entangled: neither 0 nor 1
+    cc = arso.compile_circuit(full.n, full.gates, flags=0 if suffix_reuse else arso.OPT_NO_SUFFIX_REUSE)
+    errs = arso.error_list_from_host(cc, cases)
+    score = np.zeros(len(cases))
+    arso.run_trajectories(cc, errs, full.criterion, score)
+    assert np.max(np.abs(score - expected)) < SCORE_TOL, (score, expected)
 
 
 def test_grover12_reference_state_unbiased(arso):
