@@ -6,6 +6,8 @@
 // Weights are bfloat16 (with FP32 masters for Adam); every product
 // accumulates in FP32. The MLP costs ~1.5e5 FMA per row, negligible next to
 // the trajectories that label it, so the kernels are plain tiled SIMT GEMMs.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -51,11 +53,14 @@ constexpr uint32_t GM_IDESC = idesc_bf16_f32(GM_BM, GM_BN);
 
 struct GemmOperand {
     const void *p;
-    long sr, sk;  // element strides along the row (m or n) and along k
-    int bf16;     // 1: bfloat16 elements, 0: FP32 (split into hi + lo)
+    long sr, sk;                // element strides along the row (m or n) and along k
+    int bf16;                   // 1: bfloat16 elements, 0: FP32 (split into bfloat16 terms)
+    const CUtensorMap *tmap;    // B only, optional: the same bfloat16 matrix, K-major, for TMA
 };
 
 struct GemmArgs {
+    CUtensorMap tmb;  // B by TMA (b_tma): 2-D map over (k, n), box of 8 k x 128 rows
+    int b_tma;
     int M, N, K, k_chunk;
     GemmOperand a, b;
     float *C;  // NULL: no store (the fused logit is the only output)
@@ -175,10 +180,11 @@ __device__ __forceinline__ void store_operand(const GemmOperand &o, float (&v)[G
     }
 }
 
-__global__ void __launch_bounds__(GM_THREADS, 1) umma_gemm_kernel(GemmArgs a) {
+__global__ void __launch_bounds__(GM_THREADS, 1) umma_gemm_kernel(const __grid_constant__ GemmArgs a) {
     extern __shared__ __align__(1024) uint8_t gm_smem[];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(gm_smem + GM_TILE_BYTES);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(gm_smem + GM_TILE_BYTES + 16);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(gm_smem + GM_TILE_BYTES);        // buffer free again (MMAs done)
+    uint64_t *full = reinterpret_cast<uint64_t *>(gm_smem + GM_TILE_BYTES + 16);  // B tile landed (TMA)
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(gm_smem + GM_TILE_BYTES + 32);
     float *s_z = reinterpret_cast<float *>(gm_smem + GM_TILE_BYTES + 64);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * GM_BM, n0 = blockIdx.x * GM_BN;
@@ -188,6 +194,8 @@ __global__ void __launch_bounds__(GM_THREADS, 1) umma_gemm_kernel(GemmArgs a) {
     if (threadIdx.x == 0) {
         mbar_init(bar, 1);
         mbar_init(bar + 1, 1);
+        mbar_init(full, 1);
+        mbar_init(full + 1, 1);
         fence_mbar_init();
     }
     if (warp == 0) tmem_alloc(tmem_slot, GM_BN);
@@ -200,7 +208,7 @@ __global__ void __launch_bounds__(GM_THREADS, 1) umma_gemm_kernel(GemmArgs a) {
     // take six planes and a single buffer, the other cases two buffers
     const int ta = a.a.bf16 ? 1 : 3, tb = a.b.bf16 ? 1 : 3;
     const int nst = (ta == 3 && tb == 3) ? 1 : 2;
-    uint32_t parity[2] = {0u, 0u};
+    uint32_t parity[2] = {0u, 0u}, fparity[2] = {0u, 0u};
     bool pending[2] = {false, false};
     bool bad = false;
     for (int kb = 0; kb < nkb; ++kb) {
@@ -221,7 +229,7 @@ __global__ void __launch_bounds__(GM_THREADS, 1) umma_gemm_kernel(GemmArgs a) {
             pa[1] = reinterpret_cast<uint4 *>(st + GM_A_BYTES);
             pb[0] = reinterpret_cast<uint4 *>(st + 2 * GM_A_BYTES);
             pb[1] = pa[2] = reinterpret_cast<uint4 *>(st + 2 * GM_A_BYTES + GM_B_BYTES);
-            pb[2] = nullptr;
+            pb[2] = pb[1];
         } else {  // one buffer: A0 | A1 | A2 | B0 | B1 | B2
 #pragma unroll
             for (int t = 0; t < 3; ++t) {
@@ -229,33 +237,51 @@ __global__ void __launch_bounds__(GM_THREADS, 1) umma_gemm_kernel(GemmArgs a) {
                 pb[t] = reinterpret_cast<uint4 *>(st + 3 * GM_A_BYTES + t * GM_B_BYTES);
             }
         }
+        const int k0 = kz0 + kb * GM_BK;
+        if (a.b_tma && threadIdx.x == 0) {
+            // B by TMA: one 8 k x 128 row box per k chunk, 2 KB apart, so that row
+            // groups are 128 bytes apart and k chunks 2048 (the descriptor below)
+            mbar_arrive_expect_tx(full + s, GM_B_BYTES);
+#pragma unroll
+            for (int c = 0; c < GM_BK / 8; ++c)
+                tma_load_2d(reinterpret_cast<uint8_t *>(pb[0]) + c * (GM_BN * 16), &a.tmb, k0 + 8 * c, n0, full + s);
+        }
         {
-            float va[GM_UNITS][8], vb[GM_UNITS][8];
-            const int k0 = kz0 + kb * GM_BK;
+            float va[GM_UNITS][8];
             load_operand(a.a, m0, a.M, k0, kz1, va);
-            load_operand(a.b, n0, a.N, k0, kz1, vb);
+            if (!a.b_tma) {
+                float vb[GM_UNITS][8];
+                load_operand(a.b, n0, a.N, k0, kz1, vb);
+                store_operand(a.b, vb, tb, pb[0], pb[1], pb[2]);
+            }
             store_operand(a.a, va, ta, pa[0], pa[1], pa[2]);
-            store_operand(a.b, vb, tb, pb[0], pb[1], pb[2]);
         }
         fence_proxy_async_smem();
         __syncthreads();
         if (threadIdx.x == 0) {
+            bool landed = true;
+            if (a.b_tma) {
+                landed = mbar_wait_bounded(full + s, fparity[s]);
+                bad |= !landed;
+            }
             tc_fence_after();
             uint32_t sa[3], sb[3];
 #pragma unroll
             for (int t = 0; t < 3; ++t) sa[t] = smem_u32(pa[t]), sb[t] = smem_u32(pb[t]);
+            // thread-staged planes: k chunks 128 bytes apart, row groups 1024
+            const uint32_t b_lbo = a.b_tma ? GM_BN * 16 : 128, b_sbo = a.b_tma ? 128 : 1024;
 #pragma unroll 1
-            for (int k = 0; k < GM_BK / 16; ++k) {  // 16 k per MMA: two core matrices along K
-                const uint32_t off = k * 256;
+            for (int k = 0; k < GM_BK / 16 && landed; ++k) {  // 16 k per MMA: two core matrices along K
                 // the terms A_i B_j with i + j <= 2, largest first
                 for (int i = 0; i < ta; ++i)
                     for (int j = 0; j < tb && i + j <= 2; ++j)
-                        umma_bf16(tmem, smem_desc_kmajor(sa[i] + off, 128, 1024),
-                                  smem_desc_kmajor(sb[j] + off, 128, 1024), GM_IDESC,
+                        umma_bf16(tmem, smem_desc_kmajor(sa[i] + k * 256, 128, 1024),
+                                  smem_desc_kmajor(sb[j] + k * 2 * b_lbo, b_lbo, b_sbo), GM_IDESC,
                                   (kb > 0 || k > 0 || i > 0 || j > 0) ? 1u : 0u);
             }
-            umma_commit(bar + s);
+            umma_commit(bar + s);  // with no MMA issued it arrives at once
         }
+        if (a.b_tma) fparity[s] ^= 1u;
         pending[s] = true;
     }
     for (int s = 0; s < 2; ++s)
@@ -352,6 +378,11 @@ static int umma_gemm(int M, int N, int K, GemmOperand A, GemmOperand B, float *C
     }
     if (A.bf16 && !B.bf16) throw Error(ARSO_EINVAL, "tensor-core GEMM: a bfloat16 A needs a bfloat16 B");
     GemmArgs g{};
+    if (B.tmap) {
+        if (!B.bf16) throw Error(ARSO_EINVAL, "tensor-core GEMM: TMA operands are bfloat16");
+        g.tmb = *B.tmap;
+        g.b_tma = 1;
+    }
     g.M = M, g.N = N, g.K = K, g.a = A, g.b = B, g.ldc = ldc, g.epi = epi, g.bias = bias, g.mask = mask, g.ldm = ldm;
     g.w3 = w3, g.z = z, g.colsum = colsum, g.err = nullptr;
     int splits = 1;
@@ -471,9 +502,27 @@ __global__ void sigmoid_kernel(const float *__restrict__ zp, const __nv_bfloat16
     if (i < n) out[i] = 1.f / (1.f + __expf(-logit(zp, n, b3, i)));
 }
 
+// K-major bfloat16 copies of the weight matrices for the forward GEMMs' TMA loads:
+// W1^T as 256 rows of T1_LD (>= 33) and W2^T as 256 rows of 256, both (n, k) row-major
+constexpr int T1_LD = 64;
+constexpr size_t T_W1 = 0, T_W2 = (size_t)HID * T1_LD, T_SIZE = T_W2 + (size_t)HID * HID;
+
+__device__ __forceinline__ void store_bf16(__nv_bfloat16 *w16, __nv_bfloat16 *w16t, size_t i, float x) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    w16[i] = h;
+    static_assert(OFF_W1 == 0, "W1 leads the parameter vector");
+    if (i < OFF_B1) {
+        const size_t j = i - OFF_W1;  // W1[k][n], k = j / HID
+        w16t[T_W1 + (j % HID) * T1_LD + j / HID] = h;
+    } else if (i >= OFF_W2 && i < OFF_B2) {
+        const size_t j = i - OFF_W2;
+        w16t[T_W2 + (j % HID) * HID + j / HID] = h;
+    }
+}
+
 // Adam (Kingma & Ba 2015) on the FP32 masters; refresh the bfloat16 copies
-__global__ void adam_kernel(float *w, __nv_bfloat16 *w16, const float *__restrict__ g, float *m, float *v, size_t n,
-                            float lr, float b1, float b2, float eps, float c1, float c2) {
+__global__ void adam_kernel(float *w, __nv_bfloat16 *w16, __nv_bfloat16 *w16t, const float *__restrict__ g, float *m,
+                            float *v, size_t n, float lr, float b1, float b2, float eps, float c1, float c2) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const float gi = g[i];
         const float mi = b1 * m[i] + (1.f - b1) * gi;
@@ -482,13 +531,13 @@ __global__ void adam_kernel(float *w, __nv_bfloat16 *w16, const float *__restric
         v[i] = vi;
         const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
         w[i] = wi;
-        w16[i] = __float2bfloat16_rn(wi);
+        store_bf16(w16, w16t, i, wi);
     }
 }
 
-__global__ void to_bf16_kernel(const float *__restrict__ w, __nv_bfloat16 *w16, size_t n) {
+__global__ void to_bf16_kernel(const float *__restrict__ w, __nv_bfloat16 *w16, __nv_bfloat16 *w16t, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        w16[i] = __float2bfloat16_rn(w[i]);
+        store_bf16(w16, w16t, i, w[i]);
 }
 
 // per-column sum and sum of squares (FP64) for the standardisation
@@ -520,7 +569,8 @@ __global__ void moments_kernel(const float *__restrict__ x, uint64_t n, double *
 }  // namespace arso
 
 struct arso_surrogate {
-    arso::DeviceBuffer w, w16, m, v, g, norm;
+    CUtensorMap tm_w1t, tm_w2t, tm_w2;  // TMA maps of W1^T, W2^T (forward) and W2 (dh1)
+    arso::DeviceBuffer w, w16, w16t, m, v, g, norm;
     float mean[arso::IN], sd[arso::IN];
     bool norm_set = false;
     uint64_t t = 0;
@@ -563,9 +613,11 @@ static void upload_norm(arso_surrogate *s) {
 // is fused into the second GEMM's epilogue (keep_h2 = false: h2 is not stored)
 static void mlp_forward(const arso_surrogate *s, Activations &a, int rows, bool keep_h2, cudaStream_t st) {
     const __nv_bfloat16 *w = s->w16.as<__nv_bfloat16>();
-    umma_gemm(rows, HID, IN, {a.xb.ptr, IN, 1, 0}, {w + OFF_W1, 1, HID, 1}, a.h1.as<float>(), HID, EPI_BIAS_RELU,
+    umma_gemm(rows, HID, IN, {a.xb.ptr, IN, 1, 0}, {w + OFF_W1, 1, HID, 1, &s->tm_w1t}, a.h1.as<float>(), HID,
+              EPI_BIAS_RELU,
               w + OFF_B1, nullptr, 0, nullptr, nullptr, nullptr, nullptr, st);
-    umma_gemm(rows, HID, HID, {a.h1.ptr, HID, 1, 0}, {w + OFF_W2, 1, HID, 1}, keep_h2 ? a.h2.as<float>() : nullptr,
+    umma_gemm(rows, HID, HID, {a.h1.ptr, HID, 1, 0}, {w + OFF_W2, 1, HID, 1, &s->tm_w2t},
+              keep_h2 ? a.h2.as<float>() : nullptr,
               HID, EPI_BIAS_RELU, w + OFF_B2, nullptr, 0, w + OFF_W3, a.z.as<float>(), nullptr, nullptr, st);
 }
 
@@ -584,7 +636,8 @@ static void mlp_backward(const arso_surrogate *s, Activations &a, int rows, floa
     const int s2 = umma_gemm(HID, HID, rows, {a.h1.ptr, 1, HID, 0}, {a.dh2.ptr, 1, HID, 0}, nullptr, HID, EPI_NONE,
                              nullptr, nullptr, 0, nullptr, nullptr, nullptr, &a.pw2, st);
     // dh1 = dh2 W2^T (h1 > 0), with the partials of db1 = sum_b dh1[b, :]
-    umma_gemm(rows, HID, HID, {a.dh2.ptr, HID, 1, 0}, {w + OFF_W2, HID, 1, 1}, a.dh1.as<float>(), HID, EPI_RELU_MASK,
+    umma_gemm(rows, HID, HID, {a.dh2.ptr, HID, 1, 0}, {w + OFF_W2, HID, 1, 1, &s->tm_w2}, a.dh1.as<float>(), HID,
+              EPI_RELU_MASK,
               nullptr, a.h1.as<float>(), HID, nullptr, nullptr, a.pb1.as<float>(), nullptr, st);
     // dW1[i, j] = sum_b xb[b, i] dh1[b, j]
     const int s1 = umma_gemm(IN, HID, rows, {a.xb.ptr, 1, IN, 0}, {a.dh1.ptr, 1, HID, 0}, nullptr, HID, EPI_NONE,
@@ -614,9 +667,36 @@ static void bce(const arso_surrogate *s, Activations &a, const float *y, const u
     ARSO_CUDA(cudaGetLastError());
 }
 
+// 2-D TMA map over a row-major bfloat16 matrix of `rows` x `cols` (row stride `ld`
+// elements), box of 8 columns x 128 rows; out-of-range elements read as zero
+static void encode_map(CUtensorMap *m, const void *base, uint64_t cols, uint64_t rows, uint64_t ld) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        ARSO_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !fn) throw Error(ARSO_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[2] = {cols, rows}, strides[1] = {ld * 2};
+    const cuuint32_t box[2] = {8, GM_BN}, estr[2] = {1, 1};
+    const CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw Error(ARSO_ECUDA, "cuTensorMapEncodeTiled failed");
+}
+
+static void make_weight_maps(arso_surrogate *s) {
+    const __nv_bfloat16 *t = s->w16t.as<__nv_bfloat16>();
+    encode_map(&s->tm_w1t, t + T_W1, IN, HID, T1_LD);
+    encode_map(&s->tm_w2t, t + T_W2, HID, HID, HID);
+    encode_map(&s->tm_w2, s->w16.as<__nv_bfloat16>() + OFF_W2, HID, HID, HID);
+}
+
 static void refresh_bf16(arso_surrogate *s, cudaStream_t st) {
     ProfScope ps_(ARSO_K_OTHER, N_PARAMS * 6.0, st);
-    to_bf16_kernel<<<64, 256, 0, st>>>(s->w.as<float>(), s->w16.as<__nv_bfloat16>(), N_PARAMS);
+    to_bf16_kernel<<<64, 256, 0, st>>>(s->w.as<float>(), s->w16.as<__nv_bfloat16>(), s->w16t.as<__nv_bfloat16>(),
+                                       N_PARAMS);
     ARSO_CUDA(cudaGetLastError());
 }
 
@@ -664,6 +744,9 @@ arso_status arso_surrogate_create(uint64_t seed, arso_surrogate **out) {
         fill(OFF_W3, HID, HID);
         s->w.ensure(N_PARAMS * 4);
         s->w16.ensure(N_PARAMS * 2);
+        s->w16t.ensure(T_SIZE * 2);
+        ARSO_CUDA(cudaMemset(s->w16t.ptr, 0, T_SIZE * 2));
+        make_weight_maps(s.get());
         s->m.ensure(N_PARAMS * 4);
         s->v.ensure(N_PARAMS * 4);
         s->g.ensure(N_PARAMS * 4);
@@ -783,9 +866,9 @@ arso_status arso_surrogate_train(arso_surrogate *s, const float *x, const float 
                 s->t += 1;
                 const float c1 = 1.f - (float)std::pow(0.9, (double)s->t), c2 = 1.f - (float)std::pow(0.999, (double)s->t);
                 ProfScope ps_(ARSO_K_OTHER, N_PARAMS * 22.0, st);
-                adam_kernel<<<152, 256, 0, st>>>(s->w.as<float>(), s->w16.as<__nv_bfloat16>(), s->g.as<float>(),
-                                                 s->m.as<float>(), s->v.as<float>(), N_PARAMS, (float)lr, 0.9f, 0.999f,
-                                                 1e-8f, c1, c2);
+                adam_kernel<<<152, 256, 0, st>>>(s->w.as<float>(), s->w16.as<__nv_bfloat16>(),
+                                                 s->w16t.as<__nv_bfloat16>(), s->g.as<float>(), s->m.as<float>(),
+                                                 s->v.as<float>(), N_PARAMS, (float)lr, 0.9f, 0.999f, 1e-8f, c1, c2);
                 ARSO_CUDA(cudaGetLastError());
             }
             ARSO_CUDA(cudaMemcpyAsync(&last, a.lsum.ptr, 8, cudaMemcpyDeviceToHost, st));

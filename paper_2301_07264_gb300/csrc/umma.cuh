@@ -1,7 +1,7 @@
 // Fifth-generation tensor-core primitives for sm_103a (inline PTX): tensor
-// memory allocation, tcgen05.mma issue and commit, tensor-memory loads, and the
-// mbarrier waits that order them. Every wait is bounded: after UMMA_WAIT_LIMIT
-// polls it reports failure instead of spinning on.
+// memory allocation, tcgen05.mma issue and commit, tensor-memory loads, TMA tile
+// loads, and the mbarrier waits that order them. Every wait is bounded: after
+// UMMA_WAIT_LIMIT polls it reports failure instead of spinning on.
 #pragma once
 #include <cstdint>
 
@@ -89,6 +89,23 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                      smem_u32(bar))
                  : "memory");
+}
+
+// expect `bytes` of asynchronous-copy transactions on *bar and arrive once
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// TMA: one 2-D box of the tensor map at (x, y) into shared memory, completing its
+// bytes on *bar. x is the innermost coordinate; x times the element size must be a
+// multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
 }
 
 // 32 consecutive FP32 columns of this thread's tensor-memory lane (warp w reads lanes
