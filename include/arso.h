@@ -328,6 +328,14 @@ arso_status arso_surrogate_set_norm(arso_surrogate *s, const float *mean, const 
  * weights; no update. For checking the backward kernels. */
 arso_status arso_surrogate_grads(const arso_surrogate *s, const float *x, const float *y, uint64_t n, void *stream,
                                  float *grads_out, double *loss_out);
+/* Test support for the failure path of the tensor-core GEMMs (no counterpart in
+ * the paper). Every wait of those kernels on an mbarrier is bounded; one that
+ * gives up skips the remaining MMAs, frees its tensor memory, sets an error word
+ * and returns, and the API call that launched it returns ARSO_ETIMEOUT. This
+ * makes the next GEMM launch whose B operand comes by TMA expect 16 bytes more
+ * than its loads deliver, with a short wait limit, so that its wait runs out;
+ * nothing hangs or faults and the context stays usable. One-shot, process-wide. */
+arso_status arso_debug_stall_next_gemm(void);
 /* Tolerable rate with the surrogate (Sec. IV-D, Monte Carlo branch): bisect
  * log10 p on the surrogate's prediction for the circuit's features, take the
  * bracket [p_s 10^-m, p_s 10^m] (m = opts->surrogate_margin), verify it with

@@ -386,6 +386,7 @@ for _name, _args in {
     "arso_surrogate_set_params": [_vp, _vp],
     "arso_surrogate_set_norm": [_vp, _vp, _vp],
     "arso_surrogate_grads": [_vp, _vp, _vp, C.c_uint64, _vp, _vp, _vp],
+    "arso_debug_stall_next_gemm": [],
     "arso_tolerable_rate_surrogate": [_vp, C.POINTER(Criterion), C.c_double, C.POINTER(SearchOpts), _vp,
                                       C.POINTER(RateResult)],
 }.items():
@@ -455,6 +456,12 @@ def surrogate_grads(s, x, y, stream=None):
     _check(lib.arso_surrogate_grads(s.handle, _ptr(x), _ptr(y), x.shape[0], _stream(stream), g.ctypes.data,
                                     C.byref(loss)))
     return g, loss.value
+
+
+def debug_stall_next_gemm():
+    """Make the next tensor-core GEMM with a TMA operand give up its bounded wait
+    (see include/arso.h); the call that launches it raises ArsoError(ETIMEOUT)."""
+    _check(lib.arso_debug_stall_next_gemm())
 
 
 def tolerable_rate_surrogate(circ, crit, P_target, surrogate, p_lo=0.0, p_hi=0.0, n_traj=0, seed=0, margin=0.0,

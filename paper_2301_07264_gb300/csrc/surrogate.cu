@@ -11,6 +11,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <random>
@@ -73,6 +74,8 @@ struct GemmArgs {
     float *z;
     float *colsum;  // EPI_RELU_MASK: colsum[blockIdx.y * N + n] = sum of the tile's rows of column n
     unsigned *err;
+    uint32_t wait_limit;  // polls per bounded wait
+    uint32_t extra_tx;    // failure-path test: bytes expected beyond what the TMA loads deliver
 };
 
 __device__ unsigned g_gemm_err;
@@ -214,7 +217,7 @@ __global__ void __launch_bounds__(GM_THREADS, 1) umma_gemm_kernel(const __grid_c
     for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % nst;
         if (pending[s]) {  // the MMAs of block kb - nst read this buffer
-            bad |= !mbar_wait_bounded(bar + s, parity[s]);
+            bad |= !mbar_wait_bounded(bar + s, parity[s], a.wait_limit);
             parity[s] ^= 1u;
             pending[s] = false;
         }
@@ -241,7 +244,7 @@ __global__ void __launch_bounds__(GM_THREADS, 1) umma_gemm_kernel(const __grid_c
         if (a.b_tma && threadIdx.x == 0) {
             // B by TMA: one 8 k x 128 row box per k chunk, 2 KB apart, so that row
             // groups are 128 bytes apart and k chunks 2048 (the descriptor below)
-            mbar_arrive_expect_tx(full + s, GM_B_BYTES);
+            mbar_arrive_expect_tx(full + s, GM_B_BYTES + a.extra_tx);
 #pragma unroll
             for (int c = 0; c < GM_BK / 8; ++c)
                 tma_load_2d(reinterpret_cast<uint8_t *>(pb[0]) + c * (GM_BN * 16), &a.tmb, k0 + 8 * c, n0, full + s);
@@ -261,7 +264,7 @@ __global__ void __launch_bounds__(GM_THREADS, 1) umma_gemm_kernel(const __grid_c
         if (threadIdx.x == 0) {
             bool landed = true;
             if (a.b_tma) {
-                landed = mbar_wait_bounded(full + s, fparity[s]);
+                landed = mbar_wait_bounded(full + s, fparity[s], a.wait_limit);
                 bad |= !landed;
             }
             tc_fence_after();
@@ -286,7 +289,7 @@ __global__ void __launch_bounds__(GM_THREADS, 1) umma_gemm_kernel(const __grid_c
     }
     for (int s = 0; s < 2; ++s)
         if (pending[s]) {
-            bad |= !mbar_wait_bounded(bar + s, parity[s]);
+            bad |= !mbar_wait_bounded(bar + s, parity[s], a.wait_limit);
             parity[s] ^= 1u;
         }
     bad = __syncthreads_or(bad) || nkb == 0;
@@ -362,6 +365,9 @@ __global__ void __launch_bounds__(GM_THREADS, 1) umma_gemm_kernel(const __grid_c
     if (bad && nkb > 0 && threadIdx.x == 0) atomicOr(a.err ? a.err : &g_gemm_err, 1u);
 }
 
+// set by arso_debug_stall_next_gemm: the next GEMM with a TMA operand is made to give up
+static std::atomic<bool> g_stall_next_gemm{false};
+
 // C = epi(A B^T) for the operands above. With `part` set (weight gradients, K =
 // batch rows) the K range is cut into chunks of at least 256 rows, at most about 64
 // of them, and chunk z writes its M x N partial to part + z * M * N; the caller adds
@@ -378,6 +384,11 @@ static int umma_gemm(int M, int N, int K, GemmOperand A, GemmOperand B, float *C
     }
     if (A.bf16 && !B.bf16) throw Error(ARSO_EINVAL, "tensor-core GEMM: a bfloat16 A needs a bfloat16 B");
     GemmArgs g{};
+    g.wait_limit = UMMA_WAIT_LIMIT;
+    if (B.tmap && g_stall_next_gemm.exchange(false)) {  // failure-path test (arso_debug_stall_next_gemm)
+        g.extra_tx = 16;
+        g.wait_limit = 1u << 12;
+    }
     if (B.tmap) {
         if (!B.bf16) throw Error(ARSO_EINVAL, "tensor-core GEMM: TMA operands are bfloat16");
         g.tmb = *B.tmap;
@@ -906,6 +917,11 @@ arso_status arso_surrogate_predict(const arso_surrogate *s, const float *x, uint
         set_last_error(e.what());
         return e.status;
     }
+}
+
+arso_status arso_debug_stall_next_gemm(void) {
+    g_stall_next_gemm.store(true);
+    return ARSO_OK;
 }
 
 arso_status arso_circuit_features(const arso_circuit *c, const arso_criterion *crit, float *out) {

@@ -181,3 +181,22 @@ def test_surrogate_search_agrees_with_plain_search(arso):
         assert abs(sur.p - plain.p) / plain.p < 0.05, (circ.family, sur.p, plain.p)
         if sur.verified:
             assert sur.probes < plain.probes
+
+
+def test_gemm_wait_that_runs_out_reports_timeout(arso):
+    """The failure path of the tensor-core GEMM's bounded waits: a launch made to
+    expect more TMA bytes than arrive gives up (no hang, no fault), the call
+    returns ETIMEOUT, and the next call on the same context is correct again."""
+    import time
+    s, p, pb, x, y = _setup(arso, seed=3, n=300)
+    dx = torch.from_numpy(x).cuda()
+    out = torch.empty(x.shape[0], dtype=torch.float32, device="cuda")
+    arso.debug_stall_next_gemm()
+    t0 = time.perf_counter()
+    with pytest.raises(arso.ArsoError) as e:
+        arso.surrogate_predict(s, dx, out)
+    assert e.value.status == arso.ETIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    arso.surrogate_predict(s, dx, out)
+    z, _ = mlp.forward(pb, x.astype(np.float64))
+    assert np.max(np.abs(out.cpu().numpy() - mlp.sigmoid(z))) < 1e-5
