@@ -833,13 +833,26 @@ static bool single_error_fidelities(arso_circuit *c, cudaStream_t st, std::vecto
             copy_d2h(xyz.data(), d_out.ptr, 3 * L * 8, st);
             ARSO_CUDA(cudaStreamSynchronize(st));
         } else {
-            // complex64 state in HBM, one gate and one expectation per launch, in engine order
+            // complex64 state in HBM: each gate in engine order fused with the expectations
+            // of its qubits on the amplitudes it writes; block partials of up to CH gates at a
+            // time, then one ordered reduction per chunk
             const int n = (int)c->n;
-            Scratch psi(st, c->state_bytes()), part(st, 3 * (size_t)expect_hbm_blocks(n) * 8);
-            launch_init_zero_state(psi.ptr, n, ARSO_C64, st);
+            const uint32_t blocks = expect_hbm_blocks(n);
+            const uint64_t CH = 1024;
+            std::vector<uint32_t> loc(G);
+            std::vector<uint8_t> ar(G);
             for (uint64_t pos = 0; pos < G; ++pos) {
-                const HostGate &h = c->gates[c->perm[pos]];
-                if (h.cls != GC_NOP) {
+                loc[pos] = first[c->perm[pos]];
+                ar[pos] = (uint8_t)c->gates[c->perm[pos]].arity;
+            }
+            Scratch psi(st, c->state_bytes()), part(st, CH * blocks * 6 * 8), d_loc(st, G * 4), d_ar(st, G);
+            copy_h2d(d_loc.ptr, loc.data(), G * 4, st);
+            copy_h2d(d_ar.ptr, ar.data(), G, st);
+            launch_init_zero_state(psi.ptr, n, ARSO_C64, st);
+            for (uint64_t c0 = 0; c0 < G; c0 += CH) {
+                const uint64_t c1 = std::min<uint64_t>(G, c0 + CH);
+                for (uint64_t pos = c0; pos < c1; ++pos) {
+                    const HostGate &h = c->gates[c->perm[pos]];
                     DGate d{};
                     d.cls = h.cls == GC_H ? (uint8_t)GC_DENSE1
                           : h.cls == GC_OMEGA ? (uint8_t)GC_DIAG1 : h.cls == GC_CZ ? (uint8_t)GC_DIAG2 : h.cls;
@@ -850,16 +863,14 @@ static bool single_error_fidelities(arso_circuit *c, cudaStream_t st, std::vecto
                     if (h.arity == 1 && d.cls == GC_DIAG1) {
                         m.m[0] = make_float2((float)h.m[0].real(), (float)h.m[0].imag());
                         m.m[1] = make_float2((float)h.m[3].real(), (float)h.m[3].imag());
-                    } else {
+                    } else if (h.cls != GC_NOP) {
                         for (int i = 0; i < (h.arity == 1 ? 4 : 16); ++i)
                             m.m[i] = make_float2((float)h.m[i].real(), (float)h.m[i].imag());
                     }
-                    launch_gate_pairs(psi.as<float2>(), n, d, m, st);
+                    launch_gate_expect(psi.as<float2>(), n, d, m, part.as<double>() + (pos - c0) * blocks * 6, st);
                 }
-                const uint32_t l0 = first[c->perm[pos]];
-                for (int j = 0; j < h.arity; ++j)
-                    launch_expect_hbm(psi.as<float2>(), n, j ? h.q1 : h.q0, part.as<double>(),
-                                      d_out.as<double>() + 3 * (size_t)(l0 + j), st);
+                launch_gate_expect_reduce(part.as<double>(), (uint32_t)(c1 - c0), blocks, d_loc.as<uint32_t>() + c0,
+                                          d_ar.as<uint8_t>() + c0, d_out.as<double>(), st);
             }
             copy_d2h(xyz.data(), d_out.ptr, 3 * L * 8, st);
             ARSO_CUDA(cudaStreamSynchronize(st));

@@ -134,12 +134,18 @@ void launch_init_zero_state(void *psi, int n, int precision, cudaStream_t st);
 // Pauli expectations (<X_q>, <Z_q>, <Y_q>) of the error-free state after each
 // gate: resident circuits run one CTA per cached checkpoint segment
 // (engine positions seg_pos[b] .. seg_pos[b + 1]; out[3 * location + k]), or a
-// complex64 state in HBM (one qubit per launch; partials: 3 * expect_hbm_blocks(n)).
+// complex64 state in HBM (launch_gate_expect below).
 void launch_expect_resident(const DGate *gates, const void *mats, int n, int precision, const void *ckpt,
                             const uint32_t *seg_pos, uint32_t n_seg, const uint32_t *first_loc, double *out,
                             cudaStream_t st);
 uint32_t expect_hbm_blocks(int n);
-void launch_expect_hbm(const float2 *psi, int n, uint32_t q, double *partials, double *out3, cudaStream_t st);
+// One gate fused with the expectations of its qubits on the updated state; block
+// partials at partials + pos * expect_hbm_blocks(n) * 6 (the caller offsets), added
+// in order by launch_gate_expect_reduce for `count` positions (block k: position k,
+// locations loc[k] .. loc[k] + arity[k] - 1).
+void launch_gate_expect(float2 *psi, int n, const DGate &g, const M16 &m, double *partials, cudaStream_t st);
+void launch_gate_expect_reduce(const double *partials, uint32_t count, uint32_t blocks, const uint32_t *loc,
+                               const uint8_t *arity, double *out3, cudaStream_t st);
 
 // sampling (sample.cu)
 struct SampleArgs {

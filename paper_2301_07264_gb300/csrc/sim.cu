@@ -567,47 +567,136 @@ void launch_expect_resident(const DGate *gates, const void *mats, int n, int pre
     ARSO_CUDA(cudaGetLastError());
 }
 
-// The same expectations for a complex64 state in HBM: per-block partial sums,
-// then one thread adds the blocks in order (deterministic).
-// Each thread sums its few pairs in FP32 (GB300's FP64 rate is a small
-// fraction of FP32); the block and grid sums are FP64.
-__global__ void expect_partials_kernel(const float2 *__restrict__ psi, int n, uint32_t q, double *partials) {
+// One gate on a complex64 state in HBM fused with the Pauli expectations of its
+// qubits on the amplitudes it just wrote (the pairs along each of the gate's
+// qubits lie inside the pair or quad a thread updates). Per-thread FP32 sums,
+// FP64 block sums; block b of position `pos` writes partials[(pos * blocks + b) * 6
+// + 3 j + {0, 1, 2}] = (X, Z, Y) terms of the gate's j-th qubit.
+__device__ __forceinline__ void pauli_terms_f(float2 a0, float2 a1, float &x, float &z, float &y) {
+    z += a0.x * a0.x + a0.y * a0.y - a1.x * a1.x - a1.y * a1.y;
+    x += 2.f * (a0.x * a1.x + a0.y * a1.y);
+    y += 2.f * (a0.x * a1.y - a0.y * a1.x);
+}
+
+__global__ void gate_expect_kernel(float2 *psi, int n, DGate g, M16 mm, double *partials) {
     __shared__ double red[3][32];
-    const uint64_t half = 1ull << (n - 1), bit = 1ull << q, lo = bit - 1;
-    float xf = 0.f, zf = 0.f, yf = 0.f;
-    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < half; p += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t i0 = ((p & ~lo) << 1) | (p & lo);
-        const float2 a0 = psi[i0], a1 = psi[i0 | bit];
-        zf += a0.x * a0.x + a0.y * a0.y - a1.x * a1.x - a1.y * a1.y;
-        xf += 2.f * (a0.x * a1.x + a0.y * a1.y);
-        yf += 2.f * (a0.x * a1.y - a0.y * a1.x);
+    const float2 *m16 = mm.m;
+    const float2 m0 = m16[0], m1 = m16[1], m2 = m16[2], m3 = m16[3];
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    float x0 = 0.f, z0 = 0.f, y0 = 0.f, x1 = 0.f, z1 = 0.f, y1 = 0.f;
+    if (g.arity == 1) {
+        const uint64_t bit = 1ull << g.q0, lo = bit - 1;
+        for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < (1ull << (n - 1)); p += stride) {
+            const uint64_t i0 = ((p & ~lo) << 1) | (p & lo), i1 = i0 | bit;
+            float2 a0 = psi[i0], a1 = psi[i1];
+            if (g.cls != GC_NOP) {
+                if (g.cls == GC_X) {
+                    const float2 t = a0;
+                    a0 = a1;
+                    a1 = t;
+                } else if (g.cls == GC_DIAG1) {
+                    a0 = cmul(m0, a0);
+                    a1 = cmul(m1, a1);
+                } else if (g.cls == GC_DENSE1) {
+                    const float2 b0 = cmac2(m0, a0, m1, a1), b1 = cmac2(m2, a0, m3, a1);
+                    a0 = b0;
+                    a1 = b1;
+                }
+                psi[i0] = a0;
+                psi[i1] = a1;
+            }
+            pauli_terms_f(a0, a1, x0, z0, y0);
+        }
+    } else {
+        const uint32_t lo = g.q0 < g.q1 ? g.q0 : g.q1, hi = g.q0 < g.q1 ? g.q1 : g.q0;
+        const uint64_t b0 = 1ull << g.q0, b1 = 1ull << g.q1;
+        for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < (1ull << (n - 2)); p += stride) {
+            uint64_t i = p;
+            i = ((i & ~((1ull << lo) - 1)) << 1) | (i & ((1ull << lo) - 1));
+            i = ((i & ~((1ull << hi) - 1)) << 1) | (i & ((1ull << hi) - 1));
+            const uint64_t idx[4] = {i, i | b0, i | b1, i | b0 | b1};  // local index bit(q0) + 2 bit(q1)
+            float2 a[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) a[k] = psi[idx[k]];
+            if (g.cls != GC_NOP) {
+                float2 b[4];
+                if (g.cls == GC_CX) {
+                    b[0] = a[0], b[1] = a[3], b[2] = a[2], b[3] = a[1];
+                } else if (g.cls == GC_SWAP) {
+                    b[0] = a[0], b[1] = a[2], b[2] = a[1], b[3] = a[3];
+                } else if (g.cls == GC_DIAG2) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) b[k] = cmul(m16[5 * k], a[k]);
+                } else {  // GC_DENSE2
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        float2 acc = cmac2(m16[4 * k], a[0], m16[4 * k + 1], a[1]);
+                        const float2 acc2 = cmac2(m16[4 * k + 2], a[2], m16[4 * k + 3], a[3]);
+                        acc.x += acc2.x;
+                        acc.y += acc2.y;
+                        b[k] = acc;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) psi[idx[k]] = a[k] = b[k];
+            }
+            pauli_terms_f(a[0], a[1], x0, z0, y0);  // along q0
+            pauli_terms_f(a[2], a[3], x0, z0, y0);
+            pauli_terms_f(a[0], a[2], x1, z1, y1);  // along q1
+            pauli_terms_f(a[1], a[3], x1, z1, y1);
+        }
     }
-    double x = xf, z = zf, y = yf;
+    double *out = partials + (size_t)blockIdx.x * 6;
+    double x = x0, z = z0, y = y0;
     block_sum3(x, z, y, red);
-    if (threadIdx.x == 0) {
-        partials[3 * blockIdx.x] = x;
-        partials[3 * blockIdx.x + 1] = z;
-        partials[3 * blockIdx.x + 2] = y;
+    if (threadIdx.x == 0) out[0] = x, out[1] = z, out[2] = y;
+    if (g.arity == 2) {
+        x = x1, z = z1, y = y1;
+        block_sum3(x, z, y, red);
+        if (threadIdx.x == 0) out[3] = x, out[4] = z, out[5] = y;
     }
 }
-__global__ void expect_finish_kernel(const double *partials, uint32_t blocks, double *out3) {
-    double x = 0.0, z = 0.0, y = 0.0;
-    for (uint32_t b = 0; b < blocks; ++b) x += partials[3 * b], z += partials[3 * b + 1], y += partials[3 * b + 2];
-    out3[0] = x;
-    out3[1] = z;
-    out3[2] = y;
+
+// Adds the block partials of `count` gate positions in a fixed order: block k
+// reduces position k and writes (X, Z, Y) of its qubits to out3[3 * (loc[k] + j)].
+__global__ void gate_expect_reduce_kernel(const double *__restrict__ partials, uint32_t blocks,
+                                          const uint32_t *__restrict__ loc, const uint8_t *__restrict__ arity,
+                                          double *out3) {
+    __shared__ double red[6][256];
+    const double *p = partials + (size_t)blockIdx.x * blocks * 6;
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    for (uint32_t b = threadIdx.x; b < blocks; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v[k] += p[(size_t)b * 6 + k];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) red[k][threadIdx.x] = v[k];
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3u * arity[blockIdx.x]) out3[3 * (size_t)loc[blockIdx.x] + threadIdx.x] = red[threadIdx.x][0];
+}
+
+void launch_gate_expect(float2 *psi, int n, const DGate &g, const M16 &m, double *partials, cudaStream_t st) {
+    const uint32_t blocks = expect_hbm_blocks(n);
+    ProfScope ps_(ARSO_K_OTHER, 16.0 * (double)(1ull << n), st);
+    gate_expect_kernel<<<blocks, 256, 0, st>>>(psi, n, g, m, partials);
+    ARSO_CUDA(cudaGetLastError());
+}
+
+void launch_gate_expect_reduce(const double *partials, uint32_t count, uint32_t blocks, const uint32_t *loc,
+                               const uint8_t *arity, double *out3, cudaStream_t st) {
+    if (!count) return;
+    ProfScope ps_(ARSO_K_REDUCE, 48.0 * count * blocks, st);
+    gate_expect_reduce_kernel<<<count, 256, 0, st>>>(partials, blocks, loc, arity, out3);
+    ARSO_CUDA(cudaGetLastError());
 }
 
 uint32_t expect_hbm_blocks(int n) {
     return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(((1ull << (n - 1)) + 255) / 256, 152ull * 8));
-}
-
-void launch_expect_hbm(const float2 *psi, int n, uint32_t q, double *partials, double *out3, cudaStream_t st) {
-    const uint32_t blocks = expect_hbm_blocks(n);
-    ProfScope ps_(ARSO_K_REDUCE, 8.0 * (double)(1ull << n), st);
-    expect_partials_kernel<<<blocks, 256, 0, st>>>(psi, n, q, partials);
-    expect_finish_kernel<<<1, 1, 0, st>>>(partials, blocks, out3);
-    ARSO_CUDA(cudaGetLastError());
 }
 
 }  // namespace arso
