@@ -578,72 +578,105 @@ __device__ __forceinline__ void pauli_terms_f(float2 a0, float2 a1, float &x, fl
     y += 2.f * (a0.x * a1.y - a0.y * a1.x);
 }
 
+// apply the one-qubit class to a pair
+__device__ __forceinline__ void gate1(const DGate &g, float2 m0, float2 m1, float2 m2, float2 m3, float2 &a0,
+                                      float2 &a1) {
+    if (g.cls == GC_X) {
+        const float2 t = a0;
+        a0 = a1;
+        a1 = t;
+    } else if (g.cls == GC_DIAG1) {
+        a0 = cmul(m0, a0);
+        a1 = cmul(m1, a1);
+    } else if (g.cls == GC_DENSE1) {
+        const float2 b0 = cmac2(m0, a0, m1, a1), b1 = cmac2(m2, a0, m3, a1);
+        a0 = b0;
+        a1 = b1;
+    }
+}
+
+// apply the two-qubit class to a quad (local index bit(q0) + 2 bit(q1))
+__device__ __forceinline__ void gate2(const DGate &g, const float2 *m16, float2 (&a)[4]) {
+    float2 b[4];
+    if (g.cls == GC_CX) {
+        b[0] = a[0], b[1] = a[3], b[2] = a[2], b[3] = a[1];
+    } else if (g.cls == GC_SWAP) {
+        b[0] = a[0], b[1] = a[2], b[2] = a[1], b[3] = a[3];
+    } else if (g.cls == GC_DIAG2) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) b[k] = cmul(m16[5 * k], a[k]);
+    } else {  // GC_DENSE2
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float2 acc = cmac2(m16[4 * k], a[0], m16[4 * k + 1], a[1]);
+            const float2 acc2 = cmac2(m16[4 * k + 2], a[2], m16[4 * k + 3], a[3]);
+            acc.x += acc2.x;
+            acc.y += acc2.y;
+            b[k] = acc;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a[k] = b[k];
+}
+
+// UNROLL pairs (quads) per thread and round: every load of a round is issued before
+// the first store, so that more of them are in flight (the pairs are disjoint)
+constexpr int GE_UNROLL = 4;
+
 __global__ void gate_expect_kernel(float2 *psi, int n, DGate g, M16 mm, double *partials) {
     __shared__ double red[3][32];
     const float2 *m16 = mm.m;
     const float2 m0 = m16[0], m1 = m16[1], m2 = m16[2], m3 = m16[3];
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const bool write = g.cls != GC_NOP;
     float x0 = 0.f, z0 = 0.f, y0 = 0.f, x1 = 0.f, z1 = 0.f, y1 = 0.f;
     if (g.arity == 1) {
-        const uint64_t bit = 1ull << g.q0, lo = bit - 1;
-        for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < (1ull << (n - 1)); p += stride) {
-            const uint64_t i0 = ((p & ~lo) << 1) | (p & lo), i1 = i0 | bit;
-            float2 a0 = psi[i0], a1 = psi[i1];
-            if (g.cls != GC_NOP) {
-                if (g.cls == GC_X) {
-                    const float2 t = a0;
-                    a0 = a1;
-                    a1 = t;
-                } else if (g.cls == GC_DIAG1) {
-                    a0 = cmul(m0, a0);
-                    a1 = cmul(m1, a1);
-                } else if (g.cls == GC_DENSE1) {
-                    const float2 b0 = cmac2(m0, a0, m1, a1), b1 = cmac2(m2, a0, m3, a1);
-                    a0 = b0;
-                    a1 = b1;
-                }
-                psi[i0] = a0;
-                psi[i1] = a1;
+        const uint64_t bit = 1ull << g.q0, lo = bit - 1, half = 1ull << (n - 1);
+        for (uint64_t p0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p0 < half; p0 += GE_UNROLL * stride) {
+            float2 a0[GE_UNROLL], a1[GE_UNROLL];
+            uint64_t i0[GE_UNROLL];
+#pragma unroll
+            for (int u = 0; u < GE_UNROLL; ++u) {
+                const uint64_t p = p0 + u * stride;
+                i0[u] = ((p & ~lo) << 1) | (p & lo);
+                if (p < half) a0[u] = psi[i0[u]], a1[u] = psi[i0[u] | bit];
             }
-            pauli_terms_f(a0, a1, x0, z0, y0);
+#pragma unroll
+            for (int u = 0; u < GE_UNROLL; ++u) {
+                if (p0 + u * stride >= half) break;
+                gate1(g, m0, m1, m2, m3, a0[u], a1[u]);
+                if (write) psi[i0[u]] = a0[u], psi[i0[u] | bit] = a1[u];
+                pauli_terms_f(a0[u], a1[u], x0, z0, y0);
+            }
         }
     } else {
         const uint32_t lo = g.q0 < g.q1 ? g.q0 : g.q1, hi = g.q0 < g.q1 ? g.q1 : g.q0;
-        const uint64_t b0 = 1ull << g.q0, b1 = 1ull << g.q1;
-        for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < (1ull << (n - 2)); p += stride) {
-            uint64_t i = p;
-            i = ((i & ~((1ull << lo) - 1)) << 1) | (i & ((1ull << lo) - 1));
-            i = ((i & ~((1ull << hi) - 1)) << 1) | (i & ((1ull << hi) - 1));
-            const uint64_t idx[4] = {i, i | b0, i | b1, i | b0 | b1};  // local index bit(q0) + 2 bit(q1)
-            float2 a[4];
+        const uint64_t b0 = 1ull << g.q0, b1 = 1ull << g.q1, quarter = 1ull << (n - 2);
+        for (uint64_t p0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p0 < quarter; p0 += 2 * stride) {
+            float2 a[2][4];
+            uint64_t base[2];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) a[k] = psi[idx[k]];
-            if (g.cls != GC_NOP) {
-                float2 b[4];
-                if (g.cls == GC_CX) {
-                    b[0] = a[0], b[1] = a[3], b[2] = a[2], b[3] = a[1];
-                } else if (g.cls == GC_SWAP) {
-                    b[0] = a[0], b[1] = a[2], b[2] = a[1], b[3] = a[3];
-                } else if (g.cls == GC_DIAG2) {
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) b[k] = cmul(m16[5 * k], a[k]);
-                } else {  // GC_DENSE2
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        float2 acc = cmac2(m16[4 * k], a[0], m16[4 * k + 1], a[1]);
-                        const float2 acc2 = cmac2(m16[4 * k + 2], a[2], m16[4 * k + 3], a[3]);
-                        acc.x += acc2.x;
-                        acc.y += acc2.y;
-                        b[k] = acc;
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < 4; ++k) psi[idx[k]] = a[k] = b[k];
+            for (int u = 0; u < 2; ++u) {
+                uint64_t i = p0 + u * stride;
+                if (i >= quarter) continue;
+                i = ((i & ~((1ull << lo) - 1)) << 1) | (i & ((1ull << lo) - 1));
+                i = ((i & ~((1ull << hi) - 1)) << 1) | (i & ((1ull << hi) - 1));
+                base[u] = i;
+                a[u][0] = psi[i], a[u][1] = psi[i | b0], a[u][2] = psi[i | b1], a[u][3] = psi[i | b0 | b1];
             }
-            pauli_terms_f(a[0], a[1], x0, z0, y0);  // along q0
-            pauli_terms_f(a[2], a[3], x0, z0, y0);
-            pauli_terms_f(a[0], a[2], x1, z1, y1);  // along q1
-            pauli_terms_f(a[1], a[3], x1, z1, y1);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                if (p0 + u * stride >= quarter) break;
+                if (write) {
+                    gate2(g, m16, a[u]);
+                    const uint64_t i = base[u];
+                    psi[i] = a[u][0], psi[i | b0] = a[u][1], psi[i | b1] = a[u][2], psi[i | b0 | b1] = a[u][3];
+                }
+                pauli_terms_f(a[u][0], a[u][1], x0, z0, y0);  // along q0
+                pauli_terms_f(a[u][2], a[u][3], x0, z0, y0);
+                pauli_terms_f(a[u][0], a[u][2], x1, z1, y1);  // along q1
+                pauli_terms_f(a[u][1], a[u][3], x1, z1, y1);
+            }
         }
     }
     double *out = partials + (size_t)blockIdx.x * 6;
