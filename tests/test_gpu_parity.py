@@ -583,6 +583,21 @@ def test_fast_exhaustive_streaming_matches_oracle(arso):
         assert np.max(np.abs(per[k * circ.L:(k + 1) * circ.L] - a["per_location"][e])) < SCORE_TOL
 
 
+def test_fast_exhaustive_streaming_every_gate_kind(arso):
+    # every gate class (identity, X, diagonal, dense one-qubit, CX, SWAP, diagonal and
+    # dense two-qubit) through the fused gate-and-expectation HBM kernel
+    circ = C.random_circuit(14, 60, 9)
+    crit = C.Criterion("fidelity", threshold=0.5, aggregate="mean")
+    circ.criterion = crit
+    names = {g.name for g in circ.gates}
+    assert {"ID", "X", "CX", "SWAP", "U2", "CP", "U"} <= names
+    cc = arso.compile_circuit(circ.n, circ.gates, tile_qubits=10)
+    P, per = arso.exhaustive(cc, crit)
+    a = ox.analyse(circ)
+    for k, e in enumerate(("X", "Z", "Y")):
+        assert np.max(np.abs(per[k * circ.L:(k + 1) * circ.L] - a["per_location"][e])) < SCORE_TOL
+
+
 @pytest.mark.parametrize("n,kw", [(10, {}), (14, {"tile_qubits": 10})])
 def test_quantum_volume_heavy_output_scores(arso, n, kw):
     # QV circuits (Haar U(4) layers, dense two-qubit gates) scored by binning on
