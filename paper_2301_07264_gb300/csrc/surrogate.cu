@@ -30,8 +30,9 @@ static_assert(N_PARAMS == ARSO_SURROGATE_PARAMS, "parameter layout");
 // ------------------------------------------------------------------ GEMM ---
 // C[m, n] = epi( sum_k A(m, k) B(n, k) ) on the tensor cores (tcgen05, kind::f16):
 // one CTA per 128 x 128 output tile, FP32 accumulator in tensor memory, K in
-// blocks of 64 staged through two shared-memory buffers. Operands are read with
-// element strides, A(m, k) = A[m * sr + k * sk], and converted on the way into
+// blocks of 64 staged through two shared-memory buffers. A bfloat16 B operand with
+// a tensor map comes by TMA; otherwise the CTA's threads read an operand with
+// element strides, A(m, k) = A[m * sr + k * sk], and convert it on the way into
 // shared memory: a bfloat16 operand goes in as it is; an FP32 operand is split
 // into bfloat16 terms x = x0 + x1 + x2 + r, x0 = bf16(x), x1 = bf16(x - x0),
 // x2 = bf16(x - x0 - x1), |r| <= 2^-27 |x|. Products of bfloat16 are exact in
