@@ -184,7 +184,12 @@ __device__ __forceinline__ void store_operand(const GemmOperand &o, float (&v)[G
     }
 }
 
+// One instantiation per operand route, so that each holds only its own staging code:
+// B_MODE 0: bfloat16 B by TMA; 1: bfloat16 B through the threads; 2: FP32 B through
+// the threads (six term products, one buffer). A is FP32 through the threads.
+template <int B_MODE>
 __global__ void __launch_bounds__(GM_THREADS, 1) umma_gemm_kernel(const __grid_constant__ GemmArgs a) {
+    constexpr bool B_TMA = B_MODE == 0;
     extern __shared__ __align__(1024) uint8_t gm_smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(gm_smem + GM_TILE_BYTES);        // buffer free again (MMAs done)
     uint64_t *full = reinterpret_cast<uint64_t *>(gm_smem + GM_TILE_BYTES + 16);  // B tile landed (TMA)
@@ -210,8 +215,8 @@ __global__ void __launch_bounds__(GM_THREADS, 1) umma_gemm_kernel(const __grid_c
 
     // bfloat16 terms per operand (1: a bfloat16 operand, 3: FP32); two FP32 operands
     // take six planes and a single buffer, the other cases two buffers
-    const int ta = a.a.bf16 ? 1 : 3, tb = a.b.bf16 ? 1 : 3;
-    const int nst = (ta == 3 && tb == 3) ? 1 : 2;
+    constexpr int ta = 3, tb = B_MODE == 2 ? 3 : 1;
+    constexpr int nst = tb == 3 ? 1 : 2;
     uint32_t parity[2] = {0u, 0u}, fparity[2] = {0u, 0u};
     bool pending[2] = {false, false};
     bool bad = false;
@@ -242,7 +247,7 @@ __global__ void __launch_bounds__(GM_THREADS, 1) umma_gemm_kernel(const __grid_c
             }
         }
         const int k0 = kz0 + kb * GM_BK;
-        if (a.b_tma && threadIdx.x == 0) {
+        if (B_TMA && threadIdx.x == 0) {
             // B by TMA: one 8 k x 128 row box per k chunk, 2 KB apart, so that row
             // groups are 128 bytes apart and k chunks 2048 (the descriptor below)
             mbar_arrive_expect_tx(full + s, GM_B_BYTES + a.extra_tx);
@@ -253,7 +258,7 @@ __global__ void __launch_bounds__(GM_THREADS, 1) umma_gemm_kernel(const __grid_c
         {
             float va[GM_UNITS][8];
             load_operand(a.a, m0, a.M, k0, kz1, va);
-            if (!a.b_tma) {
+            if (!B_TMA) {
                 float vb[GM_UNITS][8];
                 load_operand(a.b, n0, a.N, k0, kz1, vb);
                 store_operand(a.b, vb, tb, pb[0], pb[1], pb[2]);
@@ -264,7 +269,7 @@ __global__ void __launch_bounds__(GM_THREADS, 1) umma_gemm_kernel(const __grid_c
         __syncthreads();
         if (threadIdx.x == 0) {
             bool landed = true;
-            if (a.b_tma) {
+            if (B_TMA) {
                 landed = mbar_wait_bounded(full + s, fparity[s], a.wait_limit);
                 bad |= !landed;
             }
@@ -273,7 +278,7 @@ __global__ void __launch_bounds__(GM_THREADS, 1) umma_gemm_kernel(const __grid_c
 #pragma unroll
             for (int t = 0; t < 3; ++t) sa[t] = smem_u32(pa[t]), sb[t] = smem_u32(pb[t]);
             // thread-staged planes: k chunks 128 bytes apart, row groups 1024
-            const uint32_t b_lbo = a.b_tma ? GM_BN * 16 : 128, b_sbo = a.b_tma ? 128 : 1024;
+            constexpr uint32_t b_lbo = B_TMA ? GM_BN * 16 : 128, b_sbo = B_TMA ? 128 : 1024;
 #pragma unroll 1
             for (int k = 0; k < GM_BK / 16 && landed; ++k) {  // 16 k per MMA: two core matrices along K
                 // the terms A_i B_j with i + j <= 2, largest first
@@ -285,7 +290,7 @@ __global__ void __launch_bounds__(GM_THREADS, 1) umma_gemm_kernel(const __grid_c
             }
             umma_commit(bar + s);  // with no MMA issued it arrives at once
         }
-        if (a.b_tma) fparity[s] ^= 1u;
+        if (B_TMA) fparity[s] ^= 1u;
         pending[s] = true;
     }
     for (int s = 0; s < 2; ++s)
@@ -380,10 +385,12 @@ static int umma_gemm(int M, int N, int K, GemmOperand A, GemmOperand B, float *C
     int dev = 0;
     ARSO_CUDA(cudaGetDevice(&dev));
     if (dev >= 64 || !(attr_set >> dev & 1)) {
-        ARSO_CUDA(cudaFuncSetAttribute(umma_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, GM_SMEM));
+        ARSO_CUDA(cudaFuncSetAttribute(umma_gemm_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, GM_SMEM));
+        ARSO_CUDA(cudaFuncSetAttribute(umma_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, GM_SMEM));
+        ARSO_CUDA(cudaFuncSetAttribute(umma_gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, GM_SMEM));
         if (dev < 64) attr_set |= 1ull << dev;
     }
-    if (A.bf16 && !B.bf16) throw Error(ARSO_EINVAL, "tensor-core GEMM: a bfloat16 A needs a bfloat16 B");
+    if (A.bf16) throw Error(ARSO_EINVAL, "tensor-core GEMM: A is an FP32 operand");
     GemmArgs g{};
     g.wait_limit = UMMA_WAIT_LIMIT;
     if (B.tmap && g_stall_next_gemm.exchange(false)) {  // failure-path test (arso_debug_stall_next_gemm)
@@ -411,7 +418,9 @@ static int umma_gemm(int M, int N, int K, GemmOperand A, GemmOperand B, float *C
     const double bytes = (double)M * K * (A.bf16 ? 2 : 4) + (double)N * K * (B.bf16 ? 2 : 4) +
                          (double)M * N * 4 * splits * (g.C ? 1 : 0) + (mask ? (double)M * N * 4 : 0.0);
     ProfScope ps_(ARSO_K_GEMM, bytes, st, 2.0 * M * N * K);
-    umma_gemm_kernel<<<grid, GM_THREADS, GM_SMEM, st>>>(g);
+    if (g.b_tma) umma_gemm_kernel<0><<<grid, GM_THREADS, GM_SMEM, st>>>(g);
+    else if (B.bf16) umma_gemm_kernel<1><<<grid, GM_THREADS, GM_SMEM, st>>>(g);
+    else umma_gemm_kernel<2><<<grid, GM_THREADS, GM_SMEM, st>>>(g);
     ARSO_CUDA(cudaGetLastError());
     return splits;
 }
