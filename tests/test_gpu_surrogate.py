@@ -111,6 +111,18 @@ def test_large_batches_match_reference(arso, n):
         assert np.max(np.abs(got[k] - ref[k])) <= 1e-3 * scale + 1e-9, k
 
 
+def test_predict_across_its_row_chunks(arso):
+    # predictions run in chunks of 65536 rows; 70,001 rows cross a chunk boundary and
+    # end in a ragged 128-row tile
+    s, p, pb, x, y = _setup(arso, seed=12, n=96)
+    rng = np.random.default_rng(12)
+    x = rng.standard_normal((70_001, IN)).astype(np.float32)
+    out = torch.empty(x.shape[0], dtype=torch.float32, device="cuda")
+    arso.surrogate_predict(s, torch.from_numpy(x).cuda(), out)
+    z, _ = mlp.forward(pb, x.astype(np.float64))
+    assert np.max(np.abs(out.cpu().numpy() - mlp.sigmoid(z))) < 1e-5
+
+
 def test_gradients_are_deterministic(arso):
     s, p, pb, x, y = _setup(arso, seed=4, n=2500)
     dx, dy = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
