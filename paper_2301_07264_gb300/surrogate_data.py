@@ -16,23 +16,23 @@ from . import arso
 
 
 def rows_for_circuit(cc, crit, log10_ps, traj_per_p, seed, traj_begin=0, stream=None):
-    """Device tensors (x: n x 33 float32, y: n float32) for one compiled circuit."""
+    """Device tensors (x: n x 33 float32, y: n float32) for one compiled circuit; the
+    trajectories of all rates run in one arso_run_batch call."""
     import torch
     f = torch.from_numpy(arso.circuit_features(cc, crit)).cuda()
-    xs, ys = [], []
     c = arso.make_criterion(crit)
+    errs, scores, flags, xs = [], [], [], []
     for i, lp in enumerate(log10_ps):
         p = 10.0 ** float(lp)
-        errs = arso.sample_errors(cc, p / 3, p / 3, p / 3, seed, traj_begin + i * traj_per_p, traj_per_p, stream)
-        score = torch.empty(traj_per_p, dtype=torch.float64, device="cuda")
-        flags = torch.empty(traj_per_p, dtype=torch.uint8, device="cuda")
-        arso.run_trajectories(cc, errs, c, score, flags, stream)
+        errs.append(arso.sample_errors(cc, p / 3, p / 3, p / 3, seed, traj_begin + i * traj_per_p, traj_per_p, stream))
+        scores.append(torch.empty(traj_per_p, dtype=torch.float64, device="cuda"))
+        flags.append(torch.empty(traj_per_p, dtype=torch.uint8, device="cuda"))
         x = torch.empty((traj_per_p, arso.SURROGATE_INPUTS), dtype=torch.float32, device="cuda")
         x[:, : arso.N_FEATURES] = f
         x[:, arso.N_FEATURES] = float(lp)
         xs.append(x)
-        ys.append(flags.to(torch.float32))
-    return torch.cat(xs), torch.cat(ys)
+    arso.run_batch([cc] * len(errs), errs, [c] * len(errs), scores, flags, stream)
+    return torch.cat(xs), torch.cat([fl.to(torch.float32) for fl in flags])
 
 
 def generate(circuits, n_rows, seed, lp_lo=-5.0, lp_hi=-1.0, p_points=16, stream=None):
