@@ -404,6 +404,11 @@ def main():
         if line is not None:
             if args.workload == "grover12" and not args.no_cpu_baseline:
                 line["cpu_baseline"] = grover_cpu_baseline(args.cpu_seconds)
+            if args.workload == "exhaustive" and line.get("hbm_sweep"):
+                peak, src = _peaks()
+                h = line["hbm_sweep"]
+                h["peak_GBps"], h["peak_source"] = peak, src
+                h["frac"] = h["achieved_GBps"] / peak
             if args.workload == "search":
                 g = line["surrogate_train"]["gemm"]
                 peak, src = _bf16_peak()
