@@ -298,7 +298,13 @@ arso_status arso_tolerable_rate(const arso_circuit *c, const arso_criterion *cri
  * Adam, entirely on the GPU. Inputs are standardised with the per-column mean
  * and standard deviation of the training set (stored in the handle).
  * It narrows the bracket of arso_tolerable_rate_surrogate; the plain
- * simulator verifies the bracket and remains the fallback. */
+ * simulator verifies the bracket and remains the fallback.
+ * The GEMMs run on the tensor cores (tcgen05, BF16 operands): FP32 activations
+ * and gradients enter as three bf16 terms each, so products keep FP32 accuracy.
+ * Gradients are summed in a fixed order (bit-reproducible). Errors: ARSO_EINVAL
+ * for NULL pointers or sizes out of range (train: 1 <= n < 2^32, 1 <= batch <=
+ * 65536; grads: 1 <= n <= 2^20), ARSO_ETIMEOUT if a GEMM's bounded wait gave
+ * up, ARSO_ECUDA for a CUDA error. Device rows are caller-owned and only read. */
 #define ARSO_N_FEATURES 32
 #define ARSO_SURROGATE_INPUTS 33
 /* 32 features of a compiled circuit and criterion (host floats): n, G, L, k,
