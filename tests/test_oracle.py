@@ -386,6 +386,132 @@ def test_argmax_tie_lowest_index():
     assert criteria.score(C.Criterion("argmax", target=0), psi) == 1.0
 
 
+# ------------------------------------------ rotation and phase gates ------
+# Textbook definitions (Nielsen & Chuang, Sec. 4.2): R_P(theta) = exp(-i theta P / 2)
+# for P in {X, Y, Z}; the phase gate P(phi) = diag(1, e^{i phi}) = exp(i phi |1><1|),
+# with S = P(pi/2), SDG = P(-pi/2), T = P(pi/4), TDG = P(-pi/4). scipy's expm is an
+# independent route to the same matrices.
+
+_SIGMA = {"X": np.array([[0, 1], [1, 0]], complex), "Y": np.array([[0, -1j], [1j, 0]], complex),
+          "Z": np.array([[1, 0], [0, -1]], complex)}
+_THETAS = (0.0, 0.3, -1.1, math.pi / 2, math.pi, 2.5, 2 * math.pi - 0.2)
+
+
+def test_rotations_are_pauli_exponentials():
+    from scipy.linalg import expm
+    for axis in "XYZ":
+        for th in _THETAS:
+            got = matrix_of(C.Gate("R" + axis, (0,), (th,)))
+            assert np.max(np.abs(got - expm(-0.5j * th * _SIGMA[axis]))) < 1e-14, (axis, th)
+    # R_P(pi) = -i P
+    for axis in "XYZ":
+        assert np.allclose(matrix_of(C.Gate("R" + axis, (0,), (math.pi,))), -1j * _SIGMA[axis], atol=1e-15)
+
+
+def test_phase_gates_are_projector_exponentials():
+    from scipy.linalg import expm
+    proj1 = np.array([[0, 0], [0, 1]], complex)
+    for phi in _THETAS:
+        got = matrix_of(C.Gate("P", (0,), (phi,)))
+        assert np.max(np.abs(got - expm(1j * phi * proj1))) < 1e-14
+        # RZ(phi) = e^{-i phi / 2} P(phi)
+        rz = matrix_of(C.Gate("RZ", (0,), (phi,)))
+        assert np.max(np.abs(rz - cmath.exp(-0.5j * phi) * got)) < 1e-14
+    for name, phi in (("S", math.pi / 2), ("SDG", -math.pi / 2), ("T", math.pi / 4), ("TDG", -math.pi / 4)):
+        assert np.max(np.abs(matrix_of(C.Gate(name, (0,))) - expm(1j * phi * proj1))) < 1e-14, name
+    S, SDG, T = (matrix_of(C.Gate(k, (0,))) for k in ("S", "SDG", "T"))
+    assert np.allclose(S @ S, _SIGMA["Z"], atol=1e-15)
+    assert np.allclose(S @ SDG, np.eye(2), atol=1e-15)
+    assert np.allclose(T @ T, S, atol=1e-15)
+
+
+def test_rotation_gates_on_basis_states_closed_form():
+    # through the state-vector update on a multi-qubit register: RX(t)|0> =
+    # (cos t/2, -i sin t/2), RY(t)|0> = (cos t/2, sin t/2), RZ(t)|1> = e^{i t/2}|1>,
+    # RY(pi/2)|0> = |+>, H RZ(t) H = RX(t)
+    n = 3
+    for q in range(n):
+        for th in _THETAS:
+            c, s = math.cos(th / 2), math.sin(th / 2)
+            psi = statevector.simulate(C.Circuit(n, [C.Gate("RX", (q,), (th,))]))
+            assert abs(psi[0] - c) < 1e-15 and abs(psi[1 << q] - (-1j * s)) < 1e-15
+            psi = statevector.simulate(C.Circuit(n, [C.Gate("RY", (q,), (th,))]))
+            assert abs(psi[0] - c) < 1e-15 and abs(psi[1 << q] - s) < 1e-15
+            psi = statevector.simulate(C.Circuit(n, [C.Gate("X", (q,)), C.Gate("RZ", (q,), (th,))]))
+            assert abs(psi[1 << q] - cmath.exp(0.5j * th)) < 1e-15
+    psi = statevector.simulate(C.Circuit(1, [C.Gate("RY", (0,), (math.pi / 2,))]))
+    assert np.allclose(psi, [1 / math.sqrt(2), 1 / math.sqrt(2)], atol=1e-15)
+    rng = np.random.default_rng(11)
+    psi0 = rng.standard_normal(8) + 1j * rng.standard_normal(8)
+    for th in _THETAS:
+        a = statevector.simulate(C.Circuit(3, [C.Gate("H", (1,)), C.Gate("RZ", (1,), (th,)), C.Gate("H", (1,))]),
+                                 psi0=psi0.copy())
+        b = statevector.simulate(C.Circuit(3, [C.Gate("RX", (1,), (th,))]), psi0=psi0.copy())
+        assert np.max(np.abs(a - b)) < 1e-14
+
+
+def test_qaoa_cost_block_is_zz_exponential():
+    # the MaxCut cost block CX(a, b) RZ(2 gamma) on b CX(a, b) equals
+    # exp(-i gamma Z_a Z_b): basis state |x> picks up e^{-i gamma z_a z_b}, z = 1 - 2 bit
+    n, a, b = 3, 2, 0
+    for gamma in (0.4, 1.3, 2.9):
+        circ = [C.Gate("CX", (a, b)), C.Gate("RZ", (b,), (2 * gamma,)), C.Gate("CX", (a, b))]
+        for x in range(1 << n):
+            psi0 = np.zeros(1 << n, complex)
+            psi0[x] = 1
+            psi = statevector.simulate(C.Circuit(n, circ), psi0=psi0)
+            za, zb = 1 - 2 * (x >> a & 1), 1 - 2 * (x >> b & 1)
+            expect = np.zeros(1 << n, complex)
+            expect[x] = cmath.exp(-1j * gamma * za * zb)
+            assert np.max(np.abs(psi - expect)) < 1e-15, (gamma, x)
+    # the mixer RX(2 beta) on every qubit: |0..0> -> prod (cos b, -i sin b)
+    beta = 0.7
+    psi = statevector.simulate(C.Circuit(n, [C.Gate("RX", (q,), (2 * beta,)) for q in range(n)]))
+    for x in range(1 << n):
+        k = bin(x).count("1")
+        assert abs(psi[x] - math.cos(beta) ** (n - k) * (-1j * math.sin(beta)) ** k) < 1e-15
+
+
+def test_one_and_two_qubit_matrices_act_by_columns():
+    # a gate U on a basis state returns U's column: U|j> = sum_i U_ij |i>, with
+    # qubit q = bit q of the index and the two-qubit local index bit(q0) + 2 bit(q1)
+    rng = np.random.default_rng(12)
+    n = 4
+    M = rng.standard_normal((2, 2)) + 1j * rng.standard_normal((2, 2))
+    for q in range(n):
+        for j in range(2):
+            psi0 = np.zeros(1 << n, complex)
+            psi0[j << q] = 1
+            psi = statevector.simulate(C.Circuit(n, [C.Gate("U", (q,), (), M)]), psi0=psi0)
+            assert abs(psi[0] - M[0, j]) < 1e-15 and abs(psi[1 << q] - M[1, j]) < 1e-15
+    M4 = rng.standard_normal((4, 4)) + 1j * rng.standard_normal((4, 4))
+    q0, q1 = 3, 1
+    for j in range(4):
+        psi0 = np.zeros(1 << n, complex)
+        psi0[(j & 1) << q0 | (j >> 1) << q1] = 1
+        psi = statevector.simulate(C.Circuit(n, [C.Gate("U2", (q0, q1), (), M4)]), psi0=psi0)
+        for i in range(4):
+            assert abs(psi[(i & 1) << q0 | (i >> 1) << q1] - M4[i, j]) < 1e-15
+
+
+# --------------------------------------------------- aggregate (stderr) ----
+
+def test_aggregate_standard_error_closed_form():
+    # 0/1 scores with k ones among n: the sample variance (n - 1 in the
+    # denominator) is k (n - k) / (n (n - 1)), so stderr = sqrt(k (n - k) / (n^2 (n - 1)))
+    for n, k in ((10, 3), (400, 17), (2, 1)):
+        s = np.array([1.0] * k + [0.0] * (n - k))
+        a = montecarlo.aggregate(s, s > 0.5)
+        expect = math.sqrt(k * (n - k) / (n * n * (n - 1)))
+        assert abs(a["stderr_mean"] - expect) < 1e-15 and abs(a["stderr_pass"] - expect) < 1e-15
+        assert a["mean"] == k / n and a["pass_frac"] == k / n
+    # the reported stderr matches the spread of batch means of uniform scores
+    # (variance 1/12): sd of the mean over 64 scores = sqrt(1 / (12 * 64))
+    rng = np.random.default_rng(5)
+    errs = [montecarlo.aggregate(x, x > 0.5)["stderr_mean"] for x in rng.random((2000, 64))]
+    assert abs(np.mean(errs) / math.sqrt(1 / (12 * 64)) - 1) < 0.02
+
+
 # ------------------------------------------------------------ search ------
 
 def test_tolerable_rate_closed_form_identity_chain():
@@ -414,17 +540,81 @@ def test_tolerable_rate_uses_eq5_when_one_error_is_too_many():
 
 # --------------------------------------------- planted mistakes (CPU) -----
 
+def _pin_fails(pin, *args):
+    """True when running the pin raises AssertionError (the planted mistake is caught)."""
+    try:
+        pin(*args)
+    except AssertionError:
+        return True
+    return False
+
+
 def test_pins_catch_a_wrong_y_sign(monkeypatch):
+    # plausible mistake: Y applied with the opposite overall sign
     orig = statevector.apply_pauli
 
     def wrong(psi, n, q, code):
         orig(psi, n, q, code)
         if code == 3:
-            psi *= -1  # plausible mistake: Y with the opposite sign
+            psi *= -1
     monkeypatch.setattr(statevector, "apply_pauli", wrong)
-    psi = np.array([0.6 + 0.1j, -0.3 + 0.7j])
-    statevector.apply_pauli(psi, 1, 0, 3)
-    assert not (psi[0] == -1j * (-0.3 + 0.7j))
+    assert _pin_fails(test_eq2_golden_fixture_and_xx_example)
+    assert _pin_fails(test_eq2_single_qubit_paulis_match_paper)
+
+
+def _patched_one_qubit(monkeypatch, name, fn):
+    from oracle import gates
+    orig = gates.one_qubit
+
+    def wrong(n, params=(), matrix=None):
+        if n == name:
+            return fn(orig, params)
+        return orig(n, params, matrix)
+    monkeypatch.setattr(gates, "one_qubit", wrong)
+
+
+@pytest.mark.parametrize("mistake", ["rx_sign", "ry_transposed", "rz_full_angle", "s_is_sdg",
+                                     "p_conjugated", "sdg_is_s"])
+def test_pins_catch_rotation_and_phase_slips(monkeypatch, mistake):
+    if mistake == "rx_sign":  # +i sin instead of -i sin
+        _patched_one_qubit(monkeypatch, "RX", lambda o, p: o("RX", p).conj())
+    elif mistake == "ry_transposed":
+        _patched_one_qubit(monkeypatch, "RY", lambda o, p: o("RY", p).T)
+    elif mistake == "rz_full_angle":  # exp(-i theta Z) instead of exp(-i theta Z / 2)
+        _patched_one_qubit(monkeypatch, "RZ", lambda o, p: o("RZ", (2 * p[0],)))
+    elif mistake == "s_is_sdg":
+        _patched_one_qubit(monkeypatch, "S", lambda o, p: o("SDG", p))
+    elif mistake == "p_conjugated":
+        _patched_one_qubit(monkeypatch, "P", lambda o, p: o("P", p).conj())
+    elif mistake == "sdg_is_s":
+        _patched_one_qubit(monkeypatch, "SDG", lambda o, p: o("S", p))
+    caught = [_pin_fails(test_rotations_are_pauli_exponentials),
+              _pin_fails(test_phase_gates_are_projector_exponentials),
+              _pin_fails(test_rotation_gates_on_basis_states_closed_form),
+              _pin_fails(test_qaoa_cost_block_is_zz_exponential)]
+    assert any(caught), mistake
+
+
+def test_pins_catch_a_transposed_one_qubit_update(monkeypatch):
+    orig = statevector.apply_1q
+    monkeypatch.setattr(statevector, "apply_1q", lambda psi, n, q, U: orig(psi, n, q, U.T))
+    assert _pin_fails(test_one_and_two_qubit_matrices_act_by_columns)
+    assert _pin_fails(test_rotation_gates_on_basis_states_closed_form)
+
+
+@pytest.mark.parametrize("mistake", ["ddof0", "no_sqrt_n", "sd_not_sqrt"])
+def test_pins_catch_a_wrong_standard_error(monkeypatch, mistake):
+    def wrong(scores, flags):
+        n = len(scores)
+        sd = float(np.std(scores, ddof=0 if mistake == "ddof0" else 1))
+        if mistake == "sd_not_sqrt":
+            sd = sd * sd
+        div = 1.0 if mistake == "no_sqrt_n" else math.sqrt(n)
+        sdp = float(np.std(np.asarray(flags, float), ddof=0 if mistake == "ddof0" else 1))
+        return {"mean": float(np.mean(scores)), "pass_frac": float(np.mean(flags)),
+                "stderr_mean": sd / div, "stderr_pass": sdp / div}
+    monkeypatch.setattr(montecarlo, "aggregate", wrong)
+    assert _pin_fails(test_aggregate_standard_error_closed_form)
 
 
 def test_pins_catch_a_dropped_channel_term(monkeypatch):
