@@ -71,19 +71,16 @@ def _kernel_sha():
 
 
 def _traffic_per_slot():
-    """DRAM bytes per active trajectory slot per pass launch from the committed
-    ncu summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "pass_kernel_brickwork24.md")
+    """DRAM bytes per active trajectory slot per pass launch, from the ncu
+    capture recorded in profiles/pass_kernel_traffic.json, if that capture was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "pass_kernel_traffic.json")
     try:
-        vals = {}
         with open(path) as f:
-            for line in f:
-                if ":" in line and line.strip().startswith("- "):
-                    k, v = line.strip()[2:].split(":", 1)
-                    vals[k.strip()] = v.strip().strip("`")
-        if vals.get("source_sha") != _kernel_sha():
+            d = json.load(f)
+        if d.get("source_sha") != _kernel_sha():
             return None
-        return float(vals["dram_bytes_per_slot_launch"])
+        return float(d["dram_bytes_per_slot_launch"])
     except Exception:
         return None
 
@@ -140,73 +137,209 @@ def _dist():
 
 
 # ----------------------------------------------------------- CPU oracle ---
+# The FP64 oracle (test infrastructure) timed on this host's cores as the CPU
+# baseline: never tuned for it, run as it stands, parallel only across
+# trajectories (one worker process per core, each simulating its own errored
+# trajectory with oracle.statevector.simulate, gate chunk by gate chunk).
 
-def oracle_sample(circ, seconds=12.0):
-    """Time the FP64 oracle, as it stands, on a bounded sample of the
-    workload: the first gates of one trajectory's simulation (every errored
-    trajectory simulates all G gates; error-free ones reuse psi_R). Returns
-    (seconds per gate, gates run)."""
-    import numpy as np
-    from oracle import statevector
+def host_info():
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    import platform
+    return f"{platform.machine()} {model or platform.processor() or 'unknown CPU'}, {os.cpu_count()} logical CPUs"
+
+
+def _usable_cores(state_bytes):
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except Exception:
+        cores = os.cpu_count() or 1
+    try:  # about five state-sized temporaries per worker during a gate
+        avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+        cores = min(cores, max(1, int(avail * 0.5 // (6 * state_bytes))))
+    except Exception:
+        pass
+    return max(1, min(cores, 64))
+
+
+def _oracle_worker(conn, workload, traj):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from oracle import sampling, statevector
+    from workloads import circuits as C
+    circ = C.brickwork24(0) if workload == "brickwork24" else C.grover12(0)
+    p = 1e-3
+    events = sampling.sample_trajectory(0, traj, circ.L, p / 3, p / 3, p / 3)
+    table = statevector.location_table(circ)
+    first_loc = [0]
+    for gate in circ.gates:
+        first_loc.append(first_loc[-1] + len(gate.qubits))
     psi = statevector.zero_state(circ.n)
     g = 0
-    t0 = time.perf_counter()
-    while time.perf_counter() - t0 < seconds and g < circ.G:
-        statevector.apply_gate(psi, circ.n, circ.gates[g])
-        g += 1
-    dt = time.perf_counter() - t0
-    del psi, np
-    return dt / max(g, 1), g
+    conn.send(("ready", circ.G, circ.L, circ.n))
+    while True:
+        want = conn.recv()
+        if want is None:
+            break
+        t0 = time.perf_counter()
+        done = 0
+        while done < want:
+            g1 = min(circ.G, g + want - done)
+            # the oracle's own simulate() over the next chunk, with this trajectory's errors in it
+            ev = [(l - first_loc[g], c) for (l, c) in events if g <= table[l][0] < g1]
+            psi = statevector.simulate(C.Circuit(circ.n, circ.gates[g:g1]), ev, psi0=psi)
+            done += g1 - g
+            g = g1
+            if g == circ.G:  # trajectory finished: start the next one from |0...0>
+                psi = statevector.zero_state(circ.n)
+                g = 0
+        conn.send((time.perf_counter() - t0, done))
 
 
-def errored_fraction(L):
-    return sum(1.0 - (1.0 - p) ** L for p in P_RATES) / len(P_RATES)
+class OracleFarm:
+    """`procs` worker processes (spawn start method), each holding one errored
+    trajectory of the workload in the FP64 oracle."""
+
+    def __init__(self, workload, procs):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        self.conns, self.procs = [], []
+        for i in range(procs):
+            a, b = ctx.Pipe()
+            pr = ctx.Process(target=_oracle_worker, args=(b, workload, 1000 * i + 1), daemon=True)
+            pr.start()
+            self.conns.append(a)
+            self.procs.append(pr)
+        infos = [self._recv(i, 600) for i in range(procs)]
+        _, self.G, self.L, self.n = infos[0]
+
+    def _recv(self, i, timeout):
+        """Reply of worker i; raises if it died or stayed silent for `timeout` s."""
+        c, pr = self.conns[i], self.procs[i]
+        t0 = time.perf_counter()
+        while not c.poll(1.0):
+            if not pr.is_alive():
+                raise RuntimeError(f"oracle worker {i} exited with code {pr.exitcode}")
+            if time.perf_counter() - t0 > timeout:
+                raise RuntimeError(f"oracle worker {i} gave no answer within {timeout} s")
+        return c.recv()
+
+    def step(self, gates_per_worker):
+        """Every worker simulates the next `gates_per_worker` gates; returns
+        (wall seconds, total gates)."""
+        t0 = time.perf_counter()
+        for c in self.conns:
+            c.send(int(gates_per_worker))
+        done = sum(self._recv(i, 3600)[1] for i in range(len(self.conns)))
+        return time.perf_counter() - t0, done
+
+    def close(self):
+        for c in self.conns:
+            try:
+                c.send(None)
+            except Exception:
+                pass
+        for pr in self.procs:
+            pr.join(timeout=30)
+            if pr.is_alive():
+                pr.terminate()
+
+
+def errored_fraction(L, rates=P_RATES):
+    return sum(1.0 - (1.0 - p) ** L for p in rates) / len(rates)
+
+
+def oracle_gates_per_traj(G, L, rates, traj_per_rate):
+    """Oracle gate applications per trajectory of the workload: an errored
+    trajectory simulates all G gates, an error-free one reuses the reference
+    state (computed once for the workload: G gates over all its trajectories)."""
+    return G * (errored_fraction(L, rates) + 1.0 / (traj_per_rate * len(rates)))
+
+
+def cpu_baseline(workload, seconds, rates, traj_per_rate, state_bytes):
+    """The oracle on 1 core and on all usable cores, about `seconds` each."""
+    out = {}
+    for label, procs in (("single_core", 1), ("all_cores", _usable_cores(state_bytes))):
+        farm = None
+        try:
+            farm = OracleFarm(workload, procs)
+            dt, g = farm.step(1)  # warm-up, then calibration on about a tenth of the budget
+            dt, g = farm.step(max(1, int(0.1 * seconds / max(dt, 1e-9))))
+            per = max(1, int(seconds * g / procs / max(dt, 1e-9)))
+            dt, g = farm.step(per)
+        finally:
+            if farm:
+                farm.close()
+        gates_per_traj = oracle_gates_per_traj(farm.G, farm.L, rates, traj_per_rate)
+        out[label] = {"value": g / dt / gates_per_traj, "unit": UNIT, "cores": procs, "kind": "oracle",
+                      "sample": f"FP64 numpy oracle simulate() over {g} gates of {procs} errored {workload} "
+                                f"trajectories in {dt:.1f} s ({procs} worker processes, one trajectory each); "
+                                f"traj/s = gates/s / {gates_per_traj:.1f} oracle gates per trajectory (errored "
+                                f"fraction {errored_fraction(farm.L, rates):.3f} x G {farm.G}, plus the "
+                                f"reference state once per workload)"}
+    line = dict(out["all_cores"])
+    line["single_core"] = out["single_core"]
+    line["host"] = host_info()
+    return line
 
 
 def grover_cpu_baseline(seconds):
-    """The FP64 oracle on the Grover-12 sweep, bounded: the first gates of one
-    trajectory's simulation; a trajectory with an error simulates all G gates
-    (the GPU path restarts from a cached prefix; the oracle does not)."""
     from workloads import circuits as C
     circ = C.grover12(0)
     rates = [10 ** (-5 + 3 * i / 15) for i in range(16)]
-    frac = sum(1.0 - (1.0 - p) ** circ.L for p in rates) / len(rates)
-    sg, g = oracle_sample(circ, seconds=seconds)
-    return {"value": 1.0 / (frac * circ.G * sg), "unit": "traj/s", "cores": 1, "kind": "oracle",
-            "sample": f"FP64 numpy oracle simulate() of the first {g} gates of one Grover-12 trajectory "
-                      f"({sg * 1e6:.1f} us/gate, single-threaded); traj/s = 1 / (errored fraction {frac:.3f} x "
-                      f"G {circ.G} x sec/gate)"}
+    return cpu_baseline("grover12", seconds, rates, 100_000, 16 << circ.n)
 
 
 def run_reference(args):
-    """--impl reference: the FP64 CPU oracle timed on this host's cores."""
+    """--impl reference: the FP64 CPU oracle timed on this host's cores, on all
+    usable cores in parallel over trajectories. Each step is a bounded sample of
+    the workload (every worker simulates the next gates of its own errored
+    trajectory); value = trajectory-equivalents per second."""
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
     from workloads import circuits as C
     circ = C.brickwork24(0)
-    frac = errored_fraction(circ.L)
-    per_step = max(1.0, 60.0 / max(args.steps + args.warmup, 1))
-    for _ in range(args.warmup):
-        oracle_sample(circ, seconds=min(per_step, 2.0))
-    times = []
-    gates = 0
-    for _ in range(args.steps):
-        sg, g = oracle_sample(circ, seconds=per_step)
-        times.append(sg)
-        gates += g
-    sec_per_gate = statistics.median(times)
-    traj_per_s = 1.0 / (frac * circ.G * sec_per_gate)
+    procs = _usable_cores(16 << circ.n)
+    budget = float(os.environ.get("ARSO_REFERENCE_SECONDS", "150"))
+    per_step = max(0.5, budget / max(args.steps + args.warmup, 1))
+    gates_per_traj = oracle_gates_per_traj(circ.G, circ.L, P_RATES, TRAJ_PER_P)
+    farm = None
+    try:
+        farm = OracleFarm("brickwork24", procs)
+        dt, g = farm.step(1)
+        dt, g = farm.step(max(1, int(0.2 * per_step / max(dt, 1e-9))))
+        per = max(1, int(per_step * g / procs / max(dt, 1e-9)))
+        for _ in range(max(args.warmup - 1, 0)):
+            farm.step(per)
+        times, gates = [], 0
+        for _ in range(args.steps):
+            dt, g = farm.step(per)
+            times.append(dt)
+            gates += g
+    finally:
+        if farm:
+            farm.close()
+    total = sum(times)
+    traj_per_s = gates / total / gates_per_traj
+    sample = (f"FP64 numpy oracle simulate() over {gates} gates of {procs} errored 24-qubit brickwork trajectories "
+              f"({per} gates per worker per step, {procs} worker processes); traj/s = gates/s / "
+              f"{gates_per_traj:.1f} oracle gates per trajectory (errored fraction "
+              f"{errored_fraction(circ.L):.3f} x G {circ.G}, plus the reference state once per workload)")
     line = {
         "impl": "reference", "metric": METRIC, "value": traj_per_s, "unit": UNIT, "n_gpus": 0,
         "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * args.traj_per_step / traj_per_s, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1e3 * total / max(args.steps, 1), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": _config(circ, args),
-        "cpu_baseline": {"value": traj_per_s, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"oracle state-vector simulate() of the first gates of a 24-qubit brickwork "
-                                   f"trajectory, {gates} gates over {args.steps} steps; traj/s = 1 / "
-                                   f"(errored fraction {frac:.3f} x G {circ.G} x sec/gate)"},
+        "cpu_baseline": {"value": traj_per_s, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": sample,
+                         "host": host_info()},
         "e2e": {"value": traj_per_s, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -360,14 +493,7 @@ def run_ours(args):
                     "pass_frac_p1e-3": float(np.mean([a[1][1] for a in aggs]))},
     }
     if not args.no_cpu_baseline:
-        sg, g = oracle_sample(circ, seconds=args.cpu_seconds)
-        frac = errored_fraction(circ.L)
-        v = 1.0 / (frac * circ.G * sg)
-        line["cpu_baseline"] = {
-            "value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"FP64 numpy oracle simulate() of the first {g} gates of one 24-qubit brickwork trajectory "
-                      f"({sg * 1e3:.1f} ms/gate, single-threaded); traj/s = 1 / (errored fraction {frac:.3f} x "
-                      f"G {circ.G} x sec/gate)"}
+        line["cpu_baseline"] = cpu_baseline("brickwork24", args.cpu_seconds, P_RATES, TRAJ_PER_P, 16 << circ.n)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -385,7 +511,8 @@ def main():
                          "persistent launch)")
     ap.add_argument("--tile", type=int, default=0, help="tile qubits (0 = library default)")
     ap.add_argument("--cache-gb", type=float, default=0.0, help="prefix-cache budget (0 = library default)")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="seconds of oracle work per CPU-baseline setting (1 core, all cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-suffix", action="store_true",
                     help="run every trajectory to the end instead of scoring after its last error")

@@ -336,11 +336,13 @@ arso_status arso_surrogate_grads(const arso_surrogate *s, const float *x, const 
                                  float *grads_out, double *loss_out);
 /* Test support for the failure path of the tensor-core GEMMs (no counterpart in
  * the paper). Every wait of those kernels on an mbarrier is bounded; one that
- * gives up skips the remaining MMAs, frees its tensor memory, sets an error word
- * and returns, and the API call that launched it returns ARSO_ETIMEOUT. This
- * makes the next GEMM launch whose B operand comes by TMA expect 16 bytes more
- * than its loads deliver, with a short wait limit, so that its wait runs out;
- * nothing hangs or faults and the context stays usable. One-shot, process-wide. */
+ * gives up skips the remaining MMAs, waits (again bounded) for any of its TMA
+ * copies still in flight, frees its tensor memory, sets an error word and
+ * returns, and the API call that launched it returns ARSO_ETIMEOUT. This makes
+ * the next GEMM launch whose B operand comes by TMA arm its TMA barrier for the
+ * operand's bytes but issue no copy, with a short wait limit, so that its wait
+ * runs out with nothing outstanding; nothing hangs or faults and the context
+ * stays usable. One-shot, process-wide. */
 arso_status arso_debug_stall_next_gemm(void);
 /* Tolerable rate with the surrogate (Sec. IV-D, Monte Carlo branch): bisect
  * log10 p on the surrogate's prediction for the circuit's features, take the
@@ -375,10 +377,13 @@ arso_status arso_score_state(uint32_t n_qubits, const void *amps, const void *re
  * compiled into the library, which every GPU that loads the library holds
  * until the process exits. Limits: binning criteria up to 20 qubits (an
  * outcome bitmap of 2^20 bits), other criteria up to 34 qubits; larger
- * requests return ARSO_EINVAL. The first call on a device looks up the
- * arrays' device addresses, so make it before any stream capture. All calls on
- * a device share the arrays (each call overwrites what it reads), so calls
- * that overlap on the GPU race. It calls no cudaMalloc or cudaFree. */
+ * requests return ARSO_EINVAL. Every call looks up the arrays' device
+ * addresses in the context current on the calling thread (no allocation, and
+ * no cached address that a device reset could leave stale); the first call in
+ * a context loads the library's module there, so make it before any stream
+ * capture. All calls in a context share the arrays (each call overwrites what
+ * it reads), so calls that overlap on the GPU race. It calls no cudaMalloc or
+ * cudaFree. */
 arso_status arso_score_state_noalloc(uint32_t n_qubits, const void *amps, const void *ref,
                                      const arso_criterion *crit, void *stream, double *score_out);
 

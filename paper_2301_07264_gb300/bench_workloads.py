@@ -179,11 +179,11 @@ def search(args):
     rows = []
     for c in evals:
         cc = arso.compile_circuit(c.n, c.gates)
-        arso.tolerable_rate(cc, crit, 2 / 3, n_traj=256, seed=0, mode="mc", rel_tol=0.5, check=False)  # warm cache
+        arso.success_prob(cc, crit, 1e-3, mode="mc", n_traj=256, seed=0)  # builds the prefix cache
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         pl = arso.tolerable_rate(cc, crit, 2 / 3, n_traj=20000, seed=0, mode="mc", rel_tol=0.02, p_lo=1e-5,
-                                 p_hi=1e-1, check=False)
+                                 p_hi=1e-1)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         su = arso.tolerable_rate_surrogate(cc, crit, 2 / 3, s, n_traj=20000, seed=0, margin=0.05, p_lo=1e-5, p_hi=1e-1)
@@ -303,6 +303,21 @@ def qv(args):
             "kernels": _kernel_stats(arso)}
 
 
+def fit_inverse_gate_count(Gs, ps, G_extrapolate):
+    """Least-squares fits of the tolerable rate linear in 1 / G (Sec. V-B):
+    p* = b / G through the origin (used for the extrapolation to G_extrapolate
+    gates) and p* = a + b / G with an intercept, each with its mean squared
+    residual."""
+    g_inv, pv = 1.0 / np.asarray(Gs, dtype=float), np.asarray(ps, dtype=float)
+    b0 = float(g_inv @ pv / (g_inv @ g_inv))
+    A = np.stack([np.ones(len(Gs)), g_inv], axis=1)
+    coef, *_ = np.linalg.lstsq(A, pv, rcond=None)
+    return {"b": b0, "mse": float(np.mean((b0 * g_inv - pv) ** 2)),
+            "affine_a": float(coef[0]), "affine_b": float(coef[1]),
+            "affine_mse": float(np.mean((A @ coef - pv) ** 2)),
+            "G_56": int(G_extrapolate), "p_tol_56_extrapolated": b0 / G_extrapolate}
+
+
 def families(args):
     """Tolerable error rate (target success 0.66, the paper's figure) of the
     paper's circuit families at several sizes, through the library's Fig. 3
@@ -331,22 +346,12 @@ def families(args):
             crit = W.Criterion(circ.criterion.kind, target=circ.criterion.target, threshold=circ.criterion.threshold,
                                aggregate="mean")
             cc = arso.compile_circuit(circ.n, circ.gates)
-            r = arso.tolerable_rate(cc, crit, P_target, n_traj=4000, seed=0, rel_tol=0.05, p_lo=1e-7, p_hi=0.3,
-                                    check=False)
+            r = arso.tolerable_rate(cc, crit, P_target, n_traj=4000, seed=0, rel_tol=0.05, p_lo=1e-7, p_hi=0.3)
             rows.append({"family": name, "n": n, "G": circ.G, "L": circ.L, "p_tol": r.p, "probes": r.probes,
                          "mode": "Eq. (5)" if r.mode_used == 0 else "Monte Carlo", "p_tol_times_G": r.p * circ.G})
             Gs.append(circ.G)
             ps.append(r.p)
-        # p* = b / G (proportional, the extrapolation) and p* = a + b / G (with intercept)
-        g_inv, pv = 1.0 / np.asarray(Gs, dtype=float), np.asarray(ps)
-        b0 = float(g_inv @ pv / (g_inv @ g_inv))
-        A = np.stack([np.ones(len(Gs)), g_inv], axis=1)
-        coef, *_ = np.linalg.lstsq(A, pv, rcond=None)
-        G56 = make(56).G
-        fits[name] = {"b": b0, "mse": float(np.mean((b0 * g_inv - pv) ** 2)),
-                      "affine_a": float(coef[0]), "affine_b": float(coef[1]),
-                      "affine_mse": float(np.mean((A @ coef - pv) ** 2)),
-                      "G_56": G56, "p_tol_56_extrapolated": b0 / G56}
+        fits[name] = fit_inverse_gate_count(Gs, ps, make(56).G)
     torch.cuda.synchronize()
     sec = time.perf_counter() - t0
     return {"metric": "tolerable-rate searches/sec", "value": len(rows) / sec, "unit": "searches/s",

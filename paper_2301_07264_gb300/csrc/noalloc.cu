@@ -9,16 +9,17 @@
 // partials, the final score and the binning bitmap) lives in file-scope
 // device arrays of fixed size instead of stream-ordered allocations.
 //
-// The arrays exist once per device that loads the library and stay allocated
-// until the process exits. In host code the array names are host-side
-// stand-ins, not device addresses, so the first call on each device looks up
-// the device addresses with cudaGetSymbolAddress (with that device current)
-// and caches them; that first call should therefore come before any stream
-// capture. All calls on a device share the arrays and the arrays keep the
-// last call's contents: every call overwrites the bitmap words it uses and
-// every partial it reads, and calls that overlap on the GPU race on them.
-#include <mutex>
-
+// The arrays exist once per CUDA context that loads the library's module and
+// stay allocated until the context ends (normally process exit). In host code
+// the array names are host-side stand-ins, not device addresses, so every call
+// looks up the device addresses with cudaGetSymbolAddress in the context
+// current on the calling thread. The lookup allocates nothing; it is done per
+// call rather than cached so that a device reset or a caller-made context never
+// leaves a stale address behind. The first call in a context also loads the
+// module there, so make it before any stream capture. All calls in a context
+// share the arrays and the arrays keep the last call's contents: every call
+// overwrites the bitmap words it uses and every partial it reads, and calls
+// that overlap on the GPU race on them.
 #include "kernels.h"
 
 namespace arso {
@@ -36,26 +37,17 @@ struct NoAllocPtrs {
     double *score = nullptr;
     uint32_t *bitmap = nullptr;
 };
-constexpr int NOALLOC_MAX_DEVICES = 64;
-std::mutex g_noalloc_mu;
-NoAllocPtrs g_noalloc_ptrs[NOALLOC_MAX_DEVICES];
 
-// device addresses of the file-scope arrays for the current device
+// device addresses of the file-scope arrays in the current context
 NoAllocPtrs noalloc_setup() {
-    int dev = 0;
-    ARSO_CUDA(cudaGetDevice(&dev));
-    ARSO_REQUIRE(dev >= 0 && dev < NOALLOC_MAX_DEVICES, "device index beyond the no-allocation table");
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    NoAllocPtrs &p = g_noalloc_ptrs[dev];
-    if (!p.partials) {
-        void *a = nullptr, *b = nullptr, *c = nullptr;
-        ARSO_CUDA(cudaGetSymbolAddress(&a, g_noalloc_partials));
-        ARSO_CUDA(cudaGetSymbolAddress(&b, g_noalloc_score));
-        ARSO_CUDA(cudaGetSymbolAddress(&c, g_noalloc_bitmap));
-        p.partials = static_cast<Partial *>(a);
-        p.score = static_cast<double *>(b);
-        p.bitmap = static_cast<uint32_t *>(c);
-    }
+    void *a = nullptr, *b = nullptr, *c = nullptr;
+    ARSO_CUDA(cudaGetSymbolAddress(&a, g_noalloc_partials));
+    ARSO_CUDA(cudaGetSymbolAddress(&b, g_noalloc_score));
+    ARSO_CUDA(cudaGetSymbolAddress(&c, g_noalloc_bitmap));
+    NoAllocPtrs p;
+    p.partials = static_cast<Partial *>(a);
+    p.score = static_cast<double *>(b);
+    p.bitmap = static_cast<uint32_t *>(c);
     return p;
 }
 }  // namespace

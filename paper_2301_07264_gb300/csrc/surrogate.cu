@@ -76,7 +76,7 @@ struct GemmArgs {
     float *colsum;  // EPI_RELU_MASK: colsum[blockIdx.y * N + n] = sum of the tile's rows of column n
     unsigned *err;
     uint32_t wait_limit;  // polls per bounded wait
-    uint32_t extra_tx;    // failure-path test: bytes expected beyond what the TMA loads deliver
+    uint32_t stall;       // failure-path test: arm the TMA barrier for B's bytes but issue no copy
 };
 
 __device__ unsigned g_gemm_err;
@@ -220,6 +220,10 @@ __global__ void __launch_bounds__(GM_THREADS, 1) umma_gemm_kernel(const __grid_c
     uint32_t parity[2] = {0u, 0u}, fparity[2] = {0u, 0u};
     bool pending[2] = {false, false};
     bool bad = false;
+    // thread 0 only: a stage whose TMA copies were issued and not yet seen to land,
+    // and the barrier phase they complete (drained before the CTA returns)
+    bool tma_inflight[2] = {false, false};
+    uint32_t tma_phase[2] = {0u, 0u};
     for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % nst;
         if (pending[s]) {  // the MMAs of block kb - nst read this buffer
@@ -250,10 +254,15 @@ __global__ void __launch_bounds__(GM_THREADS, 1) umma_gemm_kernel(const __grid_c
         if (B_TMA && threadIdx.x == 0) {
             // B by TMA: one 8 k x 128 row box per k chunk, 2 KB apart, so that row
             // groups are 128 bytes apart and k chunks 2048 (the descriptor below)
-            mbar_arrive_expect_tx(full + s, GM_B_BYTES + a.extra_tx);
+            mbar_arrive_expect_tx(full + s, GM_B_BYTES);
+            if (!a.stall) {
 #pragma unroll
-            for (int c = 0; c < GM_BK / 8; ++c)
-                tma_load_2d(reinterpret_cast<uint8_t *>(pb[0]) + c * (GM_BN * 16), &a.tmb, k0 + 8 * c, n0, full + s);
+                for (int c = 0; c < GM_BK / 8; ++c)
+                    tma_load_2d(reinterpret_cast<uint8_t *>(pb[0]) + c * (GM_BN * 16), &a.tmb, k0 + 8 * c, n0,
+                                full + s);
+                tma_inflight[s] = true;
+                tma_phase[s] = fparity[s];
+            }
         }
         {
             float va[GM_UNITS][8];
@@ -271,6 +280,7 @@ __global__ void __launch_bounds__(GM_THREADS, 1) umma_gemm_kernel(const __grid_c
             bool landed = true;
             if (B_TMA) {
                 landed = mbar_wait_bounded(full + s, fparity[s], a.wait_limit);
+                if (landed) tma_inflight[s] = false;
                 bad |= !landed;
             }
             tc_fence_after();
@@ -299,6 +309,13 @@ __global__ void __launch_bounds__(GM_THREADS, 1) umma_gemm_kernel(const __grid_c
             parity[s] ^= 1u;
         }
     bad = __syncthreads_or(bad) || nkb == 0;
+    if (bad && B_TMA && threadIdx.x == 0) {
+        // a wait gave up: let copies still in flight into this CTA's shared memory
+        // land (again a bounded wait) before the memory is reused or released
+        for (int s = 0; s < 2; ++s)
+            if (tma_inflight[s]) (void)mbar_wait_bounded(full + s, tma_phase[s], a.wait_limit);
+    }
+    __syncthreads();
     tc_fence_after();
 
     if (!bad) {
@@ -394,7 +411,7 @@ static int umma_gemm(int M, int N, int K, GemmOperand A, GemmOperand B, float *C
     GemmArgs g{};
     g.wait_limit = UMMA_WAIT_LIMIT;
     if (B.tmap && g_stall_next_gemm.exchange(false)) {  // failure-path test (arso_debug_stall_next_gemm)
-        g.extra_tx = 16;
+        g.stall = 1;  // the TMA barrier waits for bytes that no copy delivers; nothing is in flight
         g.wait_limit = 1u << 12;
     }
     if (B.tmap) {

@@ -89,3 +89,17 @@ def test_phase_planner_counts(arso):
     # ceil(60,771 / 64) phases of at most 64 gates, and at most 1,310
     assert arso.plan_phases(24, C.brickwork24(0).gates, tile_qubits=13) <= 160
     assert 950 <= arso.plan_phases(12, C.grover12(0).gates) <= 1310
+
+
+def test_inverse_gate_count_fit():
+    # the Sec. V-B fit: data exactly b / G returns b with zero residual and a
+    # zero intercept; data a + b / G returns (a, b) from the affine fit
+    from paper_2301_07264_gb300.bench_workloads import fit_inverse_gate_count
+    Gs = [40, 90, 200, 350, 800]
+    f = fit_inverse_gate_count(Gs, [0.3 / g for g in Gs], 3000)
+    assert abs(f["b"] - 0.3) < 1e-12 and f["mse"] < 1e-30
+    assert abs(f["affine_a"]) < 1e-12 and abs(f["affine_b"] - 0.3) < 1e-10
+    assert f["G_56"] == 3000 and abs(f["p_tol_56_extrapolated"] - 1e-4) < 1e-15
+    f = fit_inverse_gate_count(Gs, [2e-4 + 0.25 / g for g in Gs], 1000)
+    assert abs(f["affine_a"] - 2e-4) < 1e-12 and abs(f["affine_b"] - 0.25) < 1e-10 and f["affine_mse"] < 1e-28
+    assert f["mse"] > 0
