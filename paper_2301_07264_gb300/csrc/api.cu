@@ -308,6 +308,70 @@ static const void *ref_state_ptr(const arso_circuit *c) {
     return c->d_cache.as<char>() + (size_t)(c->n_ckpt - 1) * c->state_bytes();
 }
 
+// A host gate in the form of the single-gate HBM kernels (global qubits; H and the
+// omega phases as dense / diagonal gates, CZ as a diagonal), or its adjoint.
+static void hbm_gate(const HostGate &h, bool adjoint, DGate &d, M16 &m) {
+    d = DGate{};
+    d.cls = h.cls == GC_H ? (uint8_t)GC_DENSE1
+          : h.cls == GC_OMEGA ? (uint8_t)GC_DIAG1 : h.cls == GC_CZ ? (uint8_t)GC_DIAG2 : h.cls;
+    d.arity = (uint8_t)h.arity;
+    d.q0 = (uint8_t)h.q0;
+    d.q1 = (uint8_t)h.q1;
+    const int dim = h.arity == 1 ? 2 : 4;
+    auto e = [&](int r, int col) { return adjoint ? std::conj(h.m[col * dim + r]) : h.m[r * dim + col]; };
+    auto f2 = [](std::complex<double> v) { return make_float2((float)v.real(), (float)v.imag()); };
+    m = M16{};
+    if (h.arity == 1 && d.cls == GC_DIAG1) {
+        m.m[0] = f2(e(0, 0));
+        m.m[1] = f2(e(1, 1));
+    } else if (d.cls != GC_NOP) {
+        for (int r = 0; r < dim; ++r)
+            for (int col = 0; col < dim; ++col) m.m[r * dim + col] = f2(e(r, col));
+    }
+}
+
+// Backward states for the outcome criterion's suffix reuse (streaming, complex64):
+// phi_j = (gates of passes j..P-1)^dagger |target> at every cached pass boundary j,
+// built from |target> by the adjoint gates in reverse engine order.
+static bool bwd_supported(const arso_circuit *c) { return c->engine == 1 && c->precision == ARSO_C64; }
+
+static void ensure_bwd_cache(arso_circuit *c, uint64_t target, cudaStream_t st) {
+    if (c->bwd_ready && c->bwd_target == target) return;
+    ensure_cache(c, st);
+    const size_t sb = c->state_bytes();
+    const uint32_t P = (uint32_t)c->passes.size();
+    c->bwd_ready = false;
+    c->d_bwd.ensure((size_t)c->n_ckpt * sb);
+    char *base = c->d_bwd.as<char>();
+    Scratch work(st, sb);
+    const float2 one = make_float2(1.f, 0.f);
+    ARSO_CUDA(cudaMemsetAsync(work.ptr, 0, sb, st));
+    copy_h2d(work.as<float2>() + target, &one, sizeof(float2), st);
+    ARSO_CUDA(cudaMemcpyAsync(base + (size_t)c->ckpt_pass[P] * sb, work.ptr, sb, cudaMemcpyDeviceToDevice, st));
+    for (uint32_t j = P; j-- > 0;) {
+        for (uint32_t pos = c->passes[j].ge; pos-- > c->passes[j].gb;) {
+            const HostGate &h = c->gates[c->perm[pos]];
+            if (h.cls == GC_NOP) continue;
+            DGate d;
+            M16 m;
+            hbm_gate(h, true, d, m);
+            launch_gate_pairs(work.as<float2>(), (int)c->n, d, m, st);
+        }
+        if (c->ckpt_pass[j] != NO_EVENT)
+            ARSO_CUDA(cudaMemcpyAsync(base + (size_t)c->ckpt_pass[j] * sb, work.ptr, sb, cudaMemcpyDeviceToDevice, st));
+    }
+    ARSO_CUDA(cudaStreamSynchronize(st));
+    c->bwd_target = target;
+    c->bwd_ready = true;
+}
+
+// whether the trajectories of `crit` stop after their last error's pass (fidelity,
+// and outcome probability through the backward states)
+static bool suffix_wanted(const arso_circuit *c, const DCrit &crit) {
+    if (c->flags & ARSO_OPT_NO_SUFFIX_REUSE) return false;
+    return crit.kind == ARSO_CRIT_FIDELITY || (crit.kind == ARSO_CRIT_OUTCOME && bwd_supported(c));
+}
+
 // ------------------------------------------------------------ criterion ----
 struct DevCrit {
     DCrit d{};
@@ -431,7 +495,13 @@ static void run_streaming(arso_circuit *c, const arso_error_list *e, const std::
     // the trajectory is scored right after its last error's pass against the
     // cached error-free state at that boundary (the first cached one after
     // it); other criteria need the final state (end = P - 1).
-    const bool suffix = !states_out && crit.kind == ARSO_CRIT_FIDELITY && !(c->flags & ARSO_OPT_NO_SUFFIX_REUSE);
+    // The outcome probability |<t|psi>|^2 is scored the same way, as the overlap with
+    // the backward state W^dagger |t> at that boundary (|<t|W a>| = |<W^dagger t|a>|).
+    const bool suffix = !states_out && suffix_wanted(c, crit);
+    const bool outcome_overlap = suffix && crit.kind == ARSO_CRIT_OUTCOME;
+    if (outcome_overlap) ARSO_REQUIRE(c->bwd_ready && c->bwd_target == crit.target, "backward states not built");
+    DCrit kcrit = crit;  // what the kernels score: the overlap for the outcome criterion
+    if (outcome_overlap) kcrit.kind = ARSO_CRIT_FIDELITY;
     std::vector<int> start(ids.size()), end(ids.size());
     for (size_t i = 0; i < ids.size(); ++i) {
         uint32_t fp = first_pos[i] == NO_EVENT ? P - 1 : c->pass_of_pos[first_pos[i]];
@@ -504,6 +574,7 @@ static void run_streaming(arso_circuit *c, const arso_error_list *e, const std::
         for (uint32_t j = (uint32_t)jmin; j <= (uint32_t)jmax; ++j) {
             PassArgs a = pass_args(c, j);
             a.cache = c->d_cache.ptr;
+            a.ref_cache = outcome_overlap ? c->d_bwd.ptr : nullptr;
             a.cache_slot = d_cslot.as<uint32_t>();
             a.ref_slot = c->n_ckpt - 1;
             a.work = states_out ? states_out : work.ptr;
@@ -512,7 +583,7 @@ static void run_streaming(arso_circuit *c, const arso_error_list *e, const std::
             a.slot_traj = d_slot_traj.as<uint64_t>();
             a.offsets = e->d_offsets.as<uint64_t>();
             a.keys = e->d_key.as<uint32_t>();
-            a.crit = crit;
+            a.crit = kcrit;
             a.partials = parts.as<Partial>();
             a.store_last = states_out ? 1 : 0;
             uint32_t active = 0;
@@ -520,8 +591,8 @@ static void run_streaming(arso_circuit *c, const arso_error_list *e, const std::
             run_pass(c, a, j == P - 1, (uint32_t)nb, (double)active, st);
         }
         if (!states_out)
-            launch_finish_partials(parts.as<Partial>(), tiles, (uint32_t)nb, d_slot_traj.as<uint64_t>(), crit, d_score,
-                                   d_pass, st);
+            launch_finish_partials(parts.as<Partial>(), tiles, (uint32_t)nb, d_slot_traj.as<uint64_t>(), kcrit,
+                                   d_score, d_pass, st);
         if (capture.active) {
             cudaGraphExec_t ex = capture.finish();
             graphs[key] = ex;
@@ -557,6 +628,7 @@ static void run_all(arso_circuit *c, const arso_error_list *e, const DevCrit &dc
         return;
     }
     launch_fill_error_free(e->d_first.as<uint32_t>(), e->n_traj, ref.as<double>(), dc.d.threshold, d_score, d_pass, st);
+    if (dc.d.kind == ARSO_CRIT_OUTCOME && suffix_wanted(c, dc.d)) ensure_bwd_cache(c, dc.d.target, st);
     std::vector<uint32_t> first(e->n_traj), last(e->n_traj);
     copy_d2h(first.data(), e->d_first.ptr, e->n_traj * 4, st);
     copy_d2h(last.data(), e->d_last.ptr, e->n_traj * 4, st);
@@ -771,6 +843,7 @@ static McOut mc_run_memo(arso_circuit *c, const DevCrit &dc, double p, uint64_t 
             copy_d2h(last.data(), e->d_last.ptr, n_traj * 4, st);
             ARSO_CUDA(cudaStreamSynchronize(st));
             for (uint64_t t : ids) fp.push_back(first[t]), lp.push_back(last[t]);
+            if (dc.d.kind == ARSO_CRIT_OUTCOME && suffix_wanted(c, dc.d)) ensure_bwd_cache(c, dc.d.target, st);
             run_streaming(c, e.get(), ids, fp, lp, dc.d, sc.as<double>(), pf.as<uint8_t>(), nullptr, st);
         }
         std::vector<double> sh(n_traj);
@@ -882,6 +955,105 @@ static bool single_error_fidelities(arso_circuit *c, cudaStream_t st, std::vecto
     return true;
 }
 
+// Outcome probability of every single-error state from one backward sweep of the
+// error-free state and the backward state (both carried from the circuit's end by
+// the adjoint gates): the state with P on qubit q after gate g scores
+// |<phi_g|P|psi_g>|^2 with phi_g = W^dagger |target> for the rest W of the circuit.
+// Same output order as single_error_fidelities. Returns false for streaming
+// complex128 circuits (trajectory route).
+static bool single_error_outcomes(arso_circuit *c, uint64_t target, cudaStream_t st, std::vector<double> &s) {
+    const uint64_t L = c->L, G = c->gates.size();
+    if (c->engine != 0 && c->precision != ARSO_C64) return false;
+    std::vector<double> v6(6 * std::max<uint64_t>(L, 1), 0.0);
+    if (L) {
+        ensure_cache(c, st);
+        std::vector<uint32_t> first(G);
+        for (uint64_t l = L; l-- > 0;) first[c->loc_gate[l]] = (uint32_t)l;
+        std::vector<uint32_t> loc(G);
+        std::vector<uint8_t> ar(G);
+        for (uint64_t pos = 0; pos < G; ++pos) {
+            loc[pos] = first[c->perm[pos]];
+            ar[pos] = (uint8_t)c->gates[c->perm[pos]].arity;
+        }
+        Scratch d_out(st, 6 * L * 8), d_loc(st, G * 4);
+        copy_h2d(d_loc.ptr, loc.data(), G * 4, st);
+        if (c->engine == 0) {
+            // adjoint gate table in engine order (global qubits) and its matrix pool
+            std::vector<DGate> adj(std::max<uint64_t>(G, 1));
+            std::vector<std::complex<double>> pool;
+            for (uint64_t pos = 0; pos < G; ++pos) {
+                const HostGate &h = c->gates[c->perm[pos]];
+                DGate d{};
+                d.cls = h.cls;
+                d.arity = (uint8_t)h.arity;
+                d.q0 = (uint8_t)h.q0;
+                d.q1 = (uint8_t)h.q1;
+                d.mat = h.cls == GC_OMEGA ? (8u - h.omega_k) & 7u : (uint32_t)pool.size();
+                const int dim = h.arity == 1 ? 2 : 4;
+                switch (h.cls) {
+                    case GC_DENSE1:
+                    case GC_DENSE2:
+                        for (int r = 0; r < dim; ++r)
+                            for (int col = 0; col < dim; ++col) pool.push_back(std::conj(h.m[col * dim + r]));
+                        break;
+                    case GC_DIAG1: pool.push_back(std::conj(h.m[0])); pool.push_back(std::conj(h.m[3])); break;
+                    case GC_DIAG2: for (int i = 0; i < 4; ++i) pool.push_back(std::conj(h.m[5 * i])); break;
+                    default: break;  // NOP, X, H, CX, SWAP, CZ are their own adjoints; omega: k -> -k
+                }
+                adj[pos] = d;
+            }
+            const size_t esz = c->precision == ARSO_C128 ? 16 : 8;
+            Scratch d_adj(st, adj.size() * sizeof(DGate)), d_pool(st, std::max<size_t>(pool.size(), 1) * esz);
+            copy_h2d(d_adj.ptr, adj.data(), adj.size() * sizeof(DGate), st);
+            if (c->precision == ARSO_C128) {
+                std::vector<double2> v(pool.size());
+                for (size_t i = 0; i < pool.size(); ++i) v[i] = make_double2(pool[i].real(), pool[i].imag());
+                if (!v.empty()) copy_h2d(d_pool.ptr, v.data(), v.size() * esz, st);
+            } else {
+                std::vector<float2> v(pool.size());
+                for (size_t i = 0; i < pool.size(); ++i) v[i] = make_float2((float)pool[i].real(), (float)pool[i].imag());
+                if (!v.empty()) copy_h2d(d_pool.ptr, v.data(), v.size() * esz, st);
+            }
+            launch_dual_expect_resident(d_adj.as<DGate>(), d_pool.ptr, (uint32_t)G, (int)c->n, c->precision,
+                                        ref_state_ptr(c), target, d_loc.as<uint32_t>(), d_out.as<double>(), st);
+            ARSO_CUDA(cudaStreamSynchronize(st));  // host tables above are freed on return
+        } else {
+            const int n = (int)c->n;
+            const uint32_t blocks = expect_hbm_blocks(n);
+            const uint64_t CH = 512;
+            Scratch psi(st, c->state_bytes()), phi(st, c->state_bytes()), part(st, CH * blocks * 12 * 8), d_ar(st, G);
+            copy_h2d(d_ar.ptr, ar.data(), G, st);
+            ARSO_CUDA(cudaMemcpyAsync(psi.ptr, ref_state_ptr(c), c->state_bytes(), cudaMemcpyDeviceToDevice, st));
+            const float2 one = make_float2(1.f, 0.f);
+            ARSO_CUDA(cudaMemsetAsync(phi.ptr, 0, c->state_bytes(), st));
+            copy_h2d(phi.as<float2>() + target, &one, sizeof(float2), st);
+            // positions in descending chunks [c0, c1), each walked from c1 - 1 down
+            for (uint64_t c1 = G; c1 > 0;) {
+                const uint64_t c0 = c1 > CH ? c1 - CH : 0;
+                for (uint64_t pos = c1; pos-- > c0;) {
+                    DGate d;
+                    M16 m;
+                    hbm_gate(c->gates[c->perm[pos]], true, d, m);
+                    launch_dual_gate_expect(psi.as<float2>(), phi.as<float2>(), n, d, m,
+                                            part.as<double>() + (pos - c0) * blocks * 12, st);
+                }
+                launch_dual_expect_reduce(part.as<double>(), (uint32_t)(c1 - c0), blocks, d_loc.as<uint32_t>() + c0,
+                                          d_ar.as<uint8_t>() + c0, d_out.as<double>(), st);
+                c1 = c0;
+            }
+        }
+        copy_d2h(v6.data(), d_out.ptr, 6 * L * 8, st);
+        ARSO_CUDA(cudaStreamSynchronize(st));
+    }
+    s.assign(3 * L, 0.0);
+    for (uint64_t l = 0; l < L; ++l)
+        for (int k = 0; k < 3; ++k) {
+            const double re = v6[6 * l + 2 * k], im = v6[6 * l + 2 * k + 1];
+            s[k * L + l] = re * re + im * im;  // X, Z, Y blocks
+        }
+    return true;
+}
+
 static void exhaustive_by_trajectories(arso_circuit *c, const DevCrit &dc, cudaStream_t st, std::vector<double> &s,
                                        std::vector<uint8_t> &f);
 static void exhaustive_finish(arso_circuit *c, const DevCrit &dc, cudaStream_t st, const std::vector<double> &s,
@@ -894,8 +1066,9 @@ static void exhaustive(arso_circuit *c, const DevCrit &dc, cudaStream_t st, doub
     const uint64_t T = 3 * L;
     std::vector<double> s(T);
     std::vector<uint8_t> f(T);
-    if (dc.d.kind == ARSO_CRIT_FIDELITY && !(c->flags & ARSO_OPT_NO_FAST_EXHAUSTIVE) &&
-        single_error_fidelities(c, st, s)) {
+    const bool fast = !(c->flags & ARSO_OPT_NO_FAST_EXHAUSTIVE);
+    if ((fast && dc.d.kind == ARSO_CRIT_FIDELITY && single_error_fidelities(c, st, s)) ||
+        (fast && dc.d.kind == ARSO_CRIT_OUTCOME && single_error_outcomes(c, dc.d.target, st, s))) {
         for (uint64_t i = 0; i < T; ++i) f[i] = s[i] >= dc.d.threshold;
     } else {
         exhaustive_by_trajectories(c, dc, st, s, f);

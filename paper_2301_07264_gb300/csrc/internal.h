@@ -206,6 +206,12 @@ struct arso_circuit {
     uint32_t n_ckpt = 0;                    // checkpoints (resident) or pass boundaries (streaming)
     std::vector<uint32_t> ckpt_pass;        // streaming: cached boundary index per pass
     arso::DeviceBuffer d_cache;             // n_ckpt states; the last one is psi_R
+    // streaming complex64: backward states W^dagger |bwd_target> at the cached pass
+    // boundaries (W = the error-free rest of the circuit), same entries as d_cache; the
+    // outcome criterion's suffix reuse scores trajectories against them
+    bool bwd_ready = false;
+    uint64_t bwd_target = 0;
+    arso::DeviceBuffer d_bwd;
     arso::DeviceBuffer d_offs;              // streaming: per pass, tile-high offsets
     std::vector<uint64_t> offs_base;        // per pass offset of its table in d_offs
     size_t state_bytes() const { return (size_t(1) << n) * (precision == ARSO_C128 ? 16 : 8); }

@@ -69,6 +69,8 @@ struct PassArgs {
     void *ideal_dst;
     // trajectory mode
     const void *cache;           // cached boundary states
+    const void *ref_cache;       // states the end pass is scored against, at the same entries
+                                 // (NULL: cache; backward states for the outcome criterion)
     const uint32_t *cache_slot;  // pass index -> cache entry (valid for cached boundaries)
     uint32_t ref_slot;           // cache entry of psi_R
     void *work;                  // slots * 2^n working states
@@ -146,6 +148,21 @@ uint32_t expect_hbm_blocks(int n);
 void launch_gate_expect(float2 *psi, int n, const DGate &g, const M16 &m, double *partials, cudaStream_t st);
 void launch_gate_expect_reduce(const double *partials, uint32_t count, uint32_t blocks, const uint32_t *loc,
                                const uint8_t *arity, double *out3, cudaStream_t st);
+
+// Backward single-error sweep for rank-1 criteria (outcome probability): psi and
+// phi carried backward from (psi_R, |target>) with the adjoint gates; out6[6 * location
+// + k] = (Re, Im) of <phi|X|psi>, <phi|Z|psi>, <phi|Y|psi> after the location's gate.
+// Resident: one CTA, both states in shared memory, adj[pos] the adjoint gate at
+// engine position pos (global qubits). HBM (complex64): one launch per gate with
+// partials at partials + pos * expect_hbm_blocks(n) * 12 (the caller offsets), added
+// in order by launch_dual_expect_reduce.
+void launch_dual_expect_resident(const DGate *adj, const void *mats, uint32_t G, int n, int precision,
+                                 const void *psi_R, uint64_t target, const uint32_t *first_loc, double *out6,
+                                 cudaStream_t st);
+void launch_dual_gate_expect(float2 *psi, float2 *phi, int n, const DGate &g, const M16 &m, double *partials,
+                             cudaStream_t st);
+void launch_dual_expect_reduce(const double *partials, uint32_t count, uint32_t blocks, const uint32_t *loc,
+                               const uint8_t *arity, double *out6, cudaStream_t st);
 
 // sampling (sample.cu)
 struct SampleArgs {

@@ -769,7 +769,8 @@ __global__ void __launch_bounds__(512, 1) pass_rb_kernel(PassArgs a) {
     apply_global_phase(v, c);  // global phase i^gp
     const uint64_t base = tile_base(a.rest_mask, blockIdx.x);
     if (!a.ideal && !a.store_last && a.pass == a.end_pass[slot]) {
-        const float2 *ref = static_cast<const float2 *>(a.cache) + (size_t)a.cache_slot[a.pass + 1] * N;
+        const float2 *ref = static_cast<const float2 *>(a.ref_cache ? a.ref_cache : a.cache) +
+                            (size_t)a.cache_slot[a.pass + 1] * N;
         Partial acc = empty_partial();
         score_registers(acc, a.crit, v, c, ref, [&](uint32_t j) { return gidx(base, j); });
         acc = block_reduce_partial(acc, red);
@@ -934,6 +935,73 @@ void launch_resident_rb(const ResidentArgs &a, int mode, double bytes, cudaStrea
 // their own registers, shared-memory tile, index mask and error events.
 constexpr int BATCH_THREADS = 256;
 
+// One batched resident item (see above) run by the whole CTA.
+__device__ __forceinline__ void batch_item(const BatchItem &it, const BatchCircuit &C, const uint64_t *__restrict__ ids,
+                                           unsigned char *smem_raw, Partial *red, float2 (*ubuf)[16],
+                                           RegOp (*s_ops)[MAX_PHASE_OPS]) {
+    const int t = C.n;
+    const uint32_t N = 1u << t, gsize = 1u << (t - REG_BITS), sg = threadIdx.x / gsize;
+    float2 *sm = reinterpret_cast<float2 *>(smem_raw) + (size_t)sg * N;
+    const bool active = sg < it.count;
+    const uint64_t tr = ids[it.off + (active ? sg : 0)];
+    const uint32_t load_packed = 0u | ((uint32_t)(t - 4) << 5) | ((uint32_t)(t - 3) << 10) |
+                                 ((uint32_t)(t - 2) << 15) | ((uint32_t)(t - 1) << 20);
+    TileCtx c;
+    c.m = 0;
+    c.gp = 0;
+    c.tid = threadIdx.x % gsize;
+    c.nthr = gsize;
+    set_phase(c, load_packed, t);
+    Amps v;
+    rb_load_linear(v, C.cache + (size_t)it.ck * N, t, c.tid);
+    const uint32_t *ev = C.keys + C.offsets[tr];
+    const uint32_t *ev_end = C.keys + C.offsets[tr + 1];
+    uint32_t next = ev < ev_end ? *ev : NO_EVENT;
+    const uint32_t ph0 = it.ck * C.ckpt_every;
+    if (ph0 < C.n_phases)
+        stage_ops(s_ops[0], C.rops + C.ph_gb[ph0], C.ph_gb[ph0 + 1] - C.ph_gb[ph0], threadIdx.x, BATCH_THREADS);
+    for (uint32_t ph = ph0; ph < C.n_phases; ++ph) {
+        const uint32_t buf = (ph - ph0) & 1u;
+        stage_wait();
+        if (ph + 1 < C.n_phases)
+            stage_ops(s_ops[buf ^ 1u], C.rops + C.ph_gb[ph + 1], C.ph_gb[ph + 2] - C.ph_gb[ph + 1], threadIdx.x,
+                      BATCH_THREADS);
+        const uint32_t R = C.ph_R[ph];
+        if (R != c.R) remap<true>(v, sm, c, R, t);
+        const uint32_t g0 = C.ph_gb[ph];
+        run_gates(v, c, g0, C.ph_gb[ph + 1], s_ops[buf], g0, C.mats, sm, ubuf[sg], t, ev, ev_end, next);
+    }
+    apply_global_phase(v, c);
+    const float2 *ref = C.cache + (size_t)(C.n_ckpt - 1) * N;
+    Partial acc = empty_partial();
+    score_registers(acc, C.crit, v, c, ref, [](uint32_t j) { return (uint64_t)j; });
+    // per sub-group reduction: warps reduce by shuffles, the sub-group leader combines its warps
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double a2 = __shfl_down_sync(0xffffffffu, acc.a, o);
+        const double b2 = __shfl_down_sync(0xffffffffu, acc.b, o);
+        const double mp = __shfl_down_sync(0xffffffffu, acc.maxp, o);
+        const unsigned long long mi = __shfl_down_sync(0xffffffffu, acc.idx, o);
+        acc.a += a2;
+        acc.b += b2;
+        argmax_merge(acc.maxp, acc.idx, mp, mi);
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (c.tid == 0 && active) {
+        Partial s = empty_partial();
+        const uint32_t w0 = (sg * gsize) >> 5, nw = gsize >> 5;
+        for (uint32_t w = w0; w < w0 + nw; ++w) {
+            s.a += red[w].a;
+            s.b += red[w].b;
+            argmax_merge(s.maxp, s.idx, red[w].maxp, red[w].idx);
+        }
+        const double sc = finish_score(C.crit, s);
+        C.score[tr] = sc;
+        if (C.pass_flags) C.pass_flags[tr] = sc >= C.crit.threshold;
+    }
+}
+
 __global__ void __launch_bounds__(BATCH_THREADS, 2)
     batch_resident_kernel(const BatchCircuit *__restrict__ circs, const BatchItem *__restrict__ items, uint32_t n_items,
                           uint32_t *counter, const uint64_t *__restrict__ ids) {
@@ -949,68 +1017,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2)
         const uint32_t item = s_item;
         if (item >= n_items) return;
         const BatchItem it = items[item];
-        const BatchCircuit &C = circs[it.circuit];
-        const int t = C.n;
-        const uint32_t N = 1u << t, gsize = 1u << (t - REG_BITS), sg = threadIdx.x / gsize;
-        float2 *sm = reinterpret_cast<float2 *>(smem_raw) + (size_t)sg * N;
-        const bool active = sg < it.count;
-        const uint64_t tr = ids[it.off + (active ? sg : 0)];
-        const uint32_t load_packed = 0u | ((uint32_t)(t - 4) << 5) | ((uint32_t)(t - 3) << 10) |
-                                     ((uint32_t)(t - 2) << 15) | ((uint32_t)(t - 1) << 20);
-        TileCtx c;
-        c.m = 0;
-        c.gp = 0;
-        c.tid = threadIdx.x % gsize;
-        c.nthr = gsize;
-        set_phase(c, load_packed, t);
-        Amps v;
-        rb_load_linear(v, C.cache + (size_t)it.ck * N, t, c.tid);
-        const uint32_t *ev = C.keys + C.offsets[tr];
-        const uint32_t *ev_end = C.keys + C.offsets[tr + 1];
-        uint32_t next = ev < ev_end ? *ev : NO_EVENT;
-        const uint32_t ph0 = it.ck * C.ckpt_every;
-        if (ph0 < C.n_phases)
-            stage_ops(s_ops[0], C.rops + C.ph_gb[ph0], C.ph_gb[ph0 + 1] - C.ph_gb[ph0], threadIdx.x, BATCH_THREADS);
-        for (uint32_t ph = ph0; ph < C.n_phases; ++ph) {
-            const uint32_t buf = (ph - ph0) & 1u;
-            stage_wait();
-            if (ph + 1 < C.n_phases)
-                stage_ops(s_ops[buf ^ 1u], C.rops + C.ph_gb[ph + 1], C.ph_gb[ph + 2] - C.ph_gb[ph + 1], threadIdx.x,
-                          BATCH_THREADS);
-            const uint32_t R = C.ph_R[ph];
-            if (R != c.R) remap<true>(v, sm, c, R, t);
-            const uint32_t g0 = C.ph_gb[ph];
-            run_gates(v, c, g0, C.ph_gb[ph + 1], s_ops[buf], g0, C.mats, sm, ubuf[sg], t, ev, ev_end, next);
-        }
-        apply_global_phase(v, c);
-        const float2 *ref = C.cache + (size_t)(C.n_ckpt - 1) * N;
-        Partial acc = empty_partial();
-        score_registers(acc, C.crit, v, c, ref, [](uint32_t j) { return (uint64_t)j; });
-        // per sub-group reduction: warps reduce by shuffles, the sub-group leader combines its warps
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const double a2 = __shfl_down_sync(0xffffffffu, acc.a, o);
-            const double b2 = __shfl_down_sync(0xffffffffu, acc.b, o);
-            const double mp = __shfl_down_sync(0xffffffffu, acc.maxp, o);
-            const unsigned long long mi = __shfl_down_sync(0xffffffffu, acc.idx, o);
-            acc.a += a2;
-            acc.b += b2;
-            argmax_merge(acc.maxp, acc.idx, mp, mi);
-        }
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-        __syncthreads();
-        if (c.tid == 0 && active) {
-            Partial s = empty_partial();
-            const uint32_t w0 = (sg * gsize) >> 5, nw = gsize >> 5;
-            for (uint32_t w = w0; w < w0 + nw; ++w) {
-                s.a += red[w].a;
-                s.b += red[w].b;
-                argmax_merge(s.maxp, s.idx, red[w].maxp, red[w].idx);
-            }
-            const double sc = finish_score(C.crit, s);
-            C.score[tr] = sc;
-            if (C.pass_flags) C.pass_flags[tr] = sc >= C.crit.threshold;
-        }
+        batch_item(it, circs[it.circuit], ids, smem_raw, red, ubuf, s_ops);
     }
 }
 

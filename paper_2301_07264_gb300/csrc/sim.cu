@@ -203,7 +203,7 @@ __global__ void pass_kernel(PassArgs a) {
         }
     }
     if (!a.ideal && !a.store_last && a.pass == end) {
-        const T *ref = static_cast<const T *>(a.cache) + (size_t)a.cache_slot[end + 1] * N;
+        const T *ref = static_cast<const T *>(a.ref_cache ? a.ref_cache : a.cache) + (size_t)a.cache_slot[end + 1] * N;
         Partial acc = empty_partial();
         for (uint32_t j = threadIdx.x; j < tile_n; j += blockDim.x) {
             const uint64_t gi = tile_index<T>(j, base, offs, c);
@@ -725,6 +725,223 @@ void launch_gate_expect_reduce(const double *partials, uint32_t count, uint32_t 
     if (!count) return;
     ProfScope ps_(ARSO_K_REDUCE, 48.0 * count * blocks, st);
     gate_expect_reduce_kernel<<<count, 256, 0, st>>>(partials, blocks, loc, arity, out3);
+    ARSO_CUDA(cudaGetLastError());
+}
+
+// ------------------------------------------- single-error outcome values ---
+// For a rank-1 criterion |<tau|psi>|^2 (outcome probability: tau = |t>) the final
+// state with one Pauli error P on qubit q after gate g scores |<phi_g|P|psi_g>|^2,
+// where psi_g is the error-free state after gate g and phi_g = W^dagger tau for the
+// error-free rest W of the circuit (the backward state). Both are carried backward
+// from (psi_R, tau) with the adjoint gates: at each engine position the cross terms
+// of the gate's qubits are taken, then the gate is undone on both states.
+// Per pair (a0, a1) of psi and (b0, b1) of phi along bit q (Eq. (2) for P):
+//   <phi|X|psi> += conj(b0) a1 + conj(b1) a0
+//   <phi|Z|psi> += conj(b0) a0 - conj(b1) a1
+//   <phi|Y|psi> += -i conj(b0) a1 + i conj(b1) a0
+// stored as (Re X, Im X, Re Z, Im Z, Re Y, Im Y).
+template <typename T, typename A>
+__device__ __forceinline__ void cross_terms(T a0, T a1, T b0, T b1, A (&c)[6]) {
+    const A ar0 = a0.x, ai0 = a0.y, ar1 = a1.x, ai1 = a1.y, br0 = b0.x, bi0 = b0.y, br1 = b1.x, bi1 = b1.y;
+    // conj(b) a = (br ar + bi ai) + i (br ai - bi ar)
+    const A r01 = br0 * ar1 + bi0 * ai1, i01 = br0 * ai1 - bi0 * ar1;
+    const A r10 = br1 * ar0 + bi1 * ai0, i10 = br1 * ai0 - bi1 * ar0;
+    const A r00 = br0 * ar0 + bi0 * ai0, i00 = br0 * ai0 - bi0 * ar0;
+    const A r11 = br1 * ar1 + bi1 * ai1, i11 = br1 * ai1 - bi1 * ar1;
+    c[0] += r01 + r10;
+    c[1] += i01 + i10;
+    c[2] += r00 - r11;
+    c[3] += i00 - i11;
+    c[4] += i01 - i10;  // -i (r01 + i i01) + i (r10 + i i10)
+    c[5] += r10 - r01;
+}
+
+// block-wide sum of six doubles; every thread gets the result
+__device__ __forceinline__ void block_sum6(double (&v)[6], double (*red)[32]) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) red[k][warp] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        v[k] = 0.0;
+        for (int w = 0; w < nw; ++w) v[k] += red[k][w];
+    }
+}
+
+// Whole circuit in one CTA: psi and phi in shared memory; adj[pos] is the adjoint
+// of the gate at engine position pos (global qubits, matrices in mats).
+template <typename T>
+__global__ void dual_expect_resident_kernel(const DGate *__restrict__ adj, const T *__restrict__ mats, uint32_t G,
+                                            int n, const T *__restrict__ psi_R, uint64_t target,
+                                            const uint32_t *__restrict__ first_loc, double *__restrict__ out6) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[6][32];
+    const uint32_t N = 1u << n;
+    T *s = reinterpret_cast<T *>(smem_raw);
+    T *f = s + N;
+    for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) {
+        s[i] = psi_R[i];
+        T z;
+        z.x = i == target ? 1 : 0;
+        z.y = 0;
+        f[i] = z;
+    }
+    __syncthreads();
+    for (uint32_t pos = G; pos-- > 0;) {
+        const DGate g = adj[pos];
+        for (int j = 0; j < g.arity; ++j) {
+            const uint32_t q = j ? g.q1 : g.q0, bit = 1u << q;
+            double c[6] = {0, 0, 0, 0, 0, 0};
+            for (uint32_t p = threadIdx.x; p < N / 2; p += blockDim.x) {
+                const uint32_t i0 = insert_zero(p, q);
+                cross_terms(s[i0], s[i0 | bit], f[i0], f[i0 | bit], c);
+            }
+            block_sum6(c, red);  // its barriers also end this round's reads of s and f
+            if (threadIdx.x == 0) {
+                double *o = out6 + 6 * (size_t)(first_loc[pos] + j);
+#pragma unroll
+                for (int k = 0; k < 6; ++k) o[k] = c[k];
+            }
+        }
+        if (g.cls != GC_NOP) {
+            __syncthreads();
+            tile_gate(s, n, g, mats + g.mat);
+            tile_gate(f, n, g, mats + g.mat);
+            __syncthreads();
+        }
+    }
+}
+
+void launch_dual_expect_resident(const DGate *adj, const void *mats, uint32_t G, int n, int precision,
+                                 const void *psi_R, uint64_t target, const uint32_t *first_loc, double *out6,
+                                 cudaStream_t st) {
+    const size_t smem = (size_t(2) << n) * (precision == ARSO_C64 ? 8 : 16);
+    ProfScope ps_(ARSO_K_OTHER, (double)smem, st);
+    if (precision == ARSO_C64) {
+        if (smem > 48 * 1024)
+            ARSO_CUDA(cudaFuncSetAttribute(dual_expect_resident_kernel<float2>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        dual_expect_resident_kernel<float2><<<1, 512, smem, st>>>(adj, static_cast<const float2 *>(mats), G, n,
+                                                                  static_cast<const float2 *>(psi_R), target,
+                                                                  first_loc, out6);
+    } else {
+        if (smem > 48 * 1024)
+            ARSO_CUDA(cudaFuncSetAttribute(dual_expect_resident_kernel<double2>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        dual_expect_resident_kernel<double2><<<1, 512, smem, st>>>(adj, static_cast<const double2 *>(mats), G, n,
+                                                                   static_cast<const double2 *>(psi_R), target,
+                                                                   first_loc, out6);
+    }
+    ARSO_CUDA(cudaGetLastError());
+}
+
+// The same backward step on complex64 states in HBM, one launch per gate: each
+// thread takes the cross terms of its pairs (quads) before undoing the gate on
+// them. Per-thread FP32 sums, FP64 block partials: block b of a position writes
+// partials[b * 12 + 6 j + k] for the gate's j-th qubit.
+__global__ void dual_gate_expect_kernel(float2 *psi, float2 *phi, int n, DGate g, M16 mm, double *partials) {
+    __shared__ double red[6][32];
+    const float2 *m16 = mm.m;
+    const float2 m0 = m16[0], m1 = m16[1], m2 = m16[2], m3 = m16[3];
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const bool write = g.cls != GC_NOP;
+    float c0[6] = {0, 0, 0, 0, 0, 0}, c1[6] = {0, 0, 0, 0, 0, 0};
+    if (g.arity == 1) {
+        const uint64_t bit = 1ull << g.q0, lo = bit - 1, half = 1ull << (n - 1);
+        for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < half; p += stride) {
+            const uint64_t i0 = ((p & ~lo) << 1) | (p & lo), i1 = i0 | bit;
+            float2 a0 = psi[i0], a1 = psi[i1], b0 = phi[i0], b1 = phi[i1];
+            cross_terms(a0, a1, b0, b1, c0);
+            if (write) {
+                gate1(g, m0, m1, m2, m3, a0, a1);
+                gate1(g, m0, m1, m2, m3, b0, b1);
+                psi[i0] = a0, psi[i1] = a1, phi[i0] = b0, phi[i1] = b1;
+            }
+        }
+    } else {
+        const uint32_t lo = g.q0 < g.q1 ? g.q0 : g.q1, hi = g.q0 < g.q1 ? g.q1 : g.q0;
+        const uint64_t b0 = 1ull << g.q0, b1 = 1ull << g.q1, quarter = 1ull << (n - 2);
+        for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < quarter; p += stride) {
+            uint64_t i = p;
+            i = ((i & ~((1ull << lo) - 1)) << 1) | (i & ((1ull << lo) - 1));
+            i = ((i & ~((1ull << hi) - 1)) << 1) | (i & ((1ull << hi) - 1));
+            const uint64_t idx[4] = {i, i | b0, i | b1, i | b0 | b1};
+            float2 a[4], b[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) a[k] = psi[idx[k]], b[k] = phi[idx[k]];
+            cross_terms(a[0], a[1], b[0], b[1], c0);  // along q0
+            cross_terms(a[2], a[3], b[2], b[3], c0);
+            cross_terms(a[0], a[2], b[0], b[2], c1);  // along q1
+            cross_terms(a[1], a[3], b[1], b[3], c1);
+            if (write) {
+                gate2(g, m16, a);
+                gate2(g, m16, b);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) psi[idx[k]] = a[k], phi[idx[k]] = b[k];
+            }
+        }
+    }
+    double v[6];
+    double *out = partials + (size_t)blockIdx.x * 12;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v[k] = c0[k];
+    block_sum6(v, red);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) out[k] = v[k];
+    if (g.arity == 2) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v[k] = c1[k];
+        block_sum6(v, red);
+        if (threadIdx.x == 0)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) out[6 + k] = v[k];
+    }
+}
+
+// Adds the block partials of `count` positions in a fixed order: block k reduces
+// position k and writes its qubits' six sums to out6[6 * (loc[k] + j)].
+__global__ void dual_expect_reduce_kernel(const double *__restrict__ partials, uint32_t blocks,
+                                          const uint32_t *__restrict__ loc, const uint8_t *__restrict__ arity,
+                                          double *out6) {
+    __shared__ double red[12][128];
+    const double *p = partials + (size_t)blockIdx.x * blocks * 12;
+    double v[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (uint32_t b = threadIdx.x; b < blocks; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < 12; ++k) v[k] += p[(size_t)b * 12 + k];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) red[k][threadIdx.x] = v[k];
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+#pragma unroll
+            for (int k = 0; k < 12; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x < 6u * arity[blockIdx.x]) out6[6 * (size_t)loc[blockIdx.x] + threadIdx.x] = red[threadIdx.x][0];
+}
+
+void launch_dual_gate_expect(float2 *psi, float2 *phi, int n, const DGate &g, const M16 &m, double *partials,
+                             cudaStream_t st) {
+    const uint32_t blocks = expect_hbm_blocks(n);
+    ProfScope ps_(ARSO_K_OTHER, 32.0 * (double)(1ull << n), st);
+    dual_gate_expect_kernel<<<blocks, 256, 0, st>>>(psi, phi, n, g, m, partials);
+    ARSO_CUDA(cudaGetLastError());
+}
+
+void launch_dual_expect_reduce(const double *partials, uint32_t count, uint32_t blocks, const uint32_t *loc,
+                               const uint8_t *arity, double *out6, cudaStream_t st) {
+    if (!count) return;
+    ProfScope ps_(ARSO_K_REDUCE, 96.0 * count * blocks, st);
+    dual_expect_reduce_kernel<<<count, 128, 0, st>>>(partials, blocks, loc, arity, out6);
     ARSO_CUDA(cudaGetLastError());
 }
 

@@ -659,3 +659,94 @@ def test_split_trajectory_ranges_are_bit_identical(arso, n, kw):
         arso.run_trajectories(cc, arso.sample_errors(cc, p / 3, p / 3, p / 3, seed, begin, count), crit, s)
         parts.append(s)
     assert np.array_equal(np.concatenate(parts), whole)
+
+
+# ---------------------- outcome probability: backward states (Eq. (3), Eq. (4)) ---
+
+def _outcome_case(arso, case):
+    """(circuit with an outcome criterion, compile kwargs, tolerance)."""
+    if case == "adder_resident_c64":
+        circ, kw, tol = C.cuccaro_adder(4, 11, 6), {}, SCORE_TOL
+    elif case == "adder_resident_c128":
+        circ, kw, tol = C.cuccaro_adder(2, 3, 2), {"precision": arso.C128}, 1e-12
+    elif case == "random_resident_c64":
+        circ, kw, tol = C.random_circuit(9, 90, 21), {}, SCORE_TOL
+    elif case == "random_resident_c128":
+        circ, kw, tol = C.random_circuit(7, 90, 22), {"precision": arso.C128}, 1e-12
+    elif case == "bv_streaming":
+        circ, kw, tol = C.bernstein_vazirani(15, 0b10110011010101), {"tile_qubits": 10}, SCORE_TOL
+    else:  # random_streaming: every gate kind through the HBM backward kernel
+        circ, kw, tol = C.random_circuit(14, 40, 9), {"tile_qubits": 10}, SCORE_TOL
+    if case.startswith("random"):
+        psi = statevector.simulate(circ)
+        circ.criterion = C.Criterion("outcome", target=int(np.argmax(np.abs(psi))), threshold=0.5, aggregate="mean")
+    else:
+        circ.criterion = C.Criterion("outcome", target=circ.criterion.target, threshold=0.5, aggregate="mean")
+    return circ, kw, tol
+
+
+@pytest.mark.parametrize("case", ["adder_resident_c64", "adder_resident_c128", "random_resident_c64",
+                                  "random_resident_c128", "bv_streaming", "random_streaming"])
+def test_fast_outcome_exhaustive_matches_oracle(arso, case):
+    # the backward sweep scores the single-error state with P after gate g as
+    # |<phi_g|P|psi_g>|^2 (phi_g = W^dagger |t>); the oracle simulates every such state
+    circ, kw, tol = _outcome_case(arso, case)
+    crit = circ.criterion
+    cc = arso.compile_circuit(circ.n, circ.gates, **kw)
+    P, per = arso.exhaustive(cc, crit)
+    a = ox.analyse(circ)
+    assert abs(P[0] - a["P_R"]) < tol
+    for k, e in enumerate(("X", "Z", "Y")):
+        assert abs(P[1 + k] - a["P_e"][e]) < tol, e
+        assert np.max(np.abs(per[k * circ.L:(k + 1) * circ.L] - a["per_location"][e])) < tol, e
+
+
+@pytest.mark.parametrize("case", ["adder_resident_c64", "random_streaming"])
+def test_fast_outcome_exhaustive_matches_single_error_trajectories(arso, case):
+    circ, kw, tol = _outcome_case(arso, case)
+    fast = arso.compile_circuit(circ.n, circ.gates, **kw)
+    slow = arso.compile_circuit(circ.n, circ.gates, flags=arso.OPT_NO_FAST_EXHAUSTIVE, **kw)
+    Pf, per_f = arso.exhaustive(fast, circ.criterion)
+    Ps, per_s = arso.exhaustive(slow, circ.criterion)
+    assert np.max(np.abs(per_f - per_s)) < 10 * tol
+    assert np.max(np.abs(Pf - Ps)) < 10 * tol
+
+
+def test_fast_outcome_exhaustive_streaming_adder(arso):
+    # a 14-qubit Clifford+T adder on the streaming engine: backward sweep against
+    # simulating all 3L single-error states as trajectories
+    circ = C.cuccaro_adder(6, 45, 17)
+    crit = C.Criterion("outcome", target=circ.criterion.target, threshold=0.5, aggregate="mean")
+    fast = arso.compile_circuit(circ.n, circ.gates, tile_qubits=10)
+    slow = arso.compile_circuit(circ.n, circ.gates, tile_qubits=10, flags=arso.OPT_NO_FAST_EXHAUSTIVE)
+    Pf, per_f = arso.exhaustive(fast, crit)
+    Ps, per_s = arso.exhaustive(slow, crit)
+    assert np.max(np.abs(per_f - per_s)) < 10 * SCORE_TOL
+    assert np.max(np.abs(Pf - Ps)) < 10 * SCORE_TOL
+    assert abs(Pf[0] - 1.0) < SCORE_TOL  # the error-free adder reaches its sum with certainty
+
+
+@pytest.mark.parametrize("cache_boundaries", [0, 4])
+def test_outcome_suffix_reuse_scores_equal_full_runs(arso, cache_boundaries):
+    """Outcome probability taken right after the last error as the overlap with the
+    backward state W^dagger |t> at that boundary equals the full run's |<t|psi>|^2."""
+    circ = C.cuccaro_adder(7, 101, 77)  # 16 qubits
+    sb = (1 << circ.n) * 8
+    kw = dict(tile_qubits=11, cache_bytes=cache_boundaries * sb)
+    on = arso.compile_circuit(circ.n, circ.gates, **kw)
+    off = arso.compile_circuit(circ.n, circ.gates, flags=arso.OPT_NO_SUFFIX_REUSE, **kw)
+    assert on.info().n_passes > 3
+    T, p = 64, 3e-3
+    s_on, s_off = np.zeros(T), np.zeros(T)
+    f_on, f_off = np.zeros(T, np.uint8), np.zeros(T, np.uint8)
+    arso.run_trajectories(on, arso.sample_errors(on, p / 3, p / 3, p / 3, 4, 0, T), circ.criterion, s_on, f_on)
+    arso.run_trajectories(off, arso.sample_errors(off, p / 3, p / 3, p / 3, 4, 0, T), circ.criterion, s_off, f_off)
+    assert np.max(np.abs(s_on - s_off)) < SCORE_TOL
+    away = np.abs(s_off - circ.criterion.threshold) > SCORE_TOL
+    assert np.array_equal(f_on[away], f_off[away])
+    lists = sampling.sample(4, 0, T, circ.L, p / 3, p / 3, p / 3)
+    errored = [i for i in range(T) if lists[i]]
+    assert len(errored) > 10
+    for t in errored[:3]:
+        o = criteria.score(circ.criterion, statevector.simulate(circ, lists[t]))
+        assert abs(s_on[t] - o) < SCORE_TOL
