@@ -93,7 +93,8 @@ typedef struct {
  * sweep keeps the state in one CTA (resident circuits) or in HBM (streaming
  * complex64 circuits, one gate and one expectation per launch). This flag
  * simulates the 3L single-error trajectories instead (for comparisons). */
-enum { ARSO_OPT_NO_SUFFIX_REUSE = 1, ARSO_OPT_NO_GRAPHS = 2, ARSO_OPT_NO_FAST_EXHAUSTIVE = 4 };
+enum { ARSO_OPT_NO_SUFFIX_REUSE = 1, ARSO_OPT_NO_GRAPHS = 2, ARSO_OPT_NO_FAST_EXHAUSTIVE = 4,
+       ARSO_OPT_NO_PERSISTENT = 8 /* arso_run_batch runs this circuit on its own launches */ };
 
 typedef struct arso_circuit arso_circuit;
 typedef struct arso_error_list arso_error_list;
@@ -198,14 +199,23 @@ arso_status arso_run_trajectories(const arso_circuit *c, const arso_error_list *
 arso_status arso_aggregate(const double *score, const uint8_t *pass_flags, uint64_t n, void *stream, double *out);
 
 /* Run the trajectories of many circuits of uneven sizes and depths in one
- * call (Sec. IV-B, Monte Carlo runs, for a batch of circuits). Circuits with
- * 10..13 qubits (complex64) run together in ONE persistent launch: CTAs pull
- * (circuit, block of trajectories) items from a device queue, longest first,
- * and a 2^n-amplitude circuit runs 2^(13-n) trajectories side by side in one
- * CTA. Other circuits run their own resident launch or fused pass sequence
- * (replayed from captured CUDA graphs). score_out[i] (n_traj of errors[i]
- * doubles) and pass_out[i] (bytes, or NULL; pass_out itself may be NULL) are
- * device or host pointers as in arso_run_trajectories. */
+ * call (Sec. IV-B, Monte Carlo runs, for a batch of circuits). Every complex64
+ * circuit (resident, and streaming with 13-qubit tiles) runs in ONE persistent
+ * launch: CTAs pull work from a device queue in a dependency order: the
+ * error-free score of each circuit (which the error-free trajectories take),
+ * blocks of trajectories of resident circuits (2^(13-n) side by side in one CTA,
+ * at most 32 below 10 qubits), and one pass of one trajectory of a streaming
+ * circuit per tile. Streaming trajectories run in working slots (16 GiB in all,
+ * split over the circuits by their work); a tile waits, with a bounded poll, for
+ * its slot's previous pass. Circuits compiled with ARSO_OPT_NO_PERSISTENT,
+ * complex128 circuits and streaming circuits with other tile sizes run their own
+ * launches (resident launch or captured pass sequence). score_out[i] (n_traj of
+ * errors[i] doubles) and pass_out[i] (bytes, or NULL; pass_out itself may be
+ * NULL) are device or host pointers as in arso_run_trajectories. Scores equal
+ * those of arso_run_trajectories bit for bit, except that error-free
+ * trajectories take psi_R's score summed in another order (within rounding).
+ * Errors: ARSO_EINVAL, ARSO_ENOMEM, ARSO_ECUDA, ARSO_ETIMEOUT (a dependency wait
+ * gave up; no score of the call is valid). */
 arso_status arso_run_batch(size_t count, arso_circuit *const *circuits, const arso_error_list *const *errors,
                            const arso_criterion *crits, void *stream, double *const *score_out,
                            uint8_t *const *pass_out);
@@ -407,7 +417,8 @@ enum {
     ARSO_K_REDUCE = 4,      /* criterion partials, finish, sums */
     ARSO_K_OTHER = 5,       /* bookkeeping kernels (scan, sort, fill, init) */
     ARSO_K_GEMM = 6,        /* surrogate MLP GEMMs on the tensor cores */
-    ARSO_K_COUNT = 7
+    ARSO_K_MIX = 7,         /* persistent launch of a batch of uneven circuits (arso_run_batch) */
+    ARSO_K_COUNT = 8
 };
 typedef struct {
     uint64_t launches;

@@ -199,6 +199,7 @@ def _gates_array(gates):
 OPT_NO_SUFFIX_REUSE = 1
 OPT_NO_GRAPHS = 2
 OPT_NO_FAST_EXHAUSTIVE = 4
+OPT_NO_PERSISTENT = 8
 
 
 def compile_circuit(n, gates, precision=C64, tile_qubits=0, low_qubits=0, max_batch=0, cache_bytes=0, flags=0):
@@ -288,7 +289,7 @@ class KernelStats(C.Structure):
     _fields_ = [("launches", C.c_uint64), ("ms", C.c_double), ("bytes", C.c_double), ("flops", C.c_double)]
 
 
-K_PASS, K_PASS_LAST, K_RESIDENT, K_SAMPLE, K_REDUCE, K_OTHER, K_GEMM = range(7)
+K_PASS, K_PASS_LAST, K_RESIDENT, K_SAMPLE, K_REDUCE, K_OTHER, K_GEMM, K_MIX = range(8)
 
 
 def profile_enable(on=True):

@@ -1136,7 +1136,343 @@ static void exhaustive_finish(arso_circuit *c, const DevCrit &dc, cudaStream_t s
     }
 }
 
-// Eq. (4) with E(N_e) = L p_e
+// ------------------------------------------------------ persistent batch ---
+// Every complex64 circuit of an arso_run_batch call in one launch of mix_kernel
+// (kernels.h, MixArgs). The host lists the units in dependency order:
+// error-free reference scores first, then the resident items longest first, then
+// the streaming units by their level in their working slot's chain of passes.
+enum MixKind { MK_NONE = 0, MK_SMALL = 1, MK_RES = 2, MK_STR = 3 };
+static MixKind mix_kind(const arso_circuit *c) {
+    if (c->precision != ARSO_C64 || (c->flags & ARSO_OPT_NO_PERSISTENT)) return MK_NONE;
+    if (c->engine == 0) return c->reg_blocked ? MK_RES : MK_SMALL;
+    return c->reg_blocked && c->tile_qubits == 13 ? MK_STR : MK_NONE;
+}
+
+constexpr uint64_t MIX_SLOT_BUDGET = 16ull << 30;  // working slots of all streaming circuits of a call
+
+static void run_mixed(const std::vector<size_t> &sel, arso_circuit *const *circuits,
+                      const arso_error_list *const *errors, const std::vector<DevCrit> &dcs,
+                      const std::vector<double *> &d_score, const std::vector<uint8_t *> &d_pass, cudaStream_t st) {
+    const size_t C = sel.size();
+    if (!C) return;
+    std::vector<MixKind> kind(C);
+    for (size_t q = 0; q < C; ++q) {
+        arso_circuit *c = circuits[sel[q]];
+        kind[q] = mix_kind(c);
+        ensure_cache(c, st);
+        if (kind[q] == MK_STR && dcs[sel[q]].d.kind == ARSO_CRIT_OUTCOME && suffix_wanted(c, dcs[sel[q]].d))
+            ensure_bwd_cache(c, dcs[sel[q]].d.target, st);
+    }
+    // first (and, streaming, last) event positions of every trajectory: all copies, one synchronisation
+    std::vector<std::vector<uint32_t>> first(C), last(C);
+    for (size_t q = 0; q < C; ++q) {
+        const arso_error_list *e = errors[sel[q]];
+        if (!e->n_traj) continue;
+        first[q].resize(e->n_traj);
+        copy_d2h(first[q].data(), e->d_first.ptr, e->n_traj * 4, st);
+        if (kind[q] == MK_STR) {
+            last[q].resize(e->n_traj);
+            copy_d2h(last[q].data(), e->d_last.ptr, e->n_traj * 4, st);
+        }
+    }
+    ARSO_CUDA(cudaStreamSynchronize(st));
+
+    std::vector<MixRef> refs;
+    std::vector<MixSmall> smalls;
+    std::vector<BatchCircuit> rcircs;
+    std::vector<BatchItem> items;
+    std::vector<uint64_t> ids;
+    std::vector<MixStream> streams;
+    std::vector<MixPass> spasses;
+    std::vector<MixTraj> strajs;
+    std::vector<uint32_t> scslot;
+    struct Res { uint32_t item; uint64_t cost; bool small; };
+    std::vector<Res> res_units;
+    struct Str { uint32_t stream, k, j, level; };
+    std::vector<Str> str_units;
+    // counters (zeroed): ref chunks done, then per stream slot and trajectory counters
+    uint64_t n_counters = 0, n_partials = 0, work_bytes = 0;
+    std::vector<uint64_t> ref_part_off, ref_ctr_off, st_slot_off, st_traj_off, st_part_off, st_work_off, st_pass_off,
+        st_traj_tab_off, st_cslot_off;
+    double bytes = 0.0, flops = 0.0;
+
+    // pass 1: streaming slot counts (the slot budget split by each circuit's work)
+    std::vector<std::vector<uint64_t>> sid(C);
+    std::vector<std::vector<int>> sstart(C), send(C);
+    std::vector<double> swork(C, 0.0);
+    double work_total = 0.0;
+    for (size_t q = 0; q < C; ++q) {
+        if (kind[q] != MK_STR) continue;
+        arso_circuit *c = circuits[sel[q]];
+        const uint32_t P = (uint32_t)c->passes.size();
+        const bool suffix = suffix_wanted(c, dcs[sel[q]].d);
+        for (uint64_t t = 0; t < first[q].size(); ++t) {
+            if (first[q][t] == NO_EVENT) continue;
+            uint32_t fp = c->pass_of_pos[first[q][t]];
+            while (c->ckpt_pass[fp] == NO_EVENT) --fp;
+            uint32_t lp = P - 1;
+            if (suffix) {
+                lp = c->pass_of_pos[last[q][t]];
+                while (c->ckpt_pass[lp + 1] == NO_EVENT) ++lp;
+            }
+            sid[q].push_back(t);
+            sstart[q].push_back((int)fp);
+            send[q].push_back((int)lp);
+            swork[q] += (double)(lp - fp + 1) * (double)c->state_bytes();
+        }
+        work_total += swork[q];
+    }
+    for (size_t q = 0; q < C; ++q) {
+        arso_circuit *c = circuits[sel[q]];
+        const arso_error_list *e = errors[sel[q]];
+        const DevCrit &dc = dcs[sel[q]];
+        const uint64_t N = 1ull << c->n;
+        // the circuit's error-free score, filled into its error-free trajectories
+        MixRef r{};
+        r.n = (int)c->n;
+        r.chunks = (uint32_t)((N + 8191) >> 13);
+        r.psi_R = static_cast<const float2 *>(ref_state_ptr(c));
+        r.crit = dc.d;
+        r.first = e->d_first.as<uint32_t>();
+        r.n_traj = e->n_traj;
+        r.score = d_score[sel[q]];
+        r.pass_flags = d_pass[sel[q]];
+        ref_part_off.push_back(n_partials);
+        n_partials += r.chunks;
+        ref_ctr_off.push_back(n_counters);
+        n_counters += 1;
+        refs.push_back(r);
+        bytes += (double)c->state_bytes();
+        if (kind[q] == MK_SMALL || kind[q] == MK_RES) {
+            const bool small = kind[q] == MK_SMALL;
+            std::vector<std::pair<uint32_t, uint64_t>> todo;  // (checkpoint, trajectory)
+            for (uint64_t t = 0; t < first[q].size(); ++t)
+                if (first[q][t] != NO_EVENT)
+                    todo.emplace_back((small ? first[q][t] : c->phase_of_pos[first[q][t]]) / (uint32_t)c->ckpt_every, t);
+            std::sort(todo.begin(), todo.end());
+            const uint32_t per = small ? std::min<uint32_t>(MIX_SMALL_MAX, 1u << (13 - c->n)) : 1u << (13 - c->n);
+            const uint32_t desc = small ? (uint32_t)smalls.size() : (uint32_t)rcircs.size();
+            const uint64_t G = c->gates.size();
+            for (size_t k = 0; k < todo.size(); k += per) {
+                BatchItem it{};
+                it.circuit = desc;
+                it.count = (uint32_t)std::min<size_t>(per, todo.size() - k);
+                it.ck = todo[k].first;
+                it.off = ids.size();
+                for (size_t u = 0; u < it.count; ++u) ids.push_back(todo[k + u].second);
+                const uint64_t g0 = small ? std::min<uint64_t>(G, (uint64_t)it.ck * c->ckpt_every)
+                                          : c->ph_gb[std::min<uint64_t>(c->ph_R.size(), (uint64_t)it.ck * c->ckpt_every)];
+                res_units.push_back({(uint32_t)items.size(), G - g0, small});
+                items.push_back(it);
+                bytes += (double)it.count * 2.0 * c->state_bytes();
+            }
+            if (small) {
+                MixSmall m{};
+                m.n = (int)c->n;
+                m.G = (uint32_t)G;
+                m.ckpt_every = (uint32_t)c->ckpt_every;
+                m.n_ckpt = c->n_ckpt;
+                m.gates = c->d_gates.as<DGate>();
+                m.mats = c->d_mats.as<float2>();
+                m.cache = c->d_cache.as<float2>();
+                m.offsets = e->d_offsets.as<uint64_t>();
+                m.keys = e->d_key.as<uint32_t>();
+                m.crit = dc.d;
+                m.score = d_score[sel[q]];
+                m.pass_flags = d_pass[sel[q]];
+                smalls.push_back(m);
+            } else {
+                BatchCircuit b{};
+                b.n = (int)c->n;
+                b.n_phases = (uint32_t)c->ph_R.size();
+                b.n_ckpt = c->n_ckpt;
+                b.ckpt_every = (uint32_t)c->ckpt_every;
+                b.gates = c->d_gates.as<DGate>();
+                b.mats = c->d_mats.as<float2>();
+                b.ph_gb = c->d_ph_gb.as<uint32_t>();
+                b.ph_R = c->d_ph_R.as<uint32_t>();
+                b.phase_of_pos = c->d_phase_of_pos.as<uint32_t>();
+                b.rops = c->d_rops.as<RegOp>();
+                b.cache = c->d_cache.as<float2>();
+                b.offsets = e->d_offsets.as<uint64_t>();
+                b.keys = e->d_key.as<uint32_t>();
+                b.crit = dc.d;
+                b.score = d_score[sel[q]];
+                b.pass_flags = d_pass[sel[q]];
+                rcircs.push_back(b);
+            }
+            continue;
+        }
+        // streaming: trajectories sorted by (start, end), dealt round robin to slots; each
+        // slot runs its trajectories one after another
+        const uint32_t P = (uint32_t)c->passes.size();
+        const size_t sb = c->state_bytes();
+        const uint64_t T = sid[q].size();
+        const uint32_t tiles = 1u << (c->n - c->tile_qubits);
+        const bool overlap = dc.d.kind == ARSO_CRIT_OUTCOME && suffix_wanted(c, dc.d);
+        uint64_t S = 1;
+        if (T) {
+            const double share = work_total > 0 ? swork[q] / work_total : 1.0;
+            S = std::max<uint64_t>(1, std::min<uint64_t>(T, (uint64_t)(share * (double)MIX_SLOT_BUDGET / (double)sb)));
+        }
+        std::vector<size_t> order(T);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+            return sstart[q][x] != sstart[q][y] ? sstart[q][x] < sstart[q][y] : send[q][x] < send[q][y];
+        });
+        const uint32_t si = (uint32_t)streams.size();
+        std::vector<uint32_t> slot_level(S, 0), slot_base(S, 0);
+        const uint64_t traj0 = strajs.size();
+        for (uint64_t k = 0; k < T; ++k) {
+            const size_t o = order[k];
+            const uint32_t slot = (uint32_t)(k % S);
+            MixTraj mt{};
+            mt.tr = sid[q][o];
+            mt.slot = slot;
+            mt.base = slot_base[slot];
+            mt.start = sstart[q][o];
+            mt.end = send[q][o];
+            const uint32_t len = (uint32_t)(mt.end - mt.start + 1);
+            ARSO_REQUIRE((uint64_t)slot_base[slot] + (uint64_t)len * tiles < (1ull << 32), "persistent batch: slot chain too long");
+            for (uint32_t j = (uint32_t)mt.start; j <= (uint32_t)mt.end; ++j) {
+                str_units.push_back({si, (uint32_t)k, j, slot_level[slot] + (j - (uint32_t)mt.start)});
+                bytes += 2.0 * (double)sb;
+                flops += c->passes[j].flops_per_amp * (double)N;
+            }
+            slot_level[slot] += len;
+            slot_base[slot] += len * tiles;
+            strajs.push_back(mt);
+        }
+        MixStream ms{};
+        ms.n = (int)c->n;
+        ms.t = (int)c->tile_qubits;
+        ms.c = (int)c->low_qubits;
+        ms.tiles = tiles;
+        ms.ph_gb = c->d_ph_gb.as<uint32_t>();
+        ms.ph_R = c->d_ph_R.as<uint32_t>();
+        ms.rops = c->d_rops.as<RegOp>();
+        ms.mats = c->d_mats.as<float2>();
+        ms.cache = c->d_cache.as<float2>();
+        ms.ref_cache = overlap ? c->d_bwd.as<float2>() : c->d_cache.as<float2>();
+        ms.offsets = e->d_offsets.as<uint64_t>();
+        ms.keys = e->d_key.as<uint32_t>();
+        ms.crit = dc.d;
+        if (overlap) ms.crit.kind = ARSO_CRIT_FIDELITY;  // |<t|W a>| = |<W^dagger t|a>|
+        ms.score = d_score[sel[q]];
+        ms.pass_flags = d_pass[sel[q]];
+        st_pass_off.push_back(spasses.size());
+        for (uint32_t j = 0; j < P; ++j) {
+            MixPass mp{};
+            uint64_t tm = 0;
+            for (uint32_t qq : c->passes[j].tile_qubits) tm |= 1ull << qq;
+            mp.rest_mask = ((1ull << c->n) - 1) & ~tm;
+            mp.offs = c->d_offs.as<uint32_t>() + c->offs_base[j];
+            mp.gb = c->passes[j].gb;
+            mp.pb = c->passes[j].pb;
+            mp.pe = c->passes[j].pe;
+            spasses.push_back(mp);
+        }
+        st_cslot_off.push_back(scslot.size());
+        scslot.insert(scslot.end(), c->ckpt_pass.begin(), c->ckpt_pass.end());
+        st_traj_tab_off.push_back(traj0);
+        st_slot_off.push_back(n_counters);
+        n_counters += S;
+        st_traj_off.push_back(n_counters);
+        n_counters += T;
+        st_part_off.push_back(n_partials);
+        n_partials += T * tiles;
+        st_work_off.push_back(work_bytes);
+        work_bytes += S * sb;
+        streams.push_back(ms);
+    }
+    // the unit list: references, resident items longest first, streaming units by level
+    std::stable_sort(res_units.begin(), res_units.end(), [](const Res &x, const Res &y) { return x.cost > y.cost; });
+    std::stable_sort(str_units.begin(), str_units.end(), [](const Str &x, const Str &y) { return x.level < y.level; });
+    std::vector<MixUnit> units;
+    std::vector<uint64_t> unit_end;
+    uint64_t total = 0;
+    for (size_t q = 0; q < refs.size(); ++q) {
+        units.push_back({MIX_REF, (uint32_t)q, 0, 0});
+        unit_end.push_back(total += refs[q].chunks);
+    }
+    for (const Res &r : res_units) {
+        units.push_back({r.small ? (uint32_t)MIX_SMALL : (uint32_t)MIX_RES, r.item, 0, 0});
+        unit_end.push_back(total += 1);
+    }
+    ARSO_REQUIRE(units.size() + str_units.size() < (1ull << 32), "persistent batch: too many units");
+    for (const Str &x : str_units) {
+        units.push_back({MIX_STR, x.stream, x.k, x.j});
+        unit_end.push_back(total += streams[x.stream].tiles);
+    }
+    if (!total) return;
+
+    // device tables; descriptors point into the shared buffers
+    Scratch d_units(st, units.size() * sizeof(MixUnit)), d_end(st, unit_end.size() * 8);
+    Scratch d_refs(st, std::max<size_t>(refs.size(), 1) * sizeof(MixRef));
+    Scratch d_smalls(st, std::max<size_t>(smalls.size(), 1) * sizeof(MixSmall));
+    Scratch d_rcircs(st, std::max<size_t>(rcircs.size(), 1) * sizeof(BatchCircuit));
+    Scratch d_items(st, std::max<size_t>(items.size(), 1) * sizeof(BatchItem));
+    Scratch d_ids(st, std::max<size_t>(ids.size(), 1) * 8);
+    Scratch d_streams(st, std::max<size_t>(streams.size(), 1) * sizeof(MixStream));
+    Scratch d_passes(st, std::max<size_t>(spasses.size(), 1) * sizeof(MixPass));
+    Scratch d_trajs(st, std::max<size_t>(strajs.size(), 1) * sizeof(MixTraj));
+    Scratch d_cslot(st, std::max<size_t>(scslot.size(), 1) * 4);
+    Scratch d_parts(st, std::max<uint64_t>(n_partials, 1) * sizeof(Partial));
+    Scratch d_ctr(st, std::max<uint64_t>(n_counters, 1) * 4);
+    Scratch d_work(st, work_bytes);
+    Scratch d_qc(st, 16);  // queue counter (8 bytes) and error word
+    for (size_t q = 0; q < refs.size(); ++q) {
+        refs[q].partials = d_parts.as<Partial>() + ref_part_off[q];
+        refs[q].done = d_ctr.as<uint32_t>() + ref_ctr_off[q];
+    }
+    for (size_t q = 0; q < streams.size(); ++q) {
+        MixStream &ms = streams[q];
+        ms.passes = d_passes.as<MixPass>() + st_pass_off[q];
+        ms.cache_slot = d_cslot.as<uint32_t>() + st_cslot_off[q];
+        ms.trajs = d_trajs.as<MixTraj>() + st_traj_tab_off[q];
+        ms.slot_done = d_ctr.as<uint32_t>() + st_slot_off[q];
+        ms.traj_done = d_ctr.as<uint32_t>() + st_traj_off[q];
+        ms.partials = d_parts.as<Partial>() + st_part_off[q];
+        ms.work = reinterpret_cast<float2 *>(d_work.as<char>() + st_work_off[q]);
+    }
+    auto up = [&](Scratch &d, const void *src, size_t b) {
+        if (b) copy_h2d(d.ptr, src, b, st);
+    };
+    up(d_units, units.data(), units.size() * sizeof(MixUnit));
+    up(d_end, unit_end.data(), unit_end.size() * 8);
+    up(d_refs, refs.data(), refs.size() * sizeof(MixRef));
+    up(d_smalls, smalls.data(), smalls.size() * sizeof(MixSmall));
+    up(d_rcircs, rcircs.data(), rcircs.size() * sizeof(BatchCircuit));
+    up(d_items, items.data(), items.size() * sizeof(BatchItem));
+    up(d_ids, ids.data(), ids.size() * 8);
+    up(d_streams, streams.data(), streams.size() * sizeof(MixStream));
+    up(d_passes, spasses.data(), spasses.size() * sizeof(MixPass));
+    up(d_trajs, strajs.data(), strajs.size() * sizeof(MixTraj));
+    up(d_cslot, scslot.data(), scslot.size() * 4);
+    ARSO_CUDA(cudaMemsetAsync(d_ctr.ptr, 0, std::max<uint64_t>(n_counters, 1) * 4, st));
+    ARSO_CUDA(cudaMemsetAsync(d_qc.ptr, 0, 16, st));
+    MixArgs a{};
+    a.units = d_units.as<MixUnit>();
+    a.unit_end = d_end.as<uint64_t>();
+    a.n_units = (uint32_t)units.size();
+    a.n_sub = total;
+    a.refs = d_refs.as<MixRef>();
+    a.smalls = d_smalls.as<MixSmall>();
+    a.rcircs = d_rcircs.as<BatchCircuit>();
+    a.items = d_items.as<BatchItem>();
+    a.ids = d_ids.as<uint64_t>();
+    a.streams = d_streams.as<MixStream>();
+    a.counter = d_qc.as<unsigned long long>();
+    a.err = reinterpret_cast<uint32_t *>(d_qc.as<char>() + 8);
+    a.wait_limit = 1u << 22;
+    launch_mix(a, bytes, flops, st);
+    uint32_t err = 0;
+    copy_d2h(&err, a.err, 4, st);
+    ARSO_CUDA(cudaStreamSynchronize(st));  // also keeps the host tables alive until the launch is done
+    if (err) throw Error(ARSO_ETIMEOUT, "persistent batch: a dependency wait gave up");
+}
+
+// Eq. (4) with E(N_e) = L p_e// Eq. (4) with E(N_e) = L p_e
 static double eq4(const double *P, uint64_t L, double pe) {
     const double E = (double)L * pe;
     return (P[1] + P[2] + P[3]) * E + P[0] * (1.0 - 3.0 * E);
@@ -1334,12 +1670,16 @@ arso_status arso_run_batch(size_t count, arso_circuit *const *circuits, const ar
                 d_pass[i] = nullptr;
             }
         }
-        // the register-blocked resident circuits share one persistent launch
-        std::vector<size_t> group;
+        // every complex64 circuit in one persistent launch; circuits that opt out run
+        // the earlier route (register-blocked resident circuits in one batched resident
+        // launch, the others on their own launches)
+        std::vector<size_t> mixed, group;
         for (size_t i = 0; i < count; ++i) {
-            if (circuits[i]->engine == 0 && circuits[i]->reg_blocked) group.push_back(i);
+            if (mix_kind(circuits[i]) != MK_NONE) mixed.push_back(i);
+            else if (circuits[i]->engine == 0 && circuits[i]->reg_blocked) group.push_back(i);
             else run_all(circuits[i], errors[i], dcs[i], st, d_score[i], d_pass[i]);
         }
+        run_mixed(mixed, circuits, errors, dcs, d_score, d_pass, st);
         if (!group.empty()) {
             Scratch refs(st, group.size() * 8);
             std::vector<BatchCircuit> descs(group.size());

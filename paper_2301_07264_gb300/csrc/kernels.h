@@ -119,6 +119,99 @@ struct BatchItem {
 void launch_batch_resident(const BatchCircuit *circs, const BatchItem *items, uint32_t n_items, uint32_t *counter,
                            const uint64_t *ids, double bytes, cudaStream_t st);
 
+// Persistent launch over the work of many circuits of uneven size (one launch
+// per arso_run_batch call). The work is a list of units; CTAs take sub-items
+// from one counter in list order:
+//  MIX_REF   error-free score of one circuit, one sub-item per 2^13-amplitude
+//            chunk of psi_R; the last chunk fills the circuit's error-free
+//            trajectories;
+//  MIX_SMALL a batched item of a resident circuit below 2^10 amplitudes (shared-
+//            memory gate engine, up to 32 trajectories side by side);
+//  MIX_RES   a batched register-blocked resident item (BatchItem above);
+//  MIX_STR   one pass of one trajectory of a streaming circuit, one sub-item per
+//            tile; its dependencies (the trajectory's previous pass, or the slot's
+//            previous trajectory) are per-slot counters of finished tiles, and the
+//            list is ordered so that every unit's dependencies come before it.
+enum : uint32_t { MIX_REF = 0, MIX_SMALL = 1, MIX_RES = 2, MIX_STR = 3 };
+struct MixUnit {
+    uint32_t kind;
+    uint32_t idx;  // REF: reference descriptor; SMALL / RES: item; STR: stream descriptor
+    uint32_t a, b; // STR: trajectory (index in the stream's table), pass
+};
+struct MixRef {
+    int n;
+    uint32_t chunks;         // ceil(2^n / 2^13)
+    const float2 *psi_R;
+    DCrit crit;
+    const uint32_t *first;   // per trajectory: first event position or NO_EVENT
+    uint64_t n_traj;
+    Partial *partials;       // per chunk
+    uint32_t *done;          // chunks finished (zeroed before the launch)
+    double *score;
+    uint8_t *pass_flags;
+};
+struct MixSmall {            // resident circuit of n <= 9 qubits, gate-indexed checkpoints
+    int n;
+    uint32_t G, ckpt_every, n_ckpt;
+    const DGate *gates;
+    const float2 *mats;
+    const float2 *cache;
+    const uint64_t *offsets;
+    const uint32_t *keys;
+    DCrit crit;
+    double *score;
+    uint8_t *pass_flags;
+};
+struct MixPass {
+    uint64_t rest_mask;      // global bits outside the pass's tiles
+    const uint32_t *offs;    // tile-high offsets of the pass
+    uint32_t gb, pb, pe, pad;
+};
+struct MixTraj {
+    uint64_t tr;             // trajectory index in the error list
+    uint32_t slot;           // working slot
+    uint32_t base;           // tiles the slot finished before this trajectory's first pass
+    int start, end;          // first pass (from the cached boundary before it) and scored pass
+};
+struct MixStream {
+    int n, t, c;
+    uint32_t tiles;
+    const MixPass *passes;
+    const uint32_t *ph_gb, *ph_R;
+    const RegOp *rops;
+    const float2 *mats;
+    const float2 *cache;       // cached error-free boundary states
+    const float2 *ref_cache;   // states the scored pass is compared with, same entries
+    const uint32_t *cache_slot;
+    float2 *work;              // slots x 2^n
+    uint32_t *slot_done;       // per slot: tiles finished (zeroed before the launch)
+    const uint64_t *offsets;
+    const uint32_t *keys;
+    const MixTraj *trajs;
+    Partial *partials;         // per trajectory x tiles
+    uint32_t *traj_done;       // per trajectory: tiles of its scored pass finished (zeroed)
+    DCrit crit;
+    double *score;
+    uint8_t *pass_flags;
+};
+struct MixArgs {
+    const MixUnit *units;
+    const uint64_t *unit_end;  // inclusive prefix sums of the sub-items per unit
+    uint32_t n_units;
+    uint64_t n_sub;
+    const MixRef *refs;
+    const MixSmall *smalls;
+    const BatchCircuit *rcircs;
+    const BatchItem *items;    // SMALL items index smalls, RES items index rcircs
+    const uint64_t *ids;
+    const MixStream *streams;
+    unsigned long long *counter;
+    uint32_t *err;             // bit 0: a dependency wait gave up
+    uint32_t wait_limit;       // polls per wait
+};
+constexpr uint32_t MIX_SMALL_MAX = 32;  // trajectories per SMALL item
+void launch_mix(const MixArgs &a, double bytes, double flops, cudaStream_t st);
+
 void launch_resident(const ResidentArgs &a, bool ideal, int precision, double bytes, cudaStream_t st);
 void launch_pass(const PassArgs &a, bool last, int precision, uint32_t slots, double bytes, cudaStream_t st);
 void launch_finish_partials(const Partial *partials, uint32_t tiles, uint32_t slots, const uint64_t *slot_traj,

@@ -1036,6 +1036,361 @@ void launch_batch_resident(const BatchCircuit *circs, const BatchItem *items, ui
     ARSO_CUDA(cudaGetLastError());
 }
 
+// ------------------------------------------------- persistent mixed batch ---
+// One launch over every unit of a batch of uneven circuits (MixArgs in kernels.h).
+// A CTA of 256 threads takes sub-items from one counter in list order. Streaming
+// sub-items wait (thread 0, bounded polls) for their slot's counter of finished
+// tiles; since a unit's dependencies always sit earlier in the list, the lowest
+// sub-item in progress never waits on a later one and the launch cannot deadlock.
+// A wait that gives up sets the error word; every CTA then stops at its next item.
+constexpr int MIX_THREADS = BATCH_THREADS;  // one 2^13-amplitude tile: 256 threads x 32 registers
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// thread 0: wait until *ctr >= need; false if the wait gave up or another CTA's did
+__device__ bool mix_wait(const uint32_t *ctr, uint32_t need, uint32_t limit, uint32_t *err) {
+    for (uint32_t it = 0;; ++it) {
+        if (ld_acquire_u32(ctr) >= need) return true;
+        if (it >= limit || ld_acquire_u32(err) != 0u) {
+            atomicOr(err, 1u);
+            return false;
+        }
+        __nanosleep(256);
+    }
+}
+
+__device__ __forceinline__ Partial ld_partial_cg(const Partial *p) {
+    Partial v;
+    v.a = __ldcg(&p->a);
+    v.b = __ldcg(&p->b);
+    v.maxp = __ldcg(&p->maxp);
+    v.idx = __ldcg(&p->idx);
+    return v;
+}
+
+// First unit u >= lo with unit_end[u] > i (warp 0; unit_end ascending, unit_end[lo - 1] <= i
+// by the caller's previous item): 32-way search, each round one load per lane.
+__device__ uint32_t mix_find_unit(const uint64_t *__restrict__ unit_end, uint32_t n_units, uint32_t lo, uint64_t i) {
+    if (__ldg(unit_end + lo) > i) return lo;
+    uint32_t hi = n_units - 1;  // unit_end[hi] = total > i; invariant unit_end[lo] <= i < unit_end[hi]
+    const uint32_t lane = threadIdx.x & 31u;
+    while (hi - lo > 1) {
+        const uint32_t step = (hi - lo + 31) / 32;
+        const uint32_t probe = min(lo + step * (lane + 1), hi);
+        const unsigned m = __ballot_sync(0xffffffffu, __ldg(unit_end + probe) > i);
+        const uint32_t f = (uint32_t)(__ffs(m) - 1);  // lane 31 probes hi, so m != 0
+        const uint32_t nhi = min(lo + step * (f + 1), hi);
+        lo = f == 0 ? lo : lo + step * f;
+        hi = nhi;
+    }
+    return hi;
+}
+
+// MIX_REF: chunk `chunk` of psi_R scored; the last chunk adds the chunk partials in
+// order and gives that score to every error-free trajectory of the circuit.
+__device__ __noinline__ void mix_ref(const MixRef &R, uint32_t chunk, Partial *red, uint32_t *s_flag, double *s_val) {
+    const uint32_t N = 1u << R.n, j0 = chunk << 13, j1 = min(N, j0 + 8192u);
+    Partial acc = empty_partial();
+    for (uint32_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) accumulate(acc, R.crit, R.psi_R[j], R.psi_R, j);
+    acc = block_reduce_partial(acc, red);
+    if (threadIdx.x == 0) {
+        R.partials[chunk] = acc;
+        __threadfence();
+        *s_flag = atomicAdd(R.done, 1u) == R.chunks - 1;
+    }
+    __syncthreads();
+    if (!*s_flag) return;
+    __threadfence();
+    if (threadIdx.x == 0) {
+        Partial sum = empty_partial();
+        for (uint32_t k = 0; k < R.chunks; ++k) {
+            const Partial q = ld_partial_cg(R.partials + k);
+            sum.a += q.a;
+            sum.b += q.b;
+            argmax_merge(sum.maxp, sum.idx, q.maxp, q.idx);
+        }
+        *s_val = finish_score(R.crit, sum);
+    }
+    __syncthreads();
+    const double sc = *s_val;
+    for (uint64_t t = threadIdx.x; t < R.n_traj; t += blockDim.x)
+        if (R.first[t] == NO_EVENT) {
+            R.score[t] = sc;
+            if (R.pass_flags) R.pass_flags[t] = sc >= R.crit.threshold;
+        }
+}
+
+// MIX_SMALL: up to 32 trajectories of one circuit of n <= 9 qubits side by side in
+// shared memory as one state of n + log2(count) qubits (gates touch only the low n
+// bits, so one update covers every trajectory); each trajectory's Pauli errors are
+// applied to its own block; 8 threads score each trajectory.
+__device__ __noinline__ void mix_small(const MixSmall &C, const BatchItem &it, const uint64_t *__restrict__ ids, float2 *s) {
+    __shared__ const uint32_t *s_ev[MIX_SMALL_MAX];
+    __shared__ const uint32_t *s_end[MIX_SMALL_MAX];
+    __shared__ uint32_t s_pe[MIX_SMALL_MAX];
+    const int n = C.n;
+    const uint32_t N = 1u << n, cnt = it.count;
+    int tb = n;
+    while ((1u << (tb - n)) < cnt) ++tb;  // n + ceil(log2 cnt) <= 13
+    const float2 *src = C.cache + (size_t)it.ck * N;
+    for (uint32_t i = threadIdx.x; i < (1u << tb); i += blockDim.x)
+        s[i] = (i >> n) < cnt ? src[i & (N - 1)] : make_float2(0.f, 0.f);
+    if (threadIdx.x < cnt) {
+        const uint64_t tr = ids[it.off + threadIdx.x];
+        s_ev[threadIdx.x] = C.keys + C.offsets[tr];
+        s_end[threadIdx.x] = C.keys + C.offsets[tr + 1];
+    }
+    __syncthreads();
+    const uint32_t g0 = min(C.G, it.ck * C.ckpt_every);
+    for (uint32_t g = g0; g < C.G; ++g) {
+        const DGate gate = C.gates[g];
+        if (gate.cls != GC_NOP) tile_gate(s, tb, gate, C.mats + gate.mat);
+        // this gate's error events of each trajectory: up to two, (valid | qubit << 2 | code) per half
+        bool any = false;
+        if (threadIdx.x < cnt) {
+            const uint32_t *e = s_ev[threadIdx.x], *ee = s_end[threadIdx.x];
+            uint32_t pe = 0, sh = 0;
+            while (e < ee && ev_pos(*e) == g) {
+                const uint32_t q = ev_slot(*e) ? gate.q1 : gate.q0;
+                pe |= (0x8000u | (q << 2) | ev_code(*e)) << sh;
+                sh = 16;
+                ++e;
+            }
+            s_ev[threadIdx.x] = e;
+            s_pe[threadIdx.x] = pe;
+            any = pe != 0;
+        }
+        if (__syncthreads_or(any)) {
+            for (int w = 0; w < 2; ++w) {
+                for (uint32_t p = threadIdx.x; p < (cnt << (n - 1)); p += blockDim.x) {
+                    const uint32_t k = p >> (n - 1), e = (s_pe[k] >> (16 * w)) & 0xFFFFu;
+                    if (!(e & 0x8000u)) continue;
+                    const uint32_t q = (e >> 2) & 63u, code = e & 3u, bit = 1u << q;
+                    const uint32_t i0 = (k << n) | insert_zero(p & ((N >> 1) - 1), q), i1 = i0 | bit;
+                    const float2 a0 = s[i0], a1 = s[i1];
+                    if (code == 1) {
+                        s[i0] = a1;
+                        s[i1] = a0;
+                    } else if (code == 2) {
+                        s[i1] = cneg(a1);
+                    } else {  // Y: (a0, a1) -> (-i a1, i a0), Eq. (2)
+                        s[i0] = make_float2(a1.y, -a1.x);
+                        s[i1] = make_float2(-a0.y, a0.x);
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+    // score: 8 threads per trajectory, FP64 sums, shuffles within each group of 8
+    const uint32_t k = threadIdx.x >> 3, r = threadIdx.x & 7u;
+    const float2 *ref = C.cache + (size_t)(C.n_ckpt - 1) * N;
+    Partial acc = empty_partial();
+    if (k < cnt)
+        for (uint32_t j = r; j < N; j += 8) accumulate(acc, C.crit, s[(k << n) + j], ref, j);
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+        const double a2 = __shfl_down_sync(0xffffffffu, acc.a, o, 8);
+        const double b2 = __shfl_down_sync(0xffffffffu, acc.b, o, 8);
+        const double mp = __shfl_down_sync(0xffffffffu, acc.maxp, o, 8);
+        const unsigned long long mi = __shfl_down_sync(0xffffffffu, acc.idx, o, 8);
+        acc.a += a2;
+        acc.b += b2;
+        argmax_merge(acc.maxp, acc.idx, mp, mi);
+    }
+    if (r == 0 && k < cnt) {
+        const uint64_t tr = ids[it.off + k];
+        const double sc = finish_score(C.crit, acc);
+        C.score[tr] = sc;
+        if (C.pass_flags) C.pass_flags[tr] = sc >= C.crit.threshold;
+    }
+}
+
+__device__ __noinline__ void mix_res(const BatchItem &it, const BatchCircuit &C, const uint64_t *__restrict__ ids,
+                                    unsigned char *smem_raw, Partial *red, float2 (*ubuf)[16],
+                                    RegOp (*s_ops)[MAX_PHASE_OPS]) {
+    batch_item(it, C, ids, smem_raw, red, ubuf, s_ops);
+}
+
+// MIX_STR: tile `tile` of pass j of trajectory k of stream S (the body of
+// pass_rb_kernel with explicit coordinates), after its slot's dependencies. As
+// there, only what the phase loop needs stays live across it; the rest is
+// reloaded after it.
+__device__ __forceinline__ uint64_t mix_gidx(const MixStream &S, uint32_t j, uint64_t base, uint32_t jj) {
+    return base + S.passes[j].offs[jj >> S.c] + (jj & ((1u << S.c) - 1u));
+}
+
+__device__ __forceinline__ void mix_tile(const MixArgs &A, const MixStream &S, uint32_t k, uint32_t j, uint32_t tile,
+                                         unsigned char *smem_raw, Partial *red, float2 *ubuf,
+                                         RegOp (*s_ops)[MAX_PHASE_OPS], uint32_t *s_flag) {
+    float2 *sm = reinterpret_cast<float2 *>(smem_raw);
+    const int t = S.t;
+    if (threadIdx.x == 0) {
+        const MixTraj &T = S.trajs[k];
+        *s_flag = mix_wait(S.slot_done + T.slot, T.base + (uint32_t)((int)j - T.start) * S.tiles, A.wait_limit, A.err);
+    }
+    __syncthreads();
+    if (!*s_flag) return;
+    __threadfence();
+    const uint32_t load_packed = 0u | ((uint32_t)(t - 4) << 5) | ((uint32_t)(t - 3) << 10) |
+                                 ((uint32_t)(t - 2) << 15) | ((uint32_t)(t - 1) << 20);
+    Amps v;
+    const uint32_t *ev, *ev_end;
+    {
+        const MixTraj &T = S.trajs[k];
+        const uint64_t N = 1ull << S.n;
+        const bool from_cache = (int)j == T.start;
+        const float2 *src = from_cache ? S.cache + (size_t)S.cache_slot[j] * N : S.work + (size_t)T.slot * N;
+        const uint64_t base = tile_base(S.passes[j].rest_mask, tile);
+#pragma unroll
+        for (int hi = 0; hi < 16; ++hi) {
+            const uint32_t jj = ((uint32_t)hi << (t - 4)) | (threadIdx.x << 1);
+            const float4 *pa = reinterpret_cast<const float4 *>(src + mix_gidx(S, j, base, jj));
+            // the working slot was written by other CTAs of this launch: read it through L2
+            const float4 w = from_cache ? __ldg(pa) : __ldcg(pa);
+            v.re[hi] = make_float2(w.x, w.z);
+            v.im[hi] = make_float2(w.y, w.w);
+        }
+        // this pass's events: binary search for the first key at or after the pass's first gate
+        const uint32_t *lo = S.keys + S.offsets[T.tr], *hi_ = S.keys + S.offsets[T.tr + 1];
+        ev_end = hi_;
+        const uint32_t key_lo = S.passes[j].gb << 3;
+        while (lo < hi_) {
+            const uint32_t *mid = lo + (hi_ - lo) / 2;
+            if (*mid < key_lo) lo = mid + 1;
+            else hi_ = mid;
+        }
+        ev = lo;
+    }
+    TileCtx c;
+    c.m = 0;
+    c.gp = 0;
+    c.tid = threadIdx.x;
+    c.nthr = blockDim.x;
+    set_phase(c, load_packed, t);
+    uint32_t next = ev < ev_end ? *ev : NO_EVENT;
+    const uint32_t pb = S.passes[j].pb, pe = S.passes[j].pe;
+    const uint32_t *ph_gb = S.ph_gb;
+    const RegOp *rops = S.rops;
+    if (pb < pe) stage_ops(s_ops[0], rops + ph_gb[pb], ph_gb[pb + 1] - ph_gb[pb], threadIdx.x, blockDim.x);
+    for (uint32_t ph = pb; ph < pe; ++ph) {
+        const uint32_t buf = (ph - pb) & 1u;
+        stage_wait();
+        if (ph + 1 < pe)
+            stage_ops(s_ops[buf ^ 1u], rops + ph_gb[ph + 1], ph_gb[ph + 2] - ph_gb[ph + 1], threadIdx.x, blockDim.x);
+        const uint32_t R = S.ph_R[ph];
+        if (R != c.R) remap<true>(v, sm, c, R, t);
+        const uint32_t g0 = ph_gb[ph];
+        run_gates(v, c, g0, ph_gb[ph + 1], s_ops[buf], g0, S.mats, sm, ubuf, t, ev, ev_end, next);
+    }
+    apply_global_phase(v, c);
+    const MixTraj &T = S.trajs[k];
+    const uint64_t N = 1ull << S.n;
+    const uint64_t base = tile_base(S.passes[j].rest_mask, tile);
+    const bool scored = (int)j == T.end;
+    if (scored) {
+        const float2 *ref = S.ref_cache + (size_t)S.cache_slot[j + 1] * N;
+        Partial acc = empty_partial();
+        score_registers(acc, S.crit, v, c, ref, [&](uint32_t jj) { return mix_gidx(S, j, base, jj); });
+        acc = block_reduce_partial(acc, red);
+        if (threadIdx.x == 0) S.partials[(size_t)k * S.tiles + tile] = acc;
+    } else {
+        if (c.R != load_packed) remap(v, sm, c, load_packed, t);
+        float2 *dst = S.work + (size_t)T.slot * N;
+        const uint32_t flip0 = c.m & 1u;
+#pragma unroll
+        for (int hi = 0; hi < 16; ++hi) {
+            const uint32_t jj = (((uint32_t)hi << (t - 4)) | (threadIdx.x << 1)) ^ (c.m & ~1u);
+            const float2 r = flip0 ? swp2(v.re[hi]) : v.re[hi], i = flip0 ? swp2(v.im[hi]) : v.im[hi];
+            reinterpret_cast<float4 *>(dst + mix_gidx(S, j, base, jj))[0] = make_float4(r.x, i.x, r.y, i.y);
+        }
+    }
+    // publish: this tile's writes, then the slot's counter (and the trajectory's)
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAdd(S.slot_done + T.slot, 1u);
+        *s_flag = scored && atomicAdd(S.traj_done + k, 1u) == S.tiles - 1 ? 2u : 1u;
+    }
+    __syncthreads();
+    if (*s_flag != 2u) return;
+    // last tile of the scored pass: the trajectory's partials added in the order of
+    // finish_partials_kernel, so the score equals the one of the per-pass launches
+    __threadfence();
+    Partial acc = empty_partial();
+    for (uint32_t i = threadIdx.x; i < S.tiles; i += blockDim.x) {
+        const Partial q = ld_partial_cg(S.partials + (size_t)k * S.tiles + i);
+        acc.a += q.a;
+        acc.b += q.b;
+        argmax_merge(acc.maxp, acc.idx, q.maxp, q.idx);
+    }
+    acc = block_reduce_partial(acc, red);
+    if (threadIdx.x == 0) {
+        const double sc = finish_score(S.crit, acc);
+        S.score[T.tr] = sc;
+        if (S.pass_flags) S.pass_flags[T.tr] = sc >= S.crit.threshold;
+    }
+}
+
+__global__ void __launch_bounds__(MIX_THREADS, 2) mix_kernel(const __grid_constant__ MixArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ unsigned long long s_i;
+    __shared__ uint32_t s_u, s_flag;
+    __shared__ double s_val;
+    __shared__ Partial red[MIX_THREADS / 32];
+    __shared__ float2 ubuf[8][16];
+    __shared__ RegOp s_ops[2][MAX_PHASE_OPS];
+    if (threadIdx.x == 0) s_u = 0;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_i = ld_acquire_u32(a.err) ? a.n_sub : atomicAdd(a.counter, 1ull);
+        __syncthreads();
+        const unsigned long long i = s_i;
+        if (i >= a.n_sub) return;
+        if (threadIdx.x < 32) {
+            const uint32_t u = mix_find_unit(a.unit_end, a.n_units, s_u, i);
+            if (threadIdx.x == 0) s_u = u;
+        }
+        __syncthreads();
+        const uint32_t u = s_u;
+        const MixUnit un = a.units[u];
+        const uint32_t sub = (uint32_t)(i - (u ? a.unit_end[u - 1] : 0ull));
+        if (un.kind == MIX_REF) {
+            mix_ref(a.refs[un.idx], sub, red, &s_flag, &s_val);
+        } else if (un.kind == MIX_SMALL) {
+            const BatchItem it = a.items[un.idx];
+            mix_small(a.smalls[it.circuit], it, a.ids, reinterpret_cast<float2 *>(smem_raw));
+        } else if (un.kind == MIX_RES) {
+            const BatchItem it = a.items[un.idx];
+            mix_res(it, a.rcircs[it.circuit], a.ids, smem_raw, red, ubuf, s_ops);
+        } else {
+            mix_tile(a, a.streams[un.idx], un.a, un.b, sub, smem_raw, red, ubuf[0], s_ops, &s_flag);
+        }
+    }
+}
+
+void launch_mix(const MixArgs &a, double bytes, double flops, cudaStream_t st) {
+    if (!a.n_sub) return;
+    ProfScope ps_(ARSO_K_MIX, bytes, st, flops);
+    const size_t smem = (size_t(1) << 13) * sizeof(float2);
+    static bool attr = false;
+    if (!attr) {
+        ARSO_CUDA(cudaFuncSetAttribute(mix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    int per_sm = 1, dev = 0, sms = 152;
+    ARSO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mix_kernel, MIX_THREADS, smem));
+    ARSO_CUDA(cudaGetDevice(&dev));
+    ARSO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const unsigned grid = (unsigned)std::min<uint64_t>(a.n_sub, (uint64_t)std::max(per_sm, 1) * sms);
+    mix_kernel<<<grid, MIX_THREADS, smem, st>>>(a);
+    ARSO_CUDA(cudaGetLastError());
+}
+
 // Raise the dynamic shared-memory limit of both pass variants once, before any
 // launch (and outside stream capture).
 void prepare_pass_rb() {
