@@ -151,6 +151,17 @@ arso_status arso_plan_phases(uint32_t n_qubits, const arso_gate *gates, size_t n
 arso_status arso_sample_errors(const arso_circuit *c, double p_x, double p_z, double p_y,
                                uint64_t seed, uint64_t traj_begin, uint64_t n_traj,
                                void *stream, arso_error_list **out);
+/* The error lists of many circuits in one call (Sec. IV-B.2 for a batch of
+ * circuits): entry i is exactly arso_sample_errors(circuits[i], p_x[i], p_z[i],
+ * p_y[i], seeds[i], traj_begin[i], n_traj[i]) (the same draws and events, bit
+ * for bit), but each sampling kernel runs once for the whole batch. All
+ * arrays have `count` entries (host memory); out[i] receives list i (freed by
+ * arso_error_list_free). On error every out[i] is NULL.
+ * Errors: ARSO_EINVAL, ARSO_ENOMEM, ARSO_ECUDA. */
+arso_status arso_sample_errors_batch(size_t count, const arso_circuit *const *circuits, const double *p_x,
+                                     const double *p_z, const double *p_y, const uint64_t *seeds,
+                                     const uint64_t *traj_begin, const uint64_t *n_traj, void *stream,
+                                     arso_error_list **out);
 
 /* Build an error list from explicit host events (tests, exhaustive analysis).
  * offsets: n_traj + 1 entries, events[offsets[t] .. offsets[t+1]) belong to

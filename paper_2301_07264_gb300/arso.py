@@ -92,6 +92,7 @@ _sigs = {
                            C.c_uint32, _vp, _vp, _vp],
     "arso_sample_errors": [_vp, C.c_double, C.c_double, C.c_double, C.c_uint64, C.c_uint64, C.c_uint64, _vp,
                            C.POINTER(_vp)],
+    "arso_sample_errors_batch": [C.c_size_t, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "arso_error_list_from_host": [_vp, C.c_uint64, _vp, _vp, _vp, C.POINTER(_vp)],
     "arso_error_list_info": [_vp, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)],
     "arso_error_list_copy": [_vp, _vp, _vp, _vp],
@@ -247,6 +248,22 @@ def sample_errors(circ, p_x, p_z, p_y, seed, traj_begin, n_traj, stream=None) ->
     _check(lib.arso_sample_errors(circ.handle, p_x, p_z, p_y, seed, traj_begin, n_traj, _stream(stream),
                                   C.byref(h)))
     return ErrorList(h.value, circ)
+
+
+def sample_errors_batch(circuits, p_x, p_z, p_y, seeds, traj_begin, n_traj, stream=None):
+    """Error lists of many circuits in one call (include/arso.h, arso_sample_errors_batch);
+    scalar arguments apply to every entry."""
+    n = len(circuits)
+
+    def arr(v, ct):
+        v = list(v) if hasattr(v, "__len__") else [v] * n
+        return (ct * n)(*v)
+    hs = (_vp * n)(*[c.handle for c in circuits])
+    outs = (_vp * n)()
+    _check(lib.arso_sample_errors_batch(n, hs, arr(p_x, C.c_double), arr(p_z, C.c_double), arr(p_y, C.c_double),
+                                        arr(seeds, C.c_uint64), arr(traj_begin, C.c_uint64), arr(n_traj, C.c_uint64),
+                                        _stream(stream), outs))
+    return [ErrorList(outs[i], circuits[i]) for i in range(n)]
 
 
 def error_list_from_host(circ, lists, stream=None) -> ErrorList:

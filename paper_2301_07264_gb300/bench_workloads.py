@@ -17,7 +17,8 @@ def _events():
 
 def _kernel_stats(arso):
     names = (("pass", arso.K_PASS), ("pass_last", arso.K_PASS_LAST), ("resident", arso.K_RESIDENT),
-             ("sample", arso.K_SAMPLE), ("reduce", arso.K_REDUCE), ("other", arso.K_OTHER), ("gemm", arso.K_GEMM))
+             ("sample", arso.K_SAMPLE), ("reduce", arso.K_REDUCE), ("other", arso.K_OTHER), ("gemm", arso.K_GEMM),
+             ("mix", arso.K_MIX))
     out = {}
     for name, k in names:
         st = arso.profile_read(k)
@@ -43,8 +44,8 @@ def grover12(args):
     flag_l = [torch.empty(per, dtype=torch.uint8, device="cuda") for _ in rates]
 
     def step(k):
-        # all 16 rates in one persistent launch (arso_run_batch)
-        errs = [arso.sample_errors(cc, p / 3, p / 3, p / 3, 0, k * per, per, stream) for p in rates]
+        # all 16 rates: one batched sampling call and one persistent launch (arso_run_batch)
+        errs = arso.sample_errors_batch([cc] * len(rates), rates / 3, rates / 3, rates / 3, 0, k * per, per, stream)
         arso.run_batch([cc] * len(rates), errs, [crit] * len(rates), scores, flag_l, stream)
         for i in range(len(rates)):
             res[i] += arso.aggregate(scores[i], flag_l[i], stream)[1]
@@ -70,33 +71,28 @@ def grover12(args):
             "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "grover12_sweep", "n_qubits": 12, "G": info.G, "L": info.L,
                        "rates": "16 log-spaced in [1e-5, 1e-2]", "traj_per_rate_per_step": per,
-                       "criterion": "argmax == marked", "engine": "resident (whole state in one CTA)"},
+                       "criterion": "argmax == marked",
+                       "engine": "resident (whole state in one CTA), all rates in one persistent launch"},
             "results": {"pass_frac": (res / args.steps).round(4).tolist()},
             "kernels": _kernel_stats(arso)}
 
 
 def mix256(args):
     """256 circuits of 8..22 qubits (QFT, Grover, QAOA p=2, adders) at p = 5e-4,
-    2000 trajectories each per step, one arso_run_batch call per step; the
-    streaming circuits use tile shapes picked by arso_autotune (per qubit count)."""
+    2000 trajectories each per step: one arso_sample_errors_batch call and one
+    arso_run_batch call per step (the batch runs as one persistent launch)."""
     import torch
     from paper_2301_07264_gb300 import arso
     from workloads import circuits as W
     mix = W.mix_family(0)
     p, T = 5e-4, 2000
-    tuned = {}
-    t0 = time.perf_counter()
-    for circ in mix:
-        if circ.n > 13 and circ.n not in tuned:
-            tuned[circ.n], _ = arso.autotune(circ.n, circ.gates, circ.criterion, p * 8, n_traj=64)
-    tune_s = time.perf_counter() - t0
-    ccs = [arso.compile_circuit(c.n, c.gates, **tuned.get(c.n, {})) for c in mix]
+    ccs = [arso.compile_circuit(c.n, c.gates) for c in mix]
     crits = [c.criterion for c in mix]
     outs = [torch.empty(T, dtype=torch.float64, device="cuda") for _ in mix]
     stream = torch.cuda.current_stream()
 
     def step(k):
-        errs = [arso.sample_errors(cc, p / 3, p / 3, p / 3, 0, k * T, T, stream) for cc in ccs]
+        errs = arso.sample_errors_batch(ccs, p / 3, p / 3, p / 3, 0, k * T, T, stream)
         arso.run_batch(ccs, errs, crits, outs, None, stream)
 
     for w in range(args.warmup):
@@ -112,14 +108,16 @@ def mix256(args):
     torch.cuda.synchronize()
     arso.profile_enable(False)
     sec = e0.elapsed_time(e1) / 1e3
+    launches, _, _ = arso.profile_counters()
     fams = {f: sum(1 for c in mix if c.family == f) for f in ("qft", "grover", "qaoa", "adder")}
     return {"metric": "error-injected trajectories/sec", "value": len(mix) * T * args.steps / sec,
             "unit": "traj/s", "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
             "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "mix256_p5e-4", "circuits": len(mix), "families": fams,
                        "n_range": [min(c.n for c in mix), max(c.n for c in mix)],
-                       "traj_per_circuit": T, "autotuned": {str(k): v for k, v in sorted(tuned.items())},
-                       "autotune_seconds": tune_s},
+                       "traj_per_circuit": T, "tile_qubits": 13},
+            "gpu_launches_per_step": launches / args.steps,
+            "mean_score": float(np.mean([float(o.mean()) for o in outs])),
             "kernels": _kernel_stats(arso)}
 
 

@@ -701,6 +701,77 @@ static void sample(const arso_circuit *c, double px, double pz, double py, uint6
     *out = e.release();
 }
 
+static SampleArgs sample_args(const arso_circuit *c, double px, double pz, double py, uint64_t seed, uint64_t begin,
+                              uint64_t n_traj) {
+    ARSO_REQUIRE(px >= 0 && pz >= 0 && py >= 0, "error probabilities must be >= 0");
+    const double pt = px + pz + py;
+    ARSO_REQUIRE(pt <= 1.0, "p_x + p_z + p_y must be <= 1");
+    ARSO_REQUIRE(begin + n_traj >= begin, "trajectory range overflows");
+    SampleArgs a{};
+    a.seed = seed;
+    a.traj_begin = begin;
+    a.n_traj = n_traj;
+    a.L = (uint32_t)c->L;
+    if (pt > 0 && c->L > 0) {
+        const double two32 = 4294967296.0;
+        a.thr = (uint32_t)std::min(std::floor(pt * two32), 4294967295.0);
+        const double cx = std::floor(px / pt * two32), cxz = std::floor((px + pz) / pt * two32);
+        a.cut_x_all = cx >= two32;
+        a.cut_xz_all = cxz >= two32;
+        a.cut_x = a.cut_x_all ? 0 : (uint32_t)cx;
+        a.cut_xz = a.cut_xz_all ? 0 : (uint32_t)cxz;
+    }
+    return a;
+}
+
+// Error lists of many circuits with one launch of each sampling kernel.
+static void sample_batch(size_t count, const arso_circuit *const *circuits, const double *px, const double *pz,
+                         const double *py, const uint64_t *seeds, const uint64_t *begins, const uint64_t *n_traj,
+                         cudaStream_t st, arso_error_list **out) {
+    std::vector<std::unique_ptr<arso_error_list>> lists(count);
+    std::vector<SampleJob> jobs(count);
+    uint64_t total = 0;
+    for (size_t i = 0; i < count; ++i) {
+        const arso_circuit *c = circuits[i];
+        ARSO_REQUIRE(c != nullptr, "NULL circuit");
+        SampleJob &J = jobs[i];
+        J.a = sample_args(c, px[i], pz[i], py[i], seeds[i], begins[i], n_traj[i]);
+        lists[i].reset(new_list(c, n_traj[i]));
+        J.traj0 = total;
+        total += n_traj[i];
+        J.offsets = lists[i]->d_offsets.as<uint64_t>();
+        J.loc_key = c->d_loc_key.as<uint32_t>();
+        J.first = lists[i]->d_first.as<uint32_t>();
+        J.last = lists[i]->d_last.as<uint32_t>();
+        bool identity = true;
+        for (size_t g = 0; g < c->perm.size() && identity; ++g) identity = c->perm[g] == g;
+        J.identity = identity;
+    }
+    if (count) {
+        Scratch d_jobs(st, count * sizeof(SampleJob)), counts(st, std::max<uint64_t>(total, 1) * 4),
+            totals(st, count * 8);
+        copy_h2d(d_jobs.ptr, jobs.data(), count * sizeof(SampleJob), st);
+        launch_sample_batch_count(d_jobs.as<SampleJob>(), (uint32_t)count, total, counts.as<uint32_t>(),
+                                  totals.as<uint64_t>(), st);
+        std::vector<uint64_t> ev(count);
+        copy_d2h(ev.data(), totals.ptr, count * 8, st);
+        ARSO_CUDA(cudaStreamSynchronize(st));
+        bool any = false;
+        for (size_t i = 0; i < count; ++i) {
+            lists[i]->n_events = ev[i];
+            lists[i]->d_loc.ensure(std::max<uint64_t>(ev[i], 1) * 4);
+            lists[i]->d_key.ensure(std::max<uint64_t>(ev[i], 1) * 4);
+            jobs[i].ev_loc = lists[i]->d_loc.as<uint32_t>();
+            jobs[i].ev_key = lists[i]->d_key.as<uint32_t>();
+            any |= ev[i] > 0;
+        }
+        copy_h2d(d_jobs.ptr, jobs.data(), count * sizeof(SampleJob), st);
+        launch_sample_batch_fill(d_jobs.as<SampleJob>(), (uint32_t)count, total, any, st);
+        ARSO_CUDA(cudaStreamSynchronize(st));
+    }
+    for (size_t i = 0; i < count; ++i) out[i] = lists[i].release();
+}
+
 static void list_from_host(const arso_circuit *c, uint64_t n_traj, const uint64_t *offsets, const uint32_t *events,
                            cudaStream_t st, arso_error_list **out) {
     ARSO_REQUIRE(offsets != nullptr, "offsets is NULL");
@@ -1558,6 +1629,18 @@ arso_status arso_sample_errors(const arso_circuit *c, double p_x, double p_z, do
         ARSO_REQUIRE(c && out, "NULL argument");
         *out = nullptr;
         sample(c, p_x, p_z, p_y, seed, traj_begin, n_traj, (cudaStream_t)stream, out);
+    });
+}
+
+arso_status arso_sample_errors_batch(size_t count, const arso_circuit *const *circuits, const double *p_x,
+                                     const double *p_z, const double *p_y, const uint64_t *seeds,
+                                     const uint64_t *traj_begin, const uint64_t *n_traj, void *stream,
+                                     arso_error_list **out) {
+    return guard([&] {
+        ARSO_REQUIRE(count == 0 || (circuits && p_x && p_z && p_y && seeds && traj_begin && n_traj && out),
+                     "NULL argument");
+        for (size_t i = 0; i < count; ++i) out[i] = nullptr;
+        sample_batch(count, circuits, p_x, p_z, p_y, seeds, traj_begin, n_traj, (cudaStream_t)stream, out);
     });
 }
 

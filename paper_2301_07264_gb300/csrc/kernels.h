@@ -265,6 +265,23 @@ struct SampleArgs {
     uint32_t cut_x_all, cut_xz_all; // 1 if the cut equals 2^32 (every draw below it)
 };
 void launch_sample_count(const SampleArgs &a, uint32_t *counts, cudaStream_t st);
+// Batched sampling: one job per error list, trajectories numbered globally
+// (job j owns [traj0, traj0 + a.n_traj)); counts are concatenated in that order.
+struct SampleJob {
+    SampleArgs a;
+    uint64_t traj0;
+    uint64_t *offsets;          // the list's offsets[n_traj + 1]
+    const uint32_t *loc_key;    // the circuit's location -> engine key table
+    uint32_t *ev_loc, *ev_key;  // the list's events (set after the counts are known)
+    uint32_t *first, *last;
+    uint32_t identity;          // the schedule keeps circuit order: keys need no sort
+};
+// count kernel and per-job scans (totals[j] = events of job j)
+void launch_sample_batch_count(const SampleJob *jobs, uint32_t n_jobs, uint64_t n_total, uint32_t *counts,
+                               uint64_t *totals, cudaStream_t st);
+// event fill (when any job has events) and per-trajectory sort / first and last event
+void launch_sample_batch_fill(const SampleJob *jobs, uint32_t n_jobs, uint64_t n_total, bool any_events,
+                              cudaStream_t st);
 void launch_exclusive_scan(const uint32_t *counts, uint64_t n, uint64_t *offsets, cudaStream_t st);
 void launch_sample_fill(const SampleArgs &a, const uint64_t *offsets, const uint32_t *loc_key, uint32_t *ev_loc,
                         uint32_t *ev_key, cudaStream_t st);

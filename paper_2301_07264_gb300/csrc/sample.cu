@@ -233,6 +233,193 @@ static unsigned grid_for(uint64_t work, unsigned per_block, unsigned cap) {
     return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((work + per_block - 1) / per_block, cap));
 }
 
+// ------------------------------------------------------ batched sampling ---
+// The lists of many circuits at once: the same draws, counts, scans and event
+// words as the per-list kernels above, each kernel launched once for the batch.
+// Global trajectory g belongs to the job whose [traj0, traj0 + n_traj) holds it.
+__device__ __forceinline__ uint32_t job_of(const SampleJob *__restrict__ jobs, uint32_t n_jobs, uint64_t g) {
+    uint32_t lo = 0, hi = n_jobs;  // first job with traj0 > g, minus one
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) / 2;
+        if (jobs[mid].traj0 <= g) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo - 1;
+}
+
+__global__ void sample_count_batch_kernel(const SampleJob *__restrict__ jobs, uint32_t n_jobs, uint64_t n_total,
+                                          uint32_t *counts) {
+    __shared__ uint32_t red[32];
+    for (uint64_t g = blockIdx.x; g < n_total; g += gridDim.x) {
+        const SampleJob &J = jobs[job_of(jobs, n_jobs, g)];
+        const SampleArgs &a = J.a;
+        const uint64_t t = a.traj_begin + (g - J.traj0);
+        const uint32_t pairs = a.thr ? (a.L + 1) / 2 : 0;
+        uint32_t cnt = 0;
+        for (uint32_t j = threadIdx.x; j < pairs; j += blockDim.x) {
+            const uint4 w = philox4x32_10(make_uint4(j, (uint32_t)t, (uint32_t)(t >> 32), STREAM_ERRORS),
+                                          (uint32_t)a.seed, (uint32_t)(a.seed >> 32));
+            cnt += w.x < a.thr;
+            cnt += (2 * j + 1 < a.L) && (w.z < a.thr);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cnt;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t sum = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w];
+            counts[g] = sum;
+        }
+    }
+}
+
+// one CTA per job: exclusive scan of its counts into its offsets; totals[job] = events
+__global__ void scan_batch_kernel(const SampleJob *__restrict__ jobs, const uint32_t *__restrict__ counts,
+                                  uint64_t *totals) {
+    __shared__ unsigned long long warp_tot[32];
+    __shared__ unsigned long long carry;
+    const SampleJob &J = jobs[blockIdx.x];
+    const uint64_t n = J.a.n_traj;
+    const uint32_t *cnt = counts + J.traj0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) {
+        carry = 0;
+        J.offsets[0] = 0;
+    }
+    __syncthreads();
+    for (uint64_t i0 = 0; i0 < n; i0 += blockDim.x) {
+        const uint64_t i = i0 + threadIdx.x;
+        unsigned long long incl = i < n ? cnt[i] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) warp_tot[warp] = incl;
+        __syncthreads();
+        unsigned long long before = carry;
+        for (int k = 0; k < warp; ++k) before += warp_tot[k];
+        if (i < n) J.offsets[i + 1] = before + incl;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long tot = 0;
+            for (int k = 0; k < nw; ++k) tot += warp_tot[k];
+            carry += tot;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) totals[blockIdx.x] = carry;
+}
+
+__global__ void sample_fill_batch_kernel(const SampleJob *__restrict__ jobs, uint32_t n_jobs, uint64_t n_total) {
+    __shared__ uint32_t warp_tot[32];
+    __shared__ uint32_t carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (uint64_t g = blockIdx.x; g < n_total; g += gridDim.x) {
+        const SampleJob &J = jobs[job_of(jobs, n_jobs, g)];
+        const SampleArgs &a = J.a;
+        const uint64_t b = g - J.traj0, t = a.traj_begin + b;
+        const uint64_t out0 = J.offsets[b];
+        if (J.offsets[b + 1] == out0) continue;  // no event (uniform over the CTA)
+        const uint32_t pairs = (a.L + 1) / 2;
+        if (threadIdx.x == 0) carry = 0;
+        __syncthreads();
+        for (uint32_t j0 = 0; j0 < pairs; j0 += blockDim.x) {
+            const uint32_t j = j0 + threadIdx.x;
+            uint4 w = make_uint4(0xFFFFFFFFu, 0, 0xFFFFFFFFu, 0);
+            if (j < pairs)
+                w = philox4x32_10(make_uint4(j, (uint32_t)t, (uint32_t)(t >> 32), STREAM_ERRORS), (uint32_t)a.seed,
+                                  (uint32_t)(a.seed >> 32));
+            const bool h0 = j < pairs && w.x < a.thr;
+            const bool h1 = j < pairs && (2 * j + 1 < a.L) && w.z < a.thr;
+            const uint32_t c = (uint32_t)h0 + (uint32_t)h1;
+            uint32_t incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            if (lane == 31) warp_tot[warp] = incl;
+            __syncthreads();
+            uint32_t before = carry;
+            for (int k = 0; k < warp; ++k) before += warp_tot[k];
+            uint64_t pos = out0 + before + incl - c;
+            if (h0) {
+                const uint32_t l = 2 * j, code = pauli_of(w.y, a);
+                J.ev_loc[pos] = (l << 2) | code;
+                J.ev_key[pos] = (J.loc_key[l] << 2) | code;
+                ++pos;
+            }
+            if (h1) {
+                const uint32_t l = 2 * j + 1, code = pauli_of(w.w, a);
+                J.ev_loc[pos] = (l << 2) | code;
+                J.ev_key[pos] = (J.loc_key[l] << 2) | code;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                uint32_t tot = 0;
+                for (int k = 0; k < nw; ++k) tot += warp_tot[k];
+                carry += tot;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// per trajectory: keys into engine order (when the schedule reorders gates), then the
+// first and last event positions
+__global__ void finish_batch_kernel(const SampleJob *__restrict__ jobs, uint32_t n_jobs, uint64_t n_total) {
+    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < n_total;
+         g += (uint64_t)gridDim.x * blockDim.x) {
+        const SampleJob &J = jobs[job_of(jobs, n_jobs, g)];
+        const uint64_t b = g - J.traj0, o0 = J.offsets[b], o1 = J.offsets[b + 1];
+        uint32_t *k = J.ev_key + o0;
+        const uint64_t m = o1 - o0;
+        if (!J.identity)
+            for (uint64_t i = 1; i < m; ++i) {
+                const uint32_t v = k[i];
+                uint64_t j = i;
+                while (j > 0 && k[j - 1] > v) {
+                    k[j] = k[j - 1];
+                    --j;
+                }
+                k[j] = v;
+            }
+        J.first[b] = m ? (k[0] >> 3) : NO_EVENT;
+        J.last[b] = m ? (k[m - 1] >> 3) : NO_EVENT;
+    }
+}
+
+void launch_sample_batch_count(const SampleJob *jobs, uint32_t n_jobs, uint64_t n_total, uint32_t *counts,
+                               uint64_t *totals, cudaStream_t st) {
+    if (!n_jobs) return;
+    if (n_total) {
+        ProfScope ps_(ARSO_K_SAMPLE, 4.0 * n_total, st);
+        sample_count_batch_kernel<<<(unsigned)std::min<uint64_t>(n_total, 152ull * 64), 128, 0, st>>>(jobs, n_jobs,
+                                                                                                     n_total, counts);
+        ARSO_CUDA(cudaGetLastError());
+    }
+    ProfScope ps_(ARSO_K_OTHER, 0.0, st);
+    scan_batch_kernel<<<n_jobs, 1024, 0, st>>>(jobs, counts, totals);
+    ARSO_CUDA(cudaGetLastError());
+}
+
+void launch_sample_batch_fill(const SampleJob *jobs, uint32_t n_jobs, uint64_t n_total, bool any_events,
+                              cudaStream_t st) {
+    if (!n_jobs || !n_total) return;
+    if (any_events) {
+        ProfScope ps_(ARSO_K_SAMPLE, 0.0, st);
+        sample_fill_batch_kernel<<<(unsigned)std::min<uint64_t>(n_total, 152ull * 64), 128, 0, st>>>(jobs, n_jobs,
+                                                                                                    n_total);
+        ARSO_CUDA(cudaGetLastError());
+    }
+    ProfScope ps_(ARSO_K_OTHER, 0.0, st);
+    finish_batch_kernel<<<grid_for(n_total, 128, 152 * 16), 128, 0, st>>>(jobs, n_jobs, n_total);
+    ARSO_CUDA(cudaGetLastError());
+}
+
 void launch_sample_count(const SampleArgs &a, uint32_t *counts, cudaStream_t st) {
     if (!a.n_traj) return;
     const unsigned grid = (unsigned)std::min<uint64_t>(a.n_traj, 152ull * 64);

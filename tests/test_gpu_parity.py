@@ -87,6 +87,32 @@ def test_sampling_empty_and_single(arso):
     assert np.array_equal(off, o_off) and np.array_equal(ev, o_ev)
 
 
+def test_batched_sampling_bit_exact(arso):
+    """arso_sample_errors_batch: every list equals the oracle's sampling and the
+    per-list sampler's, including trajectory ids across 2^32, single-type rates,
+    p = 0, an empty list and a streaming schedule that reorders gates (whose
+    engine-order keys decide the scores)."""
+    circs = [C.qft4_0101(), C.random_circuit(5, 37, 11), C.grover(7, 3), C.brickwork(14, 6, 2),
+             C.random_circuit(6, 50, 3), C.qaoa_maxcut(12, 5)]
+    kws = [{"precision": arso.C128}, {}, {}, {"tile_qubits": 10}, {}, {}]
+    par = [(0.2, 0.05, 0.01, 7, 2**32 - 3, 300), (0.3, 0.0, 0.0, 1, 5, 200), (1e-3, 1e-3, 1e-3, 0, 0, 64),
+           (4e-3, 4e-3, 4e-3, 2, 100, 48), (0.0, 0.0, 0.0, 4, 0, 50), (0.0, 0.0, 0.4, 2, 0, 0)]
+    ccs = [arso.compile_circuit(c.n, c.gates, **kw) for c, kw in zip(circs, kws)]
+    lists = arso.sample_errors_batch(ccs, [q[0] for q in par], [q[1] for q in par], [q[2] for q in par],
+                                     [q[3] for q in par], [q[4] for q in par], [q[5] for q in par])
+    for circ, cc, q, e in zip(circs, ccs, par, lists):
+        px, pz, py, seed, begin, T = q
+        off, ev = arso.error_list_copy(e)
+        o_off, o_ev = oracle_csr(sampling.sample(seed, begin, T, circ.L, px, pz, py))
+        assert np.array_equal(off, o_off) and np.array_equal(ev, o_ev), circ.family
+        if T:
+            single = arso.sample_errors(cc, px, pz, py, seed, begin, T)
+            a, b = np.zeros(T), np.zeros(T)
+            arso.run_trajectories(cc, e, circ.criterion, a)
+            arso.run_trajectories(cc, single, circ.criterion, b)
+            assert np.array_equal(a, b), circ.family
+
+
 # ------------------------------------------------------------ amplitudes --
 
 def _random_error_lists(circ, T, rng, max_err=4):
