@@ -29,20 +29,23 @@ namespace arso {
 
 __device__ __forceinline__ uint32_t swz(uint32_t j) { return j ^ (((j >> 4) ^ (j >> 8) ^ (j >> 12)) & 15u); }
 
-// tid's bits deposited into the tile bits that are not register bits, ascending
-__device__ __forceinline__ uint32_t thread_part(uint32_t tid, uint32_t rmask, int t) {
-    uint32_t out = 0;
-    int k = 0;
-    for (int b = 0; b < t; ++b)
-        if (!((rmask >> b) & 1u)) {
-            out |= ((tid >> k) & 1u) << b;
-            ++k;
-        }
-    return out;
+// register bit b of a packed register set (the five bits are stored in ascending order)
+__device__ __forceinline__ uint32_t rbit(uint32_t packed, int b) { return (packed >> (5 * b)) & 31u; }
+
+// tid's bits deposited into the tile bits that are not register bits, ascending:
+// a zero bit inserted at each register bit position, lowest first
+__device__ __forceinline__ uint32_t thread_part(uint32_t tid, uint32_t packed) {
+    uint32_t x = tid;
+#pragma unroll
+    for (int b = 0; b < REG_BITS; ++b) {
+        const uint32_t r = rbit(packed, b);
+        x = ((x >> r) << (r + 1)) | (x & ((1u << r) - 1u));
+    }
+    return x;
 }
 
-// register bit b of a packed register set
-__device__ __forceinline__ uint32_t rbit(uint32_t packed, int b) { return (packed >> (5 * b)) & 31u; }
+// swz(2^k): only the nibble shift that reaches the low four bits contributes
+__device__ __forceinline__ uint32_t swz_pow2(uint32_t k) { return (1u << k) | (k >= 4 ? 1u << (k & 3u) : 0u); }
 
 // register part of the local index of register ri (ri is a constant after unrolling)
 __device__ __forceinline__ uint32_t reg_part(int ri, uint32_t packed) {
@@ -386,10 +389,7 @@ __device__ __forceinline__ void apply_global_phase(Amps &a, TileCtx &c) {
 // stored index -> tile-local index bits for the load/store mapping
 __device__ __forceinline__ void set_phase(TileCtx &c, uint32_t packed, int t) {
     c.R = packed;
-    uint32_t rmask = 0;
-#pragma unroll
-    for (int b = 0; b < REG_BITS; ++b) rmask |= 1u << rbit(packed, b);
-    c.tpart = thread_part(c.tid, rmask, t);
+    c.tpart = thread_part(c.tid, packed);
 }
 
 // Shared memory holds a tile as two planes of packed neighbour pairs:
