@@ -44,8 +44,6 @@ __device__ __forceinline__ uint32_t thread_part(uint32_t tid, uint32_t packed) {
     return x;
 }
 
-// swz(2^k): only the nibble shift that reaches the low four bits contributes
-__device__ __forceinline__ uint32_t swz_pow2(uint32_t k) { return (1u << k) | (k >= 4 ? 1u << (k & 3u) : 0u); }
 
 // register part of the local index of register ri (ri is a constant after unrolling)
 __device__ __forceinline__ uint32_t reg_part(int ri, uint32_t packed) {
