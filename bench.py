@@ -347,7 +347,7 @@ def run_reference(args):
 
 
 def _config(circ, args, tile=None, passes=None):
-    return {"workload": "brickwork24_depth40_p1e-4_1e-3", "n_qubits": circ.n, "depth": 40, "G": circ.G,
+    return {"workload": f"brickwork{circ.n}_depth40_p1e-4_1e-3", "n_qubits": circ.n, "depth": 40, "G": circ.G,
             "L": circ.L, "p": list(P_RATES), "trajectories_per_p": TRAJ_PER_P,
             "traj_per_step": args.traj_per_step, "criterion": "fidelity >= 0.9 (pass fraction)",
             "prefix_reuse": True, "suffix_reuse": not getattr(args, "no_suffix", False),
@@ -374,8 +374,11 @@ def run_ours(args):
     dev = torch.cuda.current_device()
     stream = torch.cuda.Stream()  # a real stream: the pass sequences are captured and replayed as CUDA graphs
     torch.cuda.set_stream(stream)
-    circ = C.brickwork24(0)
+    circ = C.brickwork(args.qubits, 40, 0)  # 24 qubits: the benchmark circuit (brickwork24)
     crit = arso.make_criterion(circ.criterion)
+    if args.trace_all:  # algorithmic bytes of every launch, prefix-cache build and warm-up included
+        arso.profile_reset()
+        arso.profile_enable(True)
     cc = arso.compile_circuit(circ.n, circ.gates, tile_qubits=args.tile,
                               cache_bytes=int(args.cache_gb * (1 << 30)) if args.cache_gb else 0,
                               flags=arso.OPT_NO_SUFFIX_REUSE if args.no_suffix else 0)
@@ -406,6 +409,11 @@ def run_ours(args):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    before = None
+    if args.trace_all:
+        ps0 = arso.profile_read(arso.K_PASS)
+        pl0 = arso.profile_read(arso.K_PASS_LAST)
+        before = {"pass_launches": ps0.launches + pl0.launches, "pass_algorithmic_bytes": ps0.bytes + pl0.bytes}
     clocks = ClockSampler(dev)
     clocks.start()
     arso.profile_reset()
@@ -435,7 +443,11 @@ def run_ours(args):
     host_out = {p: (torch.empty(half, dtype=torch.float64, pin_memory=True).numpy(),
                     torch.empty(half, dtype=torch.uint8, pin_memory=True).numpy()) for p in P_RATES}
     e2e_steps = max(1, min(args.steps, 5))
+    if before is not None:  # the timed steps' pass launches join the whole-run count
+        before["pass_launches"] += kstats["pass"].launches + kstats["pass_last"].launches
+        before["pass_algorithmic_bytes"] += kstats["pass"].bytes + kstats["pass_last"].bytes
     arso.profile_reset()
+    arso.profile_enable(args.trace_all)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -445,6 +457,12 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_time = time.perf_counter() - t0
     _, h2d, d2h = arso.profile_counters()
+    if before is not None:  # and the end-to-end steps'
+        arso.profile_enable(False)
+        for k in (arso.K_PASS, arso.K_PASS_LAST):
+            st_ = arso.profile_read(k)
+            before["pass_launches"] += st_.launches
+            before["pass_algorithmic_bytes"] += st_.bytes
     if dist:
         t = torch.tensor([e2e_time], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -492,12 +510,38 @@ def run_ours(args):
         "results": {"pass_frac_p1e-4": float(np.mean([a[0][1] for a in aggs])),
                     "pass_frac_p1e-3": float(np.mean([a[1][1] for a in aggs]))},
     }
+    if before is not None:
+        # every pass launch of the run (cache build, warm-up, timed and end-to-end steps),
+        # for comparison with a DRAM capture of the same launches
+        line["trace_all"] = before
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline("brickwork24", args.cpu_seconds, P_RATES, TRAJ_PER_P, 16 << circ.n)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def onchip_roofline(oc, clk):
+    """The resident (whole state on chip) kernel against its on-chip roofs: the FP32
+    FMA rate (SMs x 128 lanes x 2 flop x clock) and the shared-memory bandwidth (SMs x
+    128 bytes per clock: 32 banks of 4 bytes), at the highest SM clock seen."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = float(clk.get("sm_max_mhz") or 2070.0)
+    sec = oc["ms"] / 1e3
+    tf = oc["flops"] / sec / 1e12 if sec > 0 else 0.0
+    gbs = oc["smem_bytes"] / sec / 1e9 if sec > 0 else 0.0
+    fp32_peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+    smem_peak = sms * 128 * mhz * 1e6 / 1e9
+    f_alu, f_smem = tf / fp32_peak, gbs / smem_peak
+    alu = {"bound": "alu" if f_alu >= f_smem else "smem", "kernel": oc["kernel"], "achieved": tf, "peak": fp32_peak,
+           "peak_kind": f"nominal FP32 FMA rate: {sms} SMs x 128 lanes x 2 flop x {mhz:.0f} MHz", "unit": "TFLOP/s",
+           "frac": f_alu, "traffic": None, "launches": oc["launches"], "device_ms": oc["ms"]}
+    smem = {"achieved": gbs, "peak": smem_peak, "unit": "GB/s", "frac": f_smem,
+            "peak_kind": f"shared memory: {sms} SMs x 128 B/clock x {mhz:.0f} MHz",
+            "note": "algorithmic bytes: one write and one read of the state per register-set change"}
+    return alu, smem
 
 
 def main():
@@ -510,6 +554,11 @@ def main():
                     help="default 1000 (brickwork24), 4096 (grover12: 256 per rate, several waves of the "
                          "persistent launch)")
     ap.add_argument("--tile", type=int, default=0, help="tile qubits (0 = library default)")
+    ap.add_argument("--qubits", type=int, default=24,
+                    help="brickwork qubits (24 = the benchmark circuit; smaller sizes are profiling cases)")
+    ap.add_argument("--trace-all", action="store_true",
+                    help="also report the algorithmic bytes of every pass launch of the run (cache build and "
+                         "warm-up included), to set against a DRAM capture of the same launches")
     ap.add_argument("--cache-gb", type=float, default=0.0, help="prefix-cache budget (0 = library default)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="seconds of oracle work per CPU-baseline setting (1 core, all cores)")
@@ -518,7 +567,10 @@ def main():
                     help="run every trajectory to the end instead of scoring after its last error")
     ap.add_argument("--workload", default="brickwork24", choices=["brickwork24", "grover12", "mix256", "search", "exhaustive", "qv", "families"],
                     help="brickwork24 is the benchmark line; the others measure the other configurations")
-    ap.add_argument("--search-circuits", type=int, default=8)
+    ap.add_argument("--search-circuits", type=int, default=8,
+                    help="search workload: evaluation circuits per size band (half as many at 20-24 qubits)")
+    ap.add_argument("--search-margin", type=float, default=0.08,
+                    help="search workload: half-width of the surrogate's bracket in log10 p")
     ap.add_argument("--train-rows", type=int, default=2_000_000)
     args = ap.parse_args()
     if args.traj_per_step is None:
@@ -527,8 +579,14 @@ def main():
         return run_reference(args)
     if args.workload != "brickwork24":
         from paper_2301_07264_gb300 import bench_workloads
+        clocks = ClockSampler(0)
+        clocks.start()
         line = bench_workloads.run(args)
+        clk = clocks.stop()
         if line is not None:
+            line["clocks"] = clk
+            if args.workload == "grover12":
+                line["roofline"], line["roofline_smem"] = onchip_roofline(line.pop("onchip"), clk)
             if args.workload == "grover12" and not args.no_cpu_baseline:
                 line["cpu_baseline"] = grover_cpu_baseline(args.cpu_seconds)
             if args.workload == "exhaustive" and line.get("hbm_sweep"):

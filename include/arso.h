@@ -81,20 +81,29 @@ typedef struct {
 } arso_compile_opts;
 /* Fidelity scores are taken right after a trajectory's last error, against the
  * cached error-free state at that pass boundary: the error-free suffix W is
- * unitary and common to both states, so <W a|W b> = <a|b> (exact). This flag
+ * unitary and common to both states, so <W a|W b> = <a|b> (exact). Outcome
+ * probabilities (streaming complex64 circuits) likewise, as |<phi|a>|^2 with the
+ * backward state phi = W^dagger |target> cached at that boundary. This flag
  * turns that off (every trajectory then runs to the end; for comparisons). */
 /* The streaming engine records each batch's pass launches into a CUDA graph
  * (keyed by the batch's pass range and slot count) and replays it for later
  * batches of the same shape; this flag launches every pass directly. */
-/* Exhaustive single-error analysis (Sec. IV-B.1) for the fidelity criterion
- * takes every single-error score from one error-free sweep: the state with
- * error P on qubit q after gate g has fidelity <psi_g|P|psi_g>^2 with psi_R,
- * because the rest of the circuit is unitary and maps psi_g to psi_R. The
- * sweep keeps the state in one CTA (resident circuits) or in HBM (streaming
- * complex64 circuits, one gate and one expectation per launch). This flag
+/* Exhaustive single-error analysis (Sec. IV-B.1) takes every single-error
+ * score from one sweep. Fidelity: the state with error P on qubit q after gate
+ * g has fidelity <psi_g|P|psi_g>^2 with psi_R, because the rest of the circuit
+ * is unitary and maps psi_g to psi_R, so one error-free sweep of Pauli
+ * expectations suffices; it keeps the state in one CTA (resident circuits) or in
+ * HBM (streaming complex64 circuits, one launch per gate that applies it and
+ * measures its qubits).
+ * Outcome probability: the score is |<phi_g|P|psi_g>|^2 with the backward state
+ * phi_g = W^dagger |target> for the rest W of the circuit; one backward sweep
+ * carries psi and phi from (psi_R, |target>) with the adjoint gates (one CTA,
+ * or one HBM launch per gate for streaming complex64 circuits). This flag
  * simulates the 3L single-error trajectories instead (for comparisons). */
+/* arso_run_batch runs circuits with ARSO_OPT_NO_PERSISTENT on their own
+ * launches instead of the batch's persistent launch (for comparisons). */
 enum { ARSO_OPT_NO_SUFFIX_REUSE = 1, ARSO_OPT_NO_GRAPHS = 2, ARSO_OPT_NO_FAST_EXHAUSTIVE = 4,
-       ARSO_OPT_NO_PERSISTENT = 8 /* arso_run_batch runs this circuit on its own launches */ };
+       ARSO_OPT_NO_PERSISTENT = 8 };
 
 typedef struct arso_circuit arso_circuit;
 typedef struct arso_error_list arso_error_list;
@@ -369,10 +378,16 @@ arso_status arso_debug_stall_next_gemm(void);
  * log10 p on the surrogate's prediction for the circuit's features, take the
  * bracket [p_s 10^-m, p_s 10^m] (m = opts->surrogate_margin), verify it with
  * opts->n_traj plain trajectories at each end (values straddle P_target),
- * widen it by 10^(2m) per side while it fails (at most 3 times), narrow a
- * widened bracket back to width 10^(2m) with plain probes (at most 6), and
- * answer by log-linear interpolation inside the verified bracket. If it cannot
- * be verified, fall back to arso_tolerable_rate's Monte Carlo search. */
+ * widen a failing side by 10^(2m), 10^(4m), 10^(8m) in turn, and if it still
+ * fails move that side to the search range's end (opts->p_lo / p_hi); then
+ * narrow the bracket to width 10^(2m) with plain probes (bisection in log p
+ * while wider than four such widths, then probes at the log-linear
+ * interpolation point kept inside the middle 60%; at most 24), and answer by
+ * log-linear interpolation inside it. All probes share one set of random
+ * numbers and reuse each other's trajectories. out->verified = 1 when the
+ * surrogate's (widened) bracket held, 0 when the range ends were needed.
+ * Errors: ARSO_ENOTCONVERGED when even [p_lo, p_hi] does not bracket the
+ * target. */
 arso_status arso_tolerable_rate_surrogate(const arso_circuit *c, const arso_criterion *crit, double P_target,
                                           const arso_search_opts *opts, void *stream, arso_rate_result *out);
 
@@ -436,8 +451,13 @@ typedef struct {
     double ms;              /* summed device time (timing enabled only) */
     double bytes;           /* summed algorithmic bytes (timing enabled only) */
     double flops;           /* summed algorithmic flops (timing enabled only): FP32 flops of the
-                               register-blocked streaming passes, and 2 M N K per M x N x K
-                               surrogate GEMM; 0 for other kernels */
+                               register-blocked passes and persistent-batch work (per amplitude and
+                               gate as above), and 2 M N K per M x N x K surrogate GEMM; 0 for other
+                               kernels */
+    double smem_bytes;      /* summed algorithmic shared-memory bytes (timing enabled only): per
+                               register-set change of the register-blocked kernels, one write and one
+                               read of the 2^n amplitudes (16 bytes each); per gate of the shared-memory
+                               gate engine (below 10 qubits), one read and one write of the state */
 } arso_kernel_stats;
 arso_status arso_profile_enable(int on);
 arso_status arso_profile_reset(void);

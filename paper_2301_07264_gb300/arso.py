@@ -303,7 +303,8 @@ def aggregate(score, pass_flags=None, stream=None):
 
 
 class KernelStats(C.Structure):
-    _fields_ = [("launches", C.c_uint64), ("ms", C.c_double), ("bytes", C.c_double), ("flops", C.c_double)]
+    _fields_ = [("launches", C.c_uint64), ("ms", C.c_double), ("bytes", C.c_double), ("flops", C.c_double),
+                ("smem_bytes", C.c_double)]
 
 
 K_PASS, K_PASS_LAST, K_RESIDENT, K_SAMPLE, K_REDUCE, K_OTHER, K_GEMM, K_MIX = range(8)

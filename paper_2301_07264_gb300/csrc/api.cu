@@ -246,7 +246,9 @@ static void run_pass(const arso_circuit *c, const PassArgs &a, bool last, uint32
         b.ph_gb = c->d_ph_gb.as<uint32_t>();
         b.ph_R = c->d_ph_R.as<uint32_t>();
         b.rops = c->d_rops.as<RegOp>();
-        launch_pass_rb(b, last, slots, bytes, st, c->passes[a.pass].flops_per_amp * std::ldexp(sweeps, (int)c->n));
+        const Pass &ps = c->passes[a.pass];
+        launch_pass_rb(b, last, slots, bytes, st, ps.flops_per_amp * std::ldexp(sweeps, (int)c->n),
+                       (double)(ps.remaps + ps.end_remap) * 16.0 * std::ldexp(sweeps, (int)c->n));
     } else {
         launch_pass(a, last, c->precision, slots, bytes, st);
     }
@@ -551,19 +553,22 @@ static void run_streaming(arso_circuit *c, const arso_error_list *e, const std::
         h2d(d_slot_traj.ptr, st_traj, st);
         h2d(d_start.ptr, st_start, st);
         h2d(d_end.ptr, st_end, st);
-        double batch_bytes = 0, batch_flops = 0;
+        double batch_bytes = 0, batch_flops = 0, batch_smem = 0;
         for (uint32_t j = (uint32_t)jmin; j <= (uint32_t)jmax; ++j)
             for (size_t i = 0; i < nb; ++i)
                 if (st_start[i] <= (int)j && (int)j <= st_end[i]) {
                     batch_bytes += 2.0 * sb;
                     batch_flops += c->reg_blocked ? c->passes[j].flops_per_amp * std::ldexp(1.0, (int)c->n) : 0.0;
+                    batch_smem += c->reg_blocked ? (double)(c->passes[j].remaps + c->passes[j].end_remap) * 16.0 *
+                                                       std::ldexp(1.0, (int)c->n)
+                                                 : 0.0;
                 }
         const uint64_t n_launch = (uint64_t)(jmax - jmin + 1) + (states_out ? 0 : 1);
         const GraphKey key{jmin, jmax, (uint32_t)nb};
         auto hit = graphs.find(key);
         if (hit != graphs.end()) {  // replay: the slot tables above are the only inputs that changed
             {
-                ProfScope ps_(ARSO_K_PASS, batch_bytes, st, batch_flops);
+                ProfScope ps_(ARSO_K_PASS, batch_bytes, st, batch_flops, batch_smem);
                 ARSO_CUDA(cudaGraphLaunch(hit->second, st));
             }
             prof_add_launches(ARSO_K_PASS, n_launch - 1);
@@ -597,7 +602,7 @@ static void run_streaming(arso_circuit *c, const arso_error_list *e, const std::
             cudaGraphExec_t ex = capture.finish();
             graphs[key] = ex;
             {
-                ProfScope ps_(ARSO_K_PASS, batch_bytes, st, batch_flops);
+                ProfScope ps_(ARSO_K_PASS, batch_bytes, st, batch_flops, batch_smem);
                 ARSO_CUDA(cudaGraphLaunch(ex, st));
             }
             prof_add_launches(ARSO_K_PASS, n_launch - 1);
@@ -1265,7 +1270,7 @@ static void run_mixed(const std::vector<size_t> &sel, arso_circuit *const *circu
     uint64_t n_counters = 0, n_partials = 0, work_bytes = 0;
     std::vector<uint64_t> ref_part_off, ref_ctr_off, st_slot_off, st_traj_off, st_part_off, st_work_off, st_pass_off,
         st_traj_tab_off, st_cslot_off;
-    double bytes = 0.0, flops = 0.0;
+    double bytes = 0.0, flops = 0.0, smem = 0.0;
 
     // pass 1: streaming slot counts (the slot budget split by each circuit's work)
     std::vector<std::vector<uint64_t>> sid(C);
@@ -1336,6 +1341,19 @@ static void run_mixed(const std::vector<size_t> &sel, arso_circuit *const *circu
                 res_units.push_back({(uint32_t)items.size(), G - g0, small});
                 items.push_back(it);
                 bytes += (double)it.count * 2.0 * c->state_bytes();
+                const double amps = (double)it.count * (double)N;
+                flops += (c->flops_prefix[G] - c->flops_prefix[g0]) * amps;
+                if (small) {
+                    smem += (double)(G - g0) * 16.0 * amps;  // the gate engine reads and writes the state per gate
+                } else {
+                    const uint32_t nph = (uint32_t)c->ph_R.size(), ph0 = std::min<uint32_t>(nph, it.ck * (uint32_t)c->ckpt_every);
+                    if (ph0 < nph) {
+                        const uint32_t n = c->n;
+                        const uint32_t load_packed = 0u | ((n - 4) << 5) | ((n - 3) << 10) | ((n - 2) << 15) | ((n - 1) << 20);
+                        const uint32_t remaps = (c->ph_R[ph0] != load_packed) + c->chg_prefix[nph] - c->chg_prefix[ph0 + 1];
+                        smem += (double)remaps * 16.0 * amps;
+                    }
+                }
             }
             if (small) {
                 MixSmall m{};
@@ -1409,6 +1427,7 @@ static void run_mixed(const std::vector<size_t> &sel, arso_circuit *const *circu
                 str_units.push_back({si, (uint32_t)k, j, slot_level[slot] + (j - (uint32_t)mt.start)});
                 bytes += 2.0 * (double)sb;
                 flops += c->passes[j].flops_per_amp * (double)N;
+                smem += (double)(c->passes[j].remaps + ((int)j != mt.end ? c->passes[j].end_remap : 0u)) * 16.0 * (double)N;
             }
             slot_level[slot] += len;
             slot_base[slot] += len * tiles;
@@ -1473,7 +1492,7 @@ static void run_mixed(const std::vector<size_t> &sel, arso_circuit *const *circu
     ARSO_REQUIRE(units.size() + str_units.size() < (1ull << 32), "persistent batch: too many units");
     for (const Str &x : str_units) {
         units.push_back({MIX_STR, x.stream, x.k, x.j});
-        unit_end.push_back(total += streams[x.stream].tiles);
+        unit_end.push_back(total += (streams[x.stream].tiles + MIX_TILES_PER_ITEM - 1) / MIX_TILES_PER_ITEM);
     }
     if (!total) return;
 
@@ -1536,7 +1555,7 @@ static void run_mixed(const std::vector<size_t> &sel, arso_circuit *const *circu
     a.counter = d_qc.as<unsigned long long>();
     a.err = reinterpret_cast<uint32_t *>(d_qc.as<char>() + 8);
     a.wait_limit = 1u << 22;
-    launch_mix(a, bytes, flops, st);
+    launch_mix(a, bytes, flops, smem, st);
     uint32_t err = 0;
     copy_d2h(&err, a.err, 4, st);
     ARSO_CUDA(cudaStreamSynchronize(st));  // also keeps the host tables alive until the launch is done
@@ -2124,45 +2143,47 @@ arso_status arso_tolerable_rate_surrogate(const arso_circuit *cc, const arso_cri
         };
         double lo = std::max(p_lo, std::pow(10.0, lp_s - margin)), hi = std::min(p_hi, std::pow(10.0, lp_s + margin));
         double v_lo = probe(lo), v_hi = probe(hi);
+        // widen a side that fails, by steps of 2, 4, 8 margins (every probe reuses the
+        // trajectories of the earlier ones whose error sets it shares)
         for (int widen = 0; widen < 3 && !(v_lo >= P_target && v_hi < P_target); ++widen) {
-            if (v_lo < P_target && lo > p_lo) lo = std::max(p_lo, lo * std::pow(10.0, -2 * margin)), v_lo = probe(lo);
-            if (v_hi >= P_target && hi < p_hi) hi = std::min(p_hi, hi * std::pow(10.0, 2 * margin)), v_hi = probe(hi);
+            const double step = std::pow(10.0, 2 * margin * (double)(1 << widen));
+            if (v_lo < P_target && lo > p_lo) lo = std::max(p_lo, lo / step), v_lo = probe(lo);
+            if (v_hi >= P_target && hi < p_hi) hi = std::min(p_hi, hi * step), v_hi = probe(hi);
         }
-        if (v_lo >= P_target && v_hi < P_target) {
-            // a widened bracket (the surrogate missed by more than the margin) is narrowed
-            // back to the nominal width 2 margin with plain probes, each placed at the
-            // log-linear interpolation point kept inside the middle 60% of the bracket,
-            // so the final interpolation spans no more than a nominal bracket
-            for (int r = 0; r < 6 && std::log10(hi / lo) > 2 * margin * (1 + 1e-9); ++r) {
-                const double w = std::log10(hi / lo);
-                const double fr = std::min(0.8, std::max(0.2, (v_lo - P_target) / (v_lo - v_hi)));
-                const double pm = std::pow(10.0, std::log10(lo) + fr * w);
-                const double vm = probe(pm);
-                if (vm >= P_target) lo = pm, v_lo = vm;
-                else hi = pm, v_hi = vm;
-            }
-            out->verified = 1;
-            out->converged = 1;
-            out->lo = lo;
-            out->hi = hi;
+        out->verified = v_lo >= P_target && v_hi < P_target;
+        // the surrogate missed by more than the widening reaches: the search range's ends
+        if (!out->verified) {
+            if (v_lo < P_target && lo > p_lo) lo = p_lo, v_lo = probe(lo);
+            if (v_hi >= P_target && hi < p_hi) hi = p_hi, v_hi = probe(hi);
+        }
+        if (!(v_lo >= P_target && v_hi < P_target)) {
+            out->p = v_lo < P_target ? lo : hi;
+            out->lo = out->hi = out->p;
             out->value_lo = v_lo;
             out->value_hi = v_hi;
-            const double fr = (v_lo - P_target) / (v_lo - v_hi);
-            out->p = std::pow(10.0, std::log10(lo) + fr * (std::log10(hi) - std::log10(lo)));
-            return;
+            throw Error(ARSO_ENOTCONVERGED, "target success probability is not bracketed by [p_lo, p_hi]");
         }
-        // 3. fall back to the plain Monte Carlo search
-        arso_search_opts plain = *opts;
-        plain.surrogate = nullptr;
-        plain.mode = ARSO_MODE_MONTE_CARLO;
-        arso_rate_result r{};
-        const uint32_t used = out->probes;
-        const arso_status st2 = arso_tolerable_rate(cc, crit, P_target, &plain, stream, &r);
-        *out = r;
-        out->probes += used;
-        out->used_surrogate = 1;
-        out->verified = 0;
-        if (st2 != ARSO_OK) throw Error(st2, arso_last_error());
+        // narrow a bracket wider than the nominal 10^(2 margin): bisection in log p while it
+        // is more than four nominal widths, then plain probes at the log-linear interpolation
+        // point kept inside the middle 60%, so the final interpolation spans at most a
+        // nominal bracket
+        const double nominal = 2 * margin * (1 + 1e-9);
+        for (int r = 0; r < 24 && std::log10(hi / lo) > nominal; ++r) {
+            const double w = std::log10(hi / lo);
+            const double fr = w > 4 * nominal ? 0.5 : std::min(0.8, std::max(0.2, (v_lo - P_target) / (v_lo - v_hi)));
+            const double pm = std::pow(10.0, std::log10(lo) + fr * w);
+            const double vm = probe(pm);
+            if (vm >= P_target) lo = pm, v_lo = vm;
+            else hi = pm, v_hi = vm;
+        }
+        out->converged = std::log10(hi / lo) <= nominal;
+        out->lo = lo;
+        out->hi = hi;
+        out->value_lo = v_lo;
+        out->value_hi = v_hi;
+        const double fr = (v_lo - P_target) / (v_lo - v_hi);
+        out->p = std::pow(10.0, std::log10(lo) + fr * (std::log10(hi) - std::log10(lo)));
+        if (!out->converged) throw Error(ARSO_ENOTCONVERGED, "probe budget exhausted before the nominal bracket");
     });
 }
 

@@ -326,7 +326,19 @@ static void plan_phases(arso_circuit *c) {
     for (Pass &ps : c->passes) {
         ps.flops_per_amp = 0.0;
         for (uint32_t pos = ps.gb; pos < ps.ge; ++pos) ps.flops_per_amp += gate_flops(c->gates[c->perm[pos]]);
+        // shared-memory transposes of one sweep: every change of register set, from the load layout
+        const uint32_t load_packed = pack_rbits(load_map.data());
+        uint32_t prev = load_packed;
+        ps.remaps = 0;
+        for (uint32_t ph = ps.pb; ph < ps.pe; ++ph) {
+            ps.remaps += c->ph_R[ph] != prev;
+            prev = c->ph_R[ph];
+        }
+        ps.end_remap = prev != load_packed;
     }
+    c->chg_prefix.assign(c->ph_R.size() + 1, 0);
+    for (size_t ph = 0; ph < c->ph_R.size(); ++ph)
+        c->chg_prefix[ph + 1] = c->chg_prefix[ph] + (ph > 0 && c->ph_R[ph] != c->ph_R[ph - 1]);
     c->ph_gb.push_back(c->passes.empty() ? 0 : c->passes.back().ge);  // sentinel
     c->phase_of_pos.assign(c->perm.size(), 0);
     for (size_t ph = 0; ph + 1 < c->ph_gb.size(); ++ph)
@@ -389,6 +401,8 @@ void build_circuit(arso_circuit *c, uint32_t n, const arso_gate *gates, size_t n
         schedule_streaming(c);
     }
     plan_phases(c);  // may reorder gates within a pass
+    c->flops_prefix.assign(n_gates + 1, 0.0);
+    for (size_t pos = 0; pos < n_gates; ++pos) c->flops_prefix[pos + 1] = c->flops_prefix[pos] + gate_flops(c->gates[c->perm[pos]]);
     c->pos_of.assign(n_gates, 0);
     for (size_t pos = 0; pos < c->perm.size(); ++pos) c->pos_of[c->perm[pos]] = (uint32_t)pos;
     c->pass_of_pos.assign(n_gates, 0);

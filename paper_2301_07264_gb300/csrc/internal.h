@@ -144,6 +144,8 @@ struct Pass {
     std::vector<uint32_t> tile_qubits; // sorted global qubits, tile-local bit i -> tile_qubits[i]
     uint32_t pb = 0, pe = 0;           // register-blocked phases [pb, pe)
     double flops_per_amp = 0.0;        // algorithmic FP32 flops per amplitude of one sweep
+    uint32_t remaps = 0;               // register-set changes inside the pass (from the load layout)
+    uint32_t end_remap = 0;            // 1 if the last phase's set differs from the load layout
 };
 
 struct Criterion {
@@ -194,6 +196,9 @@ struct arso_circuit {
     std::vector<uint32_t> ph_R;             // phase -> packed register bits
     std::vector<uint8_t> rpos;              // engine position -> (reg pos of q0) | (reg pos of q1) << 4, 15 = none
     std::vector<uint32_t> phase_of_pos;     // engine position -> phase
+    std::vector<double> flops_prefix;       // engine position k -> algorithmic FP32 flops per amplitude of
+                                            // gates [0, k) (the tracing counts of arso.h)
+    std::vector<uint32_t> chg_prefix;       // phase k -> phases 1 <= p < k whose register set differs from p-1's
     // device tables
     arso::DeviceBuffer d_gates;             // DGate[G] in engine order
     arso::DeviceBuffer d_mats;              // complex<float> or complex<double> pool

@@ -11,7 +11,7 @@ namespace arso {
 namespace {
 struct Pending {
     int kind;
-    double bytes, flops;
+    double bytes, flops, smem;
     cudaEvent_t a, b;
 };
 struct State {
@@ -49,6 +49,7 @@ void resolve(State &s) {
             s.stats[p.kind].ms += ms;
             s.stats[p.kind].bytes += p.bytes;
             s.stats[p.kind].flops += p.flops;
+            s.stats[p.kind].smem_bytes += p.smem;
         } else {
             cudaGetLastError();
         }
@@ -71,13 +72,13 @@ void prof_begin(int kind, double, cudaStream_t st, cudaEvent_t *ev_out) {
     if (e && cudaEventRecord(e, st) == cudaSuccess) *ev_out = e;
 }
 
-void prof_end(int kind, double bytes, cudaStream_t st, cudaEvent_t start, double flops) {
+void prof_end(int kind, double bytes, cudaStream_t st, cudaEvent_t start, double flops, double smem) {
     if (!start) return;
     State &s = state();
     std::lock_guard<std::mutex> lk(s.mu);
     cudaEvent_t e = take_event(s);
     if (e && cudaEventRecord(e, st) == cudaSuccess) {
-        s.pending.push_back(Pending{kind, bytes, flops, start, e});
+        s.pending.push_back(Pending{kind, bytes, flops, smem, start, e});
         if (s.pending.size() > 4096) resolve(s);
     } else {
         s.free_events.push_back(start);

@@ -17,14 +17,16 @@ from . import arso
 
 def rows_for_circuit(cc, crit, log10_ps, traj_per_p, seed, traj_begin=0, stream=None):
     """Device tensors (x: n x 33 float32, y: n float32) for one compiled circuit; the
-    trajectories of all rates run in one arso_run_batch call."""
+    errors of all rates are sampled in one call and their trajectories run in one
+    arso_run_batch call."""
     import torch
     f = torch.from_numpy(arso.circuit_features(cc, crit)).cuda()
     c = arso.make_criterion(crit)
-    errs, scores, flags, xs = [], [], [], []
+    ps = [10.0 ** float(lp) / 3 for lp in log10_ps]
+    errs = arso.sample_errors_batch([cc] * len(ps), ps, ps, ps, seed,
+                                    [traj_begin + i * traj_per_p for i in range(len(ps))], traj_per_p, stream)
+    scores, flags, xs = [], [], []
     for i, lp in enumerate(log10_ps):
-        p = 10.0 ** float(lp)
-        errs.append(arso.sample_errors(cc, p / 3, p / 3, p / 3, seed, traj_begin + i * traj_per_p, traj_per_p, stream))
         scores.append(torch.empty(traj_per_p, dtype=torch.float64, device="cuda"))
         flags.append(torch.empty(traj_per_p, dtype=torch.uint8, device="cuda"))
         x = torch.empty((traj_per_p, arso.SURROGATE_INPUTS), dtype=torch.float32, device="cuda")
