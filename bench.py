@@ -70,17 +70,17 @@ def _kernel_sha():
     return h.hexdigest()[:16]
 
 
-def _traffic_per_slot():
-    """DRAM bytes per active trajectory slot per pass launch, from the ncu
-    capture recorded in profiles/pass_kernel_traffic.json, if that capture was
-    taken on the current kernel source (else None)."""
+def _traffic_ratio():
+    """DRAM bytes per algorithmic byte of the pass launches, from the ncu capture
+    recorded in profiles/pass_kernel_traffic.json, if that capture was taken on the
+    current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "pass_kernel_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         if d.get("source_sha") != _kernel_sha():
             return None
-        return float(d["dram_bytes_per_slot_launch"])
+        return float(d["dram_bytes_per_algorithmic_byte"])
     except Exception:
         return None
 
@@ -481,8 +481,7 @@ def run_ours(args):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_mhz = float(clk.get("sm_max_mhz") or 2070.0)
     fp32_peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
-    tr = _traffic_per_slot()
-    avg_slots = ps.bytes / max(ps.launches, 1) / (2.0 * 8 * (1 << circ.n))
+    tr = _traffic_ratio()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
@@ -495,7 +494,7 @@ def run_ours(args):
                      "peak_kind": f"nominal FP32 FMA rate: {sms} SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz "
                                   "(max SM clock seen)",
                      "unit": "TFLOP/s", "frac": tflops / fp32_peak if fp32_peak else None,
-                     "traffic": (tr * avg_slots) if tr is not None else None,
+                     "traffic": (tr * ps.bytes / max(ps.launches, 1)) if tr is not None else None,
                      "algorithmic_flops_per_launch": ps.flops / max(ps.launches, 1),
                      "algorithmic_bytes_per_launch": ps.bytes / max(ps.launches, 1),
                      "avg_launch_ms": ps.ms / max(ps.launches, 1), "launches": ps.launches},

@@ -1492,7 +1492,7 @@ static void run_mixed(const std::vector<size_t> &sel, arso_circuit *const *circu
     ARSO_REQUIRE(units.size() + str_units.size() < (1ull << 32), "persistent batch: too many units");
     for (const Str &x : str_units) {
         units.push_back({MIX_STR, x.stream, x.k, x.j});
-        unit_end.push_back(total += (streams[x.stream].tiles + MIX_TILES_PER_ITEM - 1) / MIX_TILES_PER_ITEM);
+        unit_end.push_back(total += streams[x.stream].tiles);
     }
     if (!total) return;
 

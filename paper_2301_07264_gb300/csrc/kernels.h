@@ -130,7 +130,7 @@ void launch_batch_resident(const BatchCircuit *circs, const BatchItem *items, ui
 //            memory gate engine, up to 32 trajectories side by side);
 //  MIX_RES   a batched register-blocked resident item (BatchItem above);
 //  MIX_STR   one pass of one trajectory of a streaming circuit, one sub-item per
-//            MIX_TILES_PER_ITEM tiles; its dependencies (the trajectory's previous pass, or the slot's
+//            tile; its dependencies (the trajectory's previous pass, or the slot's
 //            previous trajectory) are per-slot counters of finished tiles, and the
 //            list is ordered so that every unit's dependencies come before it.
 enum : uint32_t { MIX_REF = 0, MIX_SMALL = 1, MIX_RES = 2, MIX_STR = 3 };
@@ -211,7 +211,6 @@ struct MixArgs {
     uint32_t wait_limit;       // polls per wait
 };
 constexpr uint32_t MIX_SMALL_MAX = 32;  // trajectories per SMALL item
-constexpr uint32_t MIX_TILES_PER_ITEM = 1;  // tiles of one streaming pass per sub-item (8: no faster)
 void launch_mix(const MixArgs &a, double bytes, double flops, double smem_bytes, cudaStream_t st);
 
 void launch_resident(const ResidentArgs &a, bool ideal, int precision, double bytes, cudaStream_t st);

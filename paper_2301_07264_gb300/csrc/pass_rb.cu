@@ -1214,32 +1214,50 @@ __device__ __noinline__ void mix_res(const BatchItem &it, const BatchCircuit &C,
     batch_item(it, C, ids, smem_raw, red, ubuf, s_ops);
 }
 
-// MIX_STR: tiles [t0, t1) of pass j of trajectory k of stream S (the body of
-// pass_rb_kernel with explicit coordinates, looped over a chunk of tiles so that the
-// dependency wait, the event search and the publication are paid once per chunk),
-// after the slot's dependencies. As there, only what the phase loop needs stays live
-// across it; the rest is reloaded after it.
+// MIX_STR: one tile of pass j of trajectory k of stream S (the body of pass_rb_kernel
+// with explicit coordinates), after the slot's dependencies. The item's coordinates live
+// in shared memory (`it`) and the stream's descriptor too: read where needed rather than
+// held in registers, since the phase loop already uses all 128 (kept in registers they
+// spilled into the loop).
+struct MixTile {
+    uint32_t k, j, tile;
+};
+
 __device__ __forceinline__ uint64_t mix_gidx(const MixStream &S, uint32_t j, uint64_t base, uint32_t jj) {
     return base + S.passes[j].offs[jj >> S.c] + (jj & ((1u << S.c) - 1u));
 }
 
-__device__ __forceinline__ void mix_tiles(const MixArgs &A, const MixStream &S, uint32_t k, uint32_t j, uint32_t t0,
-                                          uint32_t t1, unsigned char *smem_raw, Partial *red, float2 *ubuf,
-                                          RegOp (*s_ops)[MAX_PHASE_OPS], uint32_t *s_flag) {
+__device__ __forceinline__ void mix_tile(const MixArgs &A, const MixStream &S, const MixTile &it,
+                                         unsigned char *smem_raw, Partial *red, float2 *ubuf,
+                                         RegOp (*s_ops)[MAX_PHASE_OPS], uint32_t *s_flag) {
     float2 *sm = reinterpret_cast<float2 *>(smem_raw);
-    const int t = S.t;
     if (threadIdx.x == 0) {
-        const MixTraj &T = S.trajs[k];
-        *s_flag = mix_wait(S.slot_done + T.slot, T.base + (uint32_t)((int)j - T.start) * S.tiles, A.wait_limit, A.err);
+        const MixTraj &T = S.trajs[it.k];
+        *s_flag = mix_wait(S.slot_done + T.slot, T.base + (uint32_t)((int)it.j - T.start) * S.tiles, A.wait_limit,
+                           A.err);
     }
     __syncthreads();  // thread 0's acquire load, then the barrier, order the tile loads after it
     if (!*s_flag) return;
-    const uint32_t load_packed = 0u | ((uint32_t)(t - 4) << 5) | ((uint32_t)(t - 3) << 10) |
-                                 ((uint32_t)(t - 2) << 15) | ((uint32_t)(t - 1) << 20);
-    // this pass's events: binary search for the first key at or after the pass's first gate
-    const uint32_t *ev0, *ev_end;
+    const int t = S.t;
+    Amps v;
+    const uint32_t *ev, *ev_end;
     {
+        const uint32_t k = it.k, j = it.j;
         const MixTraj &T = S.trajs[k];
+        const uint64_t N = 1ull << S.n;
+        const bool from_cache = (int)j == T.start;
+        const float2 *src = from_cache ? S.cache + (size_t)S.cache_slot[j] * N : S.work + (size_t)T.slot * N;
+        const uint64_t base = tile_base(S.passes[j].rest_mask, it.tile);
+#pragma unroll
+        for (int hi = 0; hi < 16; ++hi) {
+            const uint32_t jj = ((uint32_t)hi << (t - 4)) | (threadIdx.x << 1);
+            const float4 *pa = reinterpret_cast<const float4 *>(src + mix_gidx(S, j, base, jj));
+            // the working slot was written by other CTAs of this launch: read it through L2
+            const float4 w = from_cache ? __ldg(pa) : __ldcg(pa);
+            v.re[hi] = make_float2(w.x, w.z);
+            v.im[hi] = make_float2(w.y, w.w);
+        }
+        // this pass's events: binary search for the first key at or after the pass's first gate
         const uint32_t *lo = S.keys + S.offsets[T.tr], *hi_ = S.keys + S.offsets[T.tr + 1];
         ev_end = hi_;
         const uint32_t key_lo = S.passes[j].gb << 3;
@@ -1248,85 +1266,68 @@ __device__ __forceinline__ void mix_tiles(const MixArgs &A, const MixStream &S, 
             if (*mid < key_lo) lo = mid + 1;
             else hi_ = mid;
         }
-        ev0 = lo;
+        ev = lo;
     }
-    const bool scored = (int)j == S.trajs[k].end;
-    for (uint32_t tile = t0; tile < t1; ++tile) {
-        __syncthreads();  // the previous tile's last reads of the staged records and the tile buffer
-        Amps v;
-        {
-            const MixTraj &T = S.trajs[k];
-            const uint64_t N = 1ull << S.n;
-            const bool from_cache = (int)j == T.start;
-            const float2 *src = from_cache ? S.cache + (size_t)S.cache_slot[j] * N : S.work + (size_t)T.slot * N;
-            const uint64_t base = tile_base(S.passes[j].rest_mask, tile);
+    TileCtx c;
+    c.m = 0;
+    c.gp = 0;
+    c.tid = threadIdx.x;
+    c.nthr = blockDim.x;
+    set_phase(c, 0u | ((uint32_t)(t - 4) << 5) | ((uint32_t)(t - 3) << 10) | ((uint32_t)(t - 2) << 15) |
+                     ((uint32_t)(t - 1) << 20),
+              t);
+    uint32_t next = ev < ev_end ? *ev : NO_EVENT;
+    {
+        const uint32_t pb = S.passes[it.j].pb;
+        if (pb < S.passes[it.j].pe)
+            stage_ops(s_ops[0], S.rops + S.ph_gb[pb], S.ph_gb[pb + 1] - S.ph_gb[pb], threadIdx.x, blockDim.x);
+    }
+    for (uint32_t ph = S.passes[it.j].pb, buf = 0; ph < S.passes[it.j].pe; ++ph, buf ^= 1u) {
+        stage_wait();
+        if (ph + 1 < S.passes[it.j].pe)
+            stage_ops(s_ops[buf ^ 1u], S.rops + S.ph_gb[ph + 1], S.ph_gb[ph + 2] - S.ph_gb[ph + 1], threadIdx.x,
+                      blockDim.x);
+        const uint32_t R = S.ph_R[ph];
+        if (R != c.R) remap<true>(v, sm, c, R, t);
+        const uint32_t g0 = S.ph_gb[ph];
+        run_gates(v, c, g0, S.ph_gb[ph + 1], s_ops[buf], g0, S.mats, sm, ubuf, t, ev, ev_end, next);
+    }
+    apply_global_phase(v, c);
+    const uint32_t k = it.k, j = it.j;
+    const MixTraj &T = S.trajs[k];
+    const uint64_t N = 1ull << S.n;
+    const uint64_t base = tile_base(S.passes[j].rest_mask, it.tile);
+    const bool scored = (int)j == T.end;
+    if (scored) {
+        const float2 *ref = S.ref_cache + (size_t)S.cache_slot[j + 1] * N;
+        Partial acc = empty_partial();
+        score_registers(acc, S.crit, v, c, ref, [&](uint32_t jj) { return mix_gidx(S, j, base, jj); });
+        acc = block_reduce_partial(acc, red);
+        if (threadIdx.x == 0) S.partials[(size_t)k * S.tiles + it.tile] = acc;
+    } else {
+        const uint32_t load_packed = 0u | ((uint32_t)(t - 4) << 5) | ((uint32_t)(t - 3) << 10) |
+                                     ((uint32_t)(t - 2) << 15) | ((uint32_t)(t - 1) << 20);
+        if (c.R != load_packed) remap(v, sm, c, load_packed, t);
+        float2 *dst = S.work + (size_t)T.slot * N;
+        const uint32_t flip0 = c.m & 1u;
 #pragma unroll
-            for (int hi = 0; hi < 16; ++hi) {
-                const uint32_t jj = ((uint32_t)hi << (t - 4)) | (threadIdx.x << 1);
-                const float4 *pa = reinterpret_cast<const float4 *>(src + mix_gidx(S, j, base, jj));
-                // the working slot was written by other CTAs of this launch: read it through L2
-                const float4 w = from_cache ? __ldg(pa) : __ldcg(pa);
-                v.re[hi] = make_float2(w.x, w.z);
-                v.im[hi] = make_float2(w.y, w.w);
-            }
-        }
-        const uint32_t *ev = ev0;
-        TileCtx c;
-        c.m = 0;
-        c.gp = 0;
-        c.tid = threadIdx.x;
-        c.nthr = blockDim.x;
-        set_phase(c, load_packed, t);
-        uint32_t next = ev < ev_end ? *ev : NO_EVENT;
-        const uint32_t pb = S.passes[j].pb, pe = S.passes[j].pe;
-        const uint32_t *ph_gb = S.ph_gb;
-        const RegOp *rops = S.rops;
-        if (pb < pe) stage_ops(s_ops[0], rops + ph_gb[pb], ph_gb[pb + 1] - ph_gb[pb], threadIdx.x, blockDim.x);
-        for (uint32_t ph = pb; ph < pe; ++ph) {
-            const uint32_t buf = (ph - pb) & 1u;
-            stage_wait();
-            if (ph + 1 < pe)
-                stage_ops(s_ops[buf ^ 1u], rops + ph_gb[ph + 1], ph_gb[ph + 2] - ph_gb[ph + 1], threadIdx.x,
-                          blockDim.x);
-            const uint32_t R = S.ph_R[ph];
-            if (R != c.R) remap<true>(v, sm, c, R, t);
-            const uint32_t g0 = ph_gb[ph];
-            run_gates(v, c, g0, ph_gb[ph + 1], s_ops[buf], g0, S.mats, sm, ubuf, t, ev, ev_end, next);
-        }
-        apply_global_phase(v, c);
-        const MixTraj &T = S.trajs[k];
-        const uint64_t N = 1ull << S.n;
-        const uint64_t base = tile_base(S.passes[j].rest_mask, tile);
-        if (scored) {
-            const float2 *ref = S.ref_cache + (size_t)S.cache_slot[j + 1] * N;
-            Partial acc = empty_partial();
-            score_registers(acc, S.crit, v, c, ref, [&](uint32_t jj) { return mix_gidx(S, j, base, jj); });
-            acc = block_reduce_partial(acc, red);
-            if (threadIdx.x == 0) S.partials[(size_t)k * S.tiles + tile] = acc;
-        } else {
-            if (c.R != load_packed) remap(v, sm, c, load_packed, t);
-            float2 *dst = S.work + (size_t)T.slot * N;
-            const uint32_t flip0 = c.m & 1u;
-#pragma unroll
-            for (int hi = 0; hi < 16; ++hi) {
-                const uint32_t jj = (((uint32_t)hi << (t - 4)) | (threadIdx.x << 1)) ^ (c.m & ~1u);
-                const float2 r = flip0 ? swp2(v.re[hi]) : v.re[hi], i = flip0 ? swp2(v.im[hi]) : v.im[hi];
-                reinterpret_cast<float4 *>(dst + mix_gidx(S, j, base, jj))[0] = make_float4(r.x, i.x, r.y, i.y);
-            }
+        for (int hi = 0; hi < 16; ++hi) {
+            const uint32_t jj = (((uint32_t)hi << (t - 4)) | (threadIdx.x << 1)) ^ (c.m & ~1u);
+            const float2 r = flip0 ? swp2(v.re[hi]) : v.re[hi], i = flip0 ? swp2(v.im[hi]) : v.im[hi];
+            reinterpret_cast<float4 *>(dst + mix_gidx(S, j, base, jj))[0] = make_float4(r.x, i.x, r.y, i.y);
         }
     }
     // publish: the barrier orders every thread's stores before thread 0's fence and
     // counter increments (the release the waiting CTAs acquire)
     __syncthreads();
     if (threadIdx.x == 0) {
-        const MixTraj &T = S.trajs[k];
         __threadfence();
-        atomicAdd(S.slot_done + T.slot, t1 - t0);
-        *s_flag = scored && atomicAdd(S.traj_done + k, t1 - t0) + (t1 - t0) == S.tiles ? 2u : 1u;
+        atomicAdd(S.slot_done + T.slot, 1u);
+        *s_flag = scored && atomicAdd(S.traj_done + k, 1u) == S.tiles - 1 ? 2u : 1u;
     }
     __syncthreads();
     if (*s_flag != 2u) return;
-    // last chunk of the scored pass: the trajectory's partials added in the order of
+    // last tile of the scored pass: the trajectory's partials added in the order of
     // finish_partials_kernel, so the score equals the one of the per-pass launches
     __threadfence();
     Partial acc = empty_partial();
@@ -1338,7 +1339,6 @@ __device__ __forceinline__ void mix_tiles(const MixArgs &A, const MixStream &S, 
     }
     acc = block_reduce_partial(acc, red);
     if (threadIdx.x == 0) {
-        const MixTraj &T = S.trajs[k];
         const double sc = finish_score(S.crit, acc);
         S.score[T.tr] = sc;
         if (S.pass_flags) S.pass_flags[T.tr] = sc >= S.crit.threshold;
@@ -1357,6 +1357,7 @@ __global__ void __launch_bounds__(MIX_THREADS, 2) mix_kernel(const __grid_consta
     // instead of being held in registers (the loop already uses all 128)
     __shared__ MixStream s_stream;
     __shared__ uint32_t s_stream_idx;
+    __shared__ MixTile s_tile;
     if (threadIdx.x == 0) s_u = 0, s_stream_idx = ~0u;
     for (;;) {
         __syncthreads();
@@ -1381,13 +1382,15 @@ __global__ void __launch_bounds__(MIX_THREADS, 2) mix_kernel(const __grid_consta
             const BatchItem it = a.items[un.idx];
             mix_res(it, a.rcircs[it.circuit], a.ids, smem_raw, red, ubuf, s_ops);
         } else {
-            if (threadIdx.x == 0 && s_stream_idx != un.idx) {
-                s_stream = a.streams[un.idx];
-                s_stream_idx = un.idx;
+            if (threadIdx.x == 0) {
+                if (s_stream_idx != un.idx) {
+                    s_stream = a.streams[un.idx];
+                    s_stream_idx = un.idx;
+                }
+                s_tile = MixTile{un.a, un.b, sub};
             }
             __syncthreads();
-            const uint32_t t0 = sub * MIX_TILES_PER_ITEM, t1 = min(s_stream.tiles, t0 + MIX_TILES_PER_ITEM);
-            mix_tiles(a, s_stream, un.a, un.b, t0, t1, smem_raw, red, ubuf[0], s_ops, &s_flag);
+            mix_tile(a, s_stream, s_tile, smem_raw, red, ubuf[0], s_ops, &s_flag);
         }
     }
 }
