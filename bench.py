@@ -15,7 +15,8 @@ Prints ONE JSON line (rank 0). Under torchrun every rank runs its own
 trajectory range (weak scaling, no collective on the data path); the time is
 the max over ranks after a barrier.
 
-Other configurations (--workload): grover12 (Grover, 11 search qubits + 1
+Other configurations (--workload): qft4 (4-qubit QFT on |0101>, complex128,
+1,000 trajectories at p = 1e-3), grover12 (Grover, 11 search qubits + 1
 borrowed, 16 rates, argmax), mix256 (256 uneven circuits of 8-22 qubits with
 autotuned tiles), search (surrogate-bracketed vs plain tolerable-rate search),
 exhaustive (single-error analysis by one sweep vs by trajectories), qv
@@ -296,6 +297,22 @@ def grover_cpu_baseline(seconds):
     return cpu_baseline("grover12", seconds, rates, 100_000, 16 << circ.n)
 
 
+def qft4_cpu_baseline():
+    """The FP64 oracle on the whole QFT-4 workload step (1,000 trajectories at
+    p = 1e-3 through montecarlo.run_trajectories), one core: it finishes in
+    seconds, so no sampling is needed."""
+    from oracle import montecarlo
+    from workloads import circuits as C
+    circ = C.qft4_0101()
+    p, T = 1e-3, 1000
+    t0 = time.perf_counter()
+    montecarlo.run_trajectories(circ, 0, 0, T, p / 3, p / 3, p / 3)
+    dt = time.perf_counter() - t0
+    return {"value": T / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_info(),
+            "sample": f"FP64 numpy oracle montecarlo.run_trajectories over all {T} trajectories of one step "
+                      f"({dt:.2f} s, one core)"}
+
+
 def run_reference(args):
     """--impl reference: the FP64 CPU oracle timed on this host's cores, on all
     usable cores in parallel over trajectories. Each step is a bounded sample of
@@ -564,7 +581,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-suffix", action="store_true",
                     help="run every trajectory to the end instead of scoring after its last error")
-    ap.add_argument("--workload", default="brickwork24", choices=["brickwork24", "grover12", "mix256", "search", "exhaustive", "qv", "families"],
+    ap.add_argument("--workload", default="brickwork24", choices=["brickwork24", "qft4", "grover12", "mix256", "search", "exhaustive", "qv", "families"],
                     help="brickwork24 is the benchmark line; the others measure the other configurations")
     ap.add_argument("--search-circuits", type=int, default=8,
                     help="search workload: evaluation circuits per size band (half as many at 20-24 qubits)")
@@ -588,6 +605,8 @@ def main():
                 line["roofline"], line["roofline_smem"] = onchip_roofline(line.pop("onchip"), clk)
             if args.workload == "grover12" and not args.no_cpu_baseline:
                 line["cpu_baseline"] = grover_cpu_baseline(args.cpu_seconds)
+            if args.workload == "qft4" and not args.no_cpu_baseline:
+                line["cpu_baseline"] = qft4_cpu_baseline()
             if args.workload == "exhaustive" and line.get("hbm_sweep"):
                 peak, src = _peaks()
                 h = line["hbm_sweep"]

@@ -83,6 +83,45 @@ def grover12(args):
             "kernels": _kernel_stats(arso)}
 
 
+def qft4(args):
+    """The 4-qubit QFT on |0101> (complex128, resident engine), Pauli errors at
+    p = 1e-3 after every gate, 1,000 trajectories from seed 0 per step, fidelity
+    with the ideal output state >= 0.5 (pass fraction)."""
+    import torch
+    from paper_2301_07264_gb300 import arso
+    from workloads import circuits as W
+    circ = W.qft4_0101()
+    cc = arso.compile_circuit(circ.n, circ.gates, precision=arso.C128)
+    p, T = 1e-3, 1000
+    score = torch.empty(T, dtype=torch.float64, device="cuda")
+    flags = torch.empty(T, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    res = []
+
+    def step(k):
+        errs = arso.sample_errors(cc, p / 3, p / 3, p / 3, 0, k * T, T, stream)
+        arso.run_trajectories(cc, errs, circ.criterion, score, flags, stream)
+        res.append(arso.aggregate(score, flags, stream))
+
+    for w in range(args.warmup):
+        step(1000 + w)
+    res.clear()
+    e0, e1 = _events()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(args.steps):
+        step(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    return {"metric": "error-injected trajectories/sec", "value": T * args.steps / sec, "unit": "traj/s",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "qft4_0101_p1e-3", "n_qubits": 4, "G": circ.G, "L": circ.L,
+                       "traj_per_step": T, "criterion": "fidelity >= 0.5 (pass fraction)", "precision": "complex128"},
+            "results": {"first_step_pass_frac": res[0][1], "first_step_mean_fidelity": res[0][0]}}
+
+
 def mix256(args):
     """256 circuits of 8..22 qubits (QFT, Grover, QAOA p=2, adders) at p = 5e-4,
     2000 trajectories each per step: one arso_sample_errors_batch call and one
@@ -403,4 +442,4 @@ def run(args):
     import torch
     torch.cuda.set_device(0)
     torch.cuda.set_stream(torch.cuda.Stream())
-    return {"grover12": grover12, "mix256": mix256, "search": search, "exhaustive": exhaustive, "qv": qv, "families": families}[args.workload](args)
+    return {"qft4": qft4, "grover12": grover12, "mix256": mix256, "search": search, "exhaustive": exhaustive, "qv": qv, "families": families}[args.workload](args)
