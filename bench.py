@@ -585,6 +585,9 @@ def main():
                     help="brickwork24 is the benchmark line; the others measure the other configurations")
     ap.add_argument("--search-circuits", type=int, default=8,
                     help="search workload: evaluation circuits per size band (half as many at 20-24 qubits)")
+    ap.add_argument("--search-ablation", action="store_true",
+                    help="search workload: also train a network on the three circuits of the other "
+                         "configurations only and search the 12-18-qubit circuits with it")
     ap.add_argument("--search-margin", type=float, default=0.08,
                     help="search workload: half-width of the surrogate's bracket in log10 p")
     ap.add_argument("--train-rows", type=int, default=2_000_000)

@@ -218,6 +218,24 @@ def search(args):
                            "launches": gemm.launches, "ms": gemm.ms, "share": gemm.ms / total_ms if total_ms else None,
                            "useful_tflops": gemm.flops / gemm.ms / 1e9 if gemm.ms else None},
                   "reduce_ms": ks["reduce"].ms, "other_ms": ks["other"].ms}
+    # ablation: a network trained only on the three circuits of the other configurations
+    # (QFT-4 on |0101>, Grover-12, brickwork-24), the literal reading of the training set
+    s_abl, abl_info = None, None
+    if args.search_ablation:
+        lit = [W.qft4_0101(), W.grover12(0), W.brickwork24(0)]
+        rows_per = [40_000, 40_000, 10_000]  # a 24-qubit row is a 24-qubit trajectory
+        t0 = time.perf_counter()
+        xs, ys = [], []
+        for k, (c, nr) in enumerate(zip(lit, rows_per)):
+            x_, y_ = surrogate_data.generate([c], nr, seed=40 + k, lp_lo=-5.0, lp_hi=-1.0, p_points=32)
+            xs.append(x_)
+            ys.append(y_)
+        xa, ya = torch.cat(xs), torch.cat(ys)
+        gen_a = time.perf_counter() - t0
+        s_abl = arso.surrogate_create(13)
+        loss_a = arso.surrogate_train(s_abl, xa, ya, epochs=80, batch=8192, lr=2e-3, seed=3)
+        abl_info = {"train_circuits": ["qft4_0101", "grover12", "brickwork24"], "rows": int(xa.shape[0]),
+                    "generate_seconds": gen_a, "train_loss": loss_a}
     # evaluation circuits, unseen: per band, alternating QAOA and brickwork
     rng = np.random.default_rng(2)
     nb = max(1, args.search_circuits)
@@ -243,10 +261,18 @@ def search(args):
                                            p_lo=p_lo, p_hi=p_hi)
         torch.cuda.synchronize()
         t2 = time.perf_counter()
-        rows.append({"family": c.family, "n": c.n, "G": c.G, "L": c.L, "band": _search_band(c.n),
-                     "p_plain": pl.p, "probes_plain": pl.probes, "plain_s": t1 - t0,
-                     "p_surrogate": su.p, "probes_surrogate": su.probes, "surrogate_s": t2 - t1,
-                     "verified": su.verified, "rel_err": abs(su.p - pl.p) / pl.p})
+        row = {"family": c.family, "n": c.n, "G": c.G, "L": c.L, "band": _search_band(c.n),
+               "p_plain": pl.p, "probes_plain": pl.probes, "plain_s": t1 - t0,
+               "p_surrogate": su.p, "probes_surrogate": su.probes, "surrogate_s": t2 - t1,
+               "verified": su.verified, "rel_err": abs(su.p - pl.p) / pl.p}
+        if s_abl is not None and c.n <= 18:
+            t3 = time.perf_counter()
+            ab = arso.tolerable_rate_surrogate(cc, crit, 2 / 3, s_abl, n_traj=20000, seed=0,
+                                               margin=args.search_margin, p_lo=p_lo, p_hi=p_hi)
+            torch.cuda.synchronize()
+            row["ablation"] = {"p": ab.p, "probes": ab.probes, "seconds": time.perf_counter() - t3,
+                               "verified": ab.verified, "rel_err": abs(ab.p - pl.p) / pl.p}
+        rows.append(row)
     bands = {}
     for b in sorted({r["band"] for r in rows}):
         rs = [r for r in rows if r["band"] == b]
@@ -258,6 +284,15 @@ def search(args):
                     "verified": sum(r["verified"] for r in rs),
                     "probes_plain_mean": float(np.mean([r["probes_plain"] for r in rs])),
                     "probes_surrogate_mean": float(np.mean([r["probes_surrogate"] for r in rs]))}
+    if abl_info is not None:
+        ra = [r for r in rows if "ablation" in r]
+        abl_info.update({"circuits": len(ra), "qubits": "12-18",
+                         "speedup": sum(r["plain_s"] for r in ra) / sum(r["ablation"]["seconds"] for r in ra),
+                         "speedup_main_network_same_circuits":
+                             sum(r["plain_s"] for r in ra) / sum(r["surrogate_s"] for r in ra),
+                         "probes_mean": float(np.mean([r["ablation"]["probes"] for r in ra])),
+                         "verified": sum(r["ablation"]["verified"] for r in ra),
+                         "rel_err_max": max(r["ablation"]["rel_err"] for r in ra)})
     plain_s, sur_s = sum(r["plain_s"] for r in rows), sum(r["surrogate_s"] for r in rows)
     rel = [r["rel_err"] for r in rows]
     return {"metric": "tolerable-rate searches/sec", "value": len(evals) / sur_s, "unit": "searches/s",
@@ -269,7 +304,8 @@ def search(args):
                        "target": "pass fraction >= 2/3 (fidelity >= 0.9)"},
             "plain_searches_per_s": len(evals) / plain_s, "speedup": plain_s / sur_s,
             "rel_err_max": max(rel), "rel_err_mean": float(np.mean(rel)),
-            "verified": sum(r["verified"] for r in rows), "bands": bands, "train_loss": loss,
+            "verified": sum(r["verified"] for r in rows), "bands": bands, "ablation_literal_training_set": abl_info,
+            "train_loss": loss,
             "generate_seconds": gen_s, "train_seconds": train_s, "surrogate_train": train_info, "rows": rows}
 
 
