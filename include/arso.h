@@ -239,6 +239,16 @@ arso_status arso_aggregate(const double *score, const uint8_t *pass_flags, uint6
 arso_status arso_run_batch(size_t count, arso_circuit *const *circuits, const arso_error_list *const *errors,
                            const arso_criterion *crits, void *stream, double *const *score_out,
                            uint8_t *const *pass_out);
+/* Test support for the failure path of arso_run_batch's persistent launch (no
+ * counterpart in the paper). A tile's wait for its slot's previous pass polls a
+ * bounded number of times; one that gives up sets an error word, every CTA
+ * leaves at its next queue pull, and the call returns ARSO_ETIMEOUT. This makes
+ * the next persistent launch add 2^30 to every wait's target, with a short poll
+ * limit, so that its first streaming tile's wait runs out: nothing hangs or
+ * faults, and the next call on the same context runs normally. Only a batch
+ * with a streaming circuit in the persistent launch waits at all. One-shot,
+ * process-wide. */
+arso_status arso_debug_stall_next_batch(void);
 
 /* Autotune the fused-pass schedule of a circuit by measurement: for each
  * candidate (tile_qubits in 10..14, low_qubits in 3..5) compile the circuit,

@@ -406,6 +406,7 @@ for _name, _args in {
     "arso_surrogate_set_norm": [_vp, _vp, _vp],
     "arso_surrogate_grads": [_vp, _vp, _vp, C.c_uint64, _vp, _vp, _vp],
     "arso_debug_stall_next_gemm": [],
+    "arso_debug_stall_next_batch": [],
     "arso_tolerable_rate_surrogate": [_vp, C.POINTER(Criterion), C.c_double, C.POINTER(SearchOpts), _vp,
                                       C.POINTER(RateResult)],
 }.items():
@@ -481,6 +482,12 @@ def debug_stall_next_gemm():
     """Make the next tensor-core GEMM with a TMA operand give up its bounded wait
     (see include/arso.h); the call that launches it raises ArsoError(ETIMEOUT)."""
     _check(lib.arso_debug_stall_next_gemm())
+
+
+def debug_stall_next_batch():
+    """Make the next persistent batch launch's dependency waits run out (see
+    include/arso.h); that run_batch call raises ArsoError(ETIMEOUT)."""
+    _check(lib.arso_debug_stall_next_batch())
 
 
 def tolerable_rate_surrogate(circ, crit, P_target, surrogate, p_lo=0.0, p_hi=0.0, n_traj=0, seed=0, margin=0.0,

@@ -2,6 +2,7 @@
 // trajectory engines, success probability (Sec. IV-C, Eq. (4)) and the
 // tolerable error rate (Sec. IV-D, Eq. (5), Fig. 3).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <functional>
@@ -1226,6 +1227,9 @@ static MixKind mix_kind(const arso_circuit *c) {
 
 constexpr uint64_t MIX_SLOT_BUDGET = 16ull << 30;  // working slots of all streaming circuits of a call
 
+// set by arso_debug_stall_next_batch: no dependency wait of the next persistent launch can be met
+static std::atomic<bool> g_stall_next_batch{false};
+
 static void run_mixed(const std::vector<size_t> &sel, arso_circuit *const *circuits,
                       const arso_error_list *const *errors, const std::vector<DevCrit> &dcs,
                       const std::vector<double *> &d_score, const std::vector<uint8_t *> &d_pass, cudaStream_t st) {
@@ -1555,6 +1559,10 @@ static void run_mixed(const std::vector<size_t> &sel, arso_circuit *const *circu
     a.counter = d_qc.as<unsigned long long>();
     a.err = reinterpret_cast<uint32_t *>(d_qc.as<char>() + 8);
     a.wait_limit = 1u << 22;
+    if (g_stall_next_batch.exchange(false)) {  // arso_debug_stall_next_batch: no wait can be met
+        a.stall_extra = 1u << 30;
+        a.wait_limit = 1u << 12;
+    }
     launch_mix(a, bytes, flops, smem, st);
     uint32_t err = 0;
     copy_d2h(&err, a.err, 4, st);
@@ -1562,7 +1570,7 @@ static void run_mixed(const std::vector<size_t> &sel, arso_circuit *const *circu
     if (err) throw Error(ARSO_ETIMEOUT, "persistent batch: a dependency wait gave up");
 }
 
-// Eq. (4) with E(N_e) = L p_e// Eq. (4) with E(N_e) = L p_e
+// Eq. (4) with E(N_e) = L p_e
 static double eq4(const double *P, uint64_t L, double pe) {
     const double E = (double)L * pe;
     return (P[1] + P[2] + P[3]) * E + P[0] * (1.0 - 3.0 * E);
@@ -1736,6 +1744,11 @@ arso_status arso_aggregate(const double *score, const uint8_t *pass_flags, uint6
         out[3] = std::sqrt(vp / N);
         out[4] = (double)n;
     });
+}
+
+arso_status arso_debug_stall_next_batch(void) {
+    g_stall_next_batch.store(true);
+    return ARSO_OK;
 }
 
 arso_status arso_run_batch(size_t count, arso_circuit *const *circuits, const arso_error_list *const *errors,

@@ -209,6 +209,7 @@ struct MixArgs {
     unsigned long long *counter;
     uint32_t *err;             // bit 0: a dependency wait gave up
     uint32_t wait_limit;       // polls per wait
+    uint32_t stall_extra;      // added to every wait's target: 0, except in the failure-path test
 };
 constexpr uint32_t MIX_SMALL_MAX = 32;  // trajectories per SMALL item
 void launch_mix(const MixArgs &a, double bytes, double flops, double smem_bytes, cudaStream_t st);

@@ -1049,10 +1049,12 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
     return v;
 }
 
-// thread 0: wait until *ctr >= need; false if the wait gave up or another CTA's did
-__device__ bool mix_wait(const uint32_t *ctr, uint32_t need, uint32_t limit, uint32_t *err) {
+// thread 0: wait until *ctr >= need + extra (extra is 0 except in the failure-path test);
+// false if the wait gave up or another CTA's did
+__device__ bool mix_wait(const uint32_t *ctr, uint32_t need, uint32_t extra, uint32_t limit, uint32_t *err) {
+    const uint64_t target = (uint64_t)need + extra;
     for (uint32_t it = 0;; ++it) {
-        if (ld_acquire_u32(ctr) >= need) return true;
+        if ((uint64_t)ld_acquire_u32(ctr) >= target) return true;
         if (it >= limit || ld_acquire_u32(err) != 0u) {
             atomicOr(err, 1u);
             return false;
@@ -1233,8 +1235,8 @@ __device__ __forceinline__ void mix_tile(const MixArgs &A, const MixStream &S, c
     float2 *sm = reinterpret_cast<float2 *>(smem_raw);
     if (threadIdx.x == 0) {
         const MixTraj &T = S.trajs[it.k];
-        *s_flag = mix_wait(S.slot_done + T.slot, T.base + (uint32_t)((int)it.j - T.start) * S.tiles, A.wait_limit,
-                           A.err);
+        *s_flag = mix_wait(S.slot_done + T.slot, T.base + (uint32_t)((int)it.j - T.start) * S.tiles,
+                           A.stall_extra, A.wait_limit, A.err);
     }
     __syncthreads();  // thread 0's acquire load, then the barrier, order the tile loads after it
     if (!*s_flag) return;

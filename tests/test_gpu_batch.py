@@ -151,3 +151,34 @@ def test_autotuned_schedule_against_oracle():
     psi_ref = statevector.simulate(circ)
     for t in [i for i in range(T) if lists[i]][:4]:
         assert abs(s[t] - criteria.score(circ.criterion, statevector.simulate(circ, lists[t]), psi_ref)) < 1e-5
+
+
+def test_persistent_batch_wait_that_runs_out_reports_timeout():
+    """The failure path of the persistent launch's bounded dependency waits: a
+    launch whose waits cannot be met gives up (no hang, no fault), the call
+    returns ETIMEOUT, and the next call on the same context gives the scores of
+    the circuits' own launches again."""
+    import time
+    from paper_2301_07264_gb300 import arso
+    mix = [W.qaoa_maxcut(12, 3), W.qft_basis(14, 9000), W.brickwork(15, 10, 6), W.grover(7, 3)]
+    p, T = 5e-3, 64
+    ccs, errs, crits, ref = [], [], [], []
+    for k, circ in enumerate(mix):
+        cc = arso.compile_circuit(circ.n, circ.gates)
+        e = arso.sample_errors(cc, p / 3, p / 3, p / 3, 9, 100 * k, T)
+        r = np.zeros(T)
+        arso.run_trajectories(cc, e, circ.criterion, r)
+        ccs.append(cc)
+        errs.append(e)
+        crits.append(circ.criterion)
+        ref.append(r)
+    got = [torch.full((T,), -1.0, dtype=torch.float64, device="cuda") for _ in mix]
+    arso.debug_stall_next_batch()
+    t0 = time.perf_counter()
+    with pytest.raises(arso.ArsoError) as e:
+        arso.run_batch(ccs, errs, crits, got)
+    assert e.value.status == arso.ETIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    arso.run_batch(ccs, errs, crits, got)
+    for k, circ in enumerate(mix):
+        assert np.max(np.abs(got[k].cpu().numpy() - ref[k])) < 1e-9, circ.family
