@@ -398,7 +398,8 @@ def run_ours(args):
         arso.profile_enable(True)
     cc = arso.compile_circuit(circ.n, circ.gates, tile_qubits=args.tile,
                               cache_bytes=int(args.cache_gb * (1 << 30)) if args.cache_gb else 0,
-                              flags=arso.OPT_NO_SUFFIX_REUSE if args.no_suffix else 0)
+                              flags=(arso.OPT_NO_SUFFIX_REUSE if args.no_suffix else 0) |
+                                    (arso.OPT_TENSOR_PHASES if args.tensor else 0))
     info = cc.info()
     half = args.traj_per_step // len(P_RATES)
     score = {p: torch.empty(half, dtype=torch.float64, device="cuda") for p in P_RATES}
@@ -579,6 +580,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="seconds of oracle work per CPU-baseline setting (1 core, all cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tensor", action="store_true",
+                    help="fused-unitary register phases on the tensor cores (ARSO_OPT_TENSOR_PHASES)")
     ap.add_argument("--no-suffix", action="store_true",
                     help="run every trajectory to the end instead of scoring after its last error")
     ap.add_argument("--workload", default="brickwork24", choices=["brickwork24", "qft4", "grover12", "mix256", "search", "exhaustive", "qv", "families"],

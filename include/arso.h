@@ -102,8 +102,18 @@ typedef struct {
  * simulates the 3L single-error trajectories instead (for comparisons). */
 /* arso_run_batch runs circuits with ARSO_OPT_NO_PERSISTENT on their own
  * launches instead of the batch's persistent launch (for comparisons). */
+/* ARSO_OPT_TENSOR_PHASES (streaming complex64 circuits, 12-14-qubit tiles): the
+ * phase planner forms register phases whose gates on the five register bits
+ * multiply to one 32 x 32 unitary U (the phase's other gates being diagonal),
+ * and the pass kernel applies U to the tile on the tensor cores (a 2^(t-5) x 64
+ * by 64 x 64 real contraction on FP16 operands: per entry an integer high part
+ * and a low part, under a power-of-two scale per row, the high products summed
+ * exactly and the rest in a second FP32 accumulator; about FP32 accuracy)
+ * instead of gate by gate. A phase holding one of the trajectory's Pauli errors, or with
+ * fewer than two non-diagonal gates, runs gate by gate. A wait for the tensor
+ * cores is bounded; one that gives up makes the call return ARSO_ETIMEOUT. */
 enum { ARSO_OPT_NO_SUFFIX_REUSE = 1, ARSO_OPT_NO_GRAPHS = 2, ARSO_OPT_NO_FAST_EXHAUSTIVE = 4,
-       ARSO_OPT_NO_PERSISTENT = 8 };
+       ARSO_OPT_NO_PERSISTENT = 8, ARSO_OPT_TENSOR_PHASES = 16 };
 
 typedef struct arso_circuit arso_circuit;
 typedef struct arso_error_list arso_error_list;
@@ -127,6 +137,8 @@ typedef struct {
     uint32_t tile_qubits;
     uint32_t precision;
     uint64_t checkpoint_every; /* resident: gates between cached prefix states */
+    uint32_t n_phases;      /* register phases (0 when the circuit has none) */
+    uint32_t tensor_phases; /* phases that run on the tensor cores (ARSO_OPT_TENSOR_PHASES) */
 } arso_circuit_info;
 arso_status arso_circuit_get_info(const arso_circuit *c, arso_circuit_info *out);
 
@@ -142,9 +154,10 @@ arso_status arso_plan_schedule(uint32_t n_qubits, const arso_gate *gates, size_t
                                uint32_t *perm, uint32_t *pass_begin, uint64_t *tile_mask);
 /* Host-only: the number of register-bit phases the compile step plans (each
  * phase boundary inside a pass is one shared-memory transpose of the tile);
- * 0 when the circuit does not use the register-blocked kernels. */
+ * 0 when the circuit does not use the register-blocked kernels. *n_tensor (may
+ * be NULL) receives how many of them run on the tensor cores. */
 arso_status arso_plan_phases(uint32_t n_qubits, const arso_gate *gates, size_t n_gates,
-                             const arso_compile_opts *opts, uint32_t *n_phases);
+                             const arso_compile_opts *opts, uint32_t *n_phases, uint32_t *n_tensor);
 
 /* Sample Pauli errors (Sec. IV-B.2): after every gate, each of its qubits
  * independently suffers X, Z or Y with probabilities p_x, p_z, p_y. Trajectory

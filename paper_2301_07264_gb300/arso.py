@@ -55,7 +55,8 @@ class CompileOpts(C.Structure):
 class CircuitInfo(C.Structure):
     _fields_ = [("n_qubits", C.c_uint32), ("G", C.c_uint64), ("k", C.c_uint64), ("m", C.c_uint64),
                 ("L", C.c_uint64), ("engine", C.c_uint32), ("n_passes", C.c_uint32),
-                ("tile_qubits", C.c_uint32), ("precision", C.c_uint32), ("checkpoint_every", C.c_uint64)]
+                ("tile_qubits", C.c_uint32), ("precision", C.c_uint32), ("checkpoint_every", C.c_uint64),
+                ("n_phases", C.c_uint32), ("tensor_phases", C.c_uint32)]
 
 
 class Criterion(C.Structure):
@@ -201,6 +202,7 @@ OPT_NO_SUFFIX_REUSE = 1
 OPT_NO_GRAPHS = 2
 OPT_NO_FAST_EXHAUSTIVE = 4
 OPT_NO_PERSISTENT = 8
+OPT_TENSOR_PHASES = 16
 
 
 def compile_circuit(n, gates, precision=C64, tile_qubits=0, low_qubits=0, max_batch=0, cache_bytes=0, flags=0):
@@ -539,14 +541,16 @@ def autotune(n, gates, crit, p, n_traj=64, seed=0, precision=C64, stream=None):
     return {"tile_qubits": best.tile_qubits, "low_qubits": best.low_qubits}, ms[: cnt.value]
 
 
-lib.arso_plan_phases.argtypes = [C.c_uint32, C.POINTER(Gate), C.c_size_t, C.POINTER(CompileOpts), C.POINTER(C.c_uint32)]
+lib.arso_plan_phases.argtypes = [C.c_uint32, C.POINTER(Gate), C.c_size_t, C.POINTER(CompileOpts), C.POINTER(C.c_uint32),
+                                 C.POINTER(C.c_uint32)]
 lib.arso_plan_phases.restype = C.c_int
 
 
-def plan_phases(n, gates, precision=C64, tile_qubits=0, low_qubits=0):
-    """Host-only: number of register-bit phases the compile step plans."""
+def plan_phases(n, gates, precision=C64, tile_qubits=0, low_qubits=0, flags=0, tensor=False):
+    """Host-only: number of register-bit phases the compile step plans (with
+    tensor=True, the pair (phases, phases on the tensor cores))."""
     arr, keep = _gates_array(gates)
-    opts = CompileOpts(precision, tile_qubits, low_qubits, 0, 0, 0)
-    out = C.c_uint32()
-    _check(lib.arso_plan_phases(n, arr, len(gates), C.byref(opts), C.byref(out)))
-    return out.value
+    opts = CompileOpts(precision, tile_qubits, low_qubits, 0, 0, flags)
+    out, nt = C.c_uint32(), C.c_uint32()
+    _check(lib.arso_plan_phases(n, arr, len(gates), C.byref(opts), C.byref(out), C.byref(nt)))
+    return (out.value, nt.value) if tensor else out.value

@@ -193,6 +193,7 @@ static void upload_circuit(arso_circuit *c) {
             o.aux = d.mat;
             const HostGate &h = c->gates[c->perm[pos]];
             o.pad[0] = reg_opcode(d.cls, c->rpos[pos] & 15u, c->rpos[pos] >> 4);
+            o.pad[1] = c->tensor ? (uint32_t)c->role[pos] : (uint32_t)TR_CORE;
             if (d.cls == GC_SU2) {
                 o.c0 = make_float2((float)h.m[0].real(), (float)h.m[0].imag());
                 o.c1 = make_float2((float)h.m[1].real(), (float)h.m[1].imag());
@@ -203,6 +204,16 @@ static void upload_circuit(arso_circuit *c) {
         }
         c->d_rops.ensure(ops.size() * sizeof(RegOp));
         ARSO_CUDA(cudaMemcpy(c->d_rops.ptr, ops.data(), ops.size() * sizeof(RegOp), cudaMemcpyHostToDevice));
+        if (c->tensor) {
+            c->d_ph_t.ensure(std::max<size_t>(c->ph_t.size(), 1) * 4);
+            if (!c->ph_t.empty())
+                ARSO_CUDA(cudaMemcpy(c->d_ph_t.ptr, c->ph_t.data(), c->ph_t.size() * 4, cudaMemcpyHostToDevice));
+            c->d_tmats.ensure(std::max<size_t>(c->tmats.size(), 8) * 2);
+            if (!c->tmats.empty())
+                ARSO_CUDA(cudaMemcpy(c->d_tmats.ptr, c->tmats.data(), c->tmats.size() * 2, cudaMemcpyHostToDevice));
+            c->d_terr.ensure(4);
+            ARSO_CUDA(cudaMemset(c->d_terr.ptr, 0, 4));
+        }
         c->d_phase_of_pos.ensure(std::max<size_t>(c->phase_of_pos.size(), 1) * 4);
         if (!c->phase_of_pos.empty())
             ARSO_CUDA(cudaMemcpy(c->d_phase_of_pos.ptr, c->phase_of_pos.data(), c->phase_of_pos.size() * 4,
@@ -247,11 +258,29 @@ static void run_pass(const arso_circuit *c, const PassArgs &a, bool last, uint32
         b.ph_gb = c->d_ph_gb.as<uint32_t>();
         b.ph_R = c->d_ph_R.as<uint32_t>();
         b.rops = c->d_rops.as<RegOp>();
+        if (c->tensor) {
+            b.ph_t = c->d_ph_t.as<uint32_t>();
+            b.tmats = c->d_tmats.ptr;
+            b.terr = c->d_terr.as<uint32_t>();
+        }
         const Pass &ps = c->passes[a.pass];
         launch_pass_rb(b, last, slots, bytes, st, ps.flops_per_amp * std::ldexp(sweeps, (int)c->n),
                        (double)(ps.remaps + ps.end_remap) * 16.0 * std::ldexp(sweeps, (int)c->n));
     } else {
         launch_pass(a, last, c->precision, slots, bytes, st);
+    }
+}
+
+// Synchronises; ARSO_ETIMEOUT when a tensor-phase wait of the circuit's pass
+// launches gave up since the last check (the word is cleared).
+static void check_tensor(const arso_circuit *c, cudaStream_t st) {
+    uint32_t err = 0;
+    if (c->tensor) copy_d2h(&err, c->d_terr.ptr, 4, st);
+    ARSO_CUDA(cudaStreamSynchronize(st));
+    if (err) {
+        ARSO_CUDA(cudaMemsetAsync(c->d_terr.ptr, 0, 4, st));
+        ARSO_CUDA(cudaStreamSynchronize(st));
+        throw Error(ARSO_ETIMEOUT, "tensor phase: a wait for the tensor cores gave up");
     }
 }
 
@@ -644,7 +673,7 @@ static void run_all(arso_circuit *c, const arso_error_list *e, const DevCrit &dc
     for (uint64_t i = 0; i < e->n_traj; ++i)
         if (first[i] != NO_EVENT) ids.push_back(i), fp.push_back(first[i]), lp.push_back(last[i]);
     run_streaming(c, e, ids, fp, lp, dc.d, d_score, d_pass, nullptr, st);
-    ARSO_CUDA(cudaStreamSynchronize(st));
+    check_tensor(c, st);
 }
 
 // ------------------------------------------------------------ sampling -----
@@ -1601,12 +1630,16 @@ arso_status arso_compile_circuit(uint32_t n_qubits, const arso_gate *gates, size
 void arso_circuit_free(arso_circuit *c) { delete c; }
 
 arso_status arso_plan_phases(uint32_t n_qubits, const arso_gate *gates, size_t n_gates,
-                             const arso_compile_opts *opts, uint32_t *n_phases) {
+                             const arso_compile_opts *opts, uint32_t *n_phases, uint32_t *n_tensor) {
     return guard([&] {
         ARSO_REQUIRE(n_phases != nullptr, "n_phases is NULL");
         arso_circuit c;
         build_circuit(&c, n_qubits, gates, n_gates, opts);
         *n_phases = c.reg_blocked ? (uint32_t)c.ph_R.size() : 0u;
+        if (n_tensor) {
+            *n_tensor = 0;
+            for (uint32_t t : c.ph_t) *n_tensor += t != NO_TENSOR;
+        }
     });
 }
 
@@ -1647,6 +1680,9 @@ arso_status arso_circuit_get_info(const arso_circuit *c, arso_circuit_info *out)
         out->tile_qubits = c->tile_qubits;
         out->precision = (uint32_t)c->precision;
         out->checkpoint_every = c->ckpt_every;
+        out->n_phases = c->reg_blocked ? (uint32_t)c->ph_R.size() : 0u;
+        out->tensor_phases = 0;
+        for (uint32_t t : c->ph_t) out->tensor_phases += t != NO_TENSOR;
     });
 }
 

@@ -178,27 +178,45 @@ struct PassScheduler {
     std::vector<uint32_t> indeg;
     std::set<uint32_t> ready;  // unscheduled gates whose predecessors are all scheduled
     std::vector<uint32_t> order;
+    // Tensor-phase rules: a gate runs under R when all its qubits are in R (a
+    // diagonal one always, another one while none of its qubits is frozen) or
+    // when it is diagonal. A diagonal gate with qubits in and out of R freezes
+    // its qubits in R that a non-diagonal gate of the phase already acted on.
+    bool tensor = false;
+    std::vector<uint8_t> diag;    // diagonal in the computational basis
+    std::vector<uint32_t> qmask;  // tile-local qubits of the gate
 
     static bool in(const std::vector<uint32_t> &R, uint32_t q) {
         return q == NO_NEED || std::find(R.begin(), R.end(), q) != R.end();
     }
-    // Run every ready gate whose need is in R, repeatedly. With `trial` the
+    bool runs(uint32_t g, const std::vector<uint32_t> &R, uint32_t Rm, uint32_t frozen) const {
+        if (!tensor) return in(R, need[g]);
+        if ((qmask[g] & ~Rm) == 0) return diag[g] || !(qmask[g] & frozen);
+        return diag[g] != 0;
+    }
+    // Run every ready gate that runs under R, repeatedly. With `trial` the
     // state is restored afterwards and only the weight is returned.
     double closure(const std::vector<uint32_t> &R, bool trial) {
         std::vector<std::pair<uint32_t, uint32_t>> undo;  // (gate, old indeg)
         std::set<uint32_t> rd = ready;
         double w = 0.0;
+        uint32_t Rm = 0, started = 0, frozen = 0;
+        for (uint32_t q : R) Rm |= 1u << q;
         bool progress = true;
         while (progress) {
             progress = false;
             for (auto it = rd.begin(); it != rd.end();) {
                 const uint32_t g = *it;
-                if (!in(R, need[g])) {
+                if (!runs(g, R, Rm, frozen)) {
                     ++it;
                     continue;
                 }
                 it = rd.erase(it);
                 w += weight[g];
+                if (tensor) {
+                    if ((qmask[g] & ~Rm) == 0) started |= diag[g] ? 0u : qmask[g];
+                    else frozen |= qmask[g] & Rm & started;
+                }
                 if (!trial) order.push_back(g);
                 for (uint32_t s : succ[g]) {
                     if (trial) undo.emplace_back(s, indeg[s]);
@@ -230,12 +248,131 @@ static double gate_flops(const HostGate &h) {
     }
 }
 
+static bool is_diagonal(const HostGate &h) {
+    switch (h.cls) {
+        case GC_NOP: case GC_DIAG1: case GC_DIAG2: case GC_OMEGA: case GC_CZ: return true;
+        default: return false;
+    }
+}
+
+// U <- G U for gate h on register positions p0 (and p1) of the 32-dimensional
+// register index (two-qubit matrices index bit(q0) + 2 bit(q1), row-major)
+static void left_apply(std::vector<std::complex<double>> &U, const HostGate &h, uint32_t p0, uint32_t p1) {
+    const uint32_t b0 = 1u << p0, b1 = 1u << p1;
+    for (uint32_t col = 0; col < 32; ++col) {
+        auto at = [&](uint32_t row) -> std::complex<double> & { return U[row * 32 + col]; };
+        for (uint32_t l = 0; l < 32; ++l) {
+            if (h.arity == 1) {
+                if (l & b0) continue;
+                const std::complex<double> x0 = at(l), x1 = at(l | b0);
+                at(l) = h.m[0] * x0 + h.m[1] * x1;
+                at(l | b0) = h.m[2] * x0 + h.m[3] * x1;
+            } else {
+                if (l & (b0 | b1)) continue;
+                const uint32_t ix[4] = {l, l | b0, l | b1, l | b0 | b1};
+                std::complex<double> x[4], y[4];
+                for (int k = 0; k < 4; ++k) x[k] = at(ix[k]);
+                for (int r = 0; r < 4; ++r) {
+                    y[r] = 0;
+                    for (int k = 0; k < 4; ++k) y[r] += h.m[4 * r + k] * x[k];
+                }
+                for (int k = 0; k < 4; ++k) at(ix[k]) = y[k];
+            }
+        }
+    }
+}
+
+// Nearest binary16 value of x (ties to even; |x| < 65504), as bits; *v gets its value.
+static uint16_t f16_bits(double x, double *v) {
+    const double ax = std::fabs(x);
+    const uint16_t sign = std::signbit(x) ? 0x8000u : 0u;
+    if (ax == 0.0) {
+        *v = 0.0;
+        return sign;
+    }
+    int e;
+    std::frexp(ax, &e);                      // ax in [2^(e-1), 2^e)
+    const int E = std::max(e - 1, -14);      // below 2^-14 the spacing stays 2^-24 (subnormals)
+    const double q = std::ldexp(1.0, E - 10);
+    const double r = std::nearbyint(ax / q) * q;  // round to nearest, ties to even
+    *v = sign ? -r : r;
+    if (r < std::ldexp(1.0, -14)) return (uint16_t)(sign | (uint16_t)std::ldexp(r, 24));
+    int er;
+    const double fr = std::frexp(r, &er);    // r = fr 2^er, fr in [0.5, 1)
+    const uint32_t mant = (uint32_t)std::ldexp(fr, 11) - 1024u;
+    return (uint16_t)(sign | (uint16_t)((er - 1 + 15) << 10) | (uint16_t)mant);
+}
+
+// Roles of the records of phase ph (positions [gb, ge), tile-local qubits lq0/lq1
+// indexed from pass_gb) and, when the phase qualifies, its operand images: the
+// real 64 x 64 form of U in packed-register order on both sides (index 4p + 2c +
+// lane for register 2p + lane, c = 0 real part, 1 imaginary part), B[n][k] with
+// D[row][n] = sum_k A[row][k] B[n][k], scaled by 2^8 and split into the integer
+// hi = rint(2^8 B) (|hi| <= 256, exact in fp16) and lo = fp16(2^8 B - hi).
+static void tensor_phase(arso_circuit *c, uint32_t ph, uint32_t gb, uint32_t ge, uint32_t pass_gb,
+                         const std::vector<uint32_t> &lq0, const std::vector<uint32_t> &lq1) {
+    uint32_t R[REG_BITS], Rm = 0;
+    int rp[32];
+    std::fill(rp, rp + 32, -1);
+    for (int b = 0; b < REG_BITS; ++b) {
+        R[b] = (c->ph_R[ph] >> (5 * b)) & 31u;
+        Rm |= 1u << R[b];
+        rp[R[b]] = b;
+    }
+    std::vector<std::complex<double>> U(32 * 32, 0.0);
+    for (int i = 0; i < 32; ++i) U[i * 33] = 1.0;
+    uint32_t started = 0, frozen = 0;
+    int dense = 0;
+    bool ok = true;
+    for (uint32_t pos = gb; pos < ge; ++pos) {
+        const HostGate &h = c->gates[c->perm[pos]];
+        const uint32_t a = lq0[pos - pass_gb], b = lq1[pos - pass_gb];
+        const uint32_t qm = (1u << a) | (1u << b);
+        const bool dg = is_diagonal(h);
+        if ((qm & ~Rm) == 0) {
+            c->role[pos] = TR_CORE;
+            if (!dg) {
+                ok &= (qm & frozen) == 0;
+                started |= qm;
+                ++dense;
+            }
+            left_apply(U, h, (uint32_t)rp[a], (uint32_t)rp[b]);
+        } else {
+            ok &= dg;
+            const bool after = (qm & Rm & started) != 0;
+            c->role[pos] = after ? TR_AFTER : TR_BEFORE;
+            frozen |= qm & Rm & started;
+        }
+    }
+    if (!ok || dense < TENSOR_MIN_DENSE) return;
+    c->ph_t[ph] = (uint32_t)(c->tmats.size() / TENSOR_IMAGE_HALVES);
+    const size_t base = c->tmats.size();
+    c->tmats.resize(base + TENSOR_IMAGE_HALVES);
+    uint16_t *hi = c->tmats.data() + base, *lo = hi + TENSOR_IMAGE_HALVES / 2;
+    for (uint32_t n = 0; n < 64; ++n)
+        for (uint32_t k = 0; k < 64; ++k) {
+            const uint32_t j = 2 * (n >> 2) + (n & 1u), l = 2 * (k >> 2) + (k & 1u);
+            const uint32_t co = (n >> 1) & 1u, ci = (k >> 1) & 1u;
+            const std::complex<double> u = U[j * 32 + l];
+            const double val = co == 0 ? (ci == 0 ? u.real() : -u.imag()) : (ci == 0 ? u.imag() : u.real());
+            double vh, vl;
+            const uint32_t off = ((n >> 3) * 1024 + (k >> 3) * 128 + (n & 7u) * 16 + (k & 7u) * 2) / 2;
+            const double x = std::ldexp(val, 8), xi = std::nearbyint(x);
+            hi[off] = f16_bits(xi, &vh);
+            lo[off] = f16_bits(x - xi, &vl);
+        }
+}
+
 static void plan_phases(arso_circuit *c) {
     const uint32_t t = c->tile_qubits;
     c->reg_blocked = c->precision == ARSO_C64 && t >= (uint32_t)RB_MIN_TILE;
     c->ph_gb.clear();
     c->ph_R.clear();
     c->rpos.assign(c->perm.size(), 0xFF);
+    c->tensor = c->reg_blocked && c->engine == 1 && t >= 12 && (c->flags & ARSO_OPT_TENSOR_PHASES);
+    c->ph_t.clear();
+    c->tmats.clear();
+    c->role.assign(c->perm.size(), (uint8_t)TR_CORE);
     if (!c->reg_blocked) return;
     const std::vector<uint32_t> load_map = {0, t - 4, t - 3, t - 2, t - 1};
     for (Pass &ps : c->passes) {
@@ -244,6 +381,9 @@ static void plan_phases(arso_circuit *c) {
         const uint32_t G = ps.ge - ps.gb;
         PassScheduler S;
         S.G = G;
+        S.tensor = c->tensor;
+        S.diag.resize(G);
+        S.qmask.resize(G);
         S.need.resize(G);
         S.weight.resize(G);
         S.succ.assign(G, {});
@@ -254,6 +394,8 @@ static void plan_phases(arso_circuit *c) {
             const uint32_t a = (uint32_t)local[h.q0], b = (uint32_t)local[h.q1];
             S.need[i] = need_of(h, a, b);
             S.weight[i] = gate_weight(h);
+            S.diag[i] = is_diagonal(h) ? 1 : 0;
+            S.qmask[i] = (1u << a) | (1u << b);
             const int pa = last[a], pb = h.arity == 2 ? last[b] : -1;
             if (pa >= 0) S.succ[pa].push_back(i), ++S.indeg[i];
             if (pb >= 0 && pb != pa) S.succ[pb].push_back(i), ++S.indeg[i];
@@ -284,7 +426,8 @@ static void plan_phases(arso_circuit *c) {
                         }
             R = best;
             std::sort(R.begin(), R.end());
-            ARSO_REQUIRE(R != cur, "internal: the phase planner made no progress");
+            // tensor rules: a new phase under the same set starts with nothing frozen
+            ARSO_REQUIRE(best_w > 0.0 && (R != cur || S.tensor), "internal: the phase planner made no progress");
             cur = R;
         }
         if (phases.empty()) phases.emplace_back(0u, load_map);
@@ -321,6 +464,11 @@ static void plan_phases(arso_circuit *c) {
                 }
                 c->rpos[pos] = (uint8_t)(p0 | (p1 << 4));
             }
+        }
+        if (c->tensor) {
+            c->ph_t.resize(ps.pe, NO_TENSOR);
+            for (uint32_t ph = ps.pb; ph < ps.pe; ++ph)
+                tensor_phase(c, ph, c->ph_gb[ph], ph + 1 < ps.pe ? c->ph_gb[ph + 1] : ps.ge, ps.gb, lq0, lq1);
         }
     }
     for (Pass &ps : c->passes) {

@@ -117,6 +117,26 @@ enum RegOpCode : uint32_t {
     OP_NOP = 82,
 };
 
+// Tensor-core phases (streaming complex64 circuits compiled with
+// ARSO_OPT_TENSOR_PHASES, tiles of 2^12..2^14 amplitudes). A phase whose gates on
+// its register bits multiply to one 32 x 32 unitary U, the phase's other gates
+// being diagonal, can run as a contraction on the tensor cores: the tile is a
+// matrix of 2^(t-5) rows (threads) by 32 complex columns (register index), and
+// U acts on every row. Each record of such a phase has a role (RegOp::pad[1]):
+// a core gate (inside U), or a diagonal gate run in FP32 before or after U. A
+// diagonal gate touching a register bit and another bit runs after U when a
+// non-diagonal core gate of the phase acted on that register bit before it,
+// otherwise before U; the planner admits no non-diagonal gate on that bit after
+// it in the phase, so both orders equal the records' order.
+enum TensorRole : uint32_t { TR_CORE = 0, TR_BEFORE = 1, TR_AFTER = 2 };
+constexpr uint32_t NO_TENSOR = 0xFFFFFFFFu;
+// a phase runs on the tensor cores when its unitary holds at least this many
+// non-diagonal gates (below that the FP32 gate code is cheaper)
+constexpr int TENSOR_MIN_DENSE = 2;
+// fp16 operand images of one tensor phase: hi and lo terms of the real 64 x 64
+// form of U, each 8 KiB in the tensor core's K-major shared-memory layout
+constexpr uint32_t TENSOR_IMAGE_HALVES = 2 * 64 * 64;
+
 // An event in engine order: (gate position << 3) | (slot << 2) | pauli code.
 __host__ __device__ inline uint32_t ev_pos(uint32_t e) { return e >> 3; }
 __host__ __device__ inline uint32_t ev_slot(uint32_t e) { return (e >> 2) & 1u; }
@@ -199,6 +219,13 @@ struct arso_circuit {
     std::vector<double> flops_prefix;       // engine position k -> algorithmic FP32 flops per amplitude of
                                             // gates [0, k) (the tracing counts of arso.h)
     std::vector<uint32_t> chg_prefix;       // phase k -> phases 1 <= p < k whose register set differs from p-1's
+    // tensor-core phases (ARSO_OPT_TENSOR_PHASES on a streaming complex64 circuit)
+    bool tensor = false;
+    std::vector<uint32_t> ph_t;             // phase -> index of its operand images, or NO_TENSOR
+    std::vector<uint16_t> tmats;            // TENSOR_IMAGE_HALVES fp16 values per tensor phase
+    std::vector<uint8_t> role;              // engine position -> TensorRole within its phase
+    arso::DeviceBuffer d_tmats, d_ph_t;
+    arso::DeviceBuffer d_terr;              // uint32: a tensor-phase wait gave up
     // device tables
     arso::DeviceBuffer d_gates;             // DGate[G] in engine order
     arso::DeviceBuffer d_mats;              // complex<float> or complex<double> pool

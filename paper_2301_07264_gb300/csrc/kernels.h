@@ -88,6 +88,10 @@ struct PassArgs {
     const uint32_t *ph_gb;       // phase -> first engine position (with sentinel)
     const uint32_t *ph_R;        // phase -> packed register bits
     const RegOp *rops;           // engine position -> register-kernel gate record
+    // tensor-core phases (NULL: every phase runs gate by gate)
+    const uint32_t *ph_t;        // phase -> operand-image index or NO_TENSOR
+    const void *tmats;           // TENSOR_IMAGE_HALVES fp16 values per image
+    uint32_t *terr;              // set when a wait for the tensor cores gave up
 };
 
 void launch_pass_rb(const PassArgs &a, bool last, uint32_t slots, double bytes, cudaStream_t st, double flops = 0.0,

@@ -20,10 +20,13 @@
 //    i tracked as a power gp and applied at the store.
 // Global loads and stores are 16-byte vector accesses in the mapping
 // R = {0, t-4, t-3, t-2, t-1}, whose thread bits 1..t-5 are contiguous.
+#include <cuda_fp16.h>
+
 #include <algorithm>
 
 #include "prof.h"
 #include "sim_common.cuh"
+#include "umma.cuh"
 
 namespace arso {
 
@@ -610,14 +613,20 @@ __device__ __forceinline__ void apply_op(Amps &a, TileCtx &c, const RegOp &op, c
 // Gates [g, ge) of one phase with the Pauli events that fall inside them;
 // ops[0] is the record of gate g0 (the phase's first gate). The inner loop
 // runs up to and including the next event's gate without touching the event
-// state, which stays out of the hot registers.
+// state, which stays out of the hot registers. Records whose tensor role has
+// its bit set in `skip` are passed over (tensor phases, which hold no event).
 __device__ __forceinline__ void run_gates(Amps &v, TileCtx &c, uint32_t g, uint32_t ge, const RegOp *ops, uint32_t g0,
                                           const float2 *__restrict__ mats, float2 *sm, float2 *ubuf, int t,
-                                          const uint32_t *&ev, const uint32_t *ev_end, uint32_t &next) {
+                                          const uint32_t *&ev, const uint32_t *ev_end, uint32_t &next,
+                                          uint32_t skip = 0u) {
     while (g < ge) {
         const uint32_t np = next == NO_EVENT ? ge : ev_pos(next);
         const uint32_t stop = np < ge ? np + 1 : ge;
-        for (; g < stop; ++g) apply_op(v, c, ops[g - g0], mats, sm, ubuf, t);
+        for (; g < stop; ++g) {
+            const RegOp &op = ops[g - g0];
+            if ((skip >> op.pad[1]) & 1u) continue;
+            apply_op(v, c, op, mats, sm, ubuf, t);
+        }
         if (np >= ge) break;
         const uint32_t w0 = ops[np - g0].w0;
         while (next != NO_EVENT && ev_pos(next) == np) {
@@ -644,6 +653,131 @@ __device__ __forceinline__ void stage_ops(RegOp *dst, const RegOp *src, uint32_t
 __device__ __forceinline__ void stage_wait() {
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
+}
+
+// ------------------------------------------------------- tensor phases ---
+// A phase with a fused unitary U (see the tensor-phase notes of internal.h) as
+// one contraction on the tensor cores. The tile is a matrix of 2^(t-5) rows
+// (row = thread) by 64 reals (the thread's 32 amplitudes in packed-register
+// order: for packed register p, Re a_2p, Re a_2p+1, Im a_2p, Im a_2p+1), and
+// D = A B^T with B the real 64 x 64 form of U in the same order on both sides.
+// FP32 accuracy from FP16 operands, with no bias from the tensor core's
+// accumulation (which is not rounded to nearest): each row is scaled by a power
+// of two so that its entries stay below 2^9 and split into the integer
+// hi = rint(x) and lo = fp16(x - hi) (|lo| <= 1/2); B comes from the host scaled
+// by 2^8 and split the same way (|hi| <= 256). The hi x hi products are integers
+// below 2^17 and their sums below 2^23, so their accumulator D0 is exact; the
+// other three products (hi lo, lo hi, lo lo) go to a second accumulator D1 about
+// 2^-9 of D0's size, whose rounding is negligible; D0 + D1 is formed in
+// registers. A (both terms) fills the tile's shared-memory buffer exactly; rows
+// are grouped in blocks of 128 (MMAs of M = 128, N = 64), each block with its
+// two accumulators in 128 tensor-memory columns.
+constexpr uint32_t TP_ROWS = 128;
+constexpr uint32_t TP_TERM_BYTES = TP_ROWS * 64 * 2;          // one term of one row block: 16 KiB
+constexpr uint32_t TP_IMAGE_BYTES = TENSOR_IMAGE_HALVES * 2;  // B hi and lo: 16 KiB
+constexpr uint32_t TP_IDESC = idesc_f16_f32(128, 64);
+
+__device__ __forceinline__ uint32_t h2_bits(float a, float b) {
+    const __half2 h = __floats2half2_rn(a, b);  // a in the low half (the lower K index)
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+__device__ __forceinline__ float2 h2_value(uint32_t u) {
+    const __half2 h = *reinterpret_cast<const __half2 *>(&u);
+    return __half22float2(h);
+}
+
+// cp.async copies of one phase's B images (16 KiB) into shared memory, in the
+// caller's commit group
+__device__ __forceinline__ void stage_image(unsigned char *dst, const unsigned char *src, uint32_t tid, uint32_t nthr) {
+    const uint32_t d = smem_u32(dst);
+    for (uint32_t i = tid; i < TP_IMAGE_BYTES / 16; i += nthr)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d + 16 * i), "l"(src + 16 * i) : "memory");
+}
+
+// v <- U v for every row of the tile. Each block of 128 rows (four warps) is an
+// independent group: it writes its rows of A, syncs on its own named barrier,
+// and its first thread issues the block's MMAs and commits them to the block's
+// mbarrier, which the group waits on before reading D back. The caller has
+// synced the CTA after its last read of the tile buffer `abuf`; `img` holds
+// this phase's staged B images (their cp.async copies waited for and synced).
+// Returns false when the wait for the tensor cores gave up (v then holds no
+// valid state).
+__device__ __forceinline__ bool tensor_apply(Amps &v, unsigned char *abuf, const unsigned char *img, uint32_t nblk,
+                                             uint32_t tmem, uint64_t *bars, uint32_t &parity) {
+    const uint32_t tid = threadIdx.x, blk = tid >> 7, r = tid & (TP_ROWS - 1u);
+    // row scale 2^k: sum of squares in [2^E, 2^(E+1)) bounds every entry below 2^ceil((E+1)/2)
+    float2 s2 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int p = 0; p < 16; ++p) {
+        s2 = fma2(v.re[p], v.re[p], s2);
+        s2 = fma2(v.im[p], v.im[p], s2);
+    }
+    const int E = (int)((__float_as_uint(s2.x + s2.y) >> 23) & 255u) - 127;
+    const int k = min(max(9 - ((E + 2) >> 1), -100), 100);
+    const float2 sc = bc2(__uint_as_float((uint32_t)(127 + k) << 23));
+    const float2 inv = bc2(__uint_as_float((uint32_t)(127 - k - 8) << 23));  // undoes the row and B scales
+    {
+        unsigned char *row_hi = abuf + blk * TP_TERM_BYTES + (r >> 3) * 1024u + (r & 7u) * 16u;
+        unsigned char *row_lo = row_hi + nblk * TP_TERM_BYTES;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            uint32_t hi[4], lo[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int p = 2 * u + (h >> 1);
+                const float2 x = mul2(h & 1 ? v.im[p] : v.re[p], sc);
+                const float2 rx = make_float2(rintf(x.x), rintf(x.y));
+                hi[h] = h2_bits(rx.x, rx.y);
+                lo[h] = h2_bits(x.x - rx.x, x.y - rx.y);
+            }
+            *reinterpret_cast<uint4 *>(row_hi + u * 128) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4 *>(row_lo + u * 128) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        }
+    }
+    fence_proxy_async_smem();  // A (and the staged B) visible to the tensor core
+    tc_fence_before();         // the previous phase's tensor-memory loads precede the next MMA
+    asm volatile("bar.sync %0, %1;\n" ::"r"(1u + blk), "r"(TP_ROWS) : "memory");
+    if (r == 0) {
+        tc_fence_after();
+        // descriptors of K step 0; a K step of 16 advances every operand by 256 bytes (16 in
+        // the descriptor's address field, which has room: shared addresses stay below 256 KiB)
+        const uint32_t ah = smem_u32(abuf) + blk * TP_TERM_BYTES, b0 = smem_u32(img);
+        const uint64_t dah = smem_desc_kmajor(ah, 128, 1024), dal = smem_desc_kmajor(ah + nblk * TP_TERM_BYTES, 128, 1024);
+        const uint64_t dbh = smem_desc_kmajor(b0, 128, 1024), dbl = smem_desc_kmajor(b0 + TP_IMAGE_BYTES / 2, 128, 1024);
+        const uint32_t d0 = tmem + blk * 128, d1 = d0 + 64;
+#pragma unroll
+        for (uint32_t s = 0; s < 4; ++s) {
+            const uint64_t o = 16u * s;
+            umma_bf16(d0, dah + o, dbh + o, TP_IDESC, s);
+            umma_bf16(d1, dah + o, dbl + o, TP_IDESC, s);
+            umma_bf16(d1, dal + o, dbh + o, TP_IDESC, 1);
+            umma_bf16(d1, dal + o, dbl + o, TP_IDESC, 1);
+        }
+        umma_commit(bars + blk);
+    }
+    bool ok = mbar_wait_bounded(bars + blk, parity);
+    if (!ok) (void)mbar_wait_bounded(bars + blk, parity);  // give a slow contraction one more bounded wait
+    parity ^= 1u;
+    tc_fence_after();
+    // this thread's row: tensor-memory lane 32 (warp mod 4) + lane = tid mod 128, block tid / 128
+    const uint32_t taddr = tmem + ((((tid >> 5) & 3u) * 32u) << 16) + blk * 128u;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint32_t e[32], f[32];
+        tmem_ld32_nowait(taddr + 32 * h, e);
+        tmem_ld32_nowait(taddr + 64 + 32 * h, f);
+        tmem_ld_wait();
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float2 er = make_float2(__uint_as_float(e[4 * i]), __uint_as_float(e[4 * i + 1]));
+            const float2 ei = make_float2(__uint_as_float(e[4 * i + 2]), __uint_as_float(e[4 * i + 3]));
+            const float2 fr = make_float2(__uint_as_float(f[4 * i]), __uint_as_float(f[4 * i + 1]));
+            const float2 fi = make_float2(__uint_as_float(f[4 * i + 2]), __uint_as_float(f[4 * i + 3]));
+            v.re[8 * h + i] = mul2(add2(er, fr), inv);
+            v.im[8 * h + i] = mul2(add2(ei, fi), inv);
+        }
+    }
+    return ok;
 }
 
 // Criterion partial of one thread's 32 amplitudes (true index of register ri:
@@ -693,7 +827,9 @@ __device__ __forceinline__ uint64_t tile_base(uint64_t rest_mask, uint64_t tile)
 // The phase loop holds the 64 amplitude registers; everything needed only
 // before or after it (addresses, slot data) is recomputed there instead of
 // being kept live.
-template <bool LAST>
+// TENSOR: the launch has tensor phases (a separate instantiation, so that the
+// gate-by-gate kernel's code is not shaped by the contraction path).
+template <bool LAST, bool TENSOR>
 __global__ void __launch_bounds__(512, 1) pass_rb_kernel(PassArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *sm = reinterpret_cast<float2 *>(smem_raw);
@@ -751,18 +887,75 @@ __global__ void __launch_bounds__(512, 1) pass_rb_kernel(PassArgs a) {
 
     uint32_t next = ev < ev_end ? *ev : NO_EVENT;
     const float2 *mats = static_cast<const float2 *>(a.mats);
-    if (a.pb < a.pe)
+    // tensor phases: tensor memory for D0 and D1 (128 columns per block of 128 rows), one mbarrier
+    // for the contractions' completion, and two 16 KiB buffers for the staged B images
+    __shared__ uint64_t s_tbar[4];  // one per block of 128 rows
+    __shared__ uint32_t s_tmem;
+    constexpr bool tensor = TENSOR;
+    const uint32_t nblk = blockDim.x / TP_ROWS;
+    unsigned char *img = smem_raw + ((size_t)1 << t) * sizeof(float2);
+    const unsigned char *tmats = static_cast<const unsigned char *>(a.tmats);
+    uint32_t tmem = 0, tpar = 0;
+    if (tensor) {
+        if (threadIdx.x < 32) tmem_alloc(&s_tmem, nblk * 128u);
+        if (threadIdx.x < nblk) {
+            mbar_init(&s_tbar[threadIdx.x], 1);
+            fence_mbar_init();
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        tmem = s_tmem;
+    }
+    if (a.pb < a.pe) {
+        if (tensor && a.ph_t[a.pb] != NO_TENSOR)
+            stage_image(img, tmats + (size_t)a.ph_t[a.pb] * TP_IMAGE_BYTES, threadIdx.x, blockDim.x);
         stage_ops(s_ops[0], a.rops + a.ph_gb[a.pb], a.ph_gb[a.pb + 1] - a.ph_gb[a.pb], threadIdx.x, blockDim.x);
+    }
     for (uint32_t ph = a.pb; ph < a.pe; ++ph) {
         const uint32_t buf = (ph - a.pb) & 1u;
         stage_wait();
-        if (ph + 1 < a.pe)
+        if (ph + 1 < a.pe) {
+            if (tensor && a.ph_t[ph + 1] != NO_TENSOR)
+                stage_image(img + (buf ^ 1u) * TP_IMAGE_BYTES, tmats + (size_t)a.ph_t[ph + 1] * TP_IMAGE_BYTES,
+                            threadIdx.x, blockDim.x);
             stage_ops(s_ops[buf ^ 1u], a.rops + a.ph_gb[ph + 1], a.ph_gb[ph + 2] - a.ph_gb[ph + 1], threadIdx.x,
                       blockDim.x);
+        }
         const uint32_t R = a.ph_R[ph];
         if (R != c.R) remap<true>(v, sm, c, R, t);
-        const uint32_t g0 = a.ph_gb[ph];
-        run_gates(v, c, g0, a.ph_gb[ph + 1], s_ops[buf], g0, mats, sm, ubuf, t, ev, ev_end, next);
+        const uint32_t g0 = a.ph_gb[ph], ge = a.ph_gb[ph + 1];
+        if constexpr (TENSOR) {
+            // the contraction applies U to the true amplitudes: no event of this trajectory in
+            // the phase and no mask bit on a register bit (the CTA takes the same branch)
+            uint32_t rm = 0;
+#pragma unroll
+            for (int b = 0; b < REG_BITS; ++b) rm |= 1u << rbit(R, b);
+            const bool tp =
+                a.ph_t[ph] != NO_TENSOR && (next == NO_EVENT || ev_pos(next) >= ge) && (c.m & rm) == 0u;
+            const int rounds = tp ? 2 : 1;
+#pragma unroll 1
+            for (int rd = 0; rd < rounds; ++rd) {
+                if (rd == 1) {
+                    __syncthreads();  // every thread's reads of the tile buffer are done
+                    if (!tensor_apply(v, smem_raw, img + buf * TP_IMAGE_BYTES, nblk, tmem, s_tbar, tpar))
+                        atomicOr(a.terr, 1u);
+                }
+                const uint32_t skip =
+                    tp ? (rd == 0 ? (1u << TR_CORE) | (1u << TR_AFTER) : (1u << TR_CORE) | (1u << TR_BEFORE)) : 0u;
+                run_gates(v, c, g0, ge, s_ops[buf], g0, mats, sm, ubuf, t, ev, ev_end, next, skip);
+            }
+        } else {
+            run_gates(v, c, g0, ge, s_ops[buf], g0, mats, sm, ubuf, t, ev, ev_end, next);
+        }
+    }
+    if (tensor) {
+        tc_fence_before();
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            tc_fence_after();
+            tmem_free(tmem, nblk * 128u);
+        }
     }
     apply_global_phase(v, c);  // global phase i^gp
     const uint64_t base = tile_base(a.rest_mask, blockIdx.x);
@@ -1420,9 +1613,11 @@ void launch_mix(const MixArgs &a, double bytes, double flops, double smem_bytes,
 void prepare_pass_rb() {
     static bool done = false;
     if (done) return;
-    const int smem = (1 << MAX_TILE_QUBITS) * (int)sizeof(float2);
-    ARSO_CUDA(cudaFuncSetAttribute(pass_rb_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    ARSO_CUDA(cudaFuncSetAttribute(pass_rb_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const int smem = (1 << MAX_TILE_QUBITS) * (int)sizeof(float2) + 2 * (int)TP_IMAGE_BYTES;
+    ARSO_CUDA(cudaFuncSetAttribute(pass_rb_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    ARSO_CUDA(cudaFuncSetAttribute(pass_rb_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    ARSO_CUDA(cudaFuncSetAttribute(pass_rb_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    ARSO_CUDA(cudaFuncSetAttribute(pass_rb_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     done = true;
 }
 
@@ -1432,10 +1627,16 @@ void launch_pass_rb(const PassArgs &a, bool last, uint32_t slots, double bytes, 
     prepare_pass_rb();
     const uint32_t tiles = 1u << (a.n - a.t);
     const int nt = 1 << (a.t - REG_BITS);
-    const size_t smem = (size_t(1) << a.t) * sizeof(float2);
+    const size_t smem = (size_t(1) << a.t) * sizeof(float2) + (a.ph_t ? 2 * TP_IMAGE_BYTES : 0);
+    if (a.ph_t) ARSO_REQUIRE(a.t >= 12 && a.t <= MAX_TILE_QUBITS, "tensor phases need 12-14-qubit tiles");
     dim3 grid(tiles, slots);
-    if (last) pass_rb_kernel<true><<<grid, nt, smem, st>>>(a);
-    else pass_rb_kernel<false><<<grid, nt, smem, st>>>(a);
+    if (a.ph_t) {
+        if (last) pass_rb_kernel<true, true><<<grid, nt, smem, st>>>(a);
+        else pass_rb_kernel<false, true><<<grid, nt, smem, st>>>(a);
+    } else {
+        if (last) pass_rb_kernel<true, false><<<grid, nt, smem, st>>>(a);
+        else pass_rb_kernel<false, false><<<grid, nt, smem, st>>>(a);
+    }
     ARSO_CUDA(cudaGetLastError());
 }
 

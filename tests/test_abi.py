@@ -91,6 +91,19 @@ def test_phase_planner_counts(arso):
     assert 950 <= arso.plan_phases(12, C.grover12(0).gates) <= 1310
 
 
+def test_tensor_phase_plans(arso):
+    # tensor-core phases: brickwork-24 at 13-qubit tiles plans at most 170 phases,
+    # at least 120 of them fused unitaries; without the flag, and for resident
+    # circuits, none
+    n, nt = arso.plan_phases(24, C.brickwork24(0).gates, tile_qubits=13, flags=arso.OPT_TENSOR_PHASES, tensor=True)
+    assert n <= 170 and 120 <= nt <= n
+    assert arso.plan_phases(24, C.brickwork24(0).gates, tile_qubits=13, tensor=True)[1] == 0
+    assert arso.plan_phases(12, C.grover12(0).gates, flags=arso.OPT_TENSOR_PHASES, tensor=True)[1] == 0
+    # tiles below 12 qubits never take the route
+    assert arso.plan_phases(16, C.brickwork(16, 8, 1).gates, tile_qubits=11, flags=arso.OPT_TENSOR_PHASES,
+                            tensor=True)[1] == 0
+
+
 def test_inverse_gate_count_fit():
     # the Sec. V-B fit: data exactly b / G returns b with zero residual and a
     # zero intercept; data a + b / G returns (a, b) from the affine fit
