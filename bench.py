@@ -396,7 +396,7 @@ def run_ours(args):
     if args.trace_all:  # algorithmic bytes of every launch, prefix-cache build and warm-up included
         arso.profile_reset()
         arso.profile_enable(True)
-    cc = arso.compile_circuit(circ.n, circ.gates, tile_qubits=args.tile,
+    cc = arso.compile_circuit(circ.n, circ.gates, tile_qubits=args.tile, low_qubits=args.low,
                               cache_bytes=int(args.cache_gb * (1 << 30)) if args.cache_gb else 0,
                               flags=(arso.OPT_NO_SUFFIX_REUSE if args.no_suffix else 0) |
                                     (arso.OPT_TENSOR_PHASES if args.tensor else 0))
@@ -571,6 +571,7 @@ def main():
                     help="default 1000 (brickwork24), 4096 (grover12: 256 per rate, several waves of the "
                          "persistent launch)")
     ap.add_argument("--tile", type=int, default=0, help="tile qubits (0 = library default)")
+    ap.add_argument("--low", type=int, default=0, help="contiguous low qubits of every tile (0 = library default)")
     ap.add_argument("--qubits", type=int, default=24,
                     help="brickwork qubits (24 = the benchmark circuit; smaller sizes are profiling cases)")
     ap.add_argument("--trace-all", action="store_true",

@@ -15,14 +15,18 @@
 //                gates (and the trajectory's error gates that follow them),
 //                and writes the tile back: one HBM round trip per pass.
 //
-// The pass builder is greedy in circuit order: a gate joins the current pass
-// when its qubits fit in the tile set; otherwise its qubits become blocked for
-// the rest of the pass, and so does every later gate that touches a blocked
-// qubit. The set of gates placed in a pass is therefore closed under the
-// circuit's dependencies, and concatenating the passes gives an engine order
-// that is a valid topological reordering of the circuit. Error gates stay
-// attached to the gate they follow, which keeps them correct: a gate moved
-// ahead of gate g never touches g's qubits after g.
+// The pass builder chooses each pass's tile qubits, then places gates in
+// circuit order: a gate joins the pass when its qubits are tile qubits and none
+// is blocked; otherwise its qubits become blocked for the rest of the pass, and
+// so does every later gate that touches a blocked qubit. The set of gates
+// placed in a pass is therefore closed under the circuit's dependencies, and
+// concatenating the passes gives an engine order that is a valid topological
+// reordering of the circuit. Error gates stay attached to the gate they
+// follow, which keeps them correct: a gate moved ahead of gate g never touches
+// g's qubits after g. The tile set starts from the low qubits and the qubits of
+// the first unplaced gate and grows one qubit at a time, each time by the qubit
+// whose addition places the most gates (lowest index on ties); when no single
+// qubit adds a gate, it takes the qubits of the earliest gate still left out.
 #include <algorithm>
 #include <set>
 #include <cmath>
@@ -88,6 +92,31 @@ void matrix_for(const arso_gate &g, HostGate &h) {
         ARSO_REQUIRE(std::isfinite(h.m[i].real()) && std::isfinite(h.m[i].imag()), "non-finite gate matrix entry");
 }
 
+// gates [first, G) that a pass with tile set in_s would place (circuit order,
+// blocked-qubit rule); returns their number and, when `out` is given, their indices
+static size_t pass_closure(const arso_circuit *c, const std::vector<char> &done, size_t first,
+                           const std::vector<char> &in_s, std::vector<uint32_t> *out) {
+    const uint32_t n = c->n;
+    std::vector<char> blocked(n, 0);
+    uint32_t n_blocked = 0;
+    size_t cnt = 0;
+    for (size_t g = first; g < c->gates.size() && n_blocked < n; ++g) {
+        if (done[g]) continue;
+        const HostGate &h = c->gates[g];
+        const uint32_t qs[2] = {h.q0, h.q1};
+        bool ok = true;
+        for (int j = 0; j < h.arity; ++j) ok &= !blocked[qs[j]] && in_s[qs[j]];
+        if (ok) {
+            ++cnt;
+            if (out) out->push_back((uint32_t)g);
+        } else {
+            for (int j = 0; j < h.arity; ++j)
+                if (!blocked[qs[j]]) blocked[qs[j]] = 1, ++n_blocked;
+        }
+    }
+    return cnt;
+}
+
 static void schedule_streaming(arso_circuit *c) {
     const uint32_t n = c->n, t = c->tile_qubits, lowq = c->low_qubits;
     const size_t G = c->gates.size();
@@ -96,37 +125,64 @@ static void schedule_streaming(arso_circuit *c) {
     c->passes.clear();
     c->perm.clear();
     do {
-        std::vector<char> in_s(n, 0), blocked(n, 0);
+        std::vector<char> in_s(n, 0);
         uint32_t cnt = 0;
-        for (uint32_t q = 0; q < lowq; ++q) in_s[q] = 1, ++cnt;
+        auto add = [&](uint32_t q) {
+            if (!in_s[q]) in_s[q] = 1, ++cnt;
+        };
+        for (uint32_t q = 0; q < lowq; ++q) add(q);
+        if (first < G) {
+            add(c->gates[first].q0);
+            add(c->gates[first].q1);
+        }
+        size_t placed = pass_closure(c, done, first, in_s, nullptr);
+        while (cnt < t) {
+            size_t best = placed;
+            uint32_t bq = n;
+            for (uint32_t q = 0; q < n; ++q) {
+                if (in_s[q]) continue;
+                in_s[q] = 1;
+                const size_t k = pass_closure(c, done, first, in_s, nullptr);
+                in_s[q] = 0;
+                if (k > best) best = k, bq = q;
+            }
+            if (bq < n) {
+                add(bq);
+                placed = best;
+                continue;
+            }
+            // no single qubit places another gate: the earliest gate left out that fits
+            std::vector<uint32_t> in_pass;
+            pass_closure(c, done, first, in_s, &in_pass);
+            std::vector<char> placed_g(G, 0);
+            for (uint32_t g : in_pass) placed_g[g] = 1;
+            bool grown = false;
+            for (size_t g = first; g < G && !grown; ++g) {
+                if (done[g] || placed_g[g]) continue;
+                const HostGate &h = c->gates[g];
+                const uint32_t fresh = (in_s[h.q0] ? 0u : 1u) + (h.arity == 2 && !in_s[h.q1] ? 1u : 0u);
+                if (fresh && cnt + fresh <= t) {
+                    add(h.q0);
+                    add(h.q1);
+                    grown = true;
+                }
+            }
+            if (!grown) break;
+            placed = pass_closure(c, done, first, in_s, nullptr);
+        }
+        // pad the tile to exactly t qubits (lowest unused qubits first)
+        for (uint32_t q = 0; q < n && cnt < t; ++q) add(q);
         Pass p;
         p.gb = (uint32_t)c->perm.size();
-        uint32_t n_blocked = 0;
-        for (size_t g = first; g < G && n_blocked < n; ++g) {
-            if (done[g]) continue;
-            const HostGate &h = c->gates[g];
-            uint32_t qs[2] = {h.q0, h.q1};
-            bool blk = false;
-            uint32_t fresh = 0;
-            for (int j = 0; j < h.arity; ++j) {
-                blk |= blocked[qs[j]] != 0;
-                fresh += in_s[qs[j]] ? 0 : 1;
-            }
-            if (!blk && cnt + fresh <= t) {
-                for (int j = 0; j < h.arity; ++j)
-                    if (!in_s[qs[j]]) in_s[qs[j]] = 1, ++cnt;
-                done[g] = 1;
-                --remaining;
-                c->perm.push_back((uint32_t)g);
-            } else {
-                for (int j = 0; j < h.arity; ++j)
-                    if (!blocked[qs[j]]) blocked[qs[j]] = 1, ++n_blocked;
-            }
+        std::vector<uint32_t> in_pass;
+        pass_closure(c, done, first, in_s, &in_pass);
+        ARSO_REQUIRE(!in_pass.empty() || G == 0, "internal: the pass builder placed no gate");
+        for (uint32_t g : in_pass) {
+            done[g] = 1;
+            --remaining;
+            c->perm.push_back(g);
         }
         while (first < G && done[first]) ++first;
-        // pad the tile to exactly t qubits (lowest unused qubits first)
-        for (uint32_t q = 0; q < n && cnt < t; ++q)
-            if (!in_s[q]) in_s[q] = 1, ++cnt;
         for (uint32_t q = 0; q < n; ++q)
             if (in_s[q]) p.tile_qubits.push_back(q);
         p.ge = (uint32_t)c->perm.size();
