@@ -86,6 +86,52 @@ def _traffic_ratio():
         return None
 
 
+def write_traffic(dram_csv, trace_json):
+    """profiles/pass_kernel_traffic.json from an ncu capture of every pass launch of
+    one run (dram__bytes_read.sum and dram__bytes_write.sum, --csv) and that run's
+    --trace-all line (the library's algorithmic bytes of the same launches)."""
+    import csv
+    lines = [l for l in open(dram_csv) if l.startswith('"')]
+    rows = list(csv.reader(lines))
+    h = rows[0]
+    mi, vi, ui, idi = h.index("Metric Name"), h.index("Metric Value"), h.index("Metric Unit"), h.index("ID")
+    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    rd = wr = 0.0
+    ids = set()
+    for r in rows[1:]:
+        if r[mi] == "dram__bytes_read.sum":
+            rd += float(r[vi].replace(",", "")) * scale[r[ui]]
+            ids.add(r[idi])
+        if r[mi] == "dram__bytes_write.sum":
+            wr += float(r[vi].replace(",", "")) * scale[r[ui]]
+    d = [json.loads(l) for l in open(trace_json) if l.startswith("{")][-1]
+    t = d["trace_all"]
+    n_ncu, n_alg = len(ids), t["pass_launches"]
+    out = {
+        "kernel": "pass_rb_kernel",
+        "source_sha": _kernel_sha(),
+        "source_files": ["paper_2301_07264_gb300/csrc/" + f for f in ("pass_rb.cu", "sim_common.cuh", "kernels.h",
+                                                                      "internal.h")],
+        "workload": d["config"]["workload"], "tile_qubits": d["config"].get("tile_qubits"),
+        "commands": ["python bench.py --qubits 20 --steps 2 --warmup 3 --no-cpu-baseline --trace-all > trace20.json",
+                     "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+                     "--clock-control none -k regex:pass_rb_kernel --csv --log-file dram20.csv python bench.py "
+                     "--qubits 20 --steps 2 --warmup 3 --no-cpu-baseline --trace-all",
+                     "python bench.py --write-traffic dram20.csv trace20.json"],
+        "dram_read_bytes": rd, "dram_write_bytes": wr, "launches_captured": n_ncu,
+        "algorithmic_bytes": t["pass_algorithmic_bytes"], "launches_traced": n_alg,
+        "dram_bytes_per_algorithmic_byte": round(((rd + wr) / n_ncu) / (t["pass_algorithmic_bytes"] / n_alg), 4),
+        "ratio_over_totals": round((rd + wr) / t["pass_algorithmic_bytes"], 4),
+        "note": "DRAM bytes of every pass launch of a whole 20-qubit run against the library's algorithmic bytes "
+                "(one read and one write of every swept state) of the same run, per launch (ncu may capture a "
+                "few launches fewer than the library traced). The bench multiplies the ratio by the 24-qubit "
+                "launch's algorithmic bytes.",
+    }
+    with open(os.path.join(ROOT, "profiles", "pass_kernel_traffic.json"), "w") as f:
+        json.dump(out, f, indent=1)
+    print(json.dumps(out))
+
+
 class ClockSampler:
     FIELDS = ("clocks.sm", "clocks.max.sm", "clocks_event_reasons.hw_slowdown",
               "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
@@ -396,7 +442,10 @@ def run_ours(args):
     if args.trace_all:  # algorithmic bytes of every launch, prefix-cache build and warm-up included
         arso.profile_reset()
         arso.profile_enable(True)
-    cc = arso.compile_circuit(circ.n, circ.gates, tile_qubits=args.tile, low_qubits=args.low,
+    # 12-qubit tiles: the measured best schedule for this circuit (four 128-thread CTAs per SM
+    # cover the tile loads' latency better than two 256-thread ones); 0 keeps the library default
+    tile = args.tile if args.tile >= 0 else 12
+    cc = arso.compile_circuit(circ.n, circ.gates, tile_qubits=tile, low_qubits=args.low,
                               cache_bytes=int(args.cache_gb * (1 << 30)) if args.cache_gb else 0,
                               flags=(arso.OPT_NO_SUFFIX_REUSE if args.no_suffix else 0) |
                                     (arso.OPT_TENSOR_PHASES if args.tensor else 0))
@@ -570,7 +619,10 @@ def main():
     ap.add_argument("--traj-per-step", type=int, default=None,
                     help="default 1000 (brickwork24), 4096 (grover12: 256 per rate, several waves of the "
                          "persistent launch)")
-    ap.add_argument("--tile", type=int, default=0, help="tile qubits (0 = library default)")
+    ap.add_argument("--tile", type=int, default=-1,
+                    help="tile qubits of the brickwork circuit (-1: 12, the measured best; 0: library default)")
+    ap.add_argument("--write-traffic", nargs=2, metavar=("DRAM_CSV", "TRACE_JSON"),
+                    help="write profiles/pass_kernel_traffic.json from an ncu DRAM capture and a --trace-all line")
     ap.add_argument("--low", type=int, default=0, help="contiguous low qubits of every tile (0 = library default)")
     ap.add_argument("--qubits", type=int, default=24,
                     help="brickwork qubits (24 = the benchmark circuit; smaller sizes are profiling cases)")
@@ -596,6 +648,8 @@ def main():
                     help="search workload: half-width of the surrogate's bracket in log10 p")
     ap.add_argument("--train-rows", type=int, default=2_000_000)
     args = ap.parse_args()
+    if args.write_traffic:
+        return write_traffic(*args.write_traffic)
     if args.traj_per_step is None:
         args.traj_per_step = 4096 if args.workload == "grover12" else 1000
     if args.impl == "reference":
