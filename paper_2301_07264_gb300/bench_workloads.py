@@ -239,7 +239,8 @@ def search(args):
     # evaluation circuits, unseen: per band, alternating QAOA and brickwork
     rng = np.random.default_rng(2)
     nb = max(1, args.search_circuits)
-    sizes = [(12, 14)] * nb + [(16, 18)] * nb + [(20, 22, 24)] * max(1, nb // 2)
+    n_large = args.search_large if args.search_large > 0 else max(1, nb // 2)
+    sizes = [(12, 14)] * nb + [(16, 18)] * nb + [(20, 22, 24)] * n_large
     evals = []
     for k, choice in enumerate(sizes):
         n = choice[k % len(choice)]
@@ -281,6 +282,7 @@ def search(args):
         bands[b] = {"circuits": len(rs), "qubits": sorted({r["n"] for r in rs}),
                     "plain_searches_per_s": len(rs) / pl_s, "surrogate_searches_per_s": len(rs) / su_s,
                     "speedup": pl_s / su_s, "rel_err_max": max(rel), "rel_err_mean": float(np.mean(rel)),
+                    "rel_err_p50_p90_p99": [float(np.percentile(rel, q)) for q in (50, 90, 99)],
                     "verified": sum(r["verified"] for r in rs),
                     "probes_plain_mean": float(np.mean([r["probes_plain"] for r in rs])),
                     "probes_surrogate_mean": float(np.mean([r["probes_surrogate"] for r in rs]))}
@@ -304,6 +306,7 @@ def search(args):
                        "target": "pass fraction >= 2/3 (fidelity >= 0.9)"},
             "plain_searches_per_s": len(evals) / plain_s, "speedup": plain_s / sur_s,
             "rel_err_max": max(rel), "rel_err_mean": float(np.mean(rel)),
+            "rel_err_p50_p90_p99": [float(np.percentile(rel, q)) for q in (50, 90, 99)],
             "verified": sum(r["verified"] for r in rows), "bands": bands, "ablation_literal_training_set": abl_info,
             "train_loss": loss,
             "generate_seconds": gen_s, "train_seconds": train_s, "surrogate_train": train_info, "rows": rows}
