@@ -81,7 +81,8 @@ __host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
            | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-// D[tmem] (+)= A[smem] x B[smem]^T, one elected thread
+// D[tmem] (+)= A[smem] x B[smem]^T (kind::f16: BF16 or FP16 operands, per the
+// instruction descriptor), one elected thread
 __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                           uint32_t accumulate) {
     asm volatile(
