@@ -73,8 +73,10 @@ enum { ARSO_C64 = 0, ARSO_C128 = 1 };
 
 typedef struct {
     uint32_t precision;     /* ARSO_C64 (complex64 amplitudes, FP32 arithmetic) or ARSO_C128 */
-    uint32_t tile_qubits;   /* streaming passes: qubits per shared-memory tile; 0 = auto */
-    uint32_t low_qubits;    /* streaming passes: qubits 0..low-1 are in every tile; 0 = auto */
+    uint32_t tile_qubits;   /* streaming passes: qubits per tile; 0 = auto (13 for complex64, the
+                               size arso_run_batch's persistent launch takes; arso_autotune
+                               measures 10..14) */
+    uint32_t low_qubits;    /* streaming passes: qubits 0..low-1 are in every tile; 0 = auto (4) */
     uint32_t max_batch;     /* streaming engine: trajectories resident at once; 0 = auto */
     uint64_t cache_bytes;   /* budget for cached error-free prefix states; 0 = auto */
     uint32_t flags;         /* ARSO_OPT_* */
@@ -119,7 +121,9 @@ typedef struct arso_circuit arso_circuit;
 typedef struct arso_error_list arso_error_list;
 
 /* Compile a circuit (Sec. II: a list of gates acting on n qubits) for the GPU:
- * builds gate matrices, the error-location table, the fused pass schedule and
+ * builds gate matrices, the error-location table, the fused pass schedule (each
+ * pass's tile qubits chosen to place the most gates from the circuit's
+ * frontier, Sec. II's gate order kept on every qubit) and
  * uploads them. n_qubits in [1, 30]; gates may be empty. `opts` may be NULL.
  * The error-free prefix-state cache is built lazily on first use.
  * Errors: ARSO_EINVAL (bad kind/qubit/matrix), ARSO_ENOMEM, ARSO_ECUDA. */
