@@ -146,6 +146,7 @@ def test_resident_amplitudes(arso, n, G, seed, c128):
 
 @pytest.mark.parametrize("n,G,tile,low,seed", [
     (14, 200, 8, 3, 1), (15, 300, 10, 4, 2), (16, 260, 13, 4, 3), (14, 120, 6, 1, 4), (17, 150, 14, 5, 5),
+    (17, 320, 12, 4, 6), (16, 240, 11, 3, 7),
 ])
 def test_streaming_amplitudes(arso, n, G, tile, low, seed):
     circ = C.random_circuit(n, G, seed)
@@ -165,7 +166,7 @@ def test_streaming_amplitudes(arso, n, G, tile, low, seed):
         assert np.max(np.abs(got[t] - statevector.simulate(circ, ev))) < AMP_TOL_C64, t
 
 
-@pytest.mark.parametrize("tile,seed", [(10, 11), (11, 12), (13, 13)])
+@pytest.mark.parametrize("tile,seed", [(10, 11), (11, 12), (12, 14), (13, 13)])
 def test_register_blocked_many_errors(arso, tile, seed):
     """Dense error lists: X/Y errors become index masks that later gates
     (dense, CX, CZ, diagonal, SWAP, U2) must see through."""
