@@ -641,6 +641,7 @@ def main():
                     help="brickwork24 is the benchmark line; the others measure the other configurations")
     ap.add_argument("--search-circuits", type=int, default=8,
                     help="search workload: evaluation circuits per size band (half as many at 20-24 qubits)")
+    ap.add_argument("--search-epochs", type=int, default=16, help="search workload: surrogate training epochs")
     ap.add_argument("--search-large", type=int, default=0,
                     help="search workload: evaluation circuits of 20-24 qubits (0: half of --search-circuits)")
     ap.add_argument("--search-ablation", action="store_true",

@@ -195,7 +195,7 @@ def search(args):
     gen_s = time.perf_counter() - t0
     s = arso.surrogate_create(11)
     t0 = time.perf_counter()
-    loss = arso.surrogate_train(s, x, y, epochs=4, batch=8192, lr=2e-3, seed=3)
+    loss = arso.surrogate_train(s, x, y, epochs=args.search_epochs, batch=8192, lr=2e-3, seed=3)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     # the tensor-core GEMMs' share of one profiled training epoch (a fresh network, so the
@@ -211,7 +211,7 @@ def search(args):
                                                     ("other", arso.K_OTHER))}
     total_ms = sum(v.ms for v in ks.values())
     gemm = ks["gemm"]
-    train_info = {"rows": int(x.shape[0]), "epochs": 4, "batch": 8192, "seconds": train_s,
+    train_info = {"rows": int(x.shape[0]), "epochs": args.search_epochs, "batch": 8192, "seconds": train_s,
                   "rows_per_s": 4 * int(x.shape[0]) / train_s,
                   "profiled_rows": m,
                   "gemm": {"kernel": "umma_gemm_kernel (tcgen05 kind::f16, TMEM accumulator)",
