@@ -440,7 +440,7 @@ def test_brickwork24_full_size_launch(arso):
         psi = statevector.simulate(circ, ev)
         assert torch.max(torch.abs(out[0].cpu() - torch.from_numpy(psi))).item() < AMP_TOL_C64
     full = C.brickwork24(0)
-    cc = arso.compile_circuit(24, full.gates)  # the benchmark's tile shape
+    cc = arso.compile_circuit(24, full.gates, tile_qubits=12)  # the benchmark's tile shape
     T = 64
     p = 1e-3
     errs = arso.sample_errors(cc, p / 3, p / 3, p / 3, 0, 0, T)
@@ -496,15 +496,18 @@ def brickwork24_single_errors():
     return full, cases, np.array(expected)
 
 
+@pytest.mark.parametrize("tile", [12, 13])
 @pytest.mark.parametrize("suffix_reuse", [True, False])
-def test_brickwork24_full_depth_against_oracle(arso, brickwork24_single_errors, suffix_reuse):
-    """Brickwork-24 depth 40 in the benchmark's launch configuration (default tile,
-    prefix cache): the GPU runs these trajectories through every pass after the
-    first error (suffix reuse off) or stops after the last error's pass and scores
-    against the cached error-free state there (on, as in the benchmark)."""
+def test_brickwork24_full_depth_against_oracle(arso, brickwork24_single_errors, suffix_reuse, tile):
+    """Brickwork-24 depth 40 in the benchmark's launch configuration (12-qubit tiles;
+    and the library default, 13; prefix cache): the GPU runs these trajectories
+    through every pass after the first error (suffix reuse off) or stops after the
+    last error's pass and scores against the cached error-free state there (on, as
+    in the benchmark)."""
     full, cases, expected = brickwork24_single_errors
     assert np.all((expected[:4] > 0.05) & (expected[:4] < 0.95))  # entangled: neither 0 nor 1
-    cc = arso.compile_circuit(full.n, full.gates, flags=0 if suffix_reuse else arso.OPT_NO_SUFFIX_REUSE)
+    cc = arso.compile_circuit(full.n, full.gates, tile_qubits=tile,
+                              flags=0 if suffix_reuse else arso.OPT_NO_SUFFIX_REUSE)
     errs = arso.error_list_from_host(cc, cases)
     score = np.zeros(len(cases))
     arso.run_trajectories(cc, errs, full.criterion, score)
