@@ -162,6 +162,24 @@ arso_status arso_plan_schedule(uint32_t n_qubits, const arso_gate *gates, size_t
  * be NULL) receives how many of them run on the tensor cores. */
 arso_status arso_plan_phases(uint32_t n_qubits, const arso_gate *gates, size_t n_gates,
                              const arso_compile_opts *opts, uint32_t *n_phases, uint32_t *n_tensor);
+/* Host-only test support (no counterpart in the paper): the tensor-core operand of
+ * register phase `phase` of the schedule arso_compile_circuit would build with
+ * `opts` (flags with ARSO_OPT_TENSOR_PHASES). *reg_bits: the phase's five register
+ * bits (tile-local bit positions of its pass, register bit b at bits 5b..5b+4);
+ * [*pos_begin, *pos_end): its gates as engine positions (the order arso_plan_schedule
+ * returns); *pass: its pass. roles (may be NULL; *pos_end - *pos_begin bytes, at most
+ * roles_capacity): 0 inside the phase's unitary U, 1 a diagonal gate run before U,
+ * 2 one run after it. image (may be NULL; 8192 values): the real 64 x 64 form B of U
+ * (row n = 4p + 2c + lane for output register 2p + lane, c = 0 real part, 1 imaginary
+ * part; column k likewise for the input register), scaled by 2^8 and split into the
+ * integer hi = rint(2^8 B) and lo = fp16(2^8 B - hi), both as binary16 bits: hi at
+ * index (n/8)*512 + (k/8)*64 + (n%8)*8 + k%8, lo 4096 further. *has_image = 0 when the
+ * phase runs gate by gate (image untouched). Errors: ARSO_EINVAL (phase out of range,
+ * roles_capacity too small), and as arso_compile_circuit. */
+arso_status arso_plan_tensor_phase(uint32_t n_qubits, const arso_gate *gates, size_t n_gates,
+                                   const arso_compile_opts *opts, uint32_t phase, uint32_t *reg_bits,
+                                   uint32_t *pos_begin, uint32_t *pos_end, uint32_t *pass, uint8_t *roles,
+                                   uint32_t roles_capacity, uint16_t *image, uint32_t *has_image);
 
 /* Sample Pauli errors (Sec. IV-B.2): after every gate, each of its qubits
  * independently suffers X, Z or Y with probabilities p_x, p_z, p_y. Trajectory

@@ -214,10 +214,11 @@ def compile_circuit(n, gates, precision=C64, tile_qubits=0, low_qubits=0, max_ba
     return CompiledCircuit(h.value, n)
 
 
-def plan_schedule(n, gates, precision=C64, tile_qubits=0, low_qubits=0):
-    """Host-only: (perm, pass_begin, tile_masks) of the fused pass schedule."""
+def plan_schedule(n, gates, precision=C64, tile_qubits=0, low_qubits=0, flags=0):
+    """Host-only: (perm, pass_begin, tile_masks) of the fused pass schedule (the engine
+    order depends on the phase planner, so on ARSO_OPT_TENSOR_PHASES in flags)."""
     arr, keep = _gates_array(gates)
-    opts = CompileOpts(precision, tile_qubits, low_qubits, 0, 0, 0)
+    opts = CompileOpts(precision, tile_qubits, low_qubits, 0, 0, flags)
     P = C.c_uint32()
     _check(lib.arso_plan_schedule(n, arr, len(gates), C.byref(opts), C.byref(P), 0, None, None, None))
     perm = np.zeros(max(len(gates), 1), dtype=np.uint32)
@@ -544,6 +545,29 @@ def autotune(n, gates, crit, p, n_traj=64, seed=0, precision=C64, stream=None):
 lib.arso_plan_phases.argtypes = [C.c_uint32, C.POINTER(Gate), C.c_size_t, C.POINTER(CompileOpts), C.POINTER(C.c_uint32),
                                  C.POINTER(C.c_uint32)]
 lib.arso_plan_phases.restype = C.c_int
+
+
+lib.arso_plan_tensor_phase.argtypes = [C.c_uint32, C.POINTER(Gate), C.c_size_t, C.POINTER(CompileOpts), C.c_uint32,
+                                       C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
+                                       C.POINTER(C.c_uint32), _vp, C.c_uint32, _vp, C.POINTER(C.c_uint32)]
+lib.arso_plan_tensor_phase.restype = C.c_int
+
+
+def plan_tensor_phase(n, gates, phase, tile_qubits=0, low_qubits=0, flags=OPT_TENSOR_PHASES):
+    """Host-only (see include/arso.h): a register phase's register bits, engine-position
+    range, pass, per-gate roles and, when it runs on the tensor cores, its operand image
+    (8192 binary16 values: hi then lo)."""
+    arr, keep = _gates_array(gates)
+    opts = CompileOpts(C64, tile_qubits, low_qubits, 0, 0, flags)
+    rb, pb, pe, ps, has = (C.c_uint32() for _ in range(5))
+    roles = np.zeros(max(len(gates), 1), dtype=np.uint8)
+    image = np.zeros(8192, dtype=np.uint16)
+    _check(lib.arso_plan_tensor_phase(n, arr, len(gates), C.byref(opts), phase, C.byref(rb), C.byref(pb),
+                                      C.byref(pe), C.byref(ps), roles.ctypes.data, roles.size,
+                                      image.ctypes.data, C.byref(has)))
+    R = [(rb.value >> (5 * b)) & 31 for b in range(5)]
+    return {"R": R, "pos": (pb.value, pe.value), "pass": ps.value, "roles": roles[: pe.value - pb.value].copy(),
+            "image": image if has.value else None}
 
 
 def plan_phases(n, gates, precision=C64, tile_qubits=0, low_qubits=0, flags=0, tensor=False):

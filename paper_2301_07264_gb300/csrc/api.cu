@@ -1643,6 +1643,31 @@ arso_status arso_plan_phases(uint32_t n_qubits, const arso_gate *gates, size_t n
     });
 }
 
+arso_status arso_plan_tensor_phase(uint32_t n_qubits, const arso_gate *gates, size_t n_gates,
+                                   const arso_compile_opts *opts, uint32_t phase, uint32_t *reg_bits,
+                                   uint32_t *pos_begin, uint32_t *pos_end, uint32_t *pass, uint8_t *roles,
+                                   uint32_t roles_capacity, uint16_t *image, uint32_t *has_image) {
+    return guard([&] {
+        ARSO_REQUIRE(reg_bits && pos_begin && pos_end && pass && has_image, "NULL argument");
+        arso_circuit c;
+        build_circuit(&c, n_qubits, gates, n_gates, opts);
+        ARSO_REQUIRE(c.reg_blocked && phase < c.ph_R.size(), "phase out of range");
+        *reg_bits = c.ph_R[phase];
+        *pos_begin = c.ph_gb[phase];
+        *pos_end = c.ph_gb[phase + 1];
+        *pass = c.pass_of_pos.empty() ? 0u : c.pass_of_pos[c.ph_gb[phase]];
+        if (roles) {
+            ARSO_REQUIRE(*pos_end - *pos_begin <= roles_capacity, "roles_capacity too small");
+            for (uint32_t p = *pos_begin; p < *pos_end; ++p) roles[p - *pos_begin] = c.role[p];
+        }
+        const uint32_t t = phase < c.ph_t.size() ? c.ph_t[phase] : NO_TENSOR;
+        *has_image = t != NO_TENSOR;
+        if (image && t != NO_TENSOR)
+            std::copy(c.tmats.begin() + (size_t)t * TENSOR_IMAGE_HALVES,
+                      c.tmats.begin() + (size_t)(t + 1) * TENSOR_IMAGE_HALVES, image);
+    });
+}
+
 arso_status arso_plan_schedule(uint32_t n_qubits, const arso_gate *gates, size_t n_gates,
                                const arso_compile_opts *opts, uint32_t *n_passes, uint32_t capacity, uint32_t *perm,
                                uint32_t *pass_begin, uint64_t *tile_mask) {
