@@ -86,7 +86,7 @@ def _traffic_ratio():
         return None
 
 
-def write_traffic(dram_csv, trace_json):
+def write_traffic(dram_csv, trace_json, out_path=None):
     """profiles/pass_kernel_traffic.json from an ncu capture of every pass launch of
     one run (dram__bytes_read.sum and dram__bytes_write.sum, --csv) and that run's
     --trace-all line (the library's algorithmic bytes of the same launches)."""
@@ -127,9 +127,10 @@ def write_traffic(dram_csv, trace_json):
                 "few launches fewer than the library traced). The bench multiplies the ratio by the 24-qubit "
                 "launch's algorithmic bytes.",
     }
-    with open(os.path.join(ROOT, "profiles", "pass_kernel_traffic.json"), "w") as f:
+    with open(out_path or os.path.join(ROOT, "profiles", "pass_kernel_traffic.json"), "w") as f:
         json.dump(out, f, indent=1)
     print(json.dumps(out))
+    return out
 
 
 class ClockSampler:
