@@ -79,6 +79,22 @@ def test_brickwork24_schedule_is_fused(arso):
     assert _check_schedule(C.brickwork24(0), 12, 4) <= 26
 
 
+@pytest.mark.parametrize("n,G,tile,low,frac,seed", [
+    (14, 500, 10, 1, 0.3, 21), (16, 800, 11, 2, 0.6, 22), (18, 600, 12, 3, 0.5, 23), (20, 900, 12, 4, 0.4, 24),
+    (22, 700, 13, 5, 0.5, 25), (24, 1200, 14, 4, 0.5, 26), (19, 400, 6, 3, 0.7, 27), (15, 300, 14, 5, 0.2, 28)])
+def test_frontier_schedules_of_random_circuits(arso, n, G, tile, low, frac, seed):
+    # every gate kind, two-qubit fractions 0.2-0.7, tiles 6-14, 1-5 contiguous low qubits
+    _check_schedule(C.random_circuit(n, G, seed, two_qubit_frac=frac), tile, low)
+
+
+def test_plan_tensor_phase_rejects_a_phase_out_of_range(arso):
+    circ = C.brickwork(16, 4, 1)
+    n_ph = arso.plan_phases(16, circ.gates, tile_qubits=13, flags=arso.OPT_TENSOR_PHASES)
+    with pytest.raises(arso.ArsoError) as e:
+        arso.plan_tensor_phase(16, circ.gates, n_ph, tile_qubits=13)
+    assert e.value.status == arso.EINVAL
+
+
 @pytest.mark.parametrize("make,tile,low", [(lambda: C.qaoa_maxcut(24, 2), 13, 4),
                                            (lambda: C.qft_basis(20, 12345), 13, 4),
                                            (lambda: C.cuccaro_adder(9, 301, 177), 12, 3),
